@@ -1,0 +1,209 @@
+"""Manufactured and closed-form solutions that pin the oracle (test infrastructure).
+
+Section 5.1 verifies the solver with manufactured solutions: arbitrary smooth
+u, p, x fields with the matching source terms added to each equation.  Two
+families are built here with sympy:
+
+  * TranslatingBox - a rigid translation of the whole mesh x = X + a t, a
+    velocity that is linear in space, u = (alpha + beta t + gamma t^3)(c + D x),
+    and a linear pressure, on a square with a square hole (the rigid body
+    Gamma).  Q2 velocity, Q1 pressure and Q2 position represent these fields
+    exactly on affine cells, and with gamma = 0 the nodal trajectories are
+    quadratic in time, which BDF2 integrates exactly.  The discrete solution
+    must then equal the exact one to rounding; with gamma != 0 the error is the
+    BDF2 truncation error and must fall as dt^2.
+  * SteadyMMS - the 2-D velocity and pressure of Section 5.1 (without the time
+    factors) on a unit square whose mesh is statically deformed by
+    x = X + A sin(pi X) sin(pi Y) (1, 1), run with a very large time step so the
+    converged step is the steady problem; errors must fall at the optimal rates.
+
+Each provides: volume(Xq, t) -> (f_u, g_p, f_x), gamma(Xq, t) -> g_lambda,
+border(t) -> F, exact nodal values and a Dirichlet setter.
+"""
+from __future__ import annotations
+
+import numpy as np
+import sympy as sy
+
+X_, Y_, x_, y_, t_ = sy.symbols("X Y x y t", real=True)
+
+
+def _vec_fun(exprs, args):
+    f = sy.lambdify(args, exprs, "numpy")
+
+    def call(*a):
+        shape = np.broadcast(*a).shape
+        out = f(*a)
+        return np.stack([np.broadcast_to(np.asarray(o, dtype=np.float64), shape) for o in out], axis=-1)
+    return call
+
+
+class _Manufactured:
+    """Common machinery: u(x,y,t), p(x,y,t) in physical coordinates, the
+    motion chi(X,Y,t), fluid and pseudo-solid coefficients."""
+
+    def __init__(self, u, p, chi, rho, mu, lam_s, mu_s, k=0.0, hole=None):
+        self.rho, self.mu, self.lam_s, self.mu_s, self.k = rho, mu, lam_s, mu_s, k
+        ux, uy = u
+        # fluid source: rho (d_t u|_x + (u.grad) u) - div sigma
+        grad = sy.Matrix([[sy.diff(ux, x_), sy.diff(ux, y_)], [sy.diff(uy, x_), sy.diff(uy, y_)]])
+        sigma = -p * sy.eye(2) + mu * (grad + grad.T)
+        uvec = sy.Matrix([ux, uy])
+        conv = grad * uvec
+        divs = sy.Matrix([sy.diff(sigma[0, 0], x_) + sy.diff(sigma[0, 1], y_),
+                          sy.diff(sigma[1, 0], x_) + sy.diff(sigma[1, 1], y_)])
+        fu = rho * (sy.diff(uvec, t_) + conv) - divs
+        gp = grad[0, 0] + grad[1, 1]
+        # pseudo-solid source: -div_X sigma_s(chi)
+        cx, cy = chi
+        F = sy.Matrix([[sy.diff(cx, X_), sy.diff(cx, Y_)], [sy.diff(cy, X_), sy.diff(cy, Y_)]])
+        eps = (F + F.T) / 2 - sy.eye(2)
+        sig_s = lam_s * (eps[0, 0] + eps[1, 1]) * sy.eye(2) + 2 * mu_s * eps
+        fx = -sy.Matrix([sy.diff(sig_s[0, 0], X_) + sy.diff(sig_s[0, 1], Y_),
+                         sy.diff(sig_s[1, 0], X_) + sy.diff(sig_s[1, 1], Y_)])
+        sub = {x_: cx, y_: cy}
+        self._fu = _vec_fun([fu[0].subs(sub), fu[1].subs(sub)], (X_, Y_, t_))
+        self._gp = sy.lambdify((X_, Y_, t_), gp.subs(sub), "numpy")
+        self._fx = _vec_fun([fx[0], fx[1]], (X_, Y_, t_))
+        wx, wy = sy.diff(cx, t_), sy.diff(cy, t_)
+        self._gl = _vec_fun([ux.subs(sub) - wx, uy.subs(sub) - wy], (X_, Y_, t_))
+        self._u_phys = _vec_fun([ux, uy], (x_, y_, t_))
+        self._grad_u_phys = _vec_fun([grad[0, 0], grad[0, 1], grad[1, 0], grad[1, 1]], (x_, y_, t_))
+        self._p_phys = sy.lambdify((x_, y_, t_), p, "numpy")
+        self._chi = _vec_fun([cx, cy], (X_, Y_, t_))
+        self._grad_chi = _vec_fun([F[0, 0], F[0, 1], F[1, 0], F[1, 1]], (X_, Y_, t_))
+        self.sigma = sigma
+        self.hole = hole
+        self._border = None
+        if hole is not None:
+            a, b = hole
+            # int_Gamma sigma.n ds with n the outward normal of the fluid (into the hole),
+            # on the hole moved by chi (a rigid translation on Gamma)
+            dx = cx.subs({X_: a, Y_: a}) - a
+            dy = cy.subs({X_: a, Y_: a}) - a
+            s = sy.symbols("s", real=True)
+            tot = sy.zeros(2, 1)
+            # side X = a: fluid normal +x;  X = b: -x;  Y = a: +y;  Y = b: -y
+            for (px, py, n) in (((a + dx), (s + dy), (1, 0)), ((b + dx), (s + dy), (-1, 0)),
+                                ((s + dx), (a + dy), (0, 1)), ((s + dx), (b + dy), (0, -1))):
+                sig = sigma.subs({x_: px, y_: py})
+                tvec = sig * sy.Matrix(n)
+                tot += sy.Matrix([sy.integrate(tvec[0], (s, a, b)), sy.integrate(tvec[1], (s, a, b))])
+            F_border = self.k * sy.Matrix([dx, dy]) + tot
+            self._border = _vec_fun([sy.simplify(F_border[0]), sy.simplify(F_border[1])], (t_,))
+            self._delta = _vec_fun([dx, dy], (t_,))
+            self._force = _vec_fun([-tot[0], -tot[1]], (t_,))
+
+    # ---- source interface used by oracle.fem --------------------------------
+    def volume(self, Xq, t):
+        X, Y = Xq[..., 0], Xq[..., 1]
+        gp = np.broadcast_to(np.asarray(self._gp(X, Y, t), dtype=np.float64), X.shape)
+        return self._fu(X, Y, t), gp, self._fx(X, Y, t)
+
+    def gamma(self, Xq, t):
+        return self._gl(Xq[..., 0], Xq[..., 1], t)
+
+    def border(self, t):
+        if self._border is None:
+            return np.zeros(2)
+        return self._border(np.float64(t))
+
+    # ---- exact values -------------------------------------------------------
+    def position(self, X, t):
+        return self._chi(X[..., 0], X[..., 1], t)
+
+    def velocity(self, X, t):
+        x = self.position(X, t)
+        return self._u_phys(x[..., 0], x[..., 1], t)
+
+    def pressure(self, X, t):
+        x = self.position(X, t)
+        return np.broadcast_to(np.asarray(self._p_phys(x[..., 0], x[..., 1], t), dtype=np.float64),
+                               X.shape[:-1])
+
+    def delta(self, t):
+        return self._delta(np.float64(t)) if self.hole is not None else np.zeros(2)
+
+    def force(self, t):
+        """Exact F_fluid = -int_Gamma sigma.n (n outward from the fluid)."""
+        return self._force(np.float64(t))
+
+    def set_dirichlet(self, case, t):
+        """Hold every prescribed component at its exact value at time t."""
+        from .solver import U_FIX_X, U_FIX_Y, X_FIX_X, X_FIX_Y, P_FIX
+        tg = case.tags
+        ue = self.velocity(case.X, t)
+        xe = self.position(case.X, t)
+        pe = self.pressure(case.X, t)
+        for i, bit in enumerate((U_FIX_X, U_FIX_Y)):
+            m = (tg & bit) != 0
+            case.u[m, i] = ue[m, i]
+        for i, bit in enumerate((X_FIX_X, X_FIX_Y)):
+            m = ((tg & bit) != 0) & ~case.cyl
+            case.x[m, i] = xe[m, i]
+        m = (tg & P_FIX) != 0
+        case.p[m] = pe[m]
+
+    def set_exact_state(self, case, t):
+        """Exact nodal u, x (and p, delta) at time t."""
+        case.u[:] = self.velocity(case.X, t)
+        case.x[:] = self.position(case.X, t)
+        case.p[:] = self.pressure(case.X, t)
+        if case.has_body:
+            case.delta = self.delta(t)
+
+
+def translating_box(gamma=0.0, rho=9.876, mu=1.234, k=2.5, hole=(0.4, 0.6)):
+    """Closed-form patch solution on a square with a square hole, moving
+    rigidly with x = X + a t; see the module docstring."""
+    a = (sy.Rational(3, 10), -sy.Rational(1, 5))
+    chi = (X_ + a[0] * t_, Y_ + a[1] * t_)
+    s = 1 + 2 * t_ + gamma * t_ ** 3
+    ux = s * (1 + sy.Rational(1, 2) * x_ + y_)
+    uy = s * (sy.Rational(1, 2) - sy.Rational(7, 10) * x_ + sy.Rational(1, 5) * y_)
+    p = (1 + t_) * (sy.Rational(3, 10) + sy.Rational(4, 5) * x_ - sy.Rational(3, 5) * y_)
+    return _Manufactured((ux, uy), p, chi, rho, mu, 1.0, 1.0, k=k, hole=hole)
+
+
+def steady_mms(rho=9.876, mu=1.234, amp=0.05):
+    """Section 5.1's 2-D velocity and pressure (time factors dropped) on a
+    statically deformed unit-square mesh, lambda_s = mu_s = 1."""
+    pi = sy.pi
+    chi = (X_ + amp * sy.sin(pi * X_) * sy.sin(pi * Y_), Y_ + amp * sy.sin(pi * X_) * sy.sin(pi * Y_))
+    ux = sy.sin(pi * x_) * sy.cos(pi * y_)
+    uy = sy.sin(pi * x_) * sy.sin(pi * y_)
+    p = sy.cos(pi * x_) * sy.cos(pi * y_)
+    return _Manufactured((ux, uy), p, chi, rho, mu, 1.0, 1.0)
+
+
+def error_norms(case, sol, t):
+    """Errors of the discrete state against the exact fields:
+    u in L2 and H1-seminorm and p in L2 over Omega_t, x in L2 and H1-seminorm
+    over Omega_0 (Section 5.1's norms, measured with 3x3 Gauss points)."""
+    from . import fem
+    c = case.conn
+    Xe, xe, ue = case.X[c], case.x[c], case.u[c]
+    pe = case.p[c[:, fem.VERTEX_LOCAL]]
+    eu2 = eu1 = ep2 = ex2 = ex1 = 0.0
+    for q in range(9):
+        N, M, w = fem.N_Q[q], fem.M_Q[q], fem.W_Q[q]
+        g, det = fem.physical_gradients(xe, q)
+        g0, det0 = fem.physical_gradients(Xe, q)
+        Xq = np.einsum('a,eai->ei', N, Xe)
+        xq = np.einsum('a,eai->ei', N, xe)
+        uh = np.einsum('a,eai->ei', N, ue)
+        Lh = np.einsum('eai,eaj->eij', ue, g)
+        ph = np.einsum('c,ec->e', M, pe)
+        ux = sol._u_phys(xq[:, 0], xq[:, 1], t)
+        Lx = sol._grad_u_phys(xq[:, 0], xq[:, 1], t).reshape(-1, 2, 2)
+        px = np.broadcast_to(sol._p_phys(xq[:, 0], xq[:, 1], t), ph.shape)
+        eu2 += np.sum(w * det * np.sum((uh - ux) ** 2, axis=1))
+        eu1 += np.sum(w * det * np.sum((Lh - Lx) ** 2, axis=(1, 2)))
+        ep2 += np.sum(w * det * (ph - px) ** 2)
+        Fh = np.einsum('eai,eaj->eij', xe, g0)
+        Fx = sol._grad_chi(Xq[:, 0], Xq[:, 1], t).reshape(-1, 2, 2)
+        xx = sol._chi(Xq[:, 0], Xq[:, 1], t)
+        ex2 += np.sum(w * det0 * np.sum((xq - xx) ** 2, axis=1))
+        ex1 += np.sum(w * det0 * np.sum((Fh - Fx) ** 2, axis=(1, 2)))
+    return dict(u_l2=np.sqrt(eu2), u_h1=np.sqrt(eu1), p_l2=np.sqrt(ep2),
+                x_l2=np.sqrt(ex2), x_h1=np.sqrt(ex1))

@@ -1,0 +1,304 @@
+"""Seeded synthetic inputs shared by the CUDA path, the tests and the bench.
+
+This module holds geometry and random numbers only: meshes (node coordinates,
+Q2 connectivity, boundary tags, the cylinder boundary faces) and the seeded
+initial-velocity perturbation.  It contains none of the solver's arithmetic
+(no shape functions, no quadrature, no residuals), so both the oracle and the
+CUDA path may consume what it produces.
+
+Geometry follows the two-dimensional cylinder configuration of the paper's
+VIV study (Section 6: a cylinder of diameter D centred at X_c in a rectangular
+channel, uniform inflow, slip walls, natural outflow; Eq. (flowBC), Eq. (psBC)),
+meshed here with quadratic quadrilaterals: an O-grid around the cylinder that
+is blended onto a square, surrounded by graded Cartesian blocks.
+
+Node tags are bit flags that say which nodal degrees of freedom are held by a
+Dirichlet condition; the value held is whatever the initial state carries.
+"""
+from __future__ import annotations
+
+import math
+import numpy as np
+
+# --- boundary tag bits (per node) ---------------------------------------------
+U_FIX_X = 1    # velocity x-component prescribed
+U_FIX_Y = 2    # velocity y-component prescribed
+X_FIX_X = 4    # mesh position x-component prescribed
+X_FIX_Y = 8    # mesh position y-component prescribed
+CYL = 16       # node on the rigid cylinder boundary Gamma (multiplier lives here)
+OUTLET = 32    # informational: natural outflow boundary
+P_FIX = 64     # pressure prescribed at this (vertex) node: removes the constant
+               # pressure mode of all-Dirichlet problems (Q = L^2/R, Section 3.1)
+
+INLET_TAG = U_FIX_X | U_FIX_Y | X_FIX_X | X_FIX_Y   # u = u_in, x = X
+OUTLET_TAG = OUTLET | X_FIX_X | X_FIX_Y              # stress free, x = X
+WALL_TAG = U_FIX_Y | X_FIX_Y                         # u.n = 0, x.n = X.n
+ALL_DIRICHLET_TAG = U_FIX_X | U_FIX_Y | X_FIX_X | X_FIX_Y
+
+# local edge ids of a 9-node quad (lexicographic node index 3*b + a, a along xi)
+EDGE_NODES = ((0, 3, 6), (2, 5, 8), (0, 1, 2), (6, 7, 8))
+
+
+class _NodeTable:
+    """Merges coincident nodes produced by different mesh blocks."""
+
+    def __init__(self, tol=1e-9):
+        self.tol = tol
+        self.index = {}
+        self.coords = []
+
+    def get(self, x, y):
+        key = (int(round(x / self.tol)), int(round(y / self.tol)))
+        idx = self.index.get(key)
+        if idx is None:
+            idx = len(self.coords)
+            self.index[key] = idx
+            self.coords.append((x, y))
+        return idx
+
+
+def _graded(h0, length, n):
+    """n cell widths summing to `length`, the first equal to h0 and growing
+    geometrically; uniform when h0*n already covers the length."""
+    if h0 * n >= length:
+        return np.full(n, length / n)
+    lo, hi = 1.0, 2.0
+    while h0 * (hi ** n - 1) / (hi - 1) < length:
+        hi *= 2
+    for _ in range(200):
+        q = 0.5 * (lo + hi)
+        s = h0 * (q ** n - 1) / (q - 1)
+        if s < length:
+            lo = q
+        else:
+            hi = q
+    q = 0.5 * (lo + hi)
+    w = h0 * q ** np.arange(n)
+    return w * (length / w.sum())
+
+
+def _q2_line(vertices):
+    """Vertex coordinates -> Q2 node coordinates (vertices and midpoints)."""
+    v = np.asarray(vertices, dtype=np.float64)
+    out = np.empty(2 * len(v) - 1)
+    out[0::2] = v
+    out[1::2] = 0.5 * (v[:-1] + v[1:])
+    return out
+
+
+def viv_cylinder_mesh(m=12, D=1.0, Xc=(0.0, 0.0), half=3.0,
+                      box=(-10.0, 20.0, -10.0, 10.0), q_radial=1.15):
+    """Q2 quadrilateral mesh of the channel [x0,x1]x[y0,y1] around a cylinder.
+
+    m is the number of cells along one side of the square [-half,half]^2 that
+    holds the O-grid; the O-grid has 4m cells around and m cells radially, and
+    the Cartesian surround has 8m/12 (left, top, bottom) and 20m/12 (right)
+    graded cells.  m = 12 gives 1,552 quads; m = 60 gives 38,800.
+    Returns a dict with X (n,2), conn (E,9), tags (n,), gamma_faces (F,2)
+    [element, local edge], Xc, D.
+    """
+    x0, x1, y0, y1 = box
+    cx, cy = Xc
+    r_in = 0.5 * D
+    nodes = _NodeTable()
+    conn = []
+    gamma_faces = []
+
+    # ---- O-grid: xi runs outward (radial), eta runs counter-clockwise -------
+    n_around = 8 * m              # Q2 nodes around
+    q = q_radial ** (12.0 / m)
+    sv = (q ** np.arange(m + 1) - 1.0) / (q ** m - 1.0)
+    s_nodes = _q2_line(sv)        # 2m+1 radial node parameters
+    perim = 8.0 * half
+
+    def square_point(t):
+        t = t % perim
+        h = half
+        if t < h:
+            return h, t
+        t -= h
+        if t < 2 * h:
+            return h - t, h
+        t -= 2 * h
+        if t < 2 * h:
+            return -h, h - t
+        t -= 2 * h
+        if t < 2 * h:
+            return -h + t, -h
+        t -= 2 * h
+        return h, -h + t
+
+    ring = np.empty((n_around, 2 * m + 1), dtype=np.int64)
+    for k in range(n_around):
+        th = 2.0 * math.pi * k / n_around
+        c = (cx + r_in * math.cos(th), cy + r_in * math.sin(th))
+        sq = square_point(perim * k / n_around)
+        s_pt = (cx + sq[0], cy + sq[1])
+        for r, s in enumerate(s_nodes):
+            if r == 0:
+                px, py = c
+            elif r == 2 * m:
+                px, py = s_pt
+            else:
+                px = (1 - s) * c[0] + s * s_pt[0]
+                py = (1 - s) * c[1] + s * s_pt[1]
+            ring[k, r] = nodes.get(px, py)
+    for i in range(4 * m):
+        for j in range(m):
+            el = []
+            for b in range(3):
+                k = (2 * i + b) % n_around
+                for a in range(3):
+                    el.append(ring[k, 2 * j + a])
+            if j == 0:
+                gamma_faces.append((len(conn), 0))
+            conn.append(el)
+
+    # ---- Cartesian surround --------------------------------------------------
+    nl = max(1, round(8 * m / 12))
+    nr = max(1, round(20 * m / 12))
+    nb = max(1, round(8 * m / 12))
+    nt = max(1, round(8 * m / 12))
+    h0 = 2.0 * half / m
+    wl = _graded(h0, (cx - half) - x0, nl)[::-1]
+    wr = _graded(h0, x1 - (cx + half), nr)
+    wb = _graded(h0, (cy - half) - y0, nb)[::-1]
+    wt = _graded(h0, y1 - (cy + half), nt)
+    xv = np.concatenate([[x0], x0 + np.cumsum(wl)[:-1], np.linspace(cx - half, cx + half, m + 1),
+                         (cx + half) + np.cumsum(wr)])
+    yv = np.concatenate([[y0], y0 + np.cumsum(wb)[:-1], np.linspace(cy - half, cy + half, m + 1),
+                         (cy + half) + np.cumsum(wt)])
+    xv[-1], yv[-1] = x1, y1
+    xq, yq = _q2_line(xv), _q2_line(yv)
+    for cj in range(len(yv) - 1):
+        for ci in range(len(xv) - 1):
+            if nl <= ci < nl + m and nb <= cj < nb + m:
+                continue
+            el = []
+            for b in range(3):
+                for a in range(3):
+                    el.append(nodes.get(xq[2 * ci + a], yq[2 * cj + b]))
+            conn.append(el)
+
+    X = np.array(nodes.coords, dtype=np.float64)
+    tags = np.zeros(len(X), dtype=np.int32)
+    tol = 1e-9
+    tags[np.abs(X[:, 1] - y0) < tol] |= WALL_TAG
+    tags[np.abs(X[:, 1] - y1) < tol] |= WALL_TAG
+    tags[np.abs(X[:, 0] - x1) < tol] |= OUTLET_TAG
+    tags[np.abs(X[:, 0] - x0) < tol] |= INLET_TAG
+    rr = np.hypot(X[:, 0] - cx, X[:, 1] - cy)
+    tags[np.abs(rr - r_in) < 1e-9] |= CYL
+    return dict(X=X, conn=np.array(conn, dtype=np.int64), tags=tags,
+                gamma_faces=np.array(gamma_faces, dtype=np.int64).reshape(-1, 2),
+                Xc=np.array([cx, cy], dtype=np.float64), D=float(D), name=f"viv_ogrid_m{m}")
+
+
+def square_mesh(n, hole=None, lo=0.0, hi=1.0):
+    """Uniform n x n Q2 mesh of [lo,hi]^2 with every outer node fully
+    Dirichlet (u and x).  `hole=(a,b)` removes the cells inside [a,b]^2 (a and
+    b must fall on cell boundaries) and tags its boundary as the rigid body
+    Gamma."""
+    h = (hi - lo) / n
+    nodes = _NodeTable()
+    xq = _q2_line(np.linspace(lo, hi, n + 1))
+    conn, gamma_faces = [], []
+    inside = None
+    if hole is not None:
+        ia, ib = round((hole[0] - lo) / h), round((hole[1] - lo) / h)
+        inside = (ia, ib)
+    for cj in range(n):
+        for ci in range(n):
+            if inside and inside[0] <= ci < inside[1] and inside[0] <= cj < inside[1]:
+                continue
+            el = []
+            for b in range(3):
+                for a in range(3):
+                    el.append(nodes.get(xq[2 * ci + a], xq[2 * cj + b]))
+            if inside:
+                ia, ib = inside
+                if ci == ia - 1 and ia <= cj < ib:
+                    gamma_faces.append((len(conn), 1))
+                if ci == ib and ia <= cj < ib:
+                    gamma_faces.append((len(conn), 0))
+                if cj == ia - 1 and ia <= ci < ib:
+                    gamma_faces.append((len(conn), 3))
+                if cj == ib and ia <= ci < ib:
+                    gamma_faces.append((len(conn), 2))
+            conn.append(el)
+    X = np.array(nodes.coords, dtype=np.float64)
+    tags = np.zeros(len(X), dtype=np.int32)
+    tol = 1e-9
+    outer = ((np.abs(X[:, 0] - lo) < tol) | (np.abs(X[:, 0] - hi) < tol)
+             | (np.abs(X[:, 1] - lo) < tol) | (np.abs(X[:, 1] - hi) < tol))
+    tags[outer] |= ALL_DIRICHLET_TAG
+    if hole is not None:
+        a, b = hole
+        on = (((np.abs(X[:, 0] - a) < tol) | (np.abs(X[:, 0] - b) < tol)) & (X[:, 1] > a - tol) & (X[:, 1] < b + tol)) | \
+             (((np.abs(X[:, 1] - a) < tol) | (np.abs(X[:, 1] - b) < tol)) & (X[:, 0] > a - tol) & (X[:, 0] < b + tol))
+        tags[on] |= CYL
+        c = 0.5 * (a + b)
+    else:
+        c = 0.5 * (lo + hi)
+    return dict(X=X, conn=np.array(conn, dtype=np.int64), tags=tags,
+                gamma_faces=np.array(gamma_faces, dtype=np.int64).reshape(-1, 2),
+                Xc=np.array([c, c]), D=(hole[1] - hole[0]) if hole else 0.0,
+                name=f"square_n{n}" + ("_hole" if hole else ""))
+
+
+# --- seeded normal samples: splitmix64 + Box-Muller ----------------------------
+_M64 = (1 << 64) - 1
+
+
+def _splitmix64(state):
+    state = (state + 0x9E3779B97F4A7C15) & _M64
+    z = state
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return state, z ^ (z >> 31)
+
+
+def seeded_normals(seed, n):
+    """n standard normal samples from splitmix64 (Vigna) + Box-Muller."""
+    out = np.empty(n, dtype=np.float64)
+    s = seed & _M64
+    i = 0
+    while i < n:
+        s, a = _splitmix64(s)
+        s, b = _splitmix64(s)
+        u1 = ((a >> 11) + 1) * (1.0 / 9007199254740993.0)   # (0,1]
+        u2 = (b >> 11) * (1.0 / 9007199254740992.0)         # [0,1)
+        r = math.sqrt(-2.0 * math.log(u1))
+        out[i] = r * math.cos(2.0 * math.pi * u2)
+        if i + 1 < n:
+            out[i + 1] = r * math.sin(2.0 * math.pi * u2)
+        i += 2
+    return out
+
+
+def viv_initial_velocity(mesh, U_inf=1.0, sigma=1e-3, seed=1):
+    """Nodal initial velocity: uniform inflow (U_inf, 0) plus seeded N(0, sigma^2)
+    noise on every component that no Dirichlet tag holds.  Prescribed
+    components carry their boundary value (inflow, or 0 normal to walls)."""
+    n = len(mesh["X"])
+    u = np.zeros((n, 2))
+    u[:, 0] = U_inf
+    if sigma > 0:
+        u += sigma * seeded_normals(seed, 2 * n).reshape(n, 2)
+    t = mesh["tags"]
+    fx = (t & U_FIX_X) != 0
+    fy = (t & U_FIX_Y) != 0
+    u[fx, 0] = U_inf
+    u[fy, 1] = 0.0
+    return u
+
+
+# the workloads used by the tests and the bench, by name
+def viv_case(name):
+    """Named VIV workloads: mesh refinement m, Reynolds number, reduced
+    velocity, time step, steps."""
+    table = {
+        "viv_re100_m12": dict(m=12, Re=100.0, Ustar=8.0, dt=0.1, steps=10),
+        "viv_re200_m60": dict(m=60, Re=200.0, Ustar=10.0, dt=0.02, steps=500),
+    }
+    return dict(table[name])
