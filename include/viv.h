@@ -1,0 +1,206 @@
+/*
+ * viv.h - C ABI of the B300 monolithic ALE solver for a massless,
+ * spring-mounted cylinder (vortex-induced vibrations at zero mass ratio).
+ *
+ * One implicit system per Newton step holds the fluid velocity u and
+ * pressure p on the moving mesh, the mesh position x (linear-elastic
+ * pseudo-solid on the reference mesh), the Lagrange multiplier lambda on the
+ * cylinder boundary Gamma, and the cylinder displacement delta
+ * (Section 2, Eq. system; Section 3.1, Eq. weak_system; Eq. lambda_coupling).
+ * Discretisation: Q2 velocity / Q1 pressure / Q2 position on 9-node quads,
+ * Q2 multiplier traces on Gamma, BDF2 in time with a BDF1 first step.
+ *
+ * Conventions
+ *  - Every function returns vivStatus and never aborts; on failure
+ *    viv_last_error() returns a thread-local message.
+ *  - Host pointers are read during the call only; the library copies what it
+ *    keeps.  Output host buffers are caller-allocated.
+ *  - Handles are owned by the caller and released by the matching *_destroy.
+ *  - `stream` arguments are cudaStream_t values passed as void*; NULL means the
+ *    legacy default stream.  All device work of a case is ordered on its
+ *    stream.  A case is not thread-safe; distinct cases may run concurrently.
+ *  - Device memory comes from the allocator given at mesh creation (or
+ *    cudaMalloc when NULL); a failed allocation returns VIV_ERR_OOM.
+ *  - No device code waits on a flag; there is no unbounded device wait.
+ */
+#ifndef VIV_H
+#define VIV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  VIV_OK = 0,
+  VIV_ERR_ARG = 1,             /* bad argument or inconsistent mesh */
+  VIV_ERR_OOM = 2,             /* device allocation failed */
+  VIV_ERR_CUDA = 3,            /* a CUDA runtime call failed */
+  VIV_ERR_PIVOT = 4,           /* a front met an exactly zero pivot column */
+  VIV_ERR_NEWTON = 5,          /* Newton did not reach the tolerance in max_newton */
+  VIV_ERR_NONFINITE = 6,       /* a residual or correction norm is NaN/Inf */
+  VIV_ERR_TIMEOUT = 7,         /* reserved for bounded device waits */
+  VIV_ERR_ADMISSION = 8,       /* server: request exceeds the memory budget */
+  VIV_ERR_STATE = 9            /* call out of order (e.g. solve before factor) */
+} vivStatus;
+
+/* node tag bits (per mesh node): which nodal values a Dirichlet condition holds */
+enum {
+  VIV_TAG_U_FIX_X = 1, VIV_TAG_U_FIX_Y = 2,   /* velocity component held (Eq. flowBC) */
+  VIV_TAG_X_FIX_X = 4, VIV_TAG_X_FIX_Y = 8,   /* position component held (Eq. psBC) */
+  VIV_TAG_CYL = 16,                            /* node on Gamma: x = X + delta, lambda lives here */
+  VIV_TAG_OUTLET = 32,                         /* informational */
+  VIV_TAG_P_FIX = 64                           /* pressure held (all-Dirichlet problems) */
+};
+
+/* precision of the Jacobian and factors; residual, refinement, state: FP64 always */
+enum { VIV_FP64 = 0, VIV_MIXED = 1 };
+/* what viv_assemble builds */
+enum { VIV_RES = 1, VIV_JAC = 2 };
+/* field codes of viv_mesh_dof_labels */
+enum { VIV_F_UX = 0, VIV_F_UY = 1, VIV_F_XX = 2, VIV_F_XY = 3, VIV_F_P = 4,
+       VIV_F_LX = 5, VIV_F_LY = 6, VIV_F_DX = 7, VIV_F_DY = 8 };
+
+typedef struct {
+  void* (*alloc)(size_t bytes, void* ctx);   /* returns device memory or NULL */
+  void (*free)(void* ptr, void* ctx);
+  void* ctx;
+} vivAllocator;
+
+typedef struct vivMesh vivMesh;
+typedef struct vivCase vivCase;
+
+/* Mesh description (2-D).  X: n_nodes x 2 reference coordinates (row-major).
+ * conn: n_elems x 9 node ids of each Q2 quad, lexicographic (node 3*b + a,
+ * a along xi), positively oriented.  tags: n_nodes VIV_TAG_* bit sets.
+ * gamma_faces: n_gamma_faces x 2 (element, local edge) pairs of Gamma, edges
+ * 0: xi=0 (nodes 0,3,6), 1: xi=1 (2,5,8), 2: eta=0 (0,1,2), 3: eta=1 (6,7,8).
+ * leaf_elems: nested-dissection leaf size in elements (0: default 4). */
+typedef struct {
+  int64_t n_nodes, n_elems, n_gamma_faces;
+  const double* X;
+  const int64_t* conn;
+  const int32_t* tags;
+  const int64_t* gamma_faces;
+  int32_t leaf_elems;
+} vivMeshDesc;
+
+typedef struct {
+  int64_t n_dofs;          /* unknowns: free u, p, x, lambda, and delta (2) */
+  int64_t nnz;             /* structural nonzeros of the Jacobian (CSR) */
+  int64_t n_fronts;        /* supernodes of the nested-dissection tree */
+  int64_t max_front;       /* largest front order */
+  int64_t n_levels;        /* tree height + 1 */
+  double factor_flops;     /* flops of one numeric factorisation */
+  size_t front_entries;    /* sum of front order^2 (factor storage in entries) */
+  size_t device_bytes_fp64;   /* predicted device bytes of one FP64 case */
+  size_t device_bytes_mixed;  /* predicted device bytes of one mixed case */
+  int32_t n_colors;        /* element colours of the deterministic scatter */
+} vivMeshInfo;
+
+/* Physical and solver parameters.  rho, mu: fluid density and viscosity;
+ * k: spring stiffness of Eq. solid_balance; dt: constant time step;
+ * lame_scale: lambda_s = mu_s = lame_scale / |K_0| per element;
+ * newton_tol: absolute ||NL||_2 stop; refine_tol: relative residual of the
+ * refined linear solve; refine_max: refinement sweeps (mixed path). */
+typedef struct {
+  double rho, mu, k, dt;
+  double lame_scale;
+  double newton_tol;
+  int32_t max_newton;
+  int32_t precision;       /* VIV_FP64 or VIV_MIXED */
+  double refine_tol;
+  int32_t refine_max;
+  double pivot_threshold;  /* threshold u of partial pivoting in fronts (0.01) */
+} vivParams;
+
+typedef struct {
+  int32_t newton_iters;    /* Jacobian factorisations this step */
+  int32_t refine_sweeps;   /* refinement sweeps summed over the step */
+  int32_t perturbed_pivots;/* pivots replaced by a static perturbation */
+  int32_t threshold_misses;/* pivots taken below the threshold */
+  double res_norm0, res_norm; /* ||NL|| at the predictor and at convergence */
+  double t;                /* time reached */
+  double delta[2];         /* cylinder displacement x_c - X_c */
+  double force[2];         /* F_fluid = -int_Gamma lambda */
+} vivStepInfo;
+
+/* ---- mesh: numbering, sparsity, nested dissection, symbolic factorisation
+ * (Section 4.3: the pattern is fixed because ALE moves nodes, not
+ * connectivity, so analysis runs once per mesh) --------------------------- */
+vivStatus viv_mesh_create(const vivMeshDesc* desc, const vivAllocator* alloc, void* stream,
+                          vivMesh** out);
+/* Host-only analysis of the same mesh (no device memory, no CUDA call):
+ * numbering, pattern and symbolic factorisation.  The handle answers
+ * viv_mesh_info, viv_mesh_dof_labels and viv_mesh_pattern; viv_case_create
+ * on it returns VIV_ERR_STATE. */
+vivStatus viv_mesh_analyze(const vivMeshDesc* desc, vivMesh** out);
+vivStatus viv_mesh_info(const vivMesh* mesh, vivMeshInfo* info);
+/* per unknown: owning node (n_nodes for delta) and VIV_F_* field code */
+vivStatus viv_mesh_dof_labels(const vivMesh* mesh, int64_t* node, int32_t* field);
+/* CSR pattern of the Jacobian: row_ptr (n_dofs+1), col (nnz), host buffers */
+vivStatus viv_mesh_pattern(const vivMesh* mesh, int64_t* row_ptr, int32_t* col);
+vivStatus viv_mesh_destroy(vivMesh* mesh);
+
+/* ---- case: state on the device ------------------------------------------ */
+/* u0: n_nodes x 2 host initial velocity (its prescribed components are the
+ * Dirichlet values); x starts at X, p, lambda and delta at 0. */
+vivStatus viv_case_create(vivMesh* mesh, const vivParams* params, const double* u0,
+                          void* stream, vivCase** out);
+vivStatus viv_case_destroy(vivCase* c);
+
+/* Overwrite the state.  Each pointer may be NULL (left unchanged); pointers
+ * may be host or device memory (the `device` flag documents which; copies use
+ * unified addressing).  u, x, lam: n_nodes x 2; p: n_nodes (vertex values);
+ * delta: 2.  Inside a step (after viv_begin_step) this changes the Newton
+ * iterate only; the BDF history was fixed by viv_begin_step. */
+vivStatus viv_set_state(vivCase* c, int device, const double* u, const double* p, const double* x,
+                        const double* lam, const double* delta, double t);
+/* Give the previous time level (u, x at t - dt, n_nodes x 2 each); the next
+ * step then uses BDF2 instead of the BDF1 start. */
+vivStatus viv_set_history(vivCase* c, int device, const double* u_prev, const double* x_prev);
+vivStatus viv_get_state(const vivCase* c, int device, double* u, double* p, double* x, double* lam,
+                        double* delta, double* t);
+
+/* Begin a time step: shift the BDF history and form the nodal rate
+ * coefficients (BDF1 on the first step, BDF2 after). */
+vivStatus viv_begin_step(vivCase* c);
+
+/* Residual NL(U) (Eq. nonlinear_functional_discrete) and/or Jacobian
+ * (Section 3.2, with shape derivatives) of the current state into device
+ * storage.  res_norm (nullable): ||NL||_2 on the host. */
+vivStatus viv_assemble(vivCase* c, int what, double* res_norm);
+/* copies of the assembled residual (n_dofs) / Jacobian values (nnz, FP64
+ * path: FP64; mixed path: the FP32 values widened) to host buffers */
+vivStatus viv_get_residual(const vivCase* c, double* r);
+vivStatus viv_get_jacobian(const vivCase* c, double* vals);
+
+/* Numeric multifrontal LU of the Jacobian with threshold partial pivoting
+ * inside fronts; delta is eliminated last in the root front. */
+vivStatus viv_factor(vivCase* c);
+/* Solve J dU = -NL for the Newton correction with iterative refinement
+ * against the FP64 Jacobian; sweeps (nullable) receives the sweep count. */
+vivStatus viv_solve(vivCase* c, int* sweeps);
+/* Solve J y = b for a host or device right-hand side b (n_dofs, FP64). */
+vivStatus viv_solve_rhs(vivCase* c, int device, const double* b, double* y, int* sweeps);
+/* U += dU (the last correction); Gamma nodes follow x = X + delta. */
+vivStatus viv_update(vivCase* c);
+
+/* One BDF step: begin_step, then Newton (Eq. NR_iteration) until
+ * ||NL||_2 <= newton_tol. info nullable. */
+vivStatus viv_step(vivCase* c, vivStepInfo* info);
+/* Same step with host buffers: uploads the state and history, steps, and
+ * downloads the new state (the end-to-end form of one step). */
+vivStatus viv_step_host(vivCase* c, const double* state_in, double* state_out, vivStepInfo* info);
+/* size in doubles of the packed host state used by viv_step_host */
+int64_t viv_state_size(const vivMesh* mesh);
+
+const char* viv_last_error(void);
+const char* viv_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VIV_H */

@@ -1,0 +1,544 @@
+// C ABI entry points: argument checks, the case state machine, the Newton /
+// BDF driver (Eq. NR_iteration; BDF1 first step then BDF2) and the
+// refinement loop of the linear solve.  All device work of a case is ordered
+// on its stream; the host only reads back scalars (norms) to steer Newton.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <utility>
+
+#include "viv_internal.h"
+
+namespace viv {
+void build_mesh(Mesh& m, const vivMeshDesc* d);
+void upload_mesh(Mesh& m, cudaStream_t s);
+
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+}  // namespace viv
+
+using namespace viv;
+
+#define API_BEGIN try {
+#define API_END                              \
+  }                                          \
+  catch (const viv::Error& e) {              \
+    set_error(e.msg);                        \
+    return e.status;                         \
+  }                                          \
+  catch (const std::bad_alloc&) {            \
+    set_error("host allocation failed");     \
+    return VIV_ERR_OOM;                      \
+  }                                          \
+  catch (const std::exception& e) {          \
+    set_error(e.what());                     \
+    return VIV_ERR_ARG;                      \
+  }                                          \
+  return VIV_OK;
+
+namespace {
+
+bool mixed(const vivCase* c) { return c->prm.precision == VIV_MIXED; }
+
+double read_scalar(vivCase* c, const double* dptr) {
+  VIV_CUDA(cudaMemcpyAsync(c->h_pinned, dptr, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  VIV_CUDA(cudaStreamSynchronize(c->stream));
+  return c->h_pinned[0];
+}
+
+double norm2(vivCase* c, const double* v, int64_t n) {
+  launch_norm2(v, n, c->s.partial, c->s.scal, c->stream);
+  return read_scalar(c, c->s.scal);
+}
+
+void copy_in(vivCase* c, double* dst, const double* src, size_t count) {
+  if (src) VIV_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyDefault, c->stream));
+}
+void copy_out(vivCase* c, double* dst, const double* src, size_t count) {
+  if (dst) VIV_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyDefault, c->stream));
+}
+
+void begin_step(vivCase* c) {
+  const Mesh& m = c->mesh->m;
+  CaseState& s = c->s;
+  const bool bdf2 = c->nstep > 0 || c->have_prev2;
+  if (bdf2) {
+    std::swap(s.u_nm1, s.u_n);
+    std::swap(s.x_nm1, s.x_n);
+  }
+  const size_t n2 = 2 * m.n_nodes * sizeof(double);
+  VIV_CUDA(cudaMemcpyAsync(s.u_n, s.u, n2, cudaMemcpyDeviceToDevice, c->stream));
+  VIV_CUDA(cudaMemcpyAsync(s.x_n, s.x, n2, cudaMemcpyDeviceToDevice, c->stream));
+  const double dt = c->prm.dt;
+  if (bdf2) {
+    c->c0 = 1.5 / dt;
+    launch_bdf_history(m, s, -2.0 / dt, 0.5 / dt, false, c->stream);
+  } else {
+    c->c0 = 1.0 / dt;
+    launch_bdf_history(m, s, -1.0 / dt, 0.0, false, c->stream);
+  }
+  c->step_open = true;
+  c->factored = false;
+  c->have_dU = false;
+}
+
+double assemble(vivCase* c, int what, bool want_norm) {
+  const Mesh& m = c->mesh->m;
+  VIV_CHECK(c->step_open, VIV_ERR_STATE, "viv_assemble before viv_begin_step");
+  double nr = 0;
+  if (what & VIV_RES) {
+    launch_residual(m, c->s, c->prm, c->c0, c->stream);
+    if (want_norm) nr = norm2(c, c->s.R, m.n_dofs);
+  }
+  if (what & VIV_JAC) {
+    launch_jacobian<double>(m, c->s, c->prm, c->c0, c->s.J64, c->stream);
+    if (mixed(c)) launch_f64_to_f32(c->s.J32, c->s.J64, m.row_ptr[m.n_dofs], c->stream);
+    c->factored = false;
+  }
+  return nr;
+}
+
+void factor(vivCase* c) {
+  const Mesh& m = c->mesh->m;
+  double thr = c->prm.pivot_threshold > 0 ? c->prm.pivot_threshold : 0.01;
+  if (mixed(c))
+    factor_numeric<float>(m, nullptr, c->s.J32, (float*)c->s.fronts, c->s.piv, c->s.stats, thr, c->stream);
+  else
+    factor_numeric<double>(m, c->s.J64, nullptr, (double*)c->s.fronts, c->s.piv, c->s.stats, thr, c->stream);
+  c->factored = true;
+}
+
+void lu_solve(vivCase* c, const double* b, double* x) {
+  const Mesh& m = c->mesh->m;
+  if (mixed(c))
+    solve_fronts<float>(m, (const float*)c->s.fronts, c->s.piv, b, x, (float*)c->s.vec, (float*)c->s.yv,
+                        c->stream);
+  else
+    solve_fronts<double>(m, (const double*)c->s.fronts, c->s.piv, b, x, (double*)c->s.vec,
+                         (double*)c->s.yv, c->stream);
+}
+
+// y = J^{-1} b with refinement against the FP64 Jacobian; b, y device
+int refined_solve(vivCase* c, const double* b, double* y) {
+  const Mesh& m = c->mesh->m;
+  CaseState& s = c->s;
+  const int64_t n = m.n_dofs;
+  VIV_CHECK(c->factored, VIV_ERR_STATE, "solve before factor");
+  const int max_sweeps = 1 + (c->prm.refine_max > 0 ? c->prm.refine_max : (mixed(c) ? 10 : 1));
+  const double tol = c->prm.refine_tol > 0 ? c->prm.refine_tol : 1e-13;
+  double nb = norm2(c, b, n);
+  VIV_CUDA(cudaMemsetAsync(y, 0, n * sizeof(double), c->stream));
+  VIV_CUDA(cudaMemcpyAsync(s.r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  int sweeps = 0;
+  for (;;) {
+    lu_solve(c, s.r, s.d);
+    launch_axpy(y, s.d, 1.0, n, c->stream);
+    ++sweeps;
+    if (sweeps >= max_sweeps || nb == 0) break;
+    launch_spmv_residual(m, s.J64, y, b, s.r, c->stream);
+    double nr = norm2(c, s.r, n);
+    VIV_CHECK(std::isfinite(nr), VIV_ERR_NONFINITE, "refinement residual is not finite");
+    if (nr <= tol * nb) break;
+  }
+  return sweeps;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* viv_last_error(void) { return g_err.c_str(); }
+const char* viv_version(void) { return "viv-b300 0.1 (sm_103a)"; }
+
+vivStatus viv_mesh_create(const vivMeshDesc* desc, const vivAllocator* alloc, void* stream, vivMesh** out) {
+  API_BEGIN
+  VIV_CHECK(out, VIV_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  vivMesh* h = new vivMesh();
+  try {
+    if (alloc && alloc->alloc && alloc->free) {
+      h->m.arena.alloc = *alloc;
+      h->m.arena.custom = true;
+    }
+    h->m.stream = (cudaStream_t)stream;
+    build_mesh(h->m, desc);
+    upload_mesh(h->m, (cudaStream_t)stream);
+    h->m.on_device = true;
+  } catch (...) {
+    delete h;
+    throw;
+  }
+  *out = h;
+  API_END
+}
+
+vivStatus viv_mesh_analyze(const vivMeshDesc* desc, vivMesh** out) {
+  API_BEGIN
+  VIV_CHECK(out, VIV_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  vivMesh* h = new vivMesh();
+  try {
+    build_mesh(h->m, desc);
+  } catch (...) {
+    delete h;
+    throw;
+  }
+  *out = h;
+  API_END
+}
+
+vivStatus viv_mesh_info(const vivMesh* mesh, vivMeshInfo* info) {
+  API_BEGIN
+  VIV_CHECK(mesh && info, VIV_ERR_ARG, "NULL argument");
+  const Mesh& m = mesh->m;
+  info->n_dofs = m.n_dofs;
+  info->nnz = m.row_ptr[m.n_dofs];
+  info->n_fronts = m.n_fronts;
+  info->max_front = m.max_front;
+  info->n_levels = m.n_levels;
+  info->factor_flops = m.factor_flops;
+  info->front_entries = (size_t)m.front_entries;
+  size_t nodes = (size_t)m.n_nodes, nnz = (size_t)info->nnz, nd = (size_t)m.n_dofs;
+  size_t state = 8 * (17 * nodes + (size_t)m.n_elems + 3 * nd + 2 * 296 + 64) + 4 * (size_t)m.piv_entries;
+  info->device_bytes_fp64 = state + 8 * (nnz + (size_t)m.front_entries + (size_t)m.vec_entries + nd);
+  info->device_bytes_mixed =
+      state + 8 * nnz + 4 * (nnz + (size_t)m.front_entries + (size_t)m.vec_entries + nd);
+  info->n_colors = (int32_t)m.color_off.size() - 1;
+  API_END
+}
+
+vivStatus viv_mesh_dof_labels(const vivMesh* mesh, int64_t* node, int32_t* field) {
+  API_BEGIN
+  VIV_CHECK(mesh, VIV_ERR_ARG, "NULL mesh");
+  const Mesh& m = mesh->m;
+  if (node) std::memcpy(node, m.dof_node.data(), m.n_dofs * sizeof(int64_t));
+  if (field) std::memcpy(field, m.dof_field.data(), m.n_dofs * sizeof(int32_t));
+  API_END
+}
+
+vivStatus viv_mesh_pattern(const vivMesh* mesh, int64_t* row_ptr, int32_t* col) {
+  API_BEGIN
+  VIV_CHECK(mesh, VIV_ERR_ARG, "NULL mesh");
+  const Mesh& m = mesh->m;
+  if (row_ptr) std::memcpy(row_ptr, m.row_ptr.data(), (m.n_dofs + 1) * sizeof(int64_t));
+  if (col) std::memcpy(col, m.col.data(), m.col.size() * sizeof(int32_t));
+  API_END
+}
+
+vivStatus viv_mesh_destroy(vivMesh* mesh) {
+  API_BEGIN
+  delete mesh;
+  API_END
+}
+
+vivStatus viv_case_create(vivMesh* mesh, const vivParams* prm, const double* u0, void* stream, vivCase** out) {
+  API_BEGIN
+  VIV_CHECK(mesh && prm && u0 && out, VIV_ERR_ARG, "NULL argument");
+  VIV_CHECK(prm->dt > 0 && prm->rho > 0 && prm->mu > 0, VIV_ERR_ARG, "rho, mu and dt must be positive");
+  VIV_CHECK(prm->precision == VIV_FP64 || prm->precision == VIV_MIXED, VIV_ERR_ARG, "unknown precision");
+  VIV_CHECK(mesh->m.on_device, VIV_ERR_STATE, "mesh was analysed on the host only");
+  *out = nullptr;
+  vivCase* c = new vivCase();
+  try {
+    c->mesh = mesh;
+    c->prm = *prm;
+    if (c->prm.lame_scale == 0) c->prm.lame_scale = 1.0;
+    if (c->prm.newton_tol <= 0) c->prm.newton_tol = 1e-10;
+    if (c->prm.max_newton <= 0) c->prm.max_newton = 25;
+    c->stream = (cudaStream_t)stream;
+    c->arena.alloc = mesh->m.arena.alloc;
+    c->arena.custom = mesh->m.arena.custom;
+    const Mesh& m = mesh->m;
+    const int64_t n = m.n_nodes, nd = m.n_dofs, nnz = m.row_ptr[m.n_dofs];
+    DeviceArena& A = c->arena;
+    CaseState& s = c->s;
+    s.u = A.make<double>(2 * n);
+    s.p = A.make<double>(n);
+    s.x = A.make<double>(2 * n);
+    s.lam = A.make<double>(2 * n);
+    s.delta = A.make<double>(2);
+    s.u_n = A.make<double>(2 * n);
+    s.x_n = A.make<double>(2 * n);
+    s.u_nm1 = A.make<double>(2 * n);
+    s.x_nm1 = A.make<double>(2 * n);
+    s.hu = A.make<double>(2 * n);
+    s.hx = A.make<double>(2 * n);
+    s.lame = A.make<double>(m.n_elems);
+    s.R = A.make<double>(nd);
+    s.dU = A.make<double>(nd);
+    s.r = A.make<double>(nd);
+    s.d = A.make<double>(nd);
+    s.mR = A.make<double>(nd);
+    s.y2 = A.make<double>(nd);
+    s.J64 = A.make<double>(nnz);
+    s.J32 = mixed(c) ? A.make<float>(nnz) : nullptr;
+    const size_t tsz = mixed(c) ? sizeof(float) : sizeof(double);
+    s.fronts = A.get(tsz * (size_t)m.front_entries);
+    s.vec = A.get(tsz * (size_t)m.vec_entries);
+    s.yv = A.get(tsz * (size_t)nd);
+    s.piv = A.make<int32_t>(m.piv_entries);
+    s.stats = A.make<int32_t>(4);
+    s.partial = A.make<double>(296);
+    s.scal = A.make<double>(8);
+    VIV_CUDA(cudaMallocHost(&c->h_pinned, 8 * sizeof(double)));
+    cudaStream_t st = c->stream;
+    VIV_CUDA(cudaMemcpyAsync(s.u, u0, 2 * n * sizeof(double), cudaMemcpyDefault, st));
+    VIV_CUDA(cudaMemcpyAsync(s.x, m.d_X, 2 * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    VIV_CUDA(cudaMemsetAsync(s.p, 0, n * sizeof(double), st));
+    VIV_CUDA(cudaMemsetAsync(s.lam, 0, 2 * n * sizeof(double), st));
+    VIV_CUDA(cudaMemsetAsync(s.delta, 0, 2 * sizeof(double), st));
+    VIV_CUDA(cudaMemsetAsync(s.u_nm1, 0, 2 * n * sizeof(double), st));
+    VIV_CUDA(cudaMemsetAsync(s.x_nm1, 0, 2 * n * sizeof(double), st));
+    VIV_CUDA(cudaMemsetAsync(s.stats, 0, 4 * sizeof(int32_t), st));
+    launch_element_areas(m, s.lame, c->prm.lame_scale, st);
+    VIV_CUDA(cudaStreamSynchronize(st));
+  } catch (...) {
+    if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    delete c;
+    throw;
+  }
+  *out = c;
+  API_END
+}
+
+vivStatus viv_case_destroy(vivCase* c) {
+  API_BEGIN
+  if (c) {
+    cudaStreamSynchronize(c->stream);
+    if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    delete c;
+  }
+  API_END
+}
+
+vivStatus viv_set_state(vivCase* c, int, const double* u, const double* p, const double* x, const double* lam,
+                        const double* delta, double t) {
+  API_BEGIN
+  VIV_CHECK(c, VIV_ERR_ARG, "NULL case");
+  const int64_t n = c->mesh->m.n_nodes;
+  copy_in(c, c->s.u, u, 2 * n);
+  copy_in(c, c->s.p, p, n);
+  copy_in(c, c->s.x, x, 2 * n);
+  copy_in(c, c->s.lam, lam, 2 * n);
+  copy_in(c, c->s.delta, delta, 2);
+  c->t = t;
+  VIV_CUDA(cudaStreamSynchronize(c->stream));
+  API_END
+}
+
+vivStatus viv_set_history(vivCase* c, int, const double* u_prev, const double* x_prev) {
+  API_BEGIN
+  VIV_CHECK(c && u_prev && x_prev, VIV_ERR_ARG, "NULL argument");
+  const int64_t n = c->mesh->m.n_nodes;
+  // begin_step moves u_n into u_nm1 when BDF2 is on
+  copy_in(c, c->s.u_n, u_prev, 2 * n);
+  copy_in(c, c->s.x_n, x_prev, 2 * n);
+  c->have_prev2 = true;
+  VIV_CUDA(cudaStreamSynchronize(c->stream));
+  API_END
+}
+
+vivStatus viv_get_state(const vivCase* cc, int, double* u, double* p, double* x, double* lam, double* delta,
+                        double* t) {
+  API_BEGIN
+  VIV_CHECK(cc, VIV_ERR_ARG, "NULL case");
+  vivCase* c = const_cast<vivCase*>(cc);
+  const int64_t n = c->mesh->m.n_nodes;
+  copy_out(c, u, c->s.u, 2 * n);
+  copy_out(c, p, c->s.p, n);
+  copy_out(c, x, c->s.x, 2 * n);
+  copy_out(c, lam, c->s.lam, 2 * n);
+  copy_out(c, delta, c->s.delta, 2);
+  if (t) *t = c->t;
+  VIV_CUDA(cudaStreamSynchronize(c->stream));
+  API_END
+}
+
+vivStatus viv_begin_step(vivCase* c) {
+  API_BEGIN
+  VIV_CHECK(c, VIV_ERR_ARG, "NULL case");
+  begin_step(c);
+  API_END
+}
+
+vivStatus viv_assemble(vivCase* c, int what, double* res_norm) {
+  API_BEGIN
+  VIV_CHECK(c && (what & (VIV_RES | VIV_JAC)), VIV_ERR_ARG, "bad arguments");
+  double nr = assemble(c, what, res_norm != nullptr);
+  if (res_norm) *res_norm = nr;
+  API_END
+}
+
+vivStatus viv_get_residual(const vivCase* cc, double* r) {
+  API_BEGIN
+  VIV_CHECK(cc && r, VIV_ERR_ARG, "NULL argument");
+  vivCase* c = const_cast<vivCase*>(cc);
+  copy_out(c, r, c->s.R, c->mesh->m.n_dofs);
+  VIV_CUDA(cudaStreamSynchronize(c->stream));
+  API_END
+}
+
+vivStatus viv_get_jacobian(const vivCase* cc, double* vals) {
+  API_BEGIN
+  VIV_CHECK(cc && vals, VIV_ERR_ARG, "NULL argument");
+  vivCase* c = const_cast<vivCase*>(cc);
+  copy_out(c, vals, c->s.J64, c->mesh->m.row_ptr[c->mesh->m.n_dofs]);
+  VIV_CUDA(cudaStreamSynchronize(c->stream));
+  API_END
+}
+
+vivStatus viv_factor(vivCase* c) {
+  API_BEGIN
+  VIV_CHECK(c, VIV_ERR_ARG, "NULL case");
+  factor(c);
+  API_END
+}
+
+vivStatus viv_solve(vivCase* c, int* sweeps) {
+  API_BEGIN
+  VIV_CHECK(c, VIV_ERR_ARG, "NULL case");
+  const int64_t n = c->mesh->m.n_dofs;
+  launch_scale_copy(c->s.mR, c->s.R, -1.0, n, c->stream);
+  int sw = refined_solve(c, c->s.mR, c->s.dU);
+  c->have_dU = true;
+  if (sweeps) *sweeps = sw;
+  API_END
+}
+
+vivStatus viv_solve_rhs(vivCase* c, int, const double* b, double* y, int* sweeps) {
+  API_BEGIN
+  VIV_CHECK(c && b && y, VIV_ERR_ARG, "NULL argument");
+  const int64_t n = c->mesh->m.n_dofs;
+  VIV_CUDA(cudaMemcpyAsync(c->s.mR, b, n * sizeof(double), cudaMemcpyDefault, c->stream));
+  int sw = refined_solve(c, c->s.mR, c->s.y2);
+  VIV_CUDA(cudaMemcpyAsync(y, c->s.y2, n * sizeof(double), cudaMemcpyDefault, c->stream));
+  VIV_CUDA(cudaStreamSynchronize(c->stream));
+  if (sweeps) *sweeps = sw;
+  API_END
+}
+
+vivStatus viv_update(vivCase* c) {
+  API_BEGIN
+  VIV_CHECK(c && c->have_dU, VIV_ERR_STATE, "update without a correction");
+  launch_update(c->mesh->m, c->s, c->s.dU, c->stream);
+  c->have_dU = false;
+  API_END
+}
+
+static void step_impl(vivCase* c, vivStepInfo* info) {
+  const Mesh& m = c->mesh->m;
+  begin_step(c);
+  const double tol = c->prm.newton_tol;
+  int iters = 0, sweeps = 0;
+  double n0 = 0, nr = 0;
+  int32_t st_acc[2] = {0, 0};
+  for (int it = 0;; ++it) {
+    nr = assemble(c, VIV_RES, true);
+    if (it == 0) n0 = nr;
+    VIV_CHECK(std::isfinite(nr), VIV_ERR_NONFINITE, "residual norm is not finite");
+    if (nr <= tol) break;
+    VIV_CHECK(it < c->prm.max_newton, VIV_ERR_NEWTON,
+              "Newton did not converge in " + std::to_string(c->prm.max_newton) + " iterations (|R| = " +
+                  std::to_string(nr) + ")");
+    assemble(c, VIV_JAC, false);
+    factor(c);
+    launch_scale_copy(c->s.mR, c->s.R, -1.0, m.n_dofs, c->stream);
+    sweeps += refined_solve(c, c->s.mR, c->s.dU);
+    int32_t stv[2];
+    VIV_CUDA(cudaMemcpyAsync(stv, c->s.stats, sizeof(stv), cudaMemcpyDeviceToHost, c->stream));
+    launch_update(m, c->s, c->s.dU, c->stream);
+    VIV_CUDA(cudaStreamSynchronize(c->stream));
+    st_acc[0] += stv[0];
+    st_acc[1] += stv[1];
+    ++iters;
+  }
+  c->t += c->prm.dt;
+  c->nstep += 1;
+  c->step_open = false;
+  if (info) {
+    info->newton_iters = iters;
+    info->refine_sweeps = sweeps;
+    info->perturbed_pivots = st_acc[0];
+    info->threshold_misses = st_acc[1];
+    info->res_norm0 = n0;
+    info->res_norm = nr;
+    info->t = c->t;
+    double d[2] = {0, 0}, rd[2] = {0, 0};
+    VIV_CUDA(cudaMemcpyAsync(d, c->s.delta, sizeof(d), cudaMemcpyDeviceToHost, c->stream));
+    if (m.delta_dof[0] >= 0)
+      VIV_CUDA(cudaMemcpyAsync(rd, c->s.R + m.delta_dof[0], sizeof(rd), cudaMemcpyDeviceToHost, c->stream));
+    VIV_CUDA(cudaStreamSynchronize(c->stream));
+    info->delta[0] = d[0];
+    info->delta[1] = d[1];
+    // R[delta] = k delta + int lambda, so F_fluid = -int lambda = k delta - R[delta]
+    info->force[0] = c->prm.k * d[0] - rd[0];
+    info->force[1] = c->prm.k * d[1] - rd[1];
+  }
+}
+
+vivStatus viv_step(vivCase* c, vivStepInfo* info) {
+  API_BEGIN
+  VIV_CHECK(c, VIV_ERR_ARG, "NULL case");
+  step_impl(c, info);
+  API_END
+}
+
+int64_t viv_state_size(const vivMesh* mesh) {
+  if (!mesh) return -1;
+  const int64_t n = mesh->m.n_nodes;
+  return 2 * n + n + 2 * n + 2 * n + 2 + 2 * n + 2 * n + 2;
+}
+
+// packed host state: u(2n) p(n) x(2n) lam(2n) delta(2) u_prev(2n) x_prev(2n) [t, have_prev]
+vivStatus viv_step_host(vivCase* c, const double* in, double* out, vivStepInfo* info) {
+  API_BEGIN
+  VIV_CHECK(c && in && out, VIV_ERR_ARG, "NULL argument");
+  const int64_t n = c->mesh->m.n_nodes;
+  const double* q = in;
+  copy_in(c, c->s.u, q, 2 * n);
+  q += 2 * n;
+  copy_in(c, c->s.p, q, n);
+  q += n;
+  copy_in(c, c->s.x, q, 2 * n);
+  q += 2 * n;
+  copy_in(c, c->s.lam, q, 2 * n);
+  q += 2 * n;
+  copy_in(c, c->s.delta, q, 2);
+  q += 2;
+  const double* up = q;
+  q += 2 * n;
+  const double* xp = q;
+  q += 2 * n;
+  c->t = q[0];
+  const bool have_prev = q[1] != 0.0;
+  c->nstep = 0;
+  c->have_prev2 = have_prev;
+  if (have_prev) {
+    copy_in(c, c->s.u_n, up, 2 * n);
+    copy_in(c, c->s.x_n, xp, 2 * n);
+  }
+  step_impl(c, info);
+  double* o = out;
+  copy_out(c, o, c->s.u, 2 * n);
+  o += 2 * n;
+  copy_out(c, o, c->s.p, n);
+  o += n;
+  copy_out(c, o, c->s.x, 2 * n);
+  o += 2 * n;
+  copy_out(c, o, c->s.lam, 2 * n);
+  o += 2 * n;
+  copy_out(c, o, c->s.delta, 2);
+  o += 2;
+  copy_out(c, o, c->s.u_n, 2 * n);
+  o += 2 * n;
+  copy_out(c, o, c->s.x_n, 2 * n);
+  o += 2 * n;
+  VIV_CUDA(cudaStreamSynchronize(c->stream));
+  o[0] = c->t;
+  o[1] = 1.0;
+  API_END
+}
+
+}  // extern "C"

@@ -1,0 +1,655 @@
+// Mesh analysis, run once per mesh on the host (Section 4.3: ALE moves nodes,
+// never connectivity, so numbering, sparsity and the symbolic factorisation
+// are computed once and reused by every Newton iteration of every step).
+//
+//  1. unknown numbering (node-major inside nested-dissection supernodes)
+//  2. CSR pattern of the Jacobian with the structural zeros of the block
+//     structure of Section 3.2 (zero p-p and lambda-lambda blocks, pseudo-solid
+//     rows independent of u, p, lambda)
+//  3. element-to-nonzero map (e2nz) in the canonical pair order of the
+//     element kernels, and an element colouring for a deterministic scatter
+//  4. geometric nested dissection on element centroids, supernodes, front
+//     index lists, assembly and extend-add maps, and the launch schedule of
+//     the blocked numeric factorisation
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "viv_internal.h"
+
+namespace viv {
+
+void* DeviceArena::get(size_t n) {
+  if (n == 0) n = 16;
+  n = (n + 255) & ~size_t(255);
+  void* p = nullptr;
+  if (custom) {
+    p = alloc.alloc(n, alloc.ctx);
+    if (!p) throw Error{VIV_ERR_OOM, "device allocation of " + std::to_string(n) + " bytes failed"};
+  } else {
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw Error{VIV_ERR_OOM, "cudaMalloc(" + std::to_string(n) + "): " + cudaGetErrorString(e)};
+    }
+  }
+  blocks.push_back(p);
+  bytes += n;
+  return p;
+}
+
+void DeviceArena::release() {
+  for (void* p : blocks) {
+    if (custom)
+      alloc.free(p, alloc.ctx);
+    else
+      cudaFree(p);
+  }
+  blocks.clear();
+  bytes = 0;
+}
+
+namespace {
+
+const int VERT[4] = {0, 2, 6, 8};
+const int EDGE[4][3] = {{0, 3, 6}, {2, 5, 8}, {0, 1, 2}, {6, 7, 8}};
+
+struct SN {
+  std::vector<int> nodes;
+  int parent = -1;
+  std::vector<int> kids;
+};
+
+struct Dissector {
+  const Mesh& m;
+  int leaf;
+  std::vector<double> cx, cy;
+  std::vector<int> owner, mark;
+  int stamp = 0;
+  std::vector<SN> sns;
+
+  Dissector(const Mesh& mm, int leaf_) : m(mm), leaf(leaf_) {
+    cx.resize(m.n_elems);
+    cy.resize(m.n_elems);
+    for (int64_t e = 0; e < m.n_elems; ++e) {
+      double sx = 0, sy = 0;
+      for (int a = 0; a < 9; ++a) {
+        int nd = m.conn[e * 9 + a];
+        sx += m.X[2 * nd];
+        sy += m.X[2 * nd + 1];
+      }
+      cx[e] = sx / 9;
+      cy[e] = sy / 9;
+    }
+    owner.assign(m.n_nodes, -1);
+    mark.assign(m.n_nodes, 0);
+  }
+
+  int run(std::vector<int>& el, int lo, int hi) {
+    int cnt = hi - lo;
+    if (cnt <= leaf) {
+      int id = (int)sns.size();
+      sns.emplace_back();
+      for (int q = lo; q < hi; ++q)
+        for (int a = 0; a < 9; ++a) {
+          int nd = m.conn[(int64_t)el[q] * 9 + a];
+          if (owner[nd] < 0) {
+            owner[nd] = id;
+            sns[id].nodes.push_back(nd);
+          }
+        }
+      return id;
+    }
+    double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
+    for (int q = lo; q < hi; ++q) {
+      x0 = std::min(x0, cx[el[q]]);
+      x1 = std::max(x1, cx[el[q]]);
+      y0 = std::min(y0, cy[el[q]]);
+      y1 = std::max(y1, cy[el[q]]);
+    }
+    const std::vector<double>& key = (x1 - x0 >= y1 - y0) ? cx : cy;
+    int mid = lo + cnt / 2;
+    std::nth_element(el.begin() + lo, el.begin() + mid, el.begin() + hi, [&](int a, int b) {
+      if (key[a] != key[b]) return key[a] < key[b];
+      return a < b;
+    });
+    ++stamp;
+    for (int q = lo; q < mid; ++q)
+      for (int a = 0; a < 9; ++a) mark[m.conn[(int64_t)el[q] * 9 + a]] = stamp;
+    int id = (int)sns.size();
+    sns.emplace_back();
+    for (int q = mid; q < hi; ++q)
+      for (int a = 0; a < 9; ++a) {
+        int nd = m.conn[(int64_t)el[q] * 9 + a];
+        if (mark[nd] == stamp && owner[nd] < 0) {
+          owner[nd] = id;
+          sns[id].nodes.push_back(nd);
+        }
+      }
+    int l = run(el, lo, mid);
+    int r = run(el, mid, hi);
+    sns[id].kids = {l, r};
+    sns[l].parent = id;
+    sns[r].parent = id;
+    return id;
+  }
+};
+
+int greedy_colour(const std::vector<int32_t>& items, int per, int64_t count, int64_t n_nodes,
+                  std::vector<int32_t>& off, std::vector<int32_t>& order) {
+  std::vector<uint64_t> used(n_nodes, 0);
+  std::vector<int> col(count);
+  int ncol = 0;
+  for (int64_t e = 0; e < count; ++e) {
+    uint64_t busy = 0;
+    for (int a = 0; a < per; ++a) busy |= used[items[e * per + a]];
+    int c = 0;
+    while (c < 64 && (busy >> c & 1)) ++c;
+    if (c >= 64) throw Error{VIV_ERR_ARG, "element colouring needs more than 64 colours"};
+    col[e] = c;
+    ncol = std::max(ncol, c + 1);
+    for (int a = 0; a < per; ++a) used[items[e * per + a]] |= (uint64_t(1) << c);
+  }
+  off.assign(ncol + 1, 0);
+  for (int64_t e = 0; e < count; ++e) off[col[e] + 1]++;
+  for (int c = 0; c < ncol; ++c) off[c + 1] += off[c];
+  order.assign(count, 0);
+  std::vector<int32_t> pos(off.begin(), off.end() - 1);
+  for (int64_t e = 0; e < count; ++e) order[pos[col[e]]++] = (int32_t)e;
+  return ncol;
+}
+
+}  // namespace
+
+// Build every host table of the mesh; see the file header.
+void build_mesh(Mesh& m, const vivMeshDesc* d) {
+  VIV_CHECK(d && d->X && d->conn && d->tags, VIV_ERR_ARG, "mesh description has NULL arrays");
+  VIV_CHECK(d->n_nodes > 0 && d->n_elems > 0, VIV_ERR_ARG, "empty mesh");
+  VIV_CHECK(d->n_nodes < (1LL << 30) && d->n_elems < (1LL << 28), VIV_ERR_ARG, "mesh too large");
+  VIV_CHECK(d->n_gamma_faces == 0 || d->gamma_faces, VIV_ERR_ARG, "gamma_faces is NULL");
+  const int64_t n = d->n_nodes, E = d->n_elems, F = d->n_gamma_faces;
+  m.n_nodes = n;
+  m.n_elems = E;
+  m.n_faces = F;
+  m.X.assign(d->X, d->X + 2 * n);
+  m.tags.assign(d->tags, d->tags + n);
+  m.conn.resize(E * 9);
+  for (int64_t i = 0; i < E * 9; ++i) {
+    VIV_CHECK(d->conn[i] >= 0 && d->conn[i] < n, VIV_ERR_ARG, "connectivity out of range");
+    m.conn[i] = (int32_t)d->conn[i];
+  }
+  std::vector<char> is_vertex(n, 0), cyl(n, 0);
+  for (int64_t e = 0; e < E; ++e)
+    for (int c = 0; c < 4; ++c) is_vertex[m.conn[e * 9 + VERT[c]]] = 1;
+  for (int64_t a = 0; a < n; ++a) cyl[a] = (m.tags[a] & VIV_TAG_CYL) != 0;
+  m.faces.resize(F * 3);
+  m.face_elem.resize(F);
+  for (int64_t f = 0; f < F; ++f) {
+    int64_t e = d->gamma_faces[2 * f], ed = d->gamma_faces[2 * f + 1];
+    VIV_CHECK(e >= 0 && e < E && ed >= 0 && ed < 4, VIV_ERR_ARG, "bad gamma face");
+    m.face_elem[f] = (int32_t)e;
+    for (int b = 0; b < 3; ++b) {
+      int nd = m.conn[e * 9 + EDGE[ed][b]];
+      VIV_CHECK(cyl[nd], VIV_ERR_ARG, "gamma face node is not tagged CYL");
+      m.faces[f * 3 + b] = nd;
+    }
+  }
+  const bool has_body = F > 0;
+
+  // ---- nested dissection -----------------------------------------------------
+  int leaf = d->leaf_elems > 0 ? d->leaf_elems : 4;
+  Dissector ds(m, leaf);
+  std::vector<int> el(E);
+  std::iota(el.begin(), el.end(), 0);
+  int root0 = ds.run(el, 0, (int)E);
+  // splice out empty supernodes (keep the root)
+  std::vector<SN>& sns = ds.sns;
+  int S0 = (int)sns.size();
+  std::vector<int> keep_parent(S0, -1);
+  std::vector<char> kept(S0, 0);
+  for (int s = 0; s < S0; ++s) kept[s] = !sns[s].nodes.empty() || s == root0;
+  for (int s = 0; s < S0; ++s) {
+    int p = sns[s].parent;
+    while (p >= 0 && !kept[p]) p = sns[p].parent;
+    keep_parent[s] = p;
+  }
+  if (has_body) sns[root0].nodes.push_back((int)n);   // delta pseudo-node, eliminated last
+  // postorder over kept supernodes
+  std::vector<std::vector<int>> kids(S0);
+  for (int s = 0; s < S0; ++s)
+    if (kept[s] && s != root0) kids[keep_parent[s]].push_back(s);
+  std::vector<int> post;
+  {
+    std::vector<std::pair<int, int>> st{{root0, 0}};
+    while (!st.empty()) {
+      auto& [s, i] = st.back();
+      if (i < (int)kids[s].size()) {
+        int c = kids[s][i++];
+        st.push_back({c, 0});
+      } else {
+        post.push_back(s);
+        st.pop_back();
+      }
+    }
+  }
+  const int NF = (int)post.size();
+  std::vector<int> pos_of(S0, -1);
+  for (int i = 0; i < NF; ++i) pos_of[post[i]] = i;
+  // front id of every node (n = delta)
+  std::vector<int> front_of(n + 1, -1);
+  for (int i = 0; i < NF; ++i)
+    for (int nd : sns[post[i]].nodes) front_of[nd] = i;
+  for (int64_t a = 0; a < n; ++a) VIV_CHECK(front_of[a] >= 0, VIV_ERR_ARG, "node outside every element");
+
+  // ---- unknown numbering -----------------------------------------------------
+  m.node_dof.assign(n * NSLOT, -1);
+  m.delta_dof.assign(2, -1);
+  m.f_first.resize(NF);
+  m.f_p.resize(NF);
+  m.f_parent.assign(NF, -1);
+  std::vector<int32_t> node_first(n + 1, -1), node_cnt(n + 1, 0);
+  int32_t next = 0;
+  for (int i = 0; i < NF; ++i) {
+    int s = post[i];
+    std::vector<int>& nodes = sns[s].nodes;
+    std::sort(nodes.begin(), nodes.end());
+    m.f_first[i] = next;
+    for (int nd : nodes) {
+      node_first[nd] = next;
+      if (nd == n) {
+        m.delta_dof[0] = next++;
+        m.delta_dof[1] = next++;
+      } else {
+        int32_t t = m.tags[nd];
+        int32_t* sl = &m.node_dof[(int64_t)nd * NSLOT];
+        if (!(t & VIV_TAG_U_FIX_X)) sl[S_UX] = next++;
+        if (!(t & VIV_TAG_U_FIX_Y)) sl[S_UY] = next++;
+        if (!cyl[nd] && !(t & VIV_TAG_X_FIX_X)) sl[S_XX] = next++;
+        if (!cyl[nd] && !(t & VIV_TAG_X_FIX_Y)) sl[S_XY] = next++;
+        if (is_vertex[nd] && !(t & VIV_TAG_P_FIX)) sl[S_P] = next++;
+        if (cyl[nd]) {
+          sl[S_LX] = next++;
+          sl[S_LY] = next++;
+        }
+      }
+      node_cnt[nd] = next - node_first[nd];
+    }
+    m.f_p[i] = next - m.f_first[i];
+    if (s != root0) m.f_parent[i] = pos_of[keep_parent[s]];
+  }
+  m.n_dofs = next;
+  m.dof_node.assign(next, -1);
+  m.dof_field.assign(next, -1);
+  for (int64_t a = 0; a < n; ++a)
+    for (int f = 0; f < NSLOT; ++f) {
+      int dof = m.node_dof[a * NSLOT + f];
+      if (dof >= 0) {
+        m.dof_node[dof] = a;
+        static const int code[NSLOT] = {VIV_F_UX, VIV_F_UY, VIV_F_XX, VIV_F_XY, VIV_F_P, VIV_F_LX, VIV_F_LY};
+        m.dof_field[dof] = code[f];
+      }
+    }
+  if (has_body) {
+    m.dof_node[m.delta_dof[0]] = n;
+    m.dof_field[m.delta_dof[0]] = VIV_F_DX;
+    m.dof_node[m.delta_dof[1]] = n;
+    m.dof_field[m.delta_dof[1]] = VIV_F_DY;
+  }
+
+  // ---- element slot maps -------------------------------------------------------
+  auto row_slot = [&](int64_t e, int cs) -> int32_t {   // cs: 0..35 u/x, 36..39 p
+    if (cs < 36) {
+      int a = cs / 4, f = cs % 4;
+      return m.node_dof[(int64_t)m.conn[e * 9 + a] * NSLOT + f];
+    }
+    return m.node_dof[(int64_t)m.conn[e * 9 + VERT[cs - 36]] * NSLOT + S_P];
+  };
+  auto col_slot = [&](int64_t e, int cs) -> int32_t {
+    if (cs < 36) {
+      int a = cs / 4, f = cs % 4;
+      int nd = m.conn[e * 9 + a];
+      if (f >= 2 && cyl[nd]) return m.delta_dof[f - 2];
+      return m.node_dof[(int64_t)nd * NSLOT + f];
+    }
+    return m.node_dof[(int64_t)m.conn[e * 9 + VERT[cs - 36]] * NSLOT + S_P];
+  };
+  // enumerate the structural pairs of an element in canonical order
+  auto for_pairs = [&](int64_t e, auto&& fn) {
+    for (int a = 0; a < 9; ++a)
+      for (int i = 0; i < 2; ++i)
+        for (int cs = 0; cs < 40; ++cs) fn(pairA(a, i, cs), row_slot(e, 4 * a + i), col_slot(e, cs));
+    for (int c = 0; c < 4; ++c)
+      for (int cs = 0; cs < 36; ++cs) fn(pairB(c, cs), row_slot(e, 36 + c), col_slot(e, cs));
+    for (int a = 0; a < 9; ++a)
+      for (int i = 0; i < 2; ++i)
+        for (int b = 0; b < 9; ++b)
+          for (int k = 0; k < 2; ++k)
+            fn(pairC(a, i, b, k), row_slot(e, 4 * a + 2 + i), col_slot(e, 4 * b + 2 + k));
+  };
+  auto for_face_pairs = [&](int64_t f, auto&& fn) {
+    const int32_t* fn_ = &m.faces[f * 3];
+    auto nd_dof = [&](int b, int s) { return m.node_dof[(int64_t)fn_[b] * NSLOT + s]; };
+    for (int b = 0; b < 3; ++b)
+      for (int i = 0; i < 2; ++i)
+        for (int bp = 0; bp < 3; ++bp)
+          for (int k = 0; k < 2; ++k) fn(fpairD(b, i, bp, k), nd_dof(b, S_UX + i), nd_dof(bp, S_LX + k));
+    for (int b = 0; b < 3; ++b)
+      for (int i = 0; i < 2; ++i)
+        for (int cs = 0; cs < 12; ++cs) {
+          int bp = (cs % 6) / 2, k = cs % 2;
+          int32_t c = cs < 6 ? nd_dof(bp, S_UX + k) : m.delta_dof[k];
+          fn(fpairE(b, i, cs), nd_dof(b, S_LX + i), c);
+        }
+    for (int i = 0; i < 2; ++i)
+      for (int bp = 0; bp < 3; ++bp)
+        for (int k = 0; k < 2; ++k) fn(fpairF(i, bp, k), m.delta_dof[i], nd_dof(bp, S_LX + k));
+  };
+
+  // ---- CSR pattern -------------------------------------------------------------
+  {
+    std::vector<std::vector<int32_t>> rows(m.n_dofs);
+    for (int64_t e = 0; e < E; ++e)
+      for_pairs(e, [&](int, int32_t r, int32_t c) {
+        if (r >= 0 && c >= 0) rows[r].push_back(c);
+      });
+    for (int64_t f = 0; f < F; ++f)
+      for_face_pairs(f, [&](int, int32_t r, int32_t c) {
+        if (r >= 0 && c >= 0) rows[r].push_back(c);
+      });
+    if (has_body)
+      for (int i = 0; i < 2; ++i) rows[m.delta_dof[i]].push_back(m.delta_dof[i]);
+    m.row_ptr.assign(m.n_dofs + 1, 0);
+    for (int64_t r = 0; r < m.n_dofs; ++r) {
+      auto& v = rows[r];
+      std::sort(v.begin(), v.end());
+      v.erase(std::unique(v.begin(), v.end()), v.end());
+      m.row_ptr[r + 1] = m.row_ptr[r] + (int64_t)v.size();
+    }
+    VIV_CHECK(m.row_ptr[m.n_dofs] < (1LL << 31), VIV_ERR_ARG, "too many nonzeros for int32 CSR slots");
+    m.col.resize(m.row_ptr[m.n_dofs]);
+    for (int64_t r = 0; r < m.n_dofs; ++r) std::copy(rows[r].begin(), rows[r].end(), m.col.begin() + m.row_ptr[r]);
+  }
+  auto slot = [&](int32_t r, int32_t c) -> int32_t {
+    if (r < 0 || c < 0) return -1;
+    auto b = m.col.begin() + m.row_ptr[r], en = m.col.begin() + m.row_ptr[r + 1];
+    auto it = std::lower_bound(b, en, c);
+    return (int32_t)(it - m.col.begin());
+  };
+  m.e2nz.assign(E * VOL_PAIRS, -1);
+  for (int64_t e = 0; e < E; ++e)
+    for_pairs(e, [&](int idx, int32_t r, int32_t c) { m.e2nz[e * VOL_PAIRS + idx] = slot(r, c); });
+  m.f2nz.assign(F * FACE_PAIRS, -1);
+  for (int64_t f = 0; f < F; ++f)
+    for_face_pairs(f, [&](int idx, int32_t r, int32_t c) { m.f2nz[f * FACE_PAIRS + idx] = slot(r, c); });
+  if (has_body)
+    for (int i = 0; i < 2; ++i) m.dd_nz[i] = slot(m.delta_dof[i], m.delta_dof[i]);
+
+  // ---- colours -------------------------------------------------------------------
+  greedy_colour(m.conn, 9, E, n, m.color_off, m.color_elems);
+  if (F > 0)
+    greedy_colour(m.faces, 3, F, n, m.fcolor_off, m.fcolor_faces);
+  else
+    m.fcolor_off.assign(1, 0);
+
+  // ---- symbolic factorisation on the node quotient graph ------------------------
+  std::vector<std::vector<int32_t>> adj(n + 1);
+  for (int64_t e = 0; e < E; ++e) {
+    bool touches = false;
+    for (int a = 0; a < 9; ++a) touches |= (bool)cyl[m.conn[e * 9 + a]];
+    for (int a = 0; a < 9; ++a) {
+      int na = m.conn[e * 9 + a];
+      for (int b = 0; b < 9; ++b) adj[na].push_back(m.conn[e * 9 + b]);
+      if (touches && has_body) {
+        adj[na].push_back((int)n);
+        adj[n].push_back(na);
+      }
+    }
+  }
+  for (auto& v : adj) {
+    std::sort(v.begin(), v.end());
+    v.erase(std::unique(v.begin(), v.end()), v.end());
+  }
+  m.n_fronts = NF;
+  std::vector<std::vector<int32_t>> cbn(NF);
+  std::vector<int> mk(n + 1, -1);
+  for (int i = 0; i < NF; ++i) {
+    int s = post[i];
+    for (int nd : sns[s].nodes) mk[nd] = i;
+    std::vector<int32_t> set;
+    auto consider = [&](int b) {
+      if (mk[b] == i) return;
+      if (front_of[b] <= i) return;
+      mk[b] = i;
+      set.push_back(b);
+    };
+    for (int nd : sns[s].nodes)
+      for (int b : adj[nd]) consider(b);
+    for (int c : kids[s])
+      for (int b : cbn[pos_of[c]]) consider(b);
+    std::sort(set.begin(), set.end(), [&](int a, int b) { return node_first[a] < node_first[b]; });
+    cbn[i] = std::move(set);
+  }
+  // children lists in front ids
+  m.f_child_off.assign(NF + 1, 0);
+  for (int i = 0; i < NF; ++i) m.f_child_off[i + 1] = m.f_child_off[i] + (int)kids[post[i]].size();
+  m.f_child.resize(m.f_child_off[NF]);
+  for (int i = 0; i < NF; ++i)
+    for (size_t j = 0; j < kids[post[i]].size(); ++j) m.f_child[m.f_child_off[i] + j] = pos_of[kids[post[i]][j]];
+  // index lists, offsets
+  m.f_m.resize(NF);
+  m.f_off.resize(NF + 1);
+  m.f_idx_off.resize(NF + 1);
+  m.f_vec_off.resize(NF + 1);
+  m.f_piv_off.resize(NF + 1);
+  m.f_off[0] = m.f_idx_off[0] = m.f_vec_off[0] = 0;
+  m.f_piv_off[0] = 0;
+  m.f_idx.clear();
+  m.factor_flops = 0;
+  m.max_front = 0;
+  for (int i = 0; i < NF; ++i) {
+    for (int32_t j = 0; j < m.f_p[i]; ++j) m.f_idx.push_back(m.f_first[i] + j);
+    for (int b : cbn[i])
+      for (int j = 0; j < node_cnt[b]; ++j) m.f_idx.push_back(node_first[b] + j);
+    int64_t mm = (int64_t)m.f_idx.size() - m.f_idx_off[i];
+    VIV_CHECK(mm < 46000, VIV_ERR_ARG, "front order exceeds the 32-bit local index range");
+    m.f_m[i] = (int32_t)mm;
+    m.max_front = std::max<int>(m.max_front, (int)mm);
+    m.f_idx_off[i + 1] = m.f_idx.size();
+    m.f_off[i + 1] = m.f_off[i] + mm * mm;
+    m.f_vec_off[i + 1] = m.f_vec_off[i] + mm;
+    m.f_piv_off[i + 1] = m.f_piv_off[i] + m.f_p[i];
+    double p = m.f_p[i];
+    for (int64_t j = 0; j < m.f_p[i]; ++j) {
+      double r = (double)(mm - j - 1);
+      m.factor_flops += r + 2.0 * r * r;
+    }
+    (void)p;
+  }
+  m.front_entries = m.f_off[NF];
+  m.vec_entries = m.f_vec_off[NF];
+  m.piv_entries = m.f_piv_off[NF];
+  // local index lookup
+  std::vector<int32_t> loc(m.n_dofs, -1);
+  std::vector<int32_t> front_of_dof(m.n_dofs);
+  for (int i = 0; i < NF; ++i)
+    for (int j = 0; j < m.f_p[i]; ++j) front_of_dof[m.f_first[i] + j] = i;
+  // original entries -> fronts (bucketed by the front of min(row, col))
+  {
+    const int64_t nnz = m.row_ptr[m.n_dofs];
+    std::vector<int64_t> cnt(NF + 1, 0);
+    for (int64_t r = 0; r < m.n_dofs; ++r)
+      for (int64_t q = m.row_ptr[r]; q < m.row_ptr[r + 1]; ++q) cnt[front_of_dof[std::min<int32_t>(r, m.col[q])] + 1]++;
+    for (int i = 0; i < NF; ++i) cnt[i + 1] += cnt[i];
+    m.f_nz_off.assign(cnt.begin(), cnt.end());
+    std::vector<int32_t> nz_row(nnz), nz_colv(nnz), nz_q(nnz);
+    std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+    for (int64_t r = 0; r < m.n_dofs; ++r)
+      for (int64_t q = m.row_ptr[r]; q < m.row_ptr[r + 1]; ++q) {
+        int f = front_of_dof[std::min<int32_t>(r, m.col[q])];
+        int64_t at = fill[f]++;
+        nz_row[at] = (int32_t)r;
+        nz_colv[at] = m.col[q];
+        nz_q[at] = (int32_t)q;
+      }
+    m.f_nz_csr.resize(nnz);
+    m.f_nz_pos.resize(nnz);
+    m.f_col_nz_off.assign(NF + 1, 0);
+    for (int i = 0; i < NF; ++i) {
+      int mm = m.f_m[i];
+      m.f_col_nz_off[i + 1] = m.f_col_nz_off[i] + (mm + ASM_COLS - 1) / ASM_COLS + 1;
+    }
+    m.f_col_nz.assign(m.f_col_nz_off[NF], 0);
+    std::vector<std::pair<int32_t, int32_t>> tmp;
+    for (int i = 0; i < NF; ++i) {
+      int mm = m.f_m[i];
+      for (int j = 0; j < mm; ++j) loc[m.f_idx[m.f_idx_off[i] + j]] = j;
+      tmp.clear();
+      for (int64_t at = m.f_nz_off[i]; at < m.f_nz_off[i + 1]; ++at) {
+        int32_t lr = loc[nz_row[at]], lc = loc[nz_colv[at]];
+        VIV_CHECK(lr >= 0 && lc >= 0, VIV_ERR_ARG, "symbolic: entry outside its front");
+        tmp.push_back({lr + lc * mm, nz_q[at]});
+      }
+      std::sort(tmp.begin(), tmp.end(), [&](auto& a, auto& b) {
+        int ca = a.first / mm, cb = b.first / mm;
+        if (ca != cb) return ca < cb;
+        return a.first < b.first;
+      });
+      int nch = (mm + ASM_COLS - 1) / ASM_COLS;
+      int64_t base = m.f_nz_off[i];
+      int ch = 0;
+      for (size_t t = 0; t < tmp.size(); ++t) {
+        m.f_nz_pos[base + t] = tmp[t].first;
+        m.f_nz_csr[base + t] = tmp[t].second;
+        int c = tmp[t].first / mm / ASM_COLS;
+        while (ch <= c) m.f_col_nz[m.f_col_nz_off[i] + ch++] = (int32_t)t;
+      }
+      while (ch <= nch) m.f_col_nz[m.f_col_nz_off[i] + ch++] = (int32_t)tmp.size();
+      // extend-add map of each child
+      for (int j = 0; j < mm; ++j) loc[m.f_idx[m.f_idx_off[i] + j]] = -1;
+    }
+    m.f_ea_off.assign(NF + 1, 0);
+    for (int i = 0; i < NF; ++i) m.f_ea_off[i + 1] = m.f_ea_off[i] + (m.f_m[i] - m.f_p[i]);
+    m.f_ea.assign(m.f_ea_off[NF], -1);
+    for (int i = 0; i < NF; ++i) {
+      int par = m.f_parent[i];
+      if (par < 0) {
+        VIV_CHECK(m.f_m[i] == m.f_p[i], VIV_ERR_ARG, "symbolic: root front has a contribution block");
+        continue;
+      }
+      int pm = m.f_m[par];
+      for (int j = 0; j < pm; ++j) loc[m.f_idx[m.f_idx_off[par] + j]] = j;
+      for (int j = m.f_p[i]; j < m.f_m[i]; ++j) {
+        int32_t l = loc[m.f_idx[m.f_idx_off[i] + j]];
+        VIV_CHECK(l >= 0, VIV_ERR_ARG, "symbolic: contribution block row missing in the parent");
+        m.f_ea[m.f_ea_off[i] + (j - m.f_p[i])] = l;
+      }
+      for (int j = 0; j < pm; ++j) loc[m.f_idx[m.f_idx_off[par] + j]] = -1;
+    }
+  }
+  // levels (height above the leaves)
+  m.f_level.assign(NF, 0);
+  for (int i = 0; i < NF; ++i)   // postorder: children first
+    for (int c = m.f_child_off[i]; c < m.f_child_off[i + 1]; ++c)
+      m.f_level[i] = std::max(m.f_level[i], m.f_level[m.f_child[c]] + 1);
+  m.n_levels = 0;
+  for (int i = 0; i < NF; ++i) m.n_levels = std::max(m.n_levels, m.f_level[i] + 1);
+  m.level_off.assign(m.n_levels + 1, 0);
+  for (int i = 0; i < NF; ++i) m.level_off[m.f_level[i] + 1]++;
+  for (int l = 0; l < m.n_levels; ++l) m.level_off[l + 1] += m.level_off[l];
+  m.level_fronts.assign(NF, 0);
+  {
+    std::vector<int32_t> fill(m.level_off.begin(), m.level_off.end() - 1);
+    for (int i = 0; i < NF; ++i) m.level_fronts[fill[m.f_level[i]]++] = i;
+  }
+  // launch schedule of the numeric factorisation
+  m.work.clear();
+  m.sched.clear();
+  auto push = [&](int a, int b, int c) {
+    m.work.push_back(a);
+    m.work.push_back(b);
+    m.work.push_back(c);
+  };
+  for (int l = 0; l < m.n_levels; ++l) {
+    Launch L{L_ASSEMBLE, l, 0, (int64_t)m.work.size() / 3, 0};
+    int maxp = 0;
+    for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
+      int f = m.level_fronts[q];
+      for (int c0 = 0; c0 < m.f_m[f]; c0 += ASM_COLS) push(f, c0, 0);
+      maxp = std::max(maxp, m.f_p[f]);
+    }
+    L.count = (int64_t)m.work.size() / 3 - L.item0;
+    if (L.count) m.sched.push_back(L);
+    for (int k = 0; k < maxp; k += PANEL_NB) {
+      Launch P{L_PANEL, l, k, (int64_t)m.work.size() / 3, 0};
+      for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
+        int f = m.level_fronts[q];
+        if (m.f_p[f] > k) push(f, 0, 0);
+      }
+      P.count = (int64_t)m.work.size() / 3 - P.item0;
+      if (P.count) m.sched.push_back(P);
+      Launch T{L_TRSM, l, k, (int64_t)m.work.size() / 3, 0};
+      for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
+        int f = m.level_fronts[q];
+        if (m.f_p[f] <= k) continue;
+        int nbe = std::min(PANEL_NB, m.f_p[f] - k);
+        for (int c0 = k + nbe; c0 < m.f_m[f]; c0 += TRSM_COLS) push(f, c0, 0);
+      }
+      T.count = (int64_t)m.work.size() / 3 - T.item0;
+      if (T.count) m.sched.push_back(T);
+      Launch G{L_GEMM, l, k, (int64_t)m.work.size() / 3, 0};
+      for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
+        int f = m.level_fronts[q];
+        if (m.f_p[f] <= k) continue;
+        int nbe = std::min(PANEL_NB, m.f_p[f] - k);
+        int r0 = k + nbe;
+        int tiles = (m.f_m[f] - r0 + GEMM_TILE - 1) / GEMM_TILE;
+        for (int ti = 0; ti < tiles; ++ti)
+          for (int tj = 0; tj < tiles; ++tj) push(f, ti, tj);
+      }
+      G.count = (int64_t)m.work.size() / 3 - G.item0;
+      if (G.count) m.sched.push_back(G);
+    }
+  }
+}
+
+void upload_mesh(Mesh& m, cudaStream_t s) {
+  DeviceArena& A = m.arena;
+  m.d_X = A.upload(m.X, s);
+  m.d_conn = A.upload(m.conn, s);
+  m.d_tags = A.upload(m.tags, s);
+  m.d_faces = A.upload(m.faces, s);
+  m.d_node_dof = A.upload(m.node_dof, s);
+  m.d_delta_dof = A.upload(m.delta_dof, s);
+  m.d_row_ptr = A.upload(m.row_ptr, s);
+  m.d_col = A.upload(m.col, s);
+  m.d_e2nz = A.upload(m.e2nz, s);
+  m.d_f2nz = A.upload(m.f2nz, s);
+  m.d_color_elems = A.upload(m.color_elems, s);
+  m.d_fcolor_faces = A.upload(m.fcolor_faces, s);
+  m.d_level_fronts = A.upload(m.level_fronts, s);
+  FrontTables& t = m.ft;
+  t.n_fronts = m.n_fronts;
+  t.off = A.upload(m.f_off, s);
+  t.m = A.upload(m.f_m, s);
+  t.p = A.upload(m.f_p, s);
+  t.first = A.upload(m.f_first, s);
+  t.idx_off = A.upload(m.f_idx_off, s);
+  t.idx = A.upload(m.f_idx, s);
+  t.nz_off = A.upload(m.f_nz_off, s);
+  t.nz_csr = A.upload(m.f_nz_csr, s);
+  t.nz_pos = A.upload(m.f_nz_pos, s);
+  t.child_off = A.upload(m.f_child_off, s);
+  t.child = A.upload(m.f_child, s);
+  t.ea_off = A.upload(m.f_ea_off, s);
+  t.ea = A.upload(m.f_ea, s);
+  t.parent = A.upload(m.f_parent, s);
+  t.vec_off = A.upload(m.f_vec_off, s);
+  t.piv_off = A.upload(m.f_piv_off, s);
+  t.col_nz = A.upload(m.f_col_nz, s);
+  t.col_nz_off = A.upload(m.f_col_nz_off, s);
+  t.work = A.upload(m.work, s);
+  VIV_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace viv

@@ -1,0 +1,155 @@
+// Vector kernels of the Newton driver: deterministic norms, BDF history,
+// the Newton update, the FP64 refinement residual r = b - J x (CSR SpMV).
+#include <cuda_runtime.h>
+
+#include "viv_internal.h"
+
+namespace viv {
+namespace {
+
+constexpr int NORM_BLOCKS = 296;   // 2 x 148 SMs
+constexpr int NORM_THREADS = 256;
+
+// sum of squares per block, in a fixed order for a fixed grid (deterministic)
+__global__ void __launch_bounds__(NORM_THREADS) sumsq_partial(const double* v, int64_t n, double* partial) {
+  __shared__ double red[NORM_THREADS];
+  double s = 0;
+  for (int64_t i = blockIdx.x * (int64_t)NORM_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * NORM_THREADS) {
+    double a = v[i];
+    s += a * a;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = NORM_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void __launch_bounds__(NORM_THREADS) sumsq_final(const double* partial, int n, double* out) {
+  __shared__ double red[NORM_THREADS];
+  double s = 0;
+  for (int i = threadIdx.x; i < n; i += NORM_THREADS) s += partial[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = NORM_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sqrt(red[0]);
+}
+
+__global__ void bdf_kernel(int64_t n2, const double* u_n, const double* u_nm1, const double* x_n,
+                           const double* x_nm1, double a_n, double a_nm1, double* hu, double* hx) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n2) return;
+  double su = a_n * u_n[i], sx = a_n * x_n[i];
+  if (a_nm1 != 0.0) {
+    su += a_nm1 * u_nm1[i];
+    sx += a_nm1 * x_nm1[i];
+  }
+  hu[i] = su;
+  hx[i] = sx;
+}
+
+// U += dU for every nodal field; Gamma nodes follow x = X + delta_new
+__global__ void update_kernel(int64_t n, const int32_t* node_dof, const int32_t* tags, const double* X,
+                              const int32_t* delta_dof, const double* delta, const double* dU, double* u,
+                              double* p, double* x, double* lam) {
+  int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (a >= n) return;
+  const int32_t* d = node_dof + a * NSLOT;
+  for (int i = 0; i < 2; ++i)
+    if (d[S_UX + i] >= 0) u[2 * a + i] += dU[d[S_UX + i]];
+  if (d[S_P] >= 0) p[a] += dU[d[S_P]];
+  if (tags[a] & VIV_TAG_CYL) {
+    for (int i = 0; i < 2; ++i) {
+      lam[2 * a + i] += dU[d[S_LX + i]];
+      x[2 * a + i] = X[2 * a + i] + (delta[i] + dU[delta_dof[i]]);
+    }
+  } else {
+    for (int i = 0; i < 2; ++i)
+      if (d[S_XX + i] >= 0) x[2 * a + i] += dU[d[S_XX + i]];
+  }
+}
+
+__global__ void delta_update_kernel(const int32_t* delta_dof, const double* dU, double* delta) {
+  if (threadIdx.x < 2 && delta_dof[0] >= 0) delta[threadIdx.x] += dU[delta_dof[threadIdx.x]];
+}
+
+// r = b - J x, one warp per row (rows hold ~20-90 entries)
+__global__ void spmv_residual_kernel(int64_t nrows, const int64_t* rp, const int32_t* col, const double* J,
+                                     const double* x, const double* b, double* r) {
+  int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (row >= nrows) return;
+  double s = 0;
+  for (int64_t q = rp[row] + lane; q < rp[row + 1]; q += 32) s += J[q] * x[col[q]];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) r[row] = b[row] - s;
+}
+
+__global__ void axpy_kernel(double* y, const double* x, double a, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] += a * x[i];
+}
+
+__global__ void scale_copy_kernel(double* y, const double* x, double a, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = a * x[i];
+}
+
+__global__ void f64_to_f32_kernel(float* y, const double* x, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (float)x[i];
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+void launch_norm2(const double* v, int64_t n, double* partial, double* out, cudaStream_t s) {
+  sumsq_partial<<<NORM_BLOCKS, NORM_THREADS, 0, s>>>(v, n, partial);
+  sumsq_final<<<1, NORM_THREADS, 0, s>>>(partial, NORM_BLOCKS, out);
+  VIV_CUDA(cudaGetLastError());
+}
+
+void launch_bdf_history(const Mesh& m, CaseState& st, double a_n, double a_nm1, bool, cudaStream_t s) {
+  int64_t n2 = 2 * m.n_nodes;
+  bdf_kernel<<<blocks_for(n2, 256), 256, 0, s>>>(n2, st.u_n, st.u_nm1, st.x_n, st.x_nm1, a_n, a_nm1, st.hu,
+                                                   st.hx);
+  VIV_CUDA(cudaGetLastError());
+}
+
+void launch_update(const Mesh& m, CaseState& st, const double* dU, cudaStream_t s) {
+  update_kernel<<<blocks_for(m.n_nodes, 256), 256, 0, s>>>(m.n_nodes, m.d_node_dof, m.d_tags, m.d_X,
+                                                            m.d_delta_dof, st.delta, dU, st.u, st.p, st.x,
+                                                            st.lam);
+  delta_update_kernel<<<1, 32, 0, s>>>(m.d_delta_dof, dU, st.delta);
+  VIV_CUDA(cudaGetLastError());
+}
+
+void launch_spmv_residual(const Mesh& m, const double* J, const double* x, const double* b, double* r,
+                          cudaStream_t s) {
+  int64_t threads = m.n_dofs * 32;
+  spmv_residual_kernel<<<blocks_for(threads, 256), 256, 0, s>>>(m.n_dofs, m.d_row_ptr, m.d_col, J, x, b, r);
+  VIV_CUDA(cudaGetLastError());
+}
+
+void launch_axpy(double* y, const double* x, double a, int64_t n, cudaStream_t s) {
+  axpy_kernel<<<blocks_for(n, 256), 256, 0, s>>>(y, x, a, n);
+  VIV_CUDA(cudaGetLastError());
+}
+
+void launch_scale_copy(double* y, const double* x, double a, int64_t n, cudaStream_t s) {
+  scale_copy_kernel<<<blocks_for(n, 256), 256, 0, s>>>(y, x, a, n);
+  VIV_CUDA(cudaGetLastError());
+}
+
+void launch_f64_to_f32(float* y, const double* x, int64_t n, cudaStream_t s) {
+  f64_to_f32_kernel<<<blocks_for(n, 256), 256, 0, s>>>(y, x, n);
+  VIV_CUDA(cudaGetLastError());
+}
+
+}  // namespace viv

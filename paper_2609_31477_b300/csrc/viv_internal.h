@@ -1,0 +1,228 @@
+// Internal structures shared by the host runtime and the CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/viv.h"
+
+namespace viv {
+
+// ----- error handling --------------------------------------------------------
+void set_error(const std::string& msg);
+struct Error {
+  vivStatus status;
+  std::string msg;
+};
+#define VIV_CUDA(call)                                                                  \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      throw ::viv::Error{VIV_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+#define VIV_CHECK(cond, code, msg)                 \
+  do {                                             \
+    if (!(cond)) throw ::viv::Error{code, (msg)};  \
+  } while (0)
+
+// ----- device memory ---------------------------------------------------------
+struct DeviceArena {
+  vivAllocator alloc{};
+  bool custom = false;
+  std::vector<void*> blocks;
+  size_t bytes = 0;
+  void* get(size_t n);
+  template <class T>
+  T* make(size_t count) { return static_cast<T*>(get(count * sizeof(T))); }
+  template <class T>
+  T* upload(const std::vector<T>& v, cudaStream_t s) {
+    T* d = make<T>(v.size() ? v.size() : 1);
+    if (!v.empty()) {
+      VIV_CUDA(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    }
+    return d;
+  }
+  void release();
+  ~DeviceArena() { release(); }
+};
+
+// per node field slots of node_dof
+enum { S_UX = 0, S_UY = 1, S_XX = 2, S_XY = 3, S_P = 4, S_LX = 5, S_LY = 6, NSLOT = 7 };
+
+// local pairs of the element matrix scattered through e2nz (structural nonzeros)
+constexpr int VOL_PAIRS = 1188;    // u rows x (u,x,p) + p rows x (u,x) + x rows x x
+constexpr int FACE_PAIRS = 120;    // u x lambda, lambda x (u, delta), delta x lambda
+
+// ----- blocked factorisation schedule ---------------------------------------
+enum LaunchKind { L_ASSEMBLE = 0, L_PANEL = 1, L_TRSM = 2, L_GEMM = 3 };
+struct Launch {
+  int kind;
+  int level;
+  int k;          // panel start (pivot index) for PANEL/TRSM/GEMM
+  int64_t item0;  // first work item
+  int64_t count;  // work items
+};
+
+constexpr int PANEL_NB = 32;    // pivot block
+constexpr int GEMM_TILE = 64;   // Schur update tile
+constexpr int TRSM_COLS = 64;   // columns per TRSM item
+constexpr int ASM_COLS = 32;    // parent columns per assembly item
+
+struct FrontTables {              // device copies
+  int32_t n_fronts = 0;
+  int64_t* off = nullptr;         // front storage offset (entries)
+  int32_t* m = nullptr;           // order
+  int32_t* p = nullptr;           // pivots
+  int32_t* first = nullptr;       // first own dof
+  int64_t* idx_off = nullptr;     // index list offset
+  int32_t* idx = nullptr;         // global dof of each front row/col
+  int64_t* nz_off = nullptr;      // original-entry list, sorted by local column
+  int32_t* nz_csr = nullptr;
+  int32_t* nz_pos = nullptr;      // local position row + col*m
+  int32_t* child_off = nullptr;   // children list
+  int32_t* child = nullptr;
+  int64_t* ea_off = nullptr;      // per front: positions of its CB in the parent
+  int32_t* ea = nullptr;
+  int32_t* parent = nullptr;
+  int64_t* vec_off = nullptr;     // solve workspace offset (entries)
+  int32_t* piv_off = nullptr;     // pivot list offset
+  int32_t* col_nz = nullptr;      // per front, per ASM_COLS chunk: first nz of the chunk (relative)
+  int64_t* col_nz_off = nullptr;
+  int32_t* work = nullptr;        // all work items (3 ints each)
+};
+
+struct Mesh {
+  // host copies
+  int64_t n_nodes = 0, n_elems = 0, n_faces = 0;
+  std::vector<double> X;
+  std::vector<int32_t> conn;       // E x 9
+  std::vector<int32_t> tags;
+  std::vector<int32_t> faces;      // F x 3 node ids along the edge
+  std::vector<int32_t> face_elem;
+  std::vector<int32_t> node_dof;   // n x 7
+  std::vector<int32_t> delta_dof;  // 2 (or -1)
+  int64_t n_dofs = 0;
+  std::vector<int64_t> row_ptr;
+  std::vector<int32_t> col;
+  std::vector<int32_t> e2nz;       // E x VOL_PAIRS
+  std::vector<int32_t> f2nz;       // F x FACE_PAIRS
+  int32_t dd_nz[2] = {-1, -1};     // CSR slots of (delta_i, delta_i)
+  std::vector<int32_t> color_off;  // element colours: elements sorted by colour
+  std::vector<int32_t> color_elems;
+  std::vector<int32_t> fcolor_off;
+  std::vector<int32_t> fcolor_faces;
+  std::vector<int64_t> dof_node;
+  std::vector<int32_t> dof_field;
+  // fronts (host)
+  int n_fronts = 0, n_levels = 0, max_front = 0;
+  std::vector<int64_t> f_off, f_idx_off, f_nz_off, f_ea_off, f_vec_off, f_col_nz_off;
+  std::vector<int32_t> f_m, f_p, f_first, f_idx, f_nz_csr, f_nz_pos, f_child_off, f_child, f_ea,
+      f_parent, f_piv_off, f_col_nz, f_level;
+  std::vector<int32_t> work;
+  std::vector<Launch> sched;       // numeric factorisation launches in order
+  std::vector<int32_t> level_off;  // fronts sorted by level
+  std::vector<int32_t> level_fronts;
+  int64_t front_entries = 0, vec_entries = 0, piv_entries = 0;
+  double factor_flops = 0;
+  // device copies
+  cudaStream_t stream = nullptr;
+  bool on_device = false;
+  DeviceArena arena;
+  double* d_X = nullptr;
+  int32_t* d_conn = nullptr;
+  int32_t* d_tags = nullptr;
+  int32_t* d_faces = nullptr;
+  int32_t* d_node_dof = nullptr;
+  int32_t* d_delta_dof = nullptr;
+  int64_t* d_row_ptr = nullptr;
+  int32_t* d_col = nullptr;
+  int32_t* d_e2nz = nullptr;
+  int32_t* d_f2nz = nullptr;
+  int32_t* d_color_elems = nullptr;
+  int32_t* d_fcolor_faces = nullptr;
+  int32_t* d_level_fronts = nullptr;
+  FrontTables ft;
+};
+
+// device state of one case
+struct CaseState {
+  double *u, *p, *x, *lam, *delta;      // current iterate
+  double *u_n, *x_n, *u_nm1, *x_nm1;    // history
+  double *hu, *hx;                      // BDF history part of the nodal rates
+  double* lame;                         // per element lambda_s (= mu_s)
+  double* R;                            // residual (n_dofs)
+  double* dU;                           // Newton correction
+  double* r;                            // refinement residual
+  double* d;                            // one refinement correction
+  double* mR;                           // right-hand side of the refined solve
+  double* y2;                           // solution of viv_solve_rhs
+  double* J64;                          // CSR values (FP64 path and refinement)
+  float* J32;                           // CSR values (mixed path)
+  void* fronts;                         // front pool (double or float)
+  void* vec;                            // solve workspace (double or float)
+  void* yv;                             // forward-solve vector (n_dofs)
+  int32_t* piv;                         // row pivots of all fronts
+  int32_t* stats;                       // [0] perturbed, [1] threshold misses
+  double* partial;                      // norm partial sums
+  double* scal;                         // host-visible scalars (device side)
+};
+
+}  // namespace viv
+
+struct vivMesh {
+  viv::Mesh m;
+};
+
+struct vivCase {
+  vivMesh* mesh = nullptr;
+  vivParams prm{};
+  cudaStream_t stream = nullptr;
+  viv::DeviceArena arena;
+  viv::CaseState s{};
+  double t = 0.0;
+  int nstep = 0;
+  bool have_prev2 = false;     // BDF2 available for the next step
+  bool step_open = false;      // begin_step called
+  double c0 = 0.0;             // rate coefficient of the current step
+  bool factored = false;
+  bool have_dU = false;
+  double* h_pinned = nullptr;  // pinned scalars
+};
+
+// kernels (defined in .cu files), all launched on the case stream
+namespace viv {
+void launch_element_areas(const Mesh& m, double* lame, double scale, cudaStream_t s);
+void launch_residual(const Mesh& m, const CaseState& st, const vivParams& prm, double c0, cudaStream_t s);
+template <class T>
+void launch_jacobian(const Mesh& m, const CaseState& st, const vivParams& prm, double c0, T* vals,
+                     cudaStream_t s);
+void launch_norm2(const double* v, int64_t n, double* partial, double* out, cudaStream_t s);
+void launch_bdf_history(const Mesh& m, CaseState& st, double a_n, double a_nm1, bool shift, cudaStream_t s);
+void launch_update(const Mesh& m, CaseState& st, const double* dU, cudaStream_t s);
+void launch_spmv_residual(const Mesh& m, const double* J, const double* x, const double* b, double* r,
+                          cudaStream_t s);
+void launch_axpy(double* y, const double* x, double a, int64_t n, cudaStream_t s);
+void launch_scale_copy(double* y, const double* x, double a, int64_t n, cudaStream_t s);
+void launch_f64_to_f32(float* y, const double* x, int64_t n, cudaStream_t s);
+template <class T>
+void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* fronts, int32_t* piv,
+                    int32_t* stats, double threshold, cudaStream_t s);
+template <class T>
+void solve_fronts(const Mesh& m, const T* fronts, const int32_t* piv, const double* b, double* x,
+                  T* vec, T* yv, cudaStream_t s);
+}  // namespace viv
+
+// ----- canonical order of the element matrix pairs scattered through e2nz ----
+// element column slots: 4*b + f (node b, f = u_x, u_y, x_x, x_y), 36 + c (pressure vertex c)
+namespace viv {
+__host__ __device__ inline int pairA(int a, int i, int cs) { return (2 * a + i) * 40 + cs; }     // u row x any
+__host__ __device__ inline int pairB(int c, int cs) { return 720 + c * 36 + cs; }               // p row x (u,x)
+__host__ __device__ inline int pairC(int a, int i, int b, int k) { return 864 + (2 * a + i) * 18 + 2 * b + k; }
+// face slots along the edge: b = 0..2
+__host__ __device__ inline int fpairD(int b, int i, int bp, int k) { return (2 * b + i) * 6 + 2 * bp + k; }   // u x lambda
+__host__ __device__ inline int fpairE(int b, int i, int cs12) { return 36 + (2 * b + i) * 12 + cs12; }     // lambda x (u | x->delta)
+__host__ __device__ inline int fpairF(int i, int bp, int k) { return 108 + i * 6 + 2 * bp + k; }             // delta x lambda
+}  // namespace viv

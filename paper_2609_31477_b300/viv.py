@@ -1,0 +1,325 @@
+"""Thin ctypes binding of libviv.so (the C ABI declared in include/viv.h).
+
+Argument marshalling only: every step of the solver runs in the library's
+CUDA kernels.  PyTorch supplies device memory (through the caching allocator)
+and the CUDA stream.  There is no fallback: if the library cannot be loaded,
+importing the binding raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libviv.so")
+
+VIV_FP64, VIV_MIXED = 0, 1
+VIV_RES, VIV_JAC = 1, 2
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_PIVOT", 5: "ERR_NEWTON",
+          6: "ERR_NONFINITE", 7: "ERR_TIMEOUT", 8: "ERR_ADMISSION", 9: "ERR_STATE"}
+FIELD = {0: "ux", 1: "uy", 2: "xx", 3: "xy", 4: "p", 5: "lx", 6: "ly", 7: "dx", 8: "dy"}
+
+
+class VivError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("n_elems", C.c_int64), ("n_gamma_faces", C.c_int64),
+                ("X", C.c_void_p), ("conn", C.c_void_p), ("tags", C.c_void_p),
+                ("gamma_faces", C.c_void_p), ("leaf_elems", C.c_int32)]
+
+
+class MeshInfo(C.Structure):
+    _fields_ = [("n_dofs", C.c_int64), ("nnz", C.c_int64), ("n_fronts", C.c_int64),
+                ("max_front", C.c_int64), ("n_levels", C.c_int64), ("factor_flops", C.c_double),
+                ("front_entries", C.c_size_t), ("device_bytes_fp64", C.c_size_t),
+                ("device_bytes_mixed", C.c_size_t), ("n_colors", C.c_int32)]
+
+
+class Params(C.Structure):
+    _fields_ = [("rho", C.c_double), ("mu", C.c_double), ("k", C.c_double), ("dt", C.c_double),
+                ("lame_scale", C.c_double), ("newton_tol", C.c_double), ("max_newton", C.c_int32),
+                ("precision", C.c_int32), ("refine_tol", C.c_double), ("refine_max", C.c_int32),
+                ("pivot_threshold", C.c_double)]
+
+
+class StepInfo(C.Structure):
+    _fields_ = [("newton_iters", C.c_int32), ("refine_sweeps", C.c_int32),
+                ("perturbed_pivots", C.c_int32), ("threshold_misses", C.c_int32),
+                ("res_norm0", C.c_double), ("res_norm", C.c_double), ("t", C.c_double),
+                ("delta", C.c_double * 2), ("force", C.c_double * 2)]
+
+    def as_dict(self):
+        return dict(newton_iters=self.newton_iters, refine_sweeps=self.refine_sweeps,
+                    perturbed_pivots=self.perturbed_pivots, threshold_misses=self.threshold_misses,
+                    res_norm0=self.res_norm0, res_norm=self.res_norm, t=self.t,
+                    delta=list(self.delta), force=list(self.force))
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class Allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", C.c_void_p)]
+
+
+# every symbol declared in include/viv.h, with its ctypes signature
+_P = C.c_void_p
+SIGNATURES = {
+    "viv_mesh_create": (C.c_int, [C.POINTER(MeshDesc), C.c_void_p, C.c_void_p, C.POINTER(_P)]),
+    "viv_mesh_analyze": (C.c_int, [C.POINTER(MeshDesc), C.POINTER(_P)]),
+    "viv_mesh_info": (C.c_int, [_P, C.POINTER(MeshInfo)]),
+    "viv_mesh_dof_labels": (C.c_int, [_P, _P, _P]),
+    "viv_mesh_pattern": (C.c_int, [_P, _P, _P]),
+    "viv_mesh_destroy": (C.c_int, [_P]),
+    "viv_case_create": (C.c_int, [_P, C.POINTER(Params), _P, _P, C.POINTER(_P)]),
+    "viv_case_destroy": (C.c_int, [_P]),
+    "viv_set_state": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P, C.c_double]),
+    "viv_set_history": (C.c_int, [_P, C.c_int, _P, _P]),
+    "viv_get_state": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P, C.POINTER(C.c_double)]),
+    "viv_begin_step": (C.c_int, [_P]),
+    "viv_assemble": (C.c_int, [_P, C.c_int, C.POINTER(C.c_double)]),
+    "viv_get_residual": (C.c_int, [_P, _P]),
+    "viv_get_jacobian": (C.c_int, [_P, _P]),
+    "viv_factor": (C.c_int, [_P]),
+    "viv_solve": (C.c_int, [_P, C.POINTER(C.c_int)]),
+    "viv_solve_rhs": (C.c_int, [_P, C.c_int, _P, _P, C.POINTER(C.c_int)]),
+    "viv_update": (C.c_int, [_P]),
+    "viv_step": (C.c_int, [_P, C.POINTER(StepInfo)]),
+    "viv_step_host": (C.c_int, [_P, _P, _P, C.POINTER(StepInfo)]),
+    "viv_state_size": (C.c_int64, [_P]),
+    "viv_last_error": (C.c_char_p, []),
+    "viv_version": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load libviv.so and attach signatures; raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libviv.so not built ({path}); run paper_2609_31477_b300.build.build()")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != 0:
+        raise VivError(status, _lib.viv_last_error().decode())
+
+
+def _ptr(a):
+    return C.c_void_p(a.ctypes.data) if a is not None else None
+
+
+def _dev_ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class _TorchAllocator:
+    """Routes library allocations to torch's CUDA caching allocator."""
+
+    def __init__(self, device, stream):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.stream = stream
+        self._alloc = ALLOC_FN(self.alloc)
+        self._free = FREE_FN(self.free)
+        self.struct = Allocator(self._alloc, self._free, None)
+
+    def alloc(self, n, ctx):
+        try:
+            return self.torch.cuda.caching_allocator_alloc(int(n), self.device, self.stream)
+        except Exception:
+            return None
+
+    def free(self, p, ctx):
+        self.torch.cuda.caching_allocator_delete(p)
+
+
+def _desc(mesh):
+    X = np.ascontiguousarray(mesh["X"], dtype=np.float64)
+    conn = np.ascontiguousarray(mesh["conn"], dtype=np.int64)
+    tags = np.ascontiguousarray(mesh["tags"], dtype=np.int32)
+    gf = np.ascontiguousarray(mesh["gamma_faces"], dtype=np.int64).reshape(-1, 2)
+    keep = (X, conn, tags, gf)
+    d = MeshDesc(len(X), len(conn), len(gf), _ptr(X).value, _ptr(conn).value, _ptr(tags).value,
+                 _ptr(gf).value if len(gf) else None, int(mesh.get("leaf_elems", 0)))
+    return d, keep
+
+
+class Mesh:
+    """Mesh analysed by the library: numbering, CSR pattern, e2nz, nested
+    dissection, symbolic factorisation.  device=False analyses on the host
+    only (no GPU needed)."""
+
+    def __init__(self, mesh, device=True, torch_alloc=True, stream=None):
+        lib = load()
+        self.mesh = mesh
+        d, keep = _desc(mesh)
+        h = C.c_void_p()
+        self._alloc = None
+        if device:
+            import torch
+            dev = torch.cuda.current_device()
+            st = stream if stream is not None else torch.cuda.current_stream()
+            self.stream = st
+            if torch_alloc:
+                self._alloc = _TorchAllocator(dev, st.cuda_stream)
+            _check(lib.viv_mesh_create(C.byref(d), C.byref(self._alloc.struct) if self._alloc else None,
+                                       C.c_void_p(st.cuda_stream), C.byref(h)))
+        else:
+            self.stream = None
+            _check(lib.viv_mesh_analyze(C.byref(d), C.byref(h)))
+        self.h = h
+        info = MeshInfo()
+        _check(lib.viv_mesh_info(h, C.byref(info)))
+        self.info = {f: getattr(info, f) for f, _ in MeshInfo._fields_}
+        self.n_dofs = info.n_dofs
+        self.n_nodes = len(mesh["X"])
+
+    def dof_labels(self):
+        node = np.empty(self.n_dofs, np.int64)
+        field = np.empty(self.n_dofs, np.int32)
+        _check(_lib.viv_mesh_dof_labels(self.h, _ptr(node), _ptr(field)))
+        return node, field
+
+    def pattern(self):
+        rp = np.empty(self.n_dofs + 1, np.int64)
+        _check(_lib.viv_mesh_pattern(self.h, _ptr(rp), None))
+        col = np.empty(rp[-1], np.int32)
+        _check(_lib.viv_mesh_pattern(self.h, _ptr(rp), _ptr(col)))
+        return rp, col
+
+    def state_size(self):
+        return int(_lib.viv_state_size(self.h))
+
+    def close(self):
+        if self.h:
+            _lib.viv_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Case:
+    """Device state of one cylinder case and its Newton/BDF driver."""
+
+    def __init__(self, mesh: Mesh, u0, rho, mu, k, dt, precision=VIV_FP64, lame_scale=1.0,
+                 newton_tol=1e-10, max_newton=25, refine_tol=0.0, refine_max=0, pivot_threshold=0.01):
+        lib = load()
+        self.mesh = mesh
+        self.params = Params(rho, mu, k, dt, lame_scale, newton_tol, max_newton, precision, refine_tol,
+                             refine_max, pivot_threshold)
+        u0 = np.ascontiguousarray(u0, dtype=np.float64)
+        h = C.c_void_p()
+        _check(lib.viv_case_create(mesh.h, C.byref(self.params), _ptr(u0),
+                                   C.c_void_p(mesh.stream.cuda_stream), C.byref(h)))
+        self.h = h
+        self.n = mesh.n_nodes
+
+    # state ---------------------------------------------------------------------
+    def set_state(self, u=None, p=None, x=None, lam=None, delta=None, t=0.0):
+        arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float64) for a in (u, p, x, lam, delta)]
+        _check(_lib.viv_set_state(self.h, 0, *[_ptr(a) for a in arrs], C.c_double(t)))
+
+    def set_history(self, u_prev, x_prev):
+        a = np.ascontiguousarray(u_prev, dtype=np.float64)
+        b = np.ascontiguousarray(x_prev, dtype=np.float64)
+        _check(_lib.viv_set_history(self.h, 0, _ptr(a), _ptr(b)))
+
+    def get_state(self):
+        n = self.n
+        u, p, x, lam, d = (np.empty((n, 2)), np.empty(n), np.empty((n, 2)), np.empty((n, 2)), np.empty(2))
+        t = C.c_double()
+        _check(_lib.viv_get_state(self.h, 0, _ptr(u), _ptr(p), _ptr(x), _ptr(lam), _ptr(d), C.byref(t)))
+        return dict(u=u, p=p, x=x, lam=lam, delta=d, t=t.value)
+
+    # steps of the method -------------------------------------------------------
+    def begin_step(self):
+        _check(_lib.viv_begin_step(self.h))
+
+    def assemble(self, what=VIV_RES | VIV_JAC):
+        nr = C.c_double()
+        _check(_lib.viv_assemble(self.h, what, C.byref(nr) if what & VIV_RES else None))
+        return nr.value
+
+    def residual(self):
+        r = np.empty(self.mesh.n_dofs)
+        _check(_lib.viv_get_residual(self.h, _ptr(r)))
+        return r
+
+    def jacobian_values(self):
+        v = np.empty(self.mesh.info["nnz"])
+        _check(_lib.viv_get_jacobian(self.h, _ptr(v)))
+        return v
+
+    def factor(self):
+        _check(_lib.viv_factor(self.h))
+
+    def solve(self):
+        sw = C.c_int()
+        _check(_lib.viv_solve(self.h, C.byref(sw)))
+        return sw.value
+
+    def solve_rhs(self, b):
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        y = np.empty_like(b)
+        sw = C.c_int()
+        _check(_lib.viv_solve_rhs(self.h, 0, _ptr(b), _ptr(y), C.byref(sw)))
+        return y, sw.value
+
+    def update(self):
+        _check(_lib.viv_update(self.h))
+
+    def step(self):
+        info = StepInfo()
+        _check(_lib.viv_step(self.h, C.byref(info)))
+        return info.as_dict()
+
+    def step_host(self, state_in, state_out):
+        info = StepInfo()
+        _check(_lib.viv_step_host(self.h, _ptr(state_in), _ptr(state_out), C.byref(info)))
+        return info.as_dict()
+
+    def close(self):
+        if self.h:
+            _lib.viv_case_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def stiffness(rho, U_inf, Ustar, L=1.0):
+    """Spring stiffness from the reduced velocity of a massless cylinder,
+    U* = pi U sqrt(pi rho L / k) (Section 1)."""
+    import math
+    return math.pi ** 3 * rho * L * U_inf ** 2 / Ustar ** 2
+
+
+def viv_case(mesh_obj, Re, Ustar, dt, u0, precision=VIV_FP64, U_inf=1.0, D=1.0, rho=1.0, **kw):
+    mu = rho * U_inf * D / Re
+    return Case(mesh_obj, u0, rho, mu, stiffness(rho, U_inf, Ustar), dt, precision=precision, **kw)

@@ -1,0 +1,150 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle:
+residual and Jacobian entry by entry, the refined multifrontal solve, and
+whole BDF/Newton steps on the cylinder meshes."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from paper_2609_31477_b300 import inputs as I
+from oracle.solver import viv_oracle_case
+
+from gpu_common import copy_state, perm_oracle_to_lib, push_state, rel_l2, seeded_state
+
+pytestmark = pytest.mark.gpu
+
+RE, USTAR, DT = 100.0, 8.0, 0.1
+
+
+@pytest.fixture(scope="module")
+def viv():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2609_31477_b300 import build, viv as V
+    build.build()
+    V.load()
+    return V
+
+
+def _pair(viv, m, precision, seed=3):
+    mesh = I.viv_cylinder_mesh(m)
+    u0 = I.viv_initial_velocity(mesh, 1.0, 1e-3, 1)
+    oc = viv_oracle_case(mesh, RE, USTAR, DT, u0)
+    M = viv.Mesh(mesh)
+    case = viv.viv_case(M, RE, USTAR, DT, u0, precision=precision)
+    return mesh, oc, M, case
+
+
+def _mid_step_state(viv, oc, case, seed):
+    """U^{n-1}, U^n and a Newton iterate, identical on both sides."""
+    seeded_state(oc, seed, 0.5)
+    prev = copy_state(oc)
+    seeded_state(oc, seed + 1, 0.7)
+    cur = copy_state(oc)
+    seeded_state(oc, seed + 2, 1.0)
+    it = copy_state(oc)
+    push_state(case, cur)
+    case.set_history(prev["u"], prev["x"])
+    case.begin_step()
+    push_state(case, it)
+    oc.u_n, oc.x_n = cur["u"], cur["x"]
+    oc.hist = (prev["u"], prev["x"])
+    for k, v in it.items():
+        setattr(oc, k, v.copy())
+    c0, hu, hx = oc.bdf_coefficients()
+    return c0, hu, hx
+
+
+@pytest.mark.parametrize("m", [4, 12])
+def test_residual_and_jacobian_entrywise(viv, m):
+    mesh, oc, M, case = _pair(viv, m, viv.VIV_FP64)
+    c0, hu, hx = _mid_step_state(viv, oc, case, 11)
+    perm = perm_oracle_to_lib(oc, M)
+    nr = case.assemble(viv.VIV_RES | viv.VIV_JAC)
+    R_o = oc.residual(c0, hu, hx, DT)
+    R_g = case.residual()[perm]
+    scale = np.abs(R_o).max()
+    assert np.abs(R_g - R_o).max() <= 1e-12 * scale
+    assert abs(nr - np.linalg.norm(R_o)) <= 1e-12 * np.linalg.norm(R_o)
+    J_o = oc.jacobian(c0, hu, hx, DT).tocsr()
+    rp, col = M.pattern()
+    vals = case.jacobian_values()
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(len(perm))
+    rows = np.repeat(np.arange(M.n_dofs), np.diff(rp))
+    J_g_in_o = np.asarray(J_o[inv[rows], inv[col]]).ravel()
+    jscale = np.abs(J_o.data).max()
+    err = np.abs(vals - J_g_in_o)
+    assert err.max() <= 1e-11 * jscale, (err.max(), jscale, rows[err.argmax()], col[err.argmax()])
+    # every oracle entry is inside the library's pattern (checked on the host too)
+    assert abs(np.abs(J_o).sum() - np.abs(J_g_in_o).sum()) <= 1e-9 * np.abs(J_o).sum()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("m", [4, 12])
+def test_refined_multifrontal_solve(viv, m, precision):
+    prec = viv.VIV_FP64 if precision == "fp64" else viv.VIV_MIXED
+    mesh, oc, M, case = _pair(viv, m, prec)
+    c0, hu, hx = _mid_step_state(viv, oc, case, 21)
+    perm = perm_oracle_to_lib(oc, M)
+    case.assemble(viv.VIV_RES | viv.VIV_JAC)
+    case.factor()
+    b = np.random.default_rng(5).standard_normal(M.n_dofs)
+    y, sweeps = case.solve_rhs(b)
+    J_o = oc.jacobian(c0, hu, hx, DT).tocsc()
+    y_o = spla.splu(J_o).solve(b[perm])
+    assert rel_l2(y[perm], y_o) <= 1e-10, (rel_l2(y[perm], y_o), sweeps)
+    if prec == viv.VIV_MIXED:
+        assert sweeps >= 2
+
+
+def _compare_fields(oc, st, tol_field=1e-9, tol_delta=1e-8):
+    verts = oc.is_vertex
+    errs = dict(u=rel_l2(st["u"], oc.u), p=rel_l2(st["p"][verts], oc.p[verts]), x=rel_l2(st["x"], oc.x),
+                lam=rel_l2(st["lam"][oc.cyl], oc.lam[oc.cyl]),
+                delta=np.abs(st["delta"] - oc.delta).max())
+    assert errs["u"] <= tol_field and errs["p"] <= tol_field and errs["x"] <= tol_field, errs
+    assert errs["lam"] <= tol_field and errs["delta"] <= tol_delta, errs
+    return errs
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_steps_match_oracle_small_mesh(viv, precision):
+    prec = viv.VIV_FP64 if precision == "fp64" else viv.VIV_MIXED
+    mesh, oc, M, case = _pair(viv, 4, prec)
+    for s in range(4):
+        norms = oc.step()
+        info = case.step()
+        assert info["res_norm"] <= 1e-10
+        _compare_fields(oc, case.get_state())
+        assert np.allclose(info["force"], oc.force(), atol=1e-8)
+
+
+@pytest.fixture(scope="module")
+def cylinder_reference():
+    """Oracle run of the 1,552-quad cylinder case (Re 100, U* 8, dt 0.1):
+    states after each of its 10 steps."""
+    mesh = I.viv_cylinder_mesh(12)
+    u0 = I.viv_initial_velocity(mesh, 1.0, 1e-3, 1)
+    oc = viv_oracle_case(mesh, RE, USTAR, DT, u0)
+    states = []
+    for s in range(10):
+        oc.step()
+        states.append(copy_state(oc))
+    return mesh, oc, states
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cylinder_ten_steps_match_oracle(viv, cylinder_reference, precision):
+    mesh, oc, states = cylinder_reference
+    prec = viv.VIV_FP64 if precision == "fp64" else viv.VIV_MIXED
+    u0 = I.viv_initial_velocity(mesh, 1.0, 1e-3, 1)
+    M = viv.Mesh(mesh)
+    case = viv.viv_case(M, RE, USTAR, DT, u0, precision=prec)
+    for s in range(10):
+        info = case.step()
+        assert info["res_norm"] <= 1e-10
+        st = case.get_state()
+        ref = states[s]
+        for k, v in ref.items():
+            setattr(oc, k, v)
+        _compare_fields(oc, st)
