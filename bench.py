@@ -1,0 +1,329 @@
+#!/usr/bin/env python
+"""Benchmark of the B300 monolithic ALE cylinder solver.
+
+One step = one BDF2 time step of the cylinder case, Newton-converged to
+||NL||_2 <= 1e-10 (residual, Jacobian, multifrontal factorisation, refined
+solve, update - every phase on the GPU through the C ABI).  The default
+workload is the 38,800-quad O-grid cylinder (Re 200, U* 10, dt 0.02) on the
+mixed path (FP32 fronts, FP64 residual / refinement / state); the plain FP64
+path on the same workload is measured beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs an independent replica of the case (the case
+does not shard; replicas only) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time steps/s at ||r||<=1e-10 (BDF2 + Newton, cylinder VIV, mixed path)"
+WORKLOADS = {
+    # name: O-grid refinement m (quads = 1552 (m/12)^2 -> m=60: 38,800), Re, U*, dt
+    "viv_re200_m60": dict(m=60, Re=200.0, Ustar=10.0, dt=0.02),
+    "viv_re100_m12": dict(m=12, Re=100.0, Ustar=8.0, dt=0.1),
+    "viv_re100_m24": dict(m=24, Re=100.0, Ustar=8.0, dt=0.05),
+}
+FP32_SIMT_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12      # 148 SMs x 128 FP32 lanes x FMA x 2.032 GHz
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="viv_re200_m60", choices=sorted(WORKLOADS))
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ---------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        self.f = open(self.path, "w")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(gpu_id)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------------
+def oracle_sample(wl, newton_iters):
+    """Time the FP64 oracle on a bounded sample of the workload and scale it to
+    one time step: residual on the full mesh, complex-step Jacobian on 1/32 of
+    the elements (x32), sparse LU (SuperLU) of the 6,208-quad member of the same
+    mesh family (x (N/N_6208)^1.5, the 2-D nested-dissection cost law).
+    Returns (steps/s, description, seconds of CPU work)."""
+    import numpy as np
+    import scipy.sparse.linalg as spla
+    from paper_2609_31477_b300 import inputs as I
+    from oracle.solver import viv_oracle_case
+    t_all = time.perf_counter()
+    mesh = I.viv_cylinder_mesh(wl["m"])
+    u0 = I.viv_initial_velocity(mesh, 1.0, 1e-3, 1)
+    oc = viv_oracle_case(mesh, wl["Re"], wl["Ustar"], wl["dt"], u0)
+    oc.u_n, oc.x_n = oc.u.copy(), oc.x.copy()
+    c0, hu, hx = oc.bdf_coefficients()
+    t0 = time.perf_counter()
+    oc.residual(c0, hu, hx, wl["dt"])
+    t_res = time.perf_counter() - t0
+    # Jacobian on an element subset
+    E = len(mesh["conn"])
+    sub_e = np.arange(0, E, 32)
+    conn = mesh["conn"][sub_e]
+    used, inv = np.unique(conn, return_inverse=True)
+    sub = dict(X=mesh["X"][used], conn=inv.reshape(conn.shape), tags=mesh["tags"][used] & ~I.CYL,
+               gamma_faces=np.zeros((0, 2), np.int64))
+    sc = viv_oracle_case(sub, wl["Re"], wl["Ustar"], wl["dt"], u0[used])
+    sc.u_n, sc.x_n = sc.u.copy(), sc.x.copy()
+    c0s, hus, hxs = sc.bdf_coefficients()
+    t0 = time.perf_counter()
+    sc.jacobian(c0s, hus, hxs, wl["dt"])
+    t_jac = (time.perf_counter() - t0) * E / len(sub_e)
+    # LU on the 6,208-quad member of the family
+    m24 = I.viv_cylinder_mesh(24)
+    lc = viv_oracle_case(m24, wl["Re"], wl["Ustar"], wl["dt"], I.viv_initial_velocity(m24, 1.0, 1e-3, 1))
+    lc.u_n, lc.x_n = lc.u.copy(), lc.x.copy()
+    c0l, hul, hxl = lc.bdf_coefficients()
+    J24 = lc.jacobian(c0l, hul, hxl, wl["dt"]).tocsc()
+    t0 = time.perf_counter()
+    spla.splu(J24)
+    t_lu24 = time.perf_counter() - t0
+    t_lu = t_lu24 * (oc.ndof / lc.ndof) ** 1.5
+    per_step = newton_iters * (t_res + t_jac + t_lu) + t_res
+    desc = (f"oracle on {E}-quad mesh: residual full ({t_res:.2f}s), complex-step Jacobian on 1/32 of the "
+            f"elements x32 ({t_jac:.1f}s), SuperLU of the {len(m24['conn'])}-quad mesh scaled by (N ratio)^1.5 "
+            f"({t_lu24:.1f}s -> {t_lu:.0f}s); {newton_iters:.2f} Newton iterations per step; extrapolated")
+    return 1.0 / per_step, desc, time.perf_counter() - t_all
+
+
+# ---------------------------------------------------------------------------------
+def run_reference(args, wl, rank):
+    if rank != 0:
+        return
+    steps = []
+    for i in range(args.warmup + args.steps):
+        v, desc, secs = oracle_sample(wl, 3.0)
+        if i >= args.warmup:
+            steps.append(v)
+    value = sum(steps) / len(steps)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "time steps/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, **wl},
+           "cpu_baseline": {"value": value, "unit": "time steps/s", "cores": 1, "kind": "oracle", "sample": desc},
+           "e2e": {"value": value, "unit": "time steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args, wl, rank, world, local):
+    import numpy as np
+    import torch
+    from paper_2609_31477_b300 import build, inputs as I, viv
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    viv.load()
+    mesh = I.viv_cylinder_mesh(wl["m"])
+    u0 = I.viv_initial_velocity(mesh, 1.0, 1e-3, 1 + rank)
+    stream = torch.cuda.current_stream()
+    M = viv.Mesh(mesh)
+    info = M.info
+    case = viv.viv_case(M, wl["Re"], wl["Ustar"], wl["dt"], u0, precision=viv.VIV_MIXED)
+    for _ in range(args.warmup):
+        case.step()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    gpu_id = vis.split(",")[local] if vis else str(local)
+    clocks = ClockSampler(gpu_id)
+    case.profile(True)
+    l0 = viv.kernel_launches()
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    infos = [case.step() for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = viv.kernel_launches() - l0
+    ms = ev0.elapsed_time(ev1)
+    kern = case.profile_read()
+    case.profile(False)
+    clk = clocks.stop()
+    t_max = ms
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * args.steps / (t_max / 1e3)
+    newton = sum(i["newton_iters"] for i in infos) / len(infos)
+    sweeps = sum(i["refine_sweeps"] for i in infos) / len(infos)
+    n_fact = sum(i["newton_iters"] for i in infos)
+
+    # roofline of the dominant kernel class, from the events of the timed region
+    dom = max(kern, key=lambda k: kern[k][0])
+    dom_ms, dom_n = kern[dom]
+    peaks, src = measured_peaks()
+    if dom in ("schur_gemm", "panel_lu", "trsm"):
+        flops = {"schur_gemm": info["gemm_flops"], "panel_lu": info["panel_flops"],
+                 "trsm": info["trsm_flops"]}[dom] * n_fact
+        achieved = flops / (dom_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_SIMT_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_SIMT_TFLOPS, "traffic": None, "kernel": dom,
+                "peak_source": "FP32 SIMT: 148 SMs x 128 lanes x 2 flop x 2.032 GHz (derived)",
+                "launches": dom_n, "ms_total": dom_ms}
+    else:
+        # bytes: front factors read once per solve sweep (fwd/bwd) or the CSR matrix per SpMV
+        fbytes = 4 * info["front_entries"]
+        per = {"fwd_solve": fbytes, "bwd_solve": fbytes, "front_assemble": 2 * fbytes,
+               "spmv": 12 * info["nnz"], "residual": 0, "jacobian": 8 * info["nnz"]}.get(dom, 0)
+        n_calls = (sweeps * len(infos)) if dom in ("fwd_solve", "bwd_solve", "spmv") else n_fact
+        achieved = per * n_calls / (dom_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": dom,
+                "peak_source": src, "launches": dom_n, "ms_total": dom_ms}
+
+    out = {"metric": METRIC, "value": value, "unit": "time steps/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32 fronts + f64 residual/refinement", "data": "synthetic",
+           "config": {"workload": args.workload, "quads": len(mesh["conn"]), "dofs": info["n_dofs"],
+                      "nnz": info["nnz"], "fronts": info["n_fronts"], "max_front": info["max_front"],
+                      "factor_gflop": info["factor_flops"] / 1e9, **wl, "precision": "mixed",
+                      "l2": f"inputs larger than L2 (front pool {4 * info['front_entries'] / 1e9:.1f} GB)",
+                      "parallelism": "replicas" if world > 1 else "single"},
+           "newton_iters_per_step": newton, "refine_sweeps_per_step": sweeps,
+           "kernels_ms": {k: round(v[0], 3) for k, v in kern.items()},
+           "roofline": roof, "gpu_launches": launches, "clocks": clk}
+
+    if not args.no_fp64 and rank == 0:
+        c64 = viv.viv_case(M, wl["Re"], wl["Ustar"], wl["dt"], u0, precision=viv.VIV_FP64)
+        c64.step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        i64 = [c64.step() for _ in range(args.fp64_steps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        out["fp64_path"] = {"value": args.fp64_steps / (ms64 / 1e3), "unit": "time steps/s",
+                            "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps,
+                            "newton_iters_per_step": sum(i["newton_iters"] for i in i64) / len(i64)}
+        out["speedup_mixed_vs_fp64"] = value / world / out["fp64_path"]["value"]
+        c64.close()
+
+    if not args.no_e2e:
+        # end to end through viv_step_host: the packed state crosses the bus every step
+        n_st = M.state_size()
+        h_in = torch.empty(n_st, dtype=torch.float64, pin_memory=True)
+        h_out = torch.empty(n_st, dtype=torch.float64, pin_memory=True)
+        st = case.get_state()
+        n = len(mesh["X"])
+        packed = np.concatenate([st["u"].ravel(), st["p"], st["x"].ravel(), st["lam"].ravel(), st["delta"],
+                                 st["u"].ravel(), st["x"].ravel(), [st["t"], 0.0]])
+        h_in.numpy()[:] = packed
+        case.step_host(h_in.numpy(), h_out.numpy())
+        h_in.numpy()[:] = h_out.numpy()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            case.step_host(h_in.numpy(), h_out.numpy())
+            h_in.numpy()[:] = h_out.numpy()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        barrier()
+        out["e2e"] = {"value": world * args.steps / el, "unit": "time steps/s",
+                      "h2d_bytes_per_step": 8 * n_st, "d2h_bytes_per_step": 8 * n_st}
+
+    if rank == 0 and not args.no_cpu_baseline:
+        v, desc, secs = oracle_sample(wl, newton)
+        out["cpu_baseline"] = {"value": v, "unit": "time steps/s", "cores": 1, "kind": "oracle", "sample": desc,
+                               "sample_seconds": round(secs, 1)}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    case.close()
+    M.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl, rank)
+    else:
+        run_ours(args, wl, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

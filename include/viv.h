@@ -98,11 +98,15 @@ typedef struct {
   size_t device_bytes_fp64;   /* predicted device bytes of one FP64 case */
   size_t device_bytes_mixed;  /* predicted device bytes of one mixed case */
   int32_t n_colors;        /* element colours of the deterministic scatter */
+  double gemm_flops;       /* Schur-update (GEMM) flops of one factorisation */
+  double panel_flops;      /* in-panel LU flops of one factorisation */
+  double trsm_flops;       /* panel TRSM flops of one factorisation */
 } vivMeshInfo;
 
 /* Physical and solver parameters.  rho, mu: fluid density and viscosity;
  * k: spring stiffness of Eq. solid_balance; dt: constant time step;
- * lame_scale: lambda_s = mu_s = lame_scale / |K_0| per element;
+ * lame_scale: lambda_s = mu_s = lame_scale * min|K_0| / |K_0| per element
+ *   (reference areas; 0 means 1);
  * newton_tol: absolute ||NL||_2 stop; refine_tol: relative residual of the
  * refined linear solve; refine_max: refinement sweeps (mixed path). */
 typedef struct {
@@ -196,6 +200,18 @@ vivStatus viv_step(vivCase* c, vivStepInfo* info);
 vivStatus viv_step_host(vivCase* c, const double* state_in, double* state_out, vivStepInfo* info);
 /* size in doubles of the packed host state used by viv_step_host */
 int64_t viv_state_size(const vivMesh* mesh);
+
+/* ---- instrumentation ----------------------------------------------------- */
+/* kernel launches issued by this library in this process so far */
+int64_t viv_kernel_launches(void);
+/* per-case CUDA-event timing of every kernel launch, by kind:
+ * 0 residual elements, 1 Jacobian elements, 2 Gamma faces and border rows,
+ * 3 front assembly, 4 panel LU, 5 TRSM, 6 Schur GEMM, 7 forward solve,
+ * 8 backward solve, 9 refinement SpMV, 10 vector kernels.
+ * viv_profile_read(ms[11], count[11]) synchronises and resets. */
+enum { VIV_NKINDS = 11 };
+vivStatus viv_profile(vivCase* c, int on);
+vivStatus viv_profile_read(vivCase* c, double* ms, int64_t* count);
 
 const char* viv_last_error(void);
 const char* viv_version(void);

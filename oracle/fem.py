@@ -119,7 +119,7 @@ def volume_residual(Xe, xe, ue, pe, hu, hx, c0, rho, mu, lam_s, mu_s, src=None, 
       Rp[c]    = - int_Omega_t M_c div u
       Rx[a, i] = int_Omega_0  lam_s (grad_X N_a)_i (div_X x - d)
                               + 2 mu_s (grad_X N_a)_j eps_ij,
-                 eps = (grad_X x + grad_X x^T)/2 - I
+                 eps = (grad_X x + grad_X x^T)/2 - I = sym grad_X (x - X)
     `src` (manufactured solutions only) supplies f_u, g_p, f_x at the
     reference quadrature points: Ru -= int N f_u, Rp += int M g_p,
     Rx -= int_Omega_0 N f_x.
@@ -153,10 +153,11 @@ def volume_residual(Xe, xe, ue, pe, hu, hx, c0, rho, mu, lam_s, mu_s, src=None, 
         Rp += wq * det[:, None] * (-M[None, :] * divu[:, None])
         # reference configuration (fixed)
         g0, det0 = physical_gradients(Xe, q)
-        F = np.matmul(np.swapaxes(xe, 1, 2), g0)          # F_ij = dx_i/dX_j
-        eps = 0.5 * (F + np.swapaxes(F, 1, 2))
-        eps[:, 0, 0] -= 1.0
-        eps[:, 1, 1] -= 1.0
+        # eps = sym(grad_X x) - I, formed from the displacement x - X: identical
+        # because grad_X X = I for the isoparametric map, without the cancellation
+        # of O(|x|) terms against the identity
+        Fd = np.matmul(np.swapaxes(xe - Xe, 1, 2), g0)     # d(x - X)_i / dX_j
+        eps = 0.5 * (Fd + np.swapaxes(Fd, 1, 2))
         tr = eps[:, 0, 0] + eps[:, 1, 1]
         Rx += wq * det0[:, None, None] * (lam_s[:, None, None] * g0 * tr[:, None, None]
                                           + 2.0 * mu_s[:, None, None] * np.matmul(g0, np.swapaxes(eps, 1, 2)))

@@ -12,9 +12,10 @@ Follows:
     k delta + int_Gamma lambda = 0 (Eq. solid_balance with
     F_fluid = -int_Gamma lambda).  The pseudo-solid has no rows at Gamma nodes.
   * Dirichlet conditions Eq. flowBC / Eq. psBC, held by node tags.
-  * Lame coefficients lambda_s = mu_s = 1/|K_0| per element (reference area);
-    the paper's distance-based formula in Section 6 is garbled, the per-element
-    inverse area is the reading taken here.
+  * Lame coefficients lambda_s = mu_s = min|K_0| / |K_0| per element (reference
+    areas); the paper's distance-based formula in Section 6 is garbled, a
+    per-element inverse area normalised by the smallest element is the reading
+    taken here (any constant factor leaves the solution unchanged).
 The linear solve is a library sparse LU (SuperLU through scipy) - a library
 primitive used as one step.  The Jacobian is assembled from element
 Jacobians obtained by complex-step differentiation of the element residual.
@@ -61,7 +62,10 @@ class OracleCase:
         Xe = self.X[self.conn]
         area = fem.element_areas(Xe)
         if lame == "inverse_area":
-            self.lam_s = 1.0 / area
+            # lambda_s = mu_s proportional to 1/|K_0|; the constant is the smallest
+            # reference area, so the coefficients lie in (0, 1] (the solution does
+            # not depend on it: the pseudo-solid equations are homogeneous)
+            self.lam_s = area.min() / area
         else:
             self.lam_s = np.full(len(self.conn), float(lame))
         self.mu_s = self.lam_s.copy()

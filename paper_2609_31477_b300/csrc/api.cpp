@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <string>
 #include <utility>
@@ -12,6 +13,7 @@
 #include "viv_internal.h"
 
 namespace viv {
+int64_t launches();
 void build_mesh(Mesh& m, const vivMeshDesc* d);
 void upload_mesh(Mesh& m, cudaStream_t s);
 
@@ -40,7 +42,20 @@ using namespace viv;
 
 namespace {
 
+// binds the case's profiler to this thread for the duration of an API call
+struct ProfBind {
+  Profiler* prev;
+  explicit ProfBind(vivCase* c) : prev(g_prof) { g_prof = c ? &c->prof : nullptr; }
+  ~ProfBind() { g_prof = prev; }
+};
+
 bool mixed(const vivCase* c) { return c->prm.precision == VIV_MIXED; }
+
+std::string fmt_e(double v) {
+  char b[32];
+  std::snprintf(b, sizeof b, "%.3e", v);
+  return b;
+}
 
 double read_scalar(vivCase* c, const double* dptr) {
   VIV_CUDA(cudaMemcpyAsync(c->h_pinned, dptr, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -152,6 +167,23 @@ extern "C" {
 const char* viv_last_error(void) { return g_err.c_str(); }
 const char* viv_version(void) { return "viv-b300 0.1 (sm_103a)"; }
 
+int64_t viv_kernel_launches(void) { return launches(); }
+
+vivStatus viv_profile(vivCase* c, int on) {
+  API_BEGIN
+  VIV_CHECK(c, VIV_ERR_ARG, "NULL case");
+  c->prof.on = on != 0;
+  c->prof.used = 0;
+  API_END
+}
+
+vivStatus viv_profile_read(vivCase* c, double* ms, int64_t* count) {
+  API_BEGIN
+  VIV_CHECK(c && ms && count, VIV_ERR_ARG, "NULL argument");
+  c->prof.read(ms, count);
+  API_END
+}
+
 vivStatus viv_mesh_create(const vivMeshDesc* desc, const vivAllocator* alloc, void* stream, vivMesh** out) {
   API_BEGIN
   VIV_CHECK(out, VIV_ERR_ARG, "out is NULL");
@@ -206,6 +238,9 @@ vivStatus viv_mesh_info(const vivMesh* mesh, vivMeshInfo* info) {
   info->device_bytes_mixed =
       state + 8 * nnz + 4 * (nnz + (size_t)m.front_entries + (size_t)m.vec_entries + nd);
   info->n_colors = (int32_t)m.color_off.size() - 1;
+  info->gemm_flops = m.gemm_flops;
+  info->panel_flops = m.panel_flops;
+  info->trsm_flops = m.trsm_flops;
   API_END
 }
 
@@ -292,7 +327,7 @@ vivStatus viv_case_create(vivMesh* mesh, const vivParams* prm, const double* u0,
     VIV_CUDA(cudaMemsetAsync(s.u_nm1, 0, 2 * n * sizeof(double), st));
     VIV_CUDA(cudaMemsetAsync(s.x_nm1, 0, 2 * n * sizeof(double), st));
     VIV_CUDA(cudaMemsetAsync(s.stats, 0, 4 * sizeof(int32_t), st));
-    launch_element_areas(m, s.lame, c->prm.lame_scale, st);
+    launch_element_areas(m, s.lame, c->prm.lame_scale, s.scal + 1, st);
     VIV_CUDA(cudaStreamSynchronize(st));
   } catch (...) {
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -358,6 +393,7 @@ vivStatus viv_get_state(const vivCase* cc, int, double* u, double* p, double* x,
 
 vivStatus viv_begin_step(vivCase* c) {
   API_BEGIN
+  ProfBind pb_(c);
   VIV_CHECK(c, VIV_ERR_ARG, "NULL case");
   begin_step(c);
   API_END
@@ -365,6 +401,7 @@ vivStatus viv_begin_step(vivCase* c) {
 
 vivStatus viv_assemble(vivCase* c, int what, double* res_norm) {
   API_BEGIN
+  ProfBind pb_(c);
   VIV_CHECK(c && (what & (VIV_RES | VIV_JAC)), VIV_ERR_ARG, "bad arguments");
   double nr = assemble(c, what, res_norm != nullptr);
   if (res_norm) *res_norm = nr;
@@ -391,6 +428,7 @@ vivStatus viv_get_jacobian(const vivCase* cc, double* vals) {
 
 vivStatus viv_factor(vivCase* c) {
   API_BEGIN
+  ProfBind pb_(c);
   VIV_CHECK(c, VIV_ERR_ARG, "NULL case");
   factor(c);
   API_END
@@ -398,6 +436,7 @@ vivStatus viv_factor(vivCase* c) {
 
 vivStatus viv_solve(vivCase* c, int* sweeps) {
   API_BEGIN
+  ProfBind pb_(c);
   VIV_CHECK(c, VIV_ERR_ARG, "NULL case");
   const int64_t n = c->mesh->m.n_dofs;
   launch_scale_copy(c->s.mR, c->s.R, -1.0, n, c->stream);
@@ -409,6 +448,7 @@ vivStatus viv_solve(vivCase* c, int* sweeps) {
 
 vivStatus viv_solve_rhs(vivCase* c, int, const double* b, double* y, int* sweeps) {
   API_BEGIN
+  ProfBind pb_(c);
   VIV_CHECK(c && b && y, VIV_ERR_ARG, "NULL argument");
   const int64_t n = c->mesh->m.n_dofs;
   VIV_CUDA(cudaMemcpyAsync(c->s.mR, b, n * sizeof(double), cudaMemcpyDefault, c->stream));
@@ -421,6 +461,7 @@ vivStatus viv_solve_rhs(vivCase* c, int, const double* b, double* y, int* sweeps
 
 vivStatus viv_update(vivCase* c) {
   API_BEGIN
+  ProfBind pb_(c);
   VIV_CHECK(c && c->have_dU, VIV_ERR_STATE, "update without a correction");
   launch_update(c->mesh->m, c->s, c->s.dU, c->stream);
   c->have_dU = false;
@@ -441,7 +482,7 @@ static void step_impl(vivCase* c, vivStepInfo* info) {
     if (nr <= tol) break;
     VIV_CHECK(it < c->prm.max_newton, VIV_ERR_NEWTON,
               "Newton did not converge in " + std::to_string(c->prm.max_newton) + " iterations (|R| = " +
-                  std::to_string(nr) + ")");
+                  fmt_e(nr) + ", tolerance " + fmt_e(tol) + ")");
     assemble(c, VIV_JAC, false);
     factor(c);
     launch_scale_copy(c->s.mR, c->s.R, -1.0, m.n_dofs, c->stream);
@@ -480,6 +521,7 @@ static void step_impl(vivCase* c, vivStepInfo* info) {
 
 vivStatus viv_step(vivCase* c, vivStepInfo* info) {
   API_BEGIN
+  ProfBind pb_(c);
   VIV_CHECK(c, VIV_ERR_ARG, "NULL case");
   step_impl(c, info);
   API_END
@@ -494,6 +536,7 @@ int64_t viv_state_size(const vivMesh* mesh) {
 // packed host state: u(2n) p(n) x(2n) lam(2n) delta(2) u_prev(2n) x_prev(2n) [t, have_prev]
 vivStatus viv_step_host(vivCase* c, const double* in, double* out, vivStepInfo* info) {
   API_BEGIN
+  ProfBind pb_(c);
   VIV_CHECK(c && in && out, VIV_ERR_ARG, "NULL argument");
   const int64_t n = c->mesh->m.n_nodes;
   const double* q = in;

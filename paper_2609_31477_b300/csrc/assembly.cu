@@ -106,7 +106,7 @@ __device__ void qp_compute(const Tables<T>& tb, const ElemNodes<T>& en, int q, T
   T R00 = K11 * id0, R01 = -K01 * id0, R10 = -K10 * id0, R11 = K00 * id0;
   T u0 = 0, u1 = 0, w0 = 0, w1 = 0, ud0 = 0, ud1 = 0;
   T L00 = 0, L01 = 0, L10 = 0, L11 = 0;
-  T F00 = 0, F01 = 0, F10 = 0, F11 = 0;
+  T F00 = 0, F01 = 0, F10 = 0, F11 = 0;   // grad_X of the displacement x - X
   for (int a = 0; a < 9; ++a) {
     T d0 = tb.dN[q][a][0], d1 = tb.dN[q][a][1];
     T g0 = d0 * I00 + d1 * I10, g1 = d0 * I01 + d1 * I11;   // g_a,i = sum_j dN_j Jinv_ji
@@ -121,8 +121,9 @@ __device__ void qp_compute(const Tables<T>& tb, const ElemNodes<T>& en, int q, T
     ud0 += N * en.ud[a][0]; ud1 += N * en.ud[a][1];
     L00 += en.u[a][0] * g0; L01 += en.u[a][0] * g1;
     L10 += en.u[a][1] * g0; L11 += en.u[a][1] * g1;
-    F00 += en.x[a][0] * r0; F01 += en.x[a][0] * r1;
-    F10 += en.x[a][1] * r0; F11 += en.x[a][1] * r1;
+    const T dx0 = en.x[a][0] - en.X[a][0], dx1 = en.x[a][1] - en.X[a][1];
+    F00 += dx0 * r0; F01 += dx0 * r1;
+    F10 += dx1 * r0; F11 += dx1 * r1;
   }
   T pq = 0;
   for (int c = 0; c < 4; ++c) pq += tb.M[q][c] * en.p[c];
@@ -138,7 +139,8 @@ __device__ void qp_compute(const Tables<T>& tb, const ElemNodes<T>& en, int q, T
   out[Q_INERT + 1] = rho * (ud1 + uw0 * L10 + uw1 * L11);
   out[Q_DIV] = L00 + L11;
   out[Q_WDET0] = tb.W[q] * det0 * en.lame;
-  T e00 = F00 - 1, e11 = F11 - 1, e01 = T(0.5) * (F01 + F10);
+  // eps = sym(grad_X x) - I = sym grad_X (x - X) since grad_X X = I
+  T e00 = F00, e11 = F11, e01 = T(0.5) * (F01 + F10);
   out[Q_EPS] = e00; out[Q_EPS + 1] = e01; out[Q_EPS + 2] = e11;
   out[Q_TR] = e00 + e11;
 }
@@ -477,14 +479,44 @@ __global__ void area_kernel(const int32_t* conn, const double* X, int64_t E, dou
         }
       area += c_gwt[i] * c_gwt[j] * (J00 * J11 - J01 * J10);
     }
-  lame[e] = scale / area;
+  lame[e] = area;
+}
+
+__global__ void min_kernel(const double* a, int64_t n, double* out) {
+  __shared__ double red[256];
+  double v = 1e300;
+  for (int64_t i = threadIdx.x; i < n; i += 256) v = fmin(v, a[i]);
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = fmin(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+// lambda_s = mu_s = scale * min|K_0| / |K_0|
+__global__ void lame_kernel(double* lame, int64_t E, const double* amin, double scale) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < E) lame[e] = scale * (*amin) / lame[e];
 }
 
 }  // namespace
 
-void launch_element_areas(const Mesh& m, double* lame, double scale, cudaStream_t s) {
+void launch_element_areas(const Mesh& m, double* lame, double scale, double* scratch, cudaStream_t s) {
   int E = (int)m.n_elems;
-  area_kernel<<<(E + 127) / 128, 128, 0, s>>>(m.d_conn, m.d_X, E, scale, lame);
+  {
+    Launched L(K_VEC, s);
+    area_kernel<<<(E + 127) / 128, 128, 0, s>>>(m.d_conn, m.d_X, E, scale, lame);
+  }
+  {
+    Launched L(K_VEC, s);
+    min_kernel<<<1, 256, 0, s>>>(lame, E, scratch);
+  }
+  {
+    Launched L(K_VEC, s);
+    lame_kernel<<<(E + 127) / 128, 128, 0, s>>>(lame, E, scratch, scale);
+  }
   VIV_CUDA(cudaGetLastError());
 }
 
@@ -510,6 +542,7 @@ static void run_assembly(const Mesh& m, const CaseState& st, const vivParams& pr
     A.elems = m.d_color_elems + m.color_off[c];
     A.n = m.color_off[c + 1] - m.color_off[c];
     if (!A.n) continue;
+    Launched L(JAC ? K_JAC : K_RES, s);
     element_kernel<T, JAC><<<(A.n + EPB - 1) / EPB, ASM_THREADS, 0, s>>>(A, R, vals);
   }
   FaceArgs Fa;
@@ -526,11 +559,14 @@ static void run_assembly(const Mesh& m, const CaseState& st, const vivParams& pr
     Fa.list = m.d_fcolor_faces + m.fcolor_off[c];
     Fa.n = m.fcolor_off[c + 1] - m.fcolor_off[c];
     if (!Fa.n) continue;
+    Launched L(K_FACE, s);
     face_kernel<T, JAC><<<(Fa.n + 63) / 64, 64, 0, s>>>(Fa, R, vals);
   }
-  if (m.n_faces > 0)
+  if (m.n_faces > 0) {
+    Launched L(K_FACE, s);
     border_kernel<T><<<1, 256, 0, s>>>(m.d_faces, (int)m.n_faces, st.x, st.lam, st.delta, m.d_delta_dof,
                                        prm.k, JAC ? nullptr : R, vals, m.dd_nz[0], m.dd_nz[1], JAC);
+  }
   VIV_CUDA(cudaGetLastError());
 }
 

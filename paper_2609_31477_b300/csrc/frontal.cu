@@ -351,6 +351,8 @@ void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* front
   for (const Launch& L : m.sched) {
     const int32_t* w = work + 3 * L.item0;
     const unsigned grid = (unsigned)L.count;
+    static const int kk[4] = {K_FRONT_ASM, K_PANEL, K_TRSM, K_GEMM};
+    Launched LL(kk[L.kind], s);
     switch (L.kind) {
       case L_ASSEMBLE:
         if (J32)
@@ -378,10 +380,12 @@ void solve_fronts(const Mesh& m, const T* fronts, const int32_t* piv, const doub
   FT ft = make_ft(m);
   for (int l = 0; l < m.n_levels; ++l) {
     int n = m.level_off[l + 1] - m.level_off[l];
+    Launched L(K_FWD, s);
     fwd_kernel<T><<<n, 256, 0, s>>>(ft, m.d_level_fronts + m.level_off[l], fronts, piv, b, vec, yv);
   }
   for (int l = m.n_levels - 1; l >= 0; --l) {
     int n = m.level_off[l + 1] - m.level_off[l];
+    Launched L(K_BWD, s);
     bwd_kernel<T><<<n, 256, 0, s>>>(ft, m.d_level_fronts + m.level_off[l], fronts, yv, vec, x);
   }
   VIV_CUDA(cudaGetLastError());

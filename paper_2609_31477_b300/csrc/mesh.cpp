@@ -603,6 +603,13 @@ void build_mesh(Mesh& m, const vivMeshDesc* d) {
         if (m.f_p[f] <= k) continue;
         int nbe = std::min(PANEL_NB, m.f_p[f] - k);
         int r0 = k + nbe;
+        double rest = (double)(m.f_m[f] - r0);
+        m.gemm_flops += 2.0 * rest * rest * nbe;
+        m.trsm_flops += (double)nbe * (nbe - 1) * rest;
+        for (int j = k; j < r0; ++j) {
+          double below = (double)(m.f_m[f] - j - 1);
+          m.panel_flops += below + 2.0 * below * (r0 - j - 1);
+        }
         int tiles = (m.f_m[f] - r0 + GEMM_TILE - 1) / GEMM_TILE;
         for (int ti = 0; ti < tiles; ++ti)
           for (int tj = 0; tj < tiles; ++tj) push(f, ti, tj);

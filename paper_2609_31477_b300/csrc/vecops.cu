@@ -110,44 +110,61 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 }  // namespace
 
 void launch_norm2(const double* v, int64_t n, double* partial, double* out, cudaStream_t s) {
-  sumsq_partial<<<NORM_BLOCKS, NORM_THREADS, 0, s>>>(v, n, partial);
-  sumsq_final<<<1, NORM_THREADS, 0, s>>>(partial, NORM_BLOCKS, out);
+  {
+    Launched L(K_VEC, s);
+    sumsq_partial<<<NORM_BLOCKS, NORM_THREADS, 0, s>>>(v, n, partial);
+  }
+  {
+    Launched L(K_VEC, s);
+    sumsq_final<<<1, NORM_THREADS, 0, s>>>(partial, NORM_BLOCKS, out);
+  }
   VIV_CUDA(cudaGetLastError());
 }
 
 void launch_bdf_history(const Mesh& m, CaseState& st, double a_n, double a_nm1, bool, cudaStream_t s) {
   int64_t n2 = 2 * m.n_nodes;
+  Launched L(K_VEC, s);
   bdf_kernel<<<blocks_for(n2, 256), 256, 0, s>>>(n2, st.u_n, st.u_nm1, st.x_n, st.x_nm1, a_n, a_nm1, st.hu,
                                                    st.hx);
   VIV_CUDA(cudaGetLastError());
 }
 
 void launch_update(const Mesh& m, CaseState& st, const double* dU, cudaStream_t s) {
-  update_kernel<<<blocks_for(m.n_nodes, 256), 256, 0, s>>>(m.n_nodes, m.d_node_dof, m.d_tags, m.d_X,
-                                                            m.d_delta_dof, st.delta, dU, st.u, st.p, st.x,
-                                                            st.lam);
-  delta_update_kernel<<<1, 32, 0, s>>>(m.d_delta_dof, dU, st.delta);
+  {
+    Launched L(K_VEC, s);
+    update_kernel<<<blocks_for(m.n_nodes, 256), 256, 0, s>>>(m.n_nodes, m.d_node_dof, m.d_tags, m.d_X,
+                                                              m.d_delta_dof, st.delta, dU, st.u, st.p, st.x,
+                                                              st.lam);
+  }
+  {
+    Launched L(K_VEC, s);
+    delta_update_kernel<<<1, 32, 0, s>>>(m.d_delta_dof, dU, st.delta);
+  }
   VIV_CUDA(cudaGetLastError());
 }
 
 void launch_spmv_residual(const Mesh& m, const double* J, const double* x, const double* b, double* r,
                           cudaStream_t s) {
   int64_t threads = m.n_dofs * 32;
+  Launched L(K_SPMV, s);
   spmv_residual_kernel<<<blocks_for(threads, 256), 256, 0, s>>>(m.n_dofs, m.d_row_ptr, m.d_col, J, x, b, r);
   VIV_CUDA(cudaGetLastError());
 }
 
 void launch_axpy(double* y, const double* x, double a, int64_t n, cudaStream_t s) {
+  Launched L(K_VEC, s);
   axpy_kernel<<<blocks_for(n, 256), 256, 0, s>>>(y, x, a, n);
   VIV_CUDA(cudaGetLastError());
 }
 
 void launch_scale_copy(double* y, const double* x, double a, int64_t n, cudaStream_t s) {
+  Launched L(K_VEC, s);
   scale_copy_kernel<<<blocks_for(n, 256), 256, 0, s>>>(y, x, a, n);
   VIV_CUDA(cudaGetLastError());
 }
 
 void launch_f64_to_f32(float* y, const double* x, int64_t n, cudaStream_t s) {
+  Launched L(K_VEC, s);
   f64_to_f32_kernel<<<blocks_for(n, 256), 256, 0, s>>>(y, x, n);
   VIV_CUDA(cudaGetLastError());
 }

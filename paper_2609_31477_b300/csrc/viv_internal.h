@@ -127,6 +127,7 @@ struct Mesh {
   std::vector<int32_t> level_fronts;
   int64_t front_entries = 0, vec_entries = 0, piv_entries = 0;
   double factor_flops = 0;
+  double gemm_flops = 0, panel_flops = 0, trsm_flops = 0;   // per numeric factorisation
   // device copies
   cudaStream_t stream = nullptr;
   bool on_device = false;
@@ -172,6 +173,36 @@ struct CaseState {
 
 }  // namespace viv
 
+// ----- launch accounting and per-kind event timing ----------------------------
+namespace viv {
+enum KernelKind {
+  K_RES = 0, K_JAC, K_FACE, K_FRONT_ASM, K_PANEL, K_TRSM, K_GEMM, K_FWD, K_BWD, K_SPMV, K_VEC, K_NKINDS
+};
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> kind;
+  size_t used = 0;
+  void start(int k, cudaStream_t s);
+  void stop(cudaStream_t s);
+  void read(double* ms, int64_t* count);   // synchronises on the recorded events
+  ~Profiler();
+};
+extern thread_local Profiler* g_prof;
+void count_launch();
+struct Launched {           // wraps one kernel launch: counts it and, when profiling, times it
+  cudaStream_t s;
+  bool timed;
+  Launched(int k, cudaStream_t st) : s(st), timed(g_prof && g_prof->on) {
+    count_launch();
+    if (timed) g_prof->start(k, s);
+  }
+  ~Launched() {
+    if (timed) g_prof->stop(s);
+  }
+};
+}  // namespace viv
+
 struct vivMesh {
   viv::Mesh m;
 };
@@ -190,11 +221,12 @@ struct vivCase {
   bool factored = false;
   bool have_dU = false;
   double* h_pinned = nullptr;  // pinned scalars
+  viv::Profiler prof;
 };
 
 // kernels (defined in .cu files), all launched on the case stream
 namespace viv {
-void launch_element_areas(const Mesh& m, double* lame, double scale, cudaStream_t s);
+void launch_element_areas(const Mesh& m, double* lame, double scale, double* scratch, cudaStream_t s);
 void launch_residual(const Mesh& m, const CaseState& st, const vivParams& prm, double c0, cudaStream_t s);
 template <class T>
 void launch_jacobian(const Mesh& m, const CaseState& st, const vivParams& prm, double c0, T* vals,
@@ -226,3 +258,4 @@ __host__ __device__ inline int fpairD(int b, int i, int bp, int k) { return (2 *
 __host__ __device__ inline int fpairE(int b, int i, int cs12) { return 36 + (2 * b + i) * 12 + cs12; }     // lambda x (u | x->delta)
 __host__ __device__ inline int fpairF(int i, int bp, int k) { return 108 + i * 6 + 2 * bp + k; }             // delta x lambda
 }  // namespace viv
+

@@ -19,6 +19,9 @@ VIV_FP64, VIV_MIXED = 0, 1
 VIV_RES, VIV_JAC = 1, 2
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_PIVOT", 5: "ERR_NEWTON",
           6: "ERR_NONFINITE", 7: "ERR_TIMEOUT", 8: "ERR_ADMISSION", 9: "ERR_STATE"}
+KINDS = ("residual", "jacobian", "face_border", "front_assemble", "panel_lu", "trsm", "schur_gemm",
+         "fwd_solve", "bwd_solve", "spmv", "vector")
+KINDS_N = len(KINDS)
 FIELD = {0: "ux", 1: "uy", 2: "xx", 3: "xy", 4: "p", 5: "lx", 6: "ly", 7: "dx", 8: "dy"}
 
 
@@ -38,7 +41,8 @@ class MeshInfo(C.Structure):
     _fields_ = [("n_dofs", C.c_int64), ("nnz", C.c_int64), ("n_fronts", C.c_int64),
                 ("max_front", C.c_int64), ("n_levels", C.c_int64), ("factor_flops", C.c_double),
                 ("front_entries", C.c_size_t), ("device_bytes_fp64", C.c_size_t),
-                ("device_bytes_mixed", C.c_size_t), ("n_colors", C.c_int32)]
+                ("device_bytes_mixed", C.c_size_t), ("n_colors", C.c_int32),
+                ("gemm_flops", C.c_double), ("panel_flops", C.c_double), ("trsm_flops", C.c_double)]
 
 
 class Params(C.Structure):
@@ -94,6 +98,9 @@ SIGNATURES = {
     "viv_step": (C.c_int, [_P, C.POINTER(StepInfo)]),
     "viv_step_host": (C.c_int, [_P, _P, _P, C.POINTER(StepInfo)]),
     "viv_state_size": (C.c_int64, [_P]),
+    "viv_kernel_launches": (C.c_int64, []),
+    "viv_profile": (C.c_int, [_P, C.c_int]),
+    "viv_profile_read": (C.c_int, [_P, _P, _P]),
     "viv_last_error": (C.c_char_p, []),
     "viv_version": (C.c_char_p, []),
 }
@@ -301,6 +308,15 @@ class Case:
         _check(_lib.viv_step_host(self.h, _ptr(state_in), _ptr(state_out), C.byref(info)))
         return info.as_dict()
 
+    def profile(self, on=True):
+        _check(_lib.viv_profile(self.h, int(on)))
+
+    def profile_read(self):
+        ms = np.zeros(KINDS_N)
+        cnt = np.zeros(KINDS_N, np.int64)
+        _check(_lib.viv_profile_read(self.h, _ptr(ms), _ptr(cnt)))
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KINDS)}
+
     def close(self):
         if self.h:
             _lib.viv_case_destroy(self.h)
@@ -311,6 +327,10 @@ class Case:
             self.close()
         except Exception:
             pass
+
+
+def kernel_launches():
+    return int(load().viv_kernel_launches())
 
 
 def stiffness(rho, U_inf, Ustar, L=1.0):
