@@ -189,6 +189,29 @@ vivStatus viv_factor(vivCase* c);
 vivStatus viv_solve(vivCase* c, int* sweeps);
 /* Solve J y = b for a host or device right-hand side b (n_dofs, FP64). */
 vivStatus viv_solve_rhs(vivCase* c, int device, const double* b, double* y, int* sweeps);
+/* Allocation-free solve (the paper has no counterpart; this serves callers).
+ * Some callers cannot allocate device memory while they run - a host
+ * framework whose memory pool is already committed and may not grow during a
+ * time step, or a latency-bound loop that cannot take the device-wide
+ * synchronisation of cudaMalloc/cudaFree.  This entry point performs one
+ * forward + backward multifrontal solve J x = b with the case's current
+ * factors (no refinement) and allocates nothing: its workspace is a fixed
+ * 8 MiB device array inside the library that every GPU loading the library
+ * holds until the process exits.  b and x are device pointers to n_dofs
+ * doubles (caller-owned); work is ordered on the case's stream.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) and caches it; make that first call before any
+ *    stream capture.
+ *  - A mesh whose workspace ((sum of front orders) + n_dofs, times 4 bytes on
+ *    the mixed path or 8 on the FP64 path) exceeds 8 MiB is rejected with
+ *    VIV_ERR_ARG.
+ *  - All calls share the array and it keeps the last call's contents; the
+ *    solve writes every workspace entry before reading it, so no clearing is
+ *    needed.  Calls whose GPU work overlaps (other streams or threads) race on
+ *    the array and must be ordered by the caller.
+ *  - Returns VIV_ERR_STATE if the case has not been factored. */
+vivStatus viv_lu_solve_noalloc(vivCase* c, const double* b, double* x);
+
 /* U += dU (the last correction); Gamma nodes follow x = X + delta. */
 vivStatus viv_update(vivCase* c);
 

@@ -14,6 +14,7 @@
 
 namespace viv {
 int64_t launches();
+void lu_solve_noalloc(vivCase* c, const double* b, double* x);
 void build_mesh(Mesh& m, const vivMeshDesc* d);
 void upload_mesh(Mesh& m, cudaStream_t s);
 
@@ -456,6 +457,14 @@ vivStatus viv_solve_rhs(vivCase* c, int, const double* b, double* y, int* sweeps
   VIV_CUDA(cudaMemcpyAsync(y, c->s.y2, n * sizeof(double), cudaMemcpyDefault, c->stream));
   VIV_CUDA(cudaStreamSynchronize(c->stream));
   if (sweeps) *sweeps = sw;
+  API_END
+}
+
+vivStatus viv_lu_solve_noalloc(vivCase* c, const double* b, double* x) {
+  API_BEGIN
+  VIV_CHECK(c && b && x, VIV_ERR_ARG, "NULL argument");
+  VIV_CHECK(c->factored, VIV_ERR_STATE, "viv_lu_solve_noalloc before viv_factor");
+  lu_solve_noalloc(c, b, x);
   API_END
 }
 

@@ -95,6 +95,7 @@ SIGNATURES = {
     "viv_solve": (C.c_int, [_P, C.POINTER(C.c_int)]),
     "viv_solve_rhs": (C.c_int, [_P, C.c_int, _P, _P, C.POINTER(C.c_int)]),
     "viv_update": (C.c_int, [_P]),
+    "viv_lu_solve_noalloc": (C.c_int, [_P, _P, _P]),
     "viv_step": (C.c_int, [_P, C.POINTER(StepInfo)]),
     "viv_step_host": (C.c_int, [_P, _P, _P, C.POINTER(StepInfo)]),
     "viv_state_size": (C.c_int64, [_P]),
@@ -297,6 +298,11 @@ class Case:
 
     def update(self):
         _check(_lib.viv_update(self.h))
+
+    def lu_solve_noalloc(self, b_dev, x_dev):
+        """One unrefined forward/backward solve into caller-owned device
+        tensors, using the library's fixed workspace (no allocation)."""
+        _check(_lib.viv_lu_solve_noalloc(self.h, _dev_ptr(b_dev), _dev_ptr(x_dev)))
 
     def step(self):
         info = StepInfo()
