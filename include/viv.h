@@ -146,6 +146,9 @@ vivStatus viv_mesh_info(const vivMesh* mesh, vivMeshInfo* info);
 vivStatus viv_mesh_dof_labels(const vivMesh* mesh, int64_t* node, int32_t* field);
 /* CSR pattern of the Jacobian: row_ptr (n_dofs+1), col (nnz), host buffers */
 vivStatus viv_mesh_pattern(const vivMesh* mesh, int64_t* row_ptr, int32_t* col);
+/* per front (supernode, in elimination order): order m, pivots p, tree level
+ * (0 = leaves) and parent (-1 for the root); host buffers of n_fronts */
+vivStatus viv_mesh_fronts(const vivMesh* mesh, int32_t* m, int32_t* p, int32_t* level, int32_t* parent);
 vivStatus viv_mesh_destroy(vivMesh* mesh);
 
 /* ---- case: state on the device ------------------------------------------ */

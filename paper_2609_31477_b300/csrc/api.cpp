@@ -263,6 +263,18 @@ vivStatus viv_mesh_pattern(const vivMesh* mesh, int64_t* row_ptr, int32_t* col) 
   API_END
 }
 
+vivStatus viv_mesh_fronts(const vivMesh* mesh, int32_t* m_, int32_t* p_, int32_t* level, int32_t* parent) {
+  API_BEGIN
+  VIV_CHECK(mesh, VIV_ERR_ARG, "NULL mesh");
+  const Mesh& m = mesh->m;
+  const size_t nb = (size_t)m.n_fronts * sizeof(int32_t);
+  if (m_) std::memcpy(m_, m.f_m.data(), nb);
+  if (p_) std::memcpy(p_, m.f_p.data(), nb);
+  if (level) std::memcpy(level, m.f_level.data(), nb);
+  if (parent) std::memcpy(parent, m.f_parent.data(), nb);
+  API_END
+}
+
 vivStatus viv_mesh_destroy(vivMesh* mesh) {
   API_BEGIN
   delete mesh;

@@ -8,16 +8,22 @@
 //   panel    : partial LU of PANEL_NB pivot columns with threshold partial
 //              pivoting restricted to the fully summed rows; a pivot below the
 //              threshold is counted, an empty fully summed column is replaced
-//              by a small static perturbation and counted
+//              by a small static perturbation and counted.  A front's whole
+//              m x PANEL_NB panel is held in the distributed shared memory of
+//              a cluster of PANEL_CLUSTER CTAs; pivot choice is a cluster-wide
+//              reduction read through DSMEM, and the row interchanges of the
+//              columns outside the panel are applied afterwards (laswp)
 //   trsm     : U12 = L11^{-1} A12 for the panel rows
 //   gemm     : A22 -= L21 U12 (the Schur-complement update)
 //
 // The forward and backward solves walk the same tree: each front gathers
 // its children's update vectors (extend-add on vectors), so no global atomics
 // are used and results do not depend on the launch order.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cfloat>
+#include <climits>
 
 #include "viv_internal.h"
 
@@ -196,6 +202,213 @@ __global__ void __launch_bounds__(PANEL_THREADS) panel_kernel(FT ft, const int32
   }
 }
 
+
+namespace cg = cooperative_groups;
+
+// Barrier and shared-memory addressing of a panel group: one CTA (CLN = 1) or
+// a thread-block cluster of CLN CTAs with distributed shared memory.
+template <int CLN>
+struct Group {
+  cg::cluster_group c;
+  __device__ Group() : c(cg::this_cluster()) {}
+  __device__ int rank() const { return (int)c.block_rank(); }
+  __device__ void sync() { c.sync(); }
+  template <class P>
+  __device__ P* map(P* ptr, int r) {
+    return c.map_shared_rank(ptr, r);
+  }
+};
+template <>
+struct Group<1> {
+  __device__ Group() {}
+  __device__ int rank() const { return 0; }
+  __device__ void sync() { __syncthreads(); }
+  template <class P>
+  __device__ P* map(P* ptr, int) {
+    return ptr;
+  }
+};
+
+// Panel LU of one front in shared memory: CTA q of the group holds rows
+// [k + q*chunk, k + (q+1)*chunk) of the panel columns [k, k + nbe).  Every CTA
+// derives the same pivot from the group-wide maxima; row interchanges are
+// applied inside the panel here and to the other columns by laswp_kernel.
+template <class T, int CLN, int NT>
+__global__ void __launch_bounds__(NT)
+    panel_smem_kernel(FT ft, const int32_t* work, int k, T* pool, int32_t* piv, int32_t* stats, T thresh) {
+  Group<CLN> grp;
+  const int q = grp.rank();
+  const int f = work[3 * (blockIdx.x / CLN)];
+  const int m = ft.m[f], p = ft.p[f];
+  const int nbe = min(PANEL_NB, p - k);
+  const int chunk = (m - k + CLN - 1) / CLN;
+  const int r0 = k + q * chunk;
+  const int nr = max(0, min(chunk, m - r0));
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* P = reinterpret_cast<T*>(smem_raw);          // P[c * chunk + i]: panel column c, local row i
+  __shared__ T s_cmax, s_best;
+  __shared__ int s_brow;
+  __shared__ T s_wm[NT / 32], s_wb[NT / 32];
+  __shared__ int s_wr[NT / 32];
+  __shared__ T s_prow[PANEL_NB], s_rowj[PANEL_NB], s_rowr[PANEL_NB];
+  __shared__ int s_r, s_pert, s_pivs[PANEL_NB];
+  __shared__ T s_pscale;
+  T* F = pool + ft.off[f];
+  for (int idx = threadIdx.x; idx < nr * nbe; idx += NT) {
+    const int i = idx % nr, c = idx / nr;
+    P[c * chunk + i] = F[(int64_t)(k + c) * m + r0 + i];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int jj = 0; jj < nbe; ++jj) {
+    const int j = k + jj;
+    // 1. local column maximum over rows >= j, best fully summed candidate
+    T cmax = 0, best = -1;
+    int brow = INT_MAX;
+    for (int i = threadIdx.x; i < nr; i += NT) {
+      const int g = r0 + i;
+      if (g < j) continue;
+      const T a = fabs(P[jj * chunk + i]);
+      cmax = a > cmax ? a : cmax;
+      if (g < p && (a > best || (a == best && g < brow))) {
+        best = a;
+        brow = g;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const T om = __shfl_xor_sync(0xffffffffu, cmax, o);
+      cmax = om > cmax ? om : cmax;
+      const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int orow = __shfl_xor_sync(0xffffffffu, brow, o);
+      if (ob > best || (ob == best && orow < brow)) {
+        best = ob;
+        brow = orow;
+      }
+    }
+    if (lane == 0) {
+      s_wm[wid] = cmax;
+      s_wb[wid] = best;
+      s_wr[wid] = brow;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      T cm = 0, bb = -1;
+      int br = INT_MAX;
+      for (int w = 0; w < NT / 32; ++w) {
+        cm = s_wm[w] > cm ? s_wm[w] : cm;
+        if (s_wb[w] > bb || (s_wb[w] == bb && s_wr[w] < br)) {
+          bb = s_wb[w];
+          br = s_wr[w];
+        }
+      }
+      s_cmax = cm;
+      s_best = bb;
+      s_brow = br;
+    }
+    grp.sync();
+    // 2. the same decision in every CTA: lanes of warp 0 gather the CTAs'
+    //    maxima (in parallel through DSMEM) and reduce them in a fixed order
+    const int qj = (j - k) / chunk, lj = j - k - qj * chunk;
+    if (wid == 0) {
+      T cm = 0, bb = -1, diag = 0;
+      int br = INT_MAX;
+      if (lane < CLN) {
+        cm = *grp.map(&s_cmax, lane);
+        bb = *grp.map(&s_best, lane);
+        br = *grp.map(&s_brow, lane);
+      } else if (lane == CLN) {
+        diag = fabs(grp.map(P, qj)[jj * chunk + lj]);
+      }
+      diag = __shfl_sync(0xffffffffu, diag, CLN);
+      for (int o = CLN / 2; o > 0; o >>= 1) {
+        const T om = __shfl_xor_sync(0xffffffffu, cm, o);
+        const T ob = __shfl_xor_sync(0xffffffffu, bb, o);
+        const int orr = __shfl_xor_sync(0xffffffffu, br, o);
+        if (lane < CLN) {
+          cm = om > cm ? om : cm;
+          if (ob > bb || (ob == bb && orr < br)) {
+            bb = ob;
+            br = orr;
+          }
+        }
+      }
+      if (lane == 0) {
+        int r, pert = 0;
+        if (diag > 0 && diag >= thresh * cm) {
+          r = j;
+        } else if (bb > 0) {
+          r = br;
+          if (q == 0 && bb < thresh * cm) atomicAdd(&stats[1], 1);
+        } else {
+          r = j;
+          pert = 1;
+          if (q == 0) atomicAdd(&stats[0], 1);
+        }
+        s_r = r;
+        s_pert = pert;
+        s_pivs[jj] = r;
+        s_pscale = cm;
+      }
+    }
+    __syncthreads();
+    const int r = s_r;
+    const int qr = (r - k) / chunk, lr = r - k - qr * chunk;
+    // 3. interchange rows j and r inside the panel (uniform branch: every CTA knows r)
+    if (r != j) {
+      if (threadIdx.x < nbe && (q == qj || q == qr)) {
+        s_rowj[threadIdx.x] = grp.map(P, qj)[threadIdx.x * chunk + lj];
+        s_rowr[threadIdx.x] = grp.map(P, qr)[threadIdx.x * chunk + lr];
+      }
+      grp.sync();
+      if (threadIdx.x < nbe) {
+        if (q == qj) P[threadIdx.x * chunk + lj] = s_rowr[threadIdx.x];
+        if (q == qr) P[threadIdx.x * chunk + lr] = s_rowj[threadIdx.x];
+      }
+    } else if (s_pert && q == qj && threadIdx.x == 0) {
+      const T scale = s_pscale > 0 ? s_pscale : T(1);
+      P[jj * chunk + lj] = sqrt(Eps<T>::v) * scale;
+    }
+    grp.sync();
+    // 4. pivot row from its owner, then scale and update the local rows below it
+    if (threadIdx.x < nbe) s_prow[threadIdx.x] = grp.map(P, qj)[threadIdx.x * chunk + lj];
+    __syncthreads();
+    const T inv = T(1) / s_prow[jj];
+    for (int i = threadIdx.x; i < nr; i += NT) {
+      if (r0 + i <= j) continue;
+      const T l = P[jj * chunk + i] * inv;
+      P[jj * chunk + i] = l;
+      for (int c = jj + 1; c < nbe; ++c) P[c * chunk + i] -= l * s_prow[c];
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < nr * nbe; idx += NT) {
+    const int i = idx % nr, c = idx / nr;
+    F[(int64_t)(k + c) * m + r0 + i] = P[c * chunk + i];
+  }
+  if (q == 0 && threadIdx.x < nbe) piv[ft.piv_off[f] + k + threadIdx.x] = s_pivs[threadIdx.x];
+  grp.sync();   // no CTA leaves while another may still read its shared memory
+}
+
+// row interchanges of a cluster panel applied to the columns outside it
+template <class T>
+__global__ void laswp_kernel(FT ft, const int32_t* work, int k, T* pool, const int32_t* piv) {
+  const int32_t* it = work + 3 * blockIdx.x;
+  const int f = it[0], c = it[1] + threadIdx.x;
+  const int m = ft.m[f], p = ft.p[f];
+  const int nbe = min(PANEL_NB, p - k);
+  if (c >= m || (c >= k && c < k + nbe)) return;
+  T* col = pool + ft.off[f] + (int64_t)c * m;
+  const int32_t* pv = piv + ft.piv_off[f];
+  for (int jj = 0; jj < nbe; ++jj) {
+    const int j = k + jj, r = pv[j];
+    if (r != j) {
+      const T a = col[j];
+      col[j] = col[r];
+      col[r] = a;
+    }
+  }
+}
+
 template <class T>
 __global__ void trsm_kernel(FT ft, const int32_t* work, int k, T* pool) {
   const int32_t* it = work + 3 * blockIdx.x;
@@ -276,12 +489,22 @@ __global__ void __launch_bounds__(256) gemm_kernel(FT ft, const int32_t* work, i
 }
 
 // ---- solves -----------------------------------------------------------------------
+// Each front keeps its m-vector in shared memory when it fits (else global
+// memory), gathers its children's update vectors, and applies its triangular
+// factors in 32-column blocks: one warp solves the 32 x 32 diagonal block,
+// then every thread updates the remaining rows with that block.
+constexpr int SOLVE_THREADS = 1024;
+constexpr int SOLVE_SMEM_MAX = 160 * 1024;
+
 template <class T>
-__global__ void fwd_kernel(FT ft, const int32_t* fronts, const T* pool, const int32_t* piv, const double* b,
-                           T* vec, T* yv) {
+__global__ void __launch_bounds__(SOLVE_THREADS) fwd_kernel(FT ft, const int32_t* fronts, const T* pool,
+                                                            const int32_t* piv, const double* b, T* vec, T* yv,
+                                                            bool in_smem) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int f = fronts[blockIdx.x];
   const int m = ft.m[f], p = ft.p[f], first = ft.first[f];
-  T* w = vec + ft.vec_off[f];
+  T* gw = vec + ft.vec_off[f];
+  T* w = in_smem ? reinterpret_cast<T*>(smem_raw) : gw;
   const T* F = pool + ft.off[f];
   for (int i = threadIdx.x; i < m; i += blockDim.x) w[i] = i < p ? (T)b[first + i] : T(0);
   __syncthreads();
@@ -293,48 +516,126 @@ __global__ void fwd_kernel(FT ft, const int32_t* fronts, const T* pool, const in
     for (int r = threadIdx.x; r < nc; r += blockDim.x) w[ea[r]] += wc[r];
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    const int32_t* pv = piv + ft.piv_off[f];
-    for (int j = 0; j < p; ++j) {
-      int r = pv[j];
-      if (r != j) {
-        T t = w[j];
-        w[j] = w[r];
-        w[r] = t;
+  // row interchanges, in order; pivot indices staged through shared memory
+  __shared__ int s_pv[1024];
+  const int32_t* pv = piv + ft.piv_off[f];
+  for (int j0 = 0; j0 < p; j0 += 1024) {
+    const int nj = min(1024, p - j0);
+    for (int t = threadIdx.x; t < nj; t += blockDim.x) s_pv[t] = pv[j0 + t];
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int t = 0; t < nj; ++t) {
+        const int j = j0 + t, r = s_pv[t];
+        if (r != j) {
+          const T tmp = w[j];
+          w[j] = w[r];
+          w[r] = tmp;
+        }
       }
-    }
-  }
-  __syncthreads();
-  for (int j = 0; j < p; ++j) {
-    const T xj = w[j];
-    const T* col = F + (int64_t)j * m;
-    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) w[i] -= col[i] * xj;
     __syncthreads();
   }
-  for (int i = threadIdx.x; i < p; i += blockDim.x) yv[first + i] = w[i];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __shared__ T Dg[32][33];
+  for (int jb = 0; jb < p; jb += 32) {
+    const int nb = min(32, p - jb);
+    for (int q = threadIdx.x; q < nb * 32; q += blockDim.x) {
+      const int i = q & 31, jj = q >> 5;
+      Dg[i][jj] = i < nb ? F[(int64_t)(jb + jj) * m + jb + i] : T(0);
+    }
+    __syncthreads();
+    if (wid == 0) {
+      T xv = lane < nb ? w[jb + lane] : T(0);
+      for (int jj = 0; jj < nb; ++jj) {
+        const T xj = __shfl_sync(0xffffffffu, xv, jj);
+        if (lane > jj && lane < nb) xv -= Dg[lane][jj] * xj;
+      }
+      if (lane < nb) w[jb + lane] = xv;
+    }
+    __syncthreads();
+    if (nb == 32) {
+      // 32 independent loads per row keep the memory pipeline full
+      for (int i = jb + 32 + threadIdx.x; i < m; i += blockDim.x) {
+        const T* col = F + (int64_t)jb * m + i;
+        T a[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) a[jj & 3] += col[(int64_t)jj * m] * w[jb + jj];
+        w[i] -= (a[0] + a[1]) + (a[2] + a[3]);
+      }
+    } else {
+      for (int i = jb + nb + threadIdx.x; i < m; i += blockDim.x) {
+        T acc = 0;
+        for (int jj = 0; jj < nb; ++jj) acc += F[(int64_t)(jb + jj) * m + i] * w[jb + jj];
+        w[i] -= acc;
+      }
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    if (i < p)
+      yv[first + i] = w[i];
+    else if (in_smem)
+      gw[i] = w[i];
+  }
 }
 
 template <class T>
-__global__ void bwd_kernel(FT ft, const int32_t* fronts, const T* pool, const T* yv, T* vec, double* x) {
+__global__ void __launch_bounds__(SOLVE_THREADS) bwd_kernel(FT ft, const int32_t* fronts, const T* pool,
+                                                            const T* yv, T* vec, double* x, bool in_smem) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int f = fronts[blockIdx.x];
   const int m = ft.m[f], p = ft.p[f], first = ft.first[f];
-  T* v = vec + ft.vec_off[f];
+  T* v = in_smem ? reinterpret_cast<T*>(smem_raw) : vec + ft.vec_off[f];
   const T* F = pool + ft.off[f];
   const int32_t* idx = ft.idx + ft.idx_off[f];
   for (int i = threadIdx.x; i < m; i += blockDim.x) v[i] = i < p ? yv[first + i] : (T)x[idx[i]];
   __syncthreads();
   for (int i = threadIdx.x; i < p; i += blockDim.x) {
-    T s = v[i];
-    for (int c = p; c < m; ++c) s -= F[(int64_t)c * m + i] * v[c];
-    v[i] = s;
+    // eight independent partial sums: eight loads in flight per thread
+    T a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const T* row = F + i;
+    int c = p;
+    for (; c + 8 <= m; c += 8) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a[u] += row[(int64_t)(c + u) * m] * v[c + u];
+    }
+    for (; c < m; ++c) a[0] += row[(int64_t)c * m] * v[c];
+    v[i] -= ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
   }
   __syncthreads();
-  for (int j = p - 1; j >= 0; --j) {
-    if (threadIdx.x == 0) v[j] /= F[(int64_t)j * m + j];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __shared__ T Dg[32][33];
+  for (int jb = ((p - 1) / 32) * 32; jb >= 0 && p > 0; jb -= 32) {
+    const int nb = min(32, p - jb);
+    for (int q = threadIdx.x; q < nb * 32; q += blockDim.x) {
+      const int i = q & 31, jj = q >> 5;
+      Dg[i][jj] = i < nb ? F[(int64_t)(jb + jj) * m + jb + i] : T(0);
+    }
     __syncthreads();
-    const T xj = v[j];
-    const T* col = F + (int64_t)j * m;
-    for (int i = threadIdx.x; i < j; i += blockDim.x) v[i] -= col[i] * xj;
+    if (wid == 0) {
+      T xv = lane < nb ? v[jb + lane] : T(0);
+      for (int jj = nb - 1; jj >= 0; --jj) {
+        if (lane == jj) xv /= Dg[jj][jj];
+        const T xj = __shfl_sync(0xffffffffu, xv, jj);
+        if (lane < jj) xv -= Dg[lane][jj] * xj;
+      }
+      if (lane < nb) v[jb + lane] = xv;
+    }
+    __syncthreads();
+    if (nb == 32) {
+      for (int i = threadIdx.x; i < jb; i += blockDim.x) {
+        const T* col = F + (int64_t)jb * m + i;
+        T a[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) a[jj & 3] += col[(int64_t)jj * m] * v[jb + jj];
+        v[i] -= (a[0] + a[1]) + (a[2] + a[3]);
+      }
+    } else {
+      for (int i = threadIdx.x; i < jb; i += blockDim.x) {
+        T acc = 0;
+        for (int jj = 0; jj < nb; ++jj) acc += F[(int64_t)(jb + jj) * m + i] * v[jb + jj];
+        v[i] -= acc;
+      }
+    }
     __syncthreads();
   }
   for (int i = threadIdx.x; i < p; i += blockDim.x) x[first + i] = (double)v[i];
@@ -346,12 +647,22 @@ template <class T>
 void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* fronts, int32_t* piv,
                     int32_t* stats, double threshold, cudaStream_t s) {
   FT ft = make_ft(m);
+  static bool attr_set = false;
+  if (!attr_set) {
+    VIV_CUDA(cudaFuncSetAttribute(panel_smem_kernel<T, 1, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  PANEL_SMEM_BYTES));
+    VIV_CUDA(cudaFuncSetAttribute(panel_smem_kernel<T, PANEL_CLUSTER, 256>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, PANEL_SMEM_BYTES));
+    VIV_CUDA(cudaFuncSetAttribute(fwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX));
+    VIV_CUDA(cudaFuncSetAttribute(bwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX));
+    attr_set = true;
+  }
   VIV_CUDA(cudaMemsetAsync(stats, 0, 2 * sizeof(int32_t), s));
   const int32_t* work = m.ft.work;
-  for (const Launch& L : m.sched) {
+  for (const Launch& L : m.sched[sizeof(T) == 8]) {
     const int32_t* w = work + 3 * L.item0;
     const unsigned grid = (unsigned)L.count;
-    static const int kk[4] = {K_FRONT_ASM, K_PANEL, K_TRSM, K_GEMM};
+    static const int kk[7] = {K_FRONT_ASM, K_PANEL, K_TRSM, K_GEMM, K_PANEL, K_TRSM, K_PANEL};
     Launched LL(kk[L.kind], s);
     switch (L.kind) {
       case L_ASSEMBLE:
@@ -369,6 +680,32 @@ void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* front
       case L_GEMM:
         gemm_kernel<T><<<grid, 256, 0, s>>>(ft, w, L.k, fronts);
         break;
+      case L_PANEL_1: {
+        const size_t smem = (size_t)L.aux * PANEL_NB * sizeof(T);
+        panel_smem_kernel<T, 1, 512><<<grid, 512, smem, s>>>(ft, w, L.k, fronts, piv, stats, (T)threshold);
+        break;
+      }
+      case L_PANEL_CL: {
+        const size_t smem = (size_t)L.aux * PANEL_NB * sizeof(T);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid * PANEL_CLUSTER);
+        cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = PANEL_CLUSTER;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        VIV_CUDA(cudaLaunchKernelEx(&cfg, panel_smem_kernel<T, PANEL_CLUSTER, 256>, ft, w, L.k, fronts, piv, stats,
+                                    (T)threshold));
+        break;
+      }
+      case L_LASWP:
+        laswp_kernel<T><<<grid, LASWP_COLS, 0, s>>>(ft, w, L.k, fronts, piv);
+        break;
     }
   }
   VIV_CUDA(cudaGetLastError());
@@ -378,15 +715,27 @@ template <class T>
 void solve_fronts(const Mesh& m, const T* fronts, const int32_t* piv, const double* b, double* x, T* vec,
                   T* yv, cudaStream_t s) {
   FT ft = make_ft(m);
+  static bool attr_set = false;
+  if (!attr_set) {
+    VIV_CUDA(cudaFuncSetAttribute(fwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX));
+    VIV_CUDA(cudaFuncSetAttribute(bwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX));
+    attr_set = true;
+  }
   for (int l = 0; l < m.n_levels; ++l) {
-    int n = m.level_off[l + 1] - m.level_off[l];
+    const int n = m.level_off[l + 1] - m.level_off[l];
+    const size_t need = (size_t)m.level_maxm[l] * sizeof(T);
+    const bool sm = need <= (size_t)SOLVE_SMEM_MAX;
     Launched L(K_FWD, s);
-    fwd_kernel<T><<<n, 256, 0, s>>>(ft, m.d_level_fronts + m.level_off[l], fronts, piv, b, vec, yv);
+    fwd_kernel<T><<<n, m.level_threads[l], sm ? need : 0, s>>>(ft, m.d_level_fronts + m.level_off[l], fronts, piv, b,
+                                                          vec, yv, sm);
   }
   for (int l = m.n_levels - 1; l >= 0; --l) {
-    int n = m.level_off[l + 1] - m.level_off[l];
+    const int n = m.level_off[l + 1] - m.level_off[l];
+    const size_t need = (size_t)m.level_maxm[l] * sizeof(T);
+    const bool sm = need <= (size_t)SOLVE_SMEM_MAX;
     Launched L(K_BWD, s);
-    bwd_kernel<T><<<n, 256, 0, s>>>(ft, m.d_level_fronts + m.level_off[l], fronts, yv, vec, x);
+    bwd_kernel<T><<<n, m.level_threads[l], sm ? need : 0, s>>>(ft, m.d_level_fronts + m.level_off[l], fronts, yv,
+                                                          vec, x, sm);
   }
   VIV_CUDA(cudaGetLastError());
 }

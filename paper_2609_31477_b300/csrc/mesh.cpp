@@ -558,64 +558,112 @@ void build_mesh(Mesh& m, const vivMeshDesc* d) {
   for (int i = 0; i < NF; ++i) m.level_off[m.f_level[i] + 1]++;
   for (int l = 0; l < m.n_levels; ++l) m.level_off[l + 1] += m.level_off[l];
   m.level_fronts.assign(NF, 0);
+  m.level_maxm.assign(m.n_levels, 0);
   {
     std::vector<int32_t> fill(m.level_off.begin(), m.level_off.end() - 1);
-    for (int i = 0; i < NF; ++i) m.level_fronts[fill[m.f_level[i]]++] = i;
+    for (int i = 0; i < NF; ++i) {
+      m.level_fronts[fill[m.f_level[i]]++] = i;
+      m.level_maxm[m.f_level[i]] = std::max(m.level_maxm[m.f_level[i]], m.f_m[i]);
+    }
   }
-  // launch schedule of the numeric factorisation
+  // solve threads per front, by level (small fronts get small blocks)
+  m.level_threads.assign(m.n_levels, 64);
+  for (int l = 0; l < m.n_levels; ++l) {
+    int t = ((m.level_maxm[l] / 2 + 31) / 32) * 32;
+    m.level_threads[l] = std::min(1024, std::max(64, t));
+  }
+  // launch schedules of the numeric factorisation, one per front element size
   m.work.clear();
-  m.sched.clear();
+  m.gemm_flops = m.trsm_flops = m.panel_flops = 0;
   auto push = [&](int a, int b, int c) {
     m.work.push_back(a);
     m.work.push_back(b);
     m.work.push_back(c);
   };
-  for (int l = 0; l < m.n_levels; ++l) {
-    Launch L{L_ASSEMBLE, l, 0, (int64_t)m.work.size() / 3, 0};
-    int maxp = 0;
-    for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
-      int f = m.level_fronts[q];
-      for (int c0 = 0; c0 < m.f_m[f]; c0 += ASM_COLS) push(f, c0, 0);
-      maxp = std::max(maxp, m.f_p[f]);
-    }
-    L.count = (int64_t)m.work.size() / 3 - L.item0;
-    if (L.count) m.sched.push_back(L);
-    for (int k = 0; k < maxp; k += PANEL_NB) {
-      Launch P{L_PANEL, l, k, (int64_t)m.work.size() / 3, 0};
+  for (int prec = 0; prec < 2; ++prec) {
+    const int esz = prec ? 8 : 4;
+    const int rows_cta = PANEL_SMEM_BYTES / (PANEL_NB * esz);   // panel rows one CTA holds
+    std::vector<Launch>& sched = m.sched[prec];
+    sched.clear();
+    for (int l = 0; l < m.n_levels; ++l) {
+      Launch L{L_ASSEMBLE, l, 0, (int64_t)m.work.size() / 3, 0};
+      int maxp = 0;
       for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
         int f = m.level_fronts[q];
-        if (m.f_p[f] > k) push(f, 0, 0);
+        for (int c0 = 0; c0 < m.f_m[f]; c0 += ASM_COLS) push(f, c0, 0);
+        maxp = std::max(maxp, m.f_p[f]);
       }
-      P.count = (int64_t)m.work.size() / 3 - P.item0;
-      if (P.count) m.sched.push_back(P);
-      Launch T{L_TRSM, l, k, (int64_t)m.work.size() / 3, 0};
-      for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
-        int f = m.level_fronts[q];
-        if (m.f_p[f] <= k) continue;
-        int nbe = std::min(PANEL_NB, m.f_p[f] - k);
-        for (int c0 = k + nbe; c0 < m.f_m[f]; c0 += TRSM_COLS) push(f, c0, 0);
-      }
-      T.count = (int64_t)m.work.size() / 3 - T.item0;
-      if (T.count) m.sched.push_back(T);
-      Launch G{L_GEMM, l, k, (int64_t)m.work.size() / 3, 0};
-      for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
-        int f = m.level_fronts[q];
-        if (m.f_p[f] <= k) continue;
-        int nbe = std::min(PANEL_NB, m.f_p[f] - k);
-        int r0 = k + nbe;
-        double rest = (double)(m.f_m[f] - r0);
-        m.gemm_flops += 2.0 * rest * rest * nbe;
-        m.trsm_flops += (double)nbe * (nbe - 1) * rest;
-        for (int j = k; j < r0; ++j) {
-          double below = (double)(m.f_m[f] - j - 1);
-          m.panel_flops += below + 2.0 * below * (r0 - j - 1);
+      L.count = (int64_t)m.work.size() / 3 - L.item0;
+      if (L.count) sched.push_back(L);
+      for (int k = 0; k < maxp; k += PANEL_NB) {
+        // panel kind of a front: 0 one CTA, 1 cluster, 2 global-memory fallback
+        auto kind = [&](int f) {
+          const int rows = m.f_m[f] - k;
+          if (rows <= rows_cta) return 0;
+          if ((rows + PANEL_CLUSTER - 1) / PANEL_CLUSTER <= rows_cta) return 1;
+          return 2;
+        };
+        for (int pk = 0; pk < 2; ++pk) {
+          Launch PC{pk == 0 ? L_PANEL_1 : L_PANEL_CL, l, k, (int64_t)m.work.size() / 3, 0};
+          int rows = 0;
+          for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
+            int f = m.level_fronts[q];
+            if (m.f_p[f] > k && kind(f) == pk) {
+              push(f, 0, 0);
+              const int r = m.f_m[f] - k;
+              rows = std::max(rows, pk == 0 ? r : (r + PANEL_CLUSTER - 1) / PANEL_CLUSTER);
+            }
+          }
+          PC.count = (int64_t)m.work.size() / 3 - PC.item0;
+          PC.aux = rows;
+          if (PC.count) sched.push_back(PC);
         }
-        int tiles = (m.f_m[f] - r0 + GEMM_TILE - 1) / GEMM_TILE;
-        for (int ti = 0; ti < tiles; ++ti)
-          for (int tj = 0; tj < tiles; ++tj) push(f, ti, tj);
+        Launch SW{L_LASWP, l, k, (int64_t)m.work.size() / 3, 0};
+        for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
+          int f = m.level_fronts[q];
+          if (m.f_p[f] > k && kind(f) < 2)
+            for (int c0 = 0; c0 < m.f_m[f]; c0 += LASWP_COLS) push(f, c0, 0);
+        }
+        SW.count = (int64_t)m.work.size() / 3 - SW.item0;
+        if (SW.count) sched.push_back(SW);
+        Launch P{L_PANEL, l, k, (int64_t)m.work.size() / 3, 0};
+        for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
+          int f = m.level_fronts[q];
+          if (m.f_p[f] > k && kind(f) == 2) push(f, 0, 0);
+        }
+        P.count = (int64_t)m.work.size() / 3 - P.item0;
+        if (P.count) sched.push_back(P);
+        Launch T{L_TRSM, l, k, (int64_t)m.work.size() / 3, 0};
+        for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
+          int f = m.level_fronts[q];
+          if (m.f_p[f] <= k) continue;
+          int nbe = std::min(PANEL_NB, m.f_p[f] - k);
+          for (int c0 = k + nbe; c0 < m.f_m[f]; c0 += TRSM_COLS) push(f, c0, 0);
+        }
+        T.count = (int64_t)m.work.size() / 3 - T.item0;
+        if (T.count) sched.push_back(T);
+        Launch G{L_GEMM, l, k, (int64_t)m.work.size() / 3, 0};
+        for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
+          int f = m.level_fronts[q];
+          if (m.f_p[f] <= k) continue;
+          int nbe = std::min(PANEL_NB, m.f_p[f] - k);
+          int r0 = k + nbe;
+          if (prec == 0) {
+            double rest = (double)(m.f_m[f] - r0);
+            m.gemm_flops += 2.0 * rest * rest * nbe;
+            m.trsm_flops += (double)nbe * (nbe - 1) * rest;
+            for (int j = k; j < r0; ++j) {
+              double below = (double)(m.f_m[f] - j - 1);
+              m.panel_flops += below + 2.0 * below * (r0 - j - 1);
+            }
+          }
+          int tiles = (m.f_m[f] - r0 + GEMM_TILE - 1) / GEMM_TILE;
+          for (int ti = 0; ti < tiles; ++ti)
+            for (int tj = 0; tj < tiles; ++tj) push(f, ti, tj);
+        }
+        G.count = (int64_t)m.work.size() / 3 - G.item0;
+        if (G.count) sched.push_back(G);
       }
-      G.count = (int64_t)m.work.size() / 3 - G.item0;
-      if (G.count) m.sched.push_back(G);
     }
   }
 }

@@ -57,19 +57,23 @@ constexpr int VOL_PAIRS = 1188;    // u rows x (u,x,p) + p rows x (u,x) + x rows
 constexpr int FACE_PAIRS = 120;    // u x lambda, lambda x (u, delta), delta x lambda
 
 // ----- blocked factorisation schedule ---------------------------------------
-enum LaunchKind { L_ASSEMBLE = 0, L_PANEL = 1, L_TRSM = 2, L_GEMM = 3 };
+enum LaunchKind { L_ASSEMBLE = 0, L_PANEL = 1, L_TRSM = 2, L_GEMM = 3, L_PANEL_CL = 4, L_LASWP = 5, L_PANEL_1 = 6 };
 struct Launch {
   int kind;
   int level;
   int k;          // panel start (pivot index) for PANEL/TRSM/GEMM
   int64_t item0;  // first work item
   int64_t count;  // work items
+  int aux = 0;    // PANEL_CL: rows per CTA (shared-memory sizing)
 };
 
 constexpr int PANEL_NB = 32;    // pivot block
 constexpr int GEMM_TILE = 64;   // Schur update tile
 constexpr int TRSM_COLS = 64;   // columns per TRSM item
 constexpr int ASM_COLS = 32;    // parent columns per assembly item
+constexpr int PANEL_CLUSTER = 8;          // CTAs per panel cluster
+constexpr int PANEL_SMEM_BYTES = 200 * 1024;   // panel rows held per CTA in shared memory
+constexpr int LASWP_COLS = 256;           // columns per row-interchange item
 
 struct FrontTables {              // device copies
   int32_t n_fronts = 0;
@@ -122,9 +126,11 @@ struct Mesh {
   std::vector<int32_t> f_m, f_p, f_first, f_idx, f_nz_csr, f_nz_pos, f_child_off, f_child, f_ea,
       f_parent, f_piv_off, f_col_nz, f_level;
   std::vector<int32_t> work;
-  std::vector<Launch> sched;       // numeric factorisation launches in order
+  std::vector<Launch> sched[2];    // numeric factorisation launches in order ([0] FP32, [1] FP64 fronts)
   std::vector<int32_t> level_off;  // fronts sorted by level
   std::vector<int32_t> level_fronts;
+  std::vector<int32_t> level_maxm;   // largest front order per level
+  std::vector<int32_t> level_threads;  // solve threads per front at each level
   int64_t front_entries = 0, vec_entries = 0, piv_entries = 0;
   double factor_flops = 0;
   double gemm_flops = 0, panel_flops = 0, trsm_flops = 0;   // per numeric factorisation

@@ -81,6 +81,7 @@ SIGNATURES = {
     "viv_mesh_info": (C.c_int, [_P, C.POINTER(MeshInfo)]),
     "viv_mesh_dof_labels": (C.c_int, [_P, _P, _P]),
     "viv_mesh_pattern": (C.c_int, [_P, _P, _P]),
+    "viv_mesh_fronts": (C.c_int, [_P, _P, _P, _P, _P]),
     "viv_mesh_destroy": (C.c_int, [_P]),
     "viv_case_create": (C.c_int, [_P, C.POINTER(Params), _P, _P, C.POINTER(_P)]),
     "viv_case_destroy": (C.c_int, [_P]),
@@ -213,6 +214,12 @@ class Mesh:
         col = np.empty(rp[-1], np.int32)
         _check(_lib.viv_mesh_pattern(self.h, _ptr(rp), _ptr(col)))
         return rp, col
+
+    def fronts(self):
+        n = int(self.info["n_fronts"])
+        a = [np.empty(n, np.int32) for _ in range(4)]
+        _check(_lib.viv_mesh_fronts(self.h, *[_ptr(x) for x in a]))
+        return dict(m=a[0], p=a[1], level=a[2], parent=a[3])
 
     def state_size(self):
         return int(_lib.viv_state_size(self.h))
