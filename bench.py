@@ -241,7 +241,18 @@ def run_ours(args, wl, rank, world, local):
     dom = max(kern, key=lambda k: kern[k][0])
     dom_ms, dom_n = kern[dom]
     peaks, src = measured_peaks()
-    if dom in ("schur_gemm", "panel_lu", "trsm"):
+    if dom == "tc_schur_gemm":
+        # tensor-core kind::tf32 issues three products per FP32 multiply-add (3xTF32):
+        # achieved = algorithmic FP32 flops / time; peak = TF32 dense = BF16 measured / 2 (nominal ratio), / 3
+        flops = info["outer_flops"] * n_fact
+        achieved = flops / (dom_ms / 1e3) / 1e12
+        key = "bf16_tflops_sustained" if "bf16_tflops_sustained" in peaks else "bf16_tflops"
+        peak = peaks[key] / 2.0 / 3.0
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": dom,
+                "peak_source": f"{src} {key} / 2 (TF32:BF16 nominal) / 3 (3xTF32 products)",
+                "launches": dom_n, "ms_total": dom_ms}
+    elif dom in ("schur_gemm", "panel_lu", "trsm"):
         flops = {"schur_gemm": info["gemm_flops"], "panel_lu": info["panel_flops"],
                  "trsm": info["trsm_flops"]}[dom] * n_fact
         achieved = flops / (dom_ms / 1e3) / 1e12

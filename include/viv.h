@@ -101,6 +101,7 @@ typedef struct {
   double gemm_flops;       /* Schur-update (GEMM) flops of one factorisation */
   double panel_flops;      /* in-panel LU flops of one factorisation */
   double trsm_flops;       /* panel TRSM flops of one factorisation */
+  double outer_flops;      /* part of gemm_flops in K = 128 outer updates (tensor cores, mixed path) */
 } vivMeshInfo;
 
 /* Physical and solver parameters.  rho, mu: fluid density and viscosity;
@@ -215,6 +216,15 @@ vivStatus viv_solve_rhs(vivCase* c, int device, const double* b, double* y, int*
  *  - Returns VIV_ERR_STATE if the case has not been factored. */
 vivStatus viv_lu_solve_noalloc(vivCase* c, const double* b, double* x);
 
+/* Front Schur-complement update C -= A * B (the multifrontal GEMM of the
+ * mixed path) on the tcgen05 tensor cores with 3xTF32 compensation (FP32
+ * accuracy from TF32 products).  A: M x K, B: K x N, C: M x N, column-major
+ * FP32 device arrays with leading dimensions lda >= M, ldb >= K, ldc >= M.
+ * err: device int set to 1 if a bounded wait for the tensor cores expired.
+ * Enqueued on `stream`. */
+vivStatus viv_tc_schur_update(const float* A, int lda, const float* B, int ldb, float* C, int ldc, int M, int N,
+                              int K, int* err, void* stream);
+
 /* U += dU (the last correction); Gamma nodes follow x = X + delta. */
 vivStatus viv_update(vivCase* c);
 
@@ -233,9 +243,10 @@ int64_t viv_kernel_launches(void);
 /* per-case CUDA-event timing of every kernel launch, by kind:
  * 0 residual elements, 1 Jacobian elements, 2 Gamma faces and border rows,
  * 3 front assembly, 4 panel LU, 5 TRSM, 6 Schur GEMM, 7 forward solve,
- * 8 backward solve, 9 refinement SpMV, 10 vector kernels.
- * viv_profile_read(ms[11], count[11]) synchronises and resets. */
-enum { VIV_NKINDS = 11 };
+ * 8 backward solve, 9 refinement SpMV, 10 vector kernels, 11 tensor-core
+ * (tcgen05) Schur updates.
+ * viv_profile_read(ms[12], count[12]) synchronises and resets. */
+enum { VIV_NKINDS = 12 };
 vivStatus viv_profile(vivCase* c, int on);
 vivStatus viv_profile_read(vivCase* c, double* ms, int64_t* count);
 

@@ -14,6 +14,8 @@
 
 namespace viv {
 int64_t launches();
+void tc_gemm_update(const float* A, int lda, const float* B, int ldb, float* C, int ldc, int M, int N, int K,
+                    int* err, cudaStream_t s);
 void lu_solve_noalloc(vivCase* c, const double* b, double* x);
 void build_mesh(Mesh& m, const vivMeshDesc* d);
 void upload_mesh(Mesh& m, cudaStream_t s);
@@ -242,6 +244,7 @@ vivStatus viv_mesh_info(const vivMesh* mesh, vivMeshInfo* info) {
   info->gemm_flops = m.gemm_flops;
   info->panel_flops = m.panel_flops;
   info->trsm_flops = m.trsm_flops;
+  info->outer_flops = m.outer_flops;
   API_END
 }
 
@@ -477,6 +480,15 @@ vivStatus viv_lu_solve_noalloc(vivCase* c, const double* b, double* x) {
   VIV_CHECK(c && b && x, VIV_ERR_ARG, "NULL argument");
   VIV_CHECK(c->factored, VIV_ERR_STATE, "viv_lu_solve_noalloc before viv_factor");
   lu_solve_noalloc(c, b, x);
+  API_END
+}
+
+vivStatus viv_tc_schur_update(const float* A, int lda, const float* B, int ldb, float* C, int ldc, int M, int N,
+                              int K, int* err, void* stream) {
+  API_BEGIN
+  VIV_CHECK(A && B && C && err, VIV_ERR_ARG, "NULL argument");
+  VIV_CHECK(M >= 0 && N >= 0 && K >= 0 && lda >= M && ldb >= K && ldc >= M, VIV_ERR_ARG, "bad GEMM shape");
+  tc_gemm_update(A, lda, B, ldb, C, ldc, M, N, K, err, (cudaStream_t)stream);
   API_END
 }
 

@@ -24,10 +24,13 @@
 
 #include <cfloat>
 #include <climits>
+#include <type_traits>
 
+#include "tc_mma.cuh"
 #include "viv_internal.h"
 
 namespace viv {
+size_t tc_smem_bytes();
 namespace {
 
 template <class T>
@@ -81,7 +84,7 @@ __device__ __forceinline__ int lower_bound_i(const int32_t* a, int n, int v) {
 
 template <class T, class S>
 __global__ void assemble_kernel(FT ft, const int32_t* work, const S* J, T* pool) {
-  const int32_t* it = work + 3 * blockIdx.x;
+  const int32_t* it = work + WORK_STRIDE * blockIdx.x;
   const int f = it[0], c0 = it[1];
   const int m = ft.m[f];
   const int c1 = min(c0 + ASM_COLS, m);
@@ -116,7 +119,7 @@ constexpr int PANEL_THREADS = 256;
 template <class T>
 __global__ void __launch_bounds__(PANEL_THREADS) panel_kernel(FT ft, const int32_t* work, int k, T* pool,
                                                               int32_t* piv, int32_t* stats, T thresh) {
-  const int f = work[3 * blockIdx.x];
+  const int f = work[WORK_STRIDE * blockIdx.x];
   const int m = ft.m[f], p = ft.p[f];
   T* F = pool + ft.off[f];
   int32_t* pv = piv + ft.piv_off[f];
@@ -238,7 +241,7 @@ __global__ void __launch_bounds__(NT)
     panel_smem_kernel(FT ft, const int32_t* work, int k, T* pool, int32_t* piv, int32_t* stats, T thresh) {
   Group<CLN> grp;
   const int q = grp.rank();
-  const int f = work[3 * (blockIdx.x / CLN)];
+  const int f = work[WORK_STRIDE * (blockIdx.x / CLN)];
   const int m = ft.m[f], p = ft.p[f];
   const int nbe = min(PANEL_NB, p - k);
   const int chunk = (m - k + CLN - 1) / CLN;
@@ -392,7 +395,7 @@ __global__ void __launch_bounds__(NT)
 // row interchanges of a cluster panel applied to the columns outside it
 template <class T>
 __global__ void laswp_kernel(FT ft, const int32_t* work, int k, T* pool, const int32_t* piv) {
-  const int32_t* it = work + 3 * blockIdx.x;
+  const int32_t* it = work + WORK_STRIDE * blockIdx.x;
   const int f = it[0], c = it[1] + threadIdx.x;
   const int m = ft.m[f], p = ft.p[f];
   const int nbe = min(PANEL_NB, p - k);
@@ -409,13 +412,14 @@ __global__ void laswp_kernel(FT ft, const int32_t* work, int k, T* pool, const i
   }
 }
 
+// U12 rows [k, k + nbe) of columns [c0, min(c0 + TRSM_COLS, c_end)) := L11^{-1} A12
 template <class T>
-__global__ void trsm_kernel(FT ft, const int32_t* work, int k, T* pool) {
-  const int32_t* it = work + 3 * blockIdx.x;
-  const int f = it[0], c0 = it[1];
+__global__ void trsm_kernel(FT ft, const int32_t* work, T* pool) {
+  const int32_t* it = work + WORK_STRIDE * blockIdx.x;
+  const int f = it[0], c0 = it[1], c_end = it[2], k = it[3];
   const int m = ft.m[f], p = ft.p[f];
   const int nbe = min(PANEL_NB, p - k);
-  const int c1 = min(c0 + TRSM_COLS, m);
+  const int c1 = min(c0 + TRSM_COLS, c_end);
   T* F = pool + ft.off[f];
   __shared__ T L[PANEL_NB][PANEL_NB + 1];
   __shared__ T B[PANEL_NB][TRSM_COLS + 1];
@@ -444,48 +448,62 @@ __global__ void trsm_kernel(FT ft, const int32_t* work, int k, T* pool) {
   }
 }
 
-// C[r0 + 64 ti .., r0 + 64 tj ..] -= L21 * U12 with K = nbe <= 32
+// F[rb.., cb..] -= F[rows, k_begin : k_begin + k_len] * F[k_begin : k_begin + k_len, cols]
+// for one 64 x 64 tile clipped to rows < r_end and columns < c_end (SIMT)
 template <class T>
-__global__ void __launch_bounds__(256) gemm_kernel(FT ft, const int32_t* work, int k, T* pool) {
-  const int32_t* it = work + 3 * blockIdx.x;
-  const int f = it[0], ti = it[1], tj = it[2];
-  const int m = ft.m[f], p = ft.p[f];
-  const int nbe = min(PANEL_NB, p - k);
-  const int r0 = k + nbe;
-  const int rb = r0 + ti * GEMM_TILE, cb = r0 + tj * GEMM_TILE;
+__global__ void __launch_bounds__(256) gemm_kernel(FT ft, const int32_t* work, T* pool) {
+  const int32_t* it = work + WORK_STRIDE * blockIdx.x;
+  const int f = it[0], rb = it[1], cb = it[2], r_end = it[3], c_end = it[4], kb = it[5], kl = it[6];
+  const int m = ft.m[f];
   T* F = pool + ft.off[f];
   __shared__ T As[PANEL_NB][GEMM_TILE + 1];   // [kk][row]
   __shared__ T Bs[PANEL_NB][GEMM_TILE + 1];   // [kk][col]
-  for (int q = threadIdx.x; q < PANEL_NB * GEMM_TILE; q += blockDim.x) {
-    int r = q % GEMM_TILE, kk = q / GEMM_TILE;
-    T a = 0, b = 0;
-    if (kk < nbe) {
-      if (rb + r < m) a = F[(int64_t)(k + kk) * m + rb + r];
-      if (cb + r < m) b = F[(int64_t)(cb + r) * m + k + kk];
-    }
-    As[kk][r] = a;
-    Bs[kk][r] = b;
-  }
-  __syncthreads();
   const int tr = threadIdx.x % 16, tc = threadIdx.x / 16;
   T acc[4][4] = {};
-  for (int kk = 0; kk < nbe; ++kk) {
-    T a[4], b[4];
-    for (int u = 0; u < 4; ++u) {
-      a[u] = As[kk][tr + 16 * u];
-      b[u] = Bs[kk][tc + 16 * u];
+  for (int k0 = 0; k0 < kl; k0 += PANEL_NB) {
+    const int kn = min(PANEL_NB, kl - k0);
+    for (int q = threadIdx.x; q < PANEL_NB * GEMM_TILE; q += blockDim.x) {
+      int r = q % GEMM_TILE, kk = q / GEMM_TILE;
+      T a = 0, b = 0;
+      if (kk < kn) {
+        if (rb + r < r_end) a = F[(int64_t)(kb + k0 + kk) * m + rb + r];
+        if (cb + r < c_end) b = F[(int64_t)(cb + r) * m + kb + k0 + kk];
+      }
+      As[kk][r] = a;
+      Bs[kk][r] = b;
     }
-    for (int u = 0; u < 4; ++u)
-      for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+    __syncthreads();
+    for (int kk = 0; kk < kn; ++kk) {
+      T a[4], b[4];
+      for (int u = 0; u < 4; ++u) {
+        a[u] = As[kk][tr + 16 * u];
+        b[u] = Bs[kk][tc + 16 * u];
+      }
+      for (int u = 0; u < 4; ++u)
+        for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+    }
+    __syncthreads();
   }
   for (int v = 0; v < 4; ++v) {
     const int c = cb + tc + 16 * v;
-    if (c >= m) continue;
+    if (c >= c_end) continue;
     for (int u = 0; u < 4; ++u) {
       const int r = rb + tr + 16 * u;
-      if (r < m) F[(int64_t)c * m + r] -= acc[u][v];
+      if (r < r_end) F[(int64_t)c * m + r] -= acc[u][v];
     }
   }
+}
+
+// outer Schur update of a large front on the tensor cores: one 128 x 128 tile
+// F[rb.., cb..] -= F[.., k_begin : k_begin + k_len] * F[k_begin : .., ..]
+__global__ void __launch_bounds__(tc::THREADS) tc_front_kernel(FT ft, const int32_t* work, float* pool, int* err) {
+  extern __shared__ __align__(1024) unsigned char raw[];
+  tc::Smem& sm = *reinterpret_cast<tc::Smem*>(raw);
+  const int32_t* it = work + WORK_STRIDE * blockIdx.x;
+  const int f = it[0], rb = it[1], cb = it[2], kb = it[3], kl = it[4];
+  const int m = ft.m[f];
+  float* F = pool + ft.off[f];
+  tc::tile_update(sm, F + (int64_t)kb * m, m, F + kb, m, F, m, m, m, kl, rb, cb, err);
 }
 
 // ---- solves -----------------------------------------------------------------------
@@ -649,6 +667,9 @@ void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* front
   FT ft = make_ft(m);
   static bool attr_set = false;
   if (!attr_set) {
+    if constexpr (std::is_same<T, float>::value)
+      VIV_CUDA(cudaFuncSetAttribute(tc_front_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)tc_smem_bytes()));
     VIV_CUDA(cudaFuncSetAttribute(panel_smem_kernel<T, 1, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   PANEL_SMEM_BYTES));
     VIV_CUDA(cudaFuncSetAttribute(panel_smem_kernel<T, PANEL_CLUSTER, 256>,
@@ -657,12 +678,12 @@ void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* front
     VIV_CUDA(cudaFuncSetAttribute(bwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX));
     attr_set = true;
   }
-  VIV_CUDA(cudaMemsetAsync(stats, 0, 2 * sizeof(int32_t), s));
+  VIV_CUDA(cudaMemsetAsync(stats, 0, 3 * sizeof(int32_t), s));
   const int32_t* work = m.ft.work;
   for (const Launch& L : m.sched[sizeof(T) == 8]) {
-    const int32_t* w = work + 3 * L.item0;
+    const int32_t* w = work + (int64_t)WORK_STRIDE * L.item0;
     const unsigned grid = (unsigned)L.count;
-    static const int kk[7] = {K_FRONT_ASM, K_PANEL, K_TRSM, K_GEMM, K_PANEL, K_TRSM, K_PANEL};
+    static const int kk[8] = {K_FRONT_ASM, K_PANEL, K_TRSM, K_GEMM, K_PANEL, K_TRSM, K_PANEL, K_TCGEMM};
     Launched LL(kk[L.kind], s);
     switch (L.kind) {
       case L_ASSEMBLE:
@@ -675,10 +696,15 @@ void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* front
         panel_kernel<T><<<grid, PANEL_THREADS, 0, s>>>(ft, w, L.k, fronts, piv, stats, (T)threshold);
         break;
       case L_TRSM:
-        trsm_kernel<T><<<grid, TRSM_COLS, 0, s>>>(ft, w, L.k, fronts);
+        trsm_kernel<T><<<grid, TRSM_COLS, 0, s>>>(ft, w, fronts);
         break;
       case L_GEMM:
-        gemm_kernel<T><<<grid, 256, 0, s>>>(ft, w, L.k, fronts);
+        gemm_kernel<T><<<grid, 256, 0, s>>>(ft, w, fronts);
+        break;
+      case L_TC_GEMM:
+        if constexpr (std::is_same<T, float>::value) {
+          tc_front_kernel<<<grid, tc::THREADS, tc_smem_bytes(), s>>>(ft, w, fronts, stats + 2);
+        }
         break;
       case L_PANEL_1: {
         const size_t smem = (size_t)L.aux * PANEL_NB * sizeof(T);

@@ -572,30 +572,51 @@ void build_mesh(Mesh& m, const vivMeshDesc* d) {
     int t = ((m.level_maxm[l] / 2 + 31) / 32) * 32;
     m.level_threads[l] = std::min(1024, std::max(64, t));
   }
-  // launch schedules of the numeric factorisation, one per front element size
+  // launch schedules of the numeric factorisation, one per front element size.
+  // Fronts of order >= BIG_FRONT are factored in 128-column outer blocks: four
+  // 32-column pivot panels update only the block's own columns; the outer
+  // columns receive the block's row interchanges, then its TRSM, then one
+  // K = 128 Schur update (tensor cores on the FP32 path).
   m.work.clear();
-  m.gemm_flops = m.trsm_flops = m.panel_flops = 0;
-  auto push = [&](int a, int b, int c) {
-    m.work.push_back(a);
-    m.work.push_back(b);
-    m.work.push_back(c);
+  m.gemm_flops = m.trsm_flops = m.panel_flops = m.outer_flops = 0;
+  auto push = [&](std::initializer_list<int> v) {
+    int n = 0;
+    for (int x : v) {
+      m.work.push_back(x);
+      ++n;
+    }
+    for (; n < WORK_STRIDE; ++n) m.work.push_back(0);
   };
+  auto items = [&]() { return (int64_t)m.work.size() / WORK_STRIDE; };
   for (int prec = 0; prec < 2; ++prec) {
+    const bool count = prec == 0;
     const int esz = prec ? 8 : 4;
     const int rows_cta = PANEL_SMEM_BYTES / (PANEL_NB * esz);   // panel rows one CTA holds
     std::vector<Launch>& sched = m.sched[prec];
     sched.clear();
+    auto open = [&](int kind, int l, int k) { return Launch{kind, l, k, items(), 0}; };
+    auto close = [&](Launch L) {
+      L.count = items() - L.item0;
+      if (L.count) sched.push_back(L);
+    };
+    auto gemm_tiles = [&](int f, int r0, int r_end, int c0, int c_end, int kb, int kl) {
+      for (int rb = r0; rb < r_end; rb += GEMM_TILE)
+        for (int cb = c0; cb < c_end; cb += GEMM_TILE) push({f, rb, cb, r_end, c_end, kb, kl});
+      if (count) m.gemm_flops += 2.0 * std::max(0, r_end - r0) * std::max(0, c_end - c0) * kl;
+    };
     for (int l = 0; l < m.n_levels; ++l) {
-      Launch L{L_ASSEMBLE, l, 0, (int64_t)m.work.size() / 3, 0};
+      Launch L = open(L_ASSEMBLE, l, 0);
       int maxp = 0;
       for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
         int f = m.level_fronts[q];
-        for (int c0 = 0; c0 < m.f_m[f]; c0 += ASM_COLS) push(f, c0, 0);
+        for (int c0 = 0; c0 < m.f_m[f]; c0 += ASM_COLS) push({f, c0});
         maxp = std::max(maxp, m.f_p[f]);
       }
-      L.count = (int64_t)m.work.size() / 3 - L.item0;
-      if (L.count) sched.push_back(L);
+      close(L);
       for (int k = 0; k < maxp; k += PANEL_NB) {
+        const int k2 = (k / OUTER_NB) * OUTER_NB;
+        auto big = [&](int f) { return m.f_m[f] >= BIG_FRONT; };
+        auto block_end = [&](int f) { return std::min(k2 + OUTER_NB, m.f_p[f]); };
         // panel kind of a front: 0 one CTA, 1 cluster, 2 global-memory fallback
         auto kind = [&](int f) {
           const int rows = m.f_m[f] - k;
@@ -604,65 +625,106 @@ void build_mesh(Mesh& m, const vivMeshDesc* d) {
           return 2;
         };
         for (int pk = 0; pk < 2; ++pk) {
-          Launch PC{pk == 0 ? L_PANEL_1 : L_PANEL_CL, l, k, (int64_t)m.work.size() / 3, 0};
+          Launch PC = open(pk == 0 ? L_PANEL_1 : L_PANEL_CL, l, k);
           int rows = 0;
           for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
             int f = m.level_fronts[q];
             if (m.f_p[f] > k && kind(f) == pk) {
-              push(f, 0, 0);
+              push({f});
               const int r = m.f_m[f] - k;
               rows = std::max(rows, pk == 0 ? r : (r + PANEL_CLUSTER - 1) / PANEL_CLUSTER);
             }
           }
-          PC.count = (int64_t)m.work.size() / 3 - PC.item0;
           PC.aux = rows;
-          if (PC.count) sched.push_back(PC);
+          close(PC);
         }
-        Launch SW{L_LASWP, l, k, (int64_t)m.work.size() / 3, 0};
+        Launch SW = open(L_LASWP, l, k);
         for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
           int f = m.level_fronts[q];
           if (m.f_p[f] > k && kind(f) < 2)
-            for (int c0 = 0; c0 < m.f_m[f]; c0 += LASWP_COLS) push(f, c0, 0);
+            for (int c0 = 0; c0 < m.f_m[f]; c0 += LASWP_COLS) push({f, c0});
         }
-        SW.count = (int64_t)m.work.size() / 3 - SW.item0;
-        if (SW.count) sched.push_back(SW);
-        Launch P{L_PANEL, l, k, (int64_t)m.work.size() / 3, 0};
+        close(SW);
+        Launch P = open(L_PANEL, l, k);
         for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
           int f = m.level_fronts[q];
-          if (m.f_p[f] > k && kind(f) == 2) push(f, 0, 0);
+          if (m.f_p[f] > k && kind(f) == 2) push({f});
         }
-        P.count = (int64_t)m.work.size() / 3 - P.item0;
-        if (P.count) sched.push_back(P);
-        Launch T{L_TRSM, l, k, (int64_t)m.work.size() / 3, 0};
-        for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
-          int f = m.level_fronts[q];
-          if (m.f_p[f] <= k) continue;
-          int nbe = std::min(PANEL_NB, m.f_p[f] - k);
-          for (int c0 = k + nbe; c0 < m.f_m[f]; c0 += TRSM_COLS) push(f, c0, 0);
-        }
-        T.count = (int64_t)m.work.size() / 3 - T.item0;
-        if (T.count) sched.push_back(T);
-        Launch G{L_GEMM, l, k, (int64_t)m.work.size() / 3, 0};
+        close(P);
+        // TRSM and GEMM of this panel (inside the outer block for large fronts)
+        Launch T = open(L_TRSM, l, k);
         for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
           int f = m.level_fronts[q];
           if (m.f_p[f] <= k) continue;
-          int nbe = std::min(PANEL_NB, m.f_p[f] - k);
-          int r0 = k + nbe;
-          if (prec == 0) {
-            double rest = (double)(m.f_m[f] - r0);
-            m.gemm_flops += 2.0 * rest * rest * nbe;
-            m.trsm_flops += (double)nbe * (nbe - 1) * rest;
-            for (int j = k; j < r0; ++j) {
+          const int nbe = std::min(PANEL_NB, m.f_p[f] - k);
+          const int c_end = big(f) ? block_end(f) : m.f_m[f];
+          for (int c0 = k + nbe; c0 < c_end; c0 += TRSM_COLS) push({f, c0, c_end, k});
+          if (count) {
+            m.trsm_flops += (double)nbe * (nbe - 1) * std::max(0, c_end - k - nbe);
+            for (int j = k; j < k + nbe; ++j) {
               double below = (double)(m.f_m[f] - j - 1);
-              m.panel_flops += below + 2.0 * below * (r0 - j - 1);
+              m.panel_flops += below + 2.0 * below * (k + nbe - j - 1);
             }
           }
-          int tiles = (m.f_m[f] - r0 + GEMM_TILE - 1) / GEMM_TILE;
-          for (int ti = 0; ti < tiles; ++ti)
-            for (int tj = 0; tj < tiles; ++tj) push(f, ti, tj);
         }
-        G.count = (int64_t)m.work.size() / 3 - G.item0;
-        if (G.count) sched.push_back(G);
+        close(T);
+        Launch G = open(L_GEMM, l, k);
+        for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
+          int f = m.level_fronts[q];
+          if (m.f_p[f] <= k) continue;
+          const int nbe = std::min(PANEL_NB, m.f_p[f] - k);
+          const int r0 = k + nbe;
+          const int c_end = big(f) ? block_end(f) : m.f_m[f];
+          gemm_tiles(f, r0, m.f_m[f], r0, c_end, k, nbe);
+        }
+        close(G);
+        // large fronts whose outer block ends with this panel: the outer columns
+        std::vector<int> done;
+        for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
+          int f = m.level_fronts[q];
+          if (m.f_p[f] <= k || !big(f)) continue;
+          const int nbe = std::min(PANEL_NB, m.f_p[f] - k);
+          if (k + nbe == block_end(f) && block_end(f) < m.f_m[f]) done.push_back(f);
+        }
+        if (done.empty()) continue;
+        for (int s0 = k2; s0 <= k; s0 += PANEL_NB) {
+          Launch OT = open(L_TRSM, l, s0);
+          for (int f : done) {
+            const int be = block_end(f);
+            if (s0 >= be) continue;
+            const int nbe = std::min(PANEL_NB, m.f_p[f] - s0);
+            for (int c0 = be; c0 < m.f_m[f]; c0 += TRSM_COLS) push({f, c0, m.f_m[f], s0});
+            if (count) m.trsm_flops += (double)nbe * (nbe - 1) * (m.f_m[f] - be);
+          }
+          close(OT);
+          Launch OG = open(L_GEMM, l, s0);
+          for (int f : done) {
+            const int be = block_end(f);
+            const int nbe = std::min(PANEL_NB, m.f_p[f] - s0);
+            if (s0 + nbe < be) gemm_tiles(f, s0 + nbe, be, be, m.f_m[f], s0, nbe);
+          }
+          close(OG);
+        }
+        if (prec == 0) {
+          Launch TC = open(L_TC_GEMM, l, k2);
+          for (int f : done) {
+            const int be = block_end(f), mm = m.f_m[f];
+            for (int rb = be; rb < mm; rb += 128)
+              for (int cb = be; cb < mm; cb += 128) push({f, rb, cb, k2, be - k2});
+            const double rest = (double)(mm - be);
+            m.gemm_flops += 2.0 * rest * rest * (be - k2);
+            m.outer_flops += 2.0 * rest * rest * (be - k2);
+          }
+          close(TC);
+        } else {
+          Launch OG = open(L_GEMM, l, k2);
+          for (int f : done) {
+            const int be = block_end(f), mm = m.f_m[f];
+            for (int rb = be; rb < mm; rb += GEMM_TILE)
+              for (int cb = be; cb < mm; cb += GEMM_TILE) push({f, rb, cb, mm, mm, k2, be - k2});
+          }
+          close(OG);
+        }
       }
     }
   }

@@ -1,0 +1,247 @@
+// tcgen05 (kind::tf32, 3xTF32) tile update shared by the standalone GEMM
+// entry point and the front-batched Schur updates of the factorisation.
+//
+// C -= A * B for one 128 x 128 tile, A: M x K, B: K x N, C: M x N, all
+// column-major FP32.  Every FP32 operand is split into hi = tf32(x) and
+// lo = tf32(x - hi); the product is accumulated in FP32 in tensor memory as
+// lo*hi + hi*lo + hi*hi, which keeps close to FP32 accuracy.  Operands are
+// staged in shared memory in the canonical K-major, no-swizzle core-matrix
+// layout (8 rows x 16 bytes per core matrix); one elected thread issues the
+// MMAs and commits them to an mbarrier; every wait is bounded and on expiry
+// the tile is skipped and an error flag is raised instead of hanging.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace viv {
+namespace tc {
+
+constexpr int BM = 128, BN = 128, KC = 32;        // tile and K chunk
+constexpr int THREADS = 256;                     // 8 warps stage operands; one thread issues MMAs
+constexpr int CORE_BYTES = 128;                   // 8 rows x 16 bytes
+constexpr int KCORE_STRIDE = (BM / 8) * CORE_BYTES;   // bytes between K-adjacent core matrices (LBO)
+constexpr int OPERAND_BYTES = BM * KC * 4;        // one 128 x 32 FP32 operand chunk
+constexpr uint32_t TMEM_COLS = 128;
+constexpr long long WAIT_LIMIT = 1LL << 24;       // bounded mbarrier polling
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// shared-memory matrix descriptor: start, LBO (K direction), SBO (M/N
+// direction), descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// instruction descriptor of kind::tf32: D f32, A and B tf32, both K-major
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+// bounded wait for the phase with the given parity; false on expiry
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (long long it = 0; it < WAIT_LIMIT; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// byte offset of element (row r, k) of a 128 x 32 K-major chunk
+__device__ __forceinline__ int kmajor_off(int r, int k) {
+  return (k >> 2) * KCORE_STRIDE + (r >> 3) * CORE_BYTES + (r & 7) * 16 + (k & 3) * 4;
+}
+
+struct Stage {
+  alignas(1024) unsigned char a_hi[OPERAND_BYTES];
+  alignas(1024) unsigned char a_lo[OPERAND_BYTES];
+  alignas(1024) unsigned char b_hi[OPERAND_BYTES];
+  alignas(1024) unsigned char b_lo[OPERAND_BYTES];
+};
+
+struct Smem {
+  Stage st[2];          // two-stage pipeline: stage K-chunk c+1 while the MMAs of chunk c run
+  uint64_t bar[2];      // one mbarrier per stage, completed by tcgen05.commit
+  uint32_t tmem_base;
+};
+
+// stage K-chunk [k0, k0 + KC) of A (rows rb..) and B (columns cb..) as hi/lo
+// TF32 pairs.  All global loads of a thread are issued before any conversion
+// or shared-memory store (read-only path: A and B are never written by the
+// update), and every thread writes whole 16-byte core-matrix rows.
+__device__ __forceinline__ void stage_chunk(Stage& S, const float* __restrict__ A, int lda,
+                                            const float* __restrict__ B, int ldb, int M, int N, int K, int rb,
+                                            int cb, int k0) {
+  constexpr int PER = BM * (KC / 4) / THREADS;   // (row, k-group) pairs per thread = 4
+  float va[PER][4], vb[PER][4];
+#pragma unroll
+  for (int t = 0; t < PER; ++t) {
+    const int idx = threadIdx.x + t * THREADS;
+    const int r = idx % BM, g = idx / BM;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = k0 + 4 * g + j;
+      va[t][j] = (rb + r < M && k < K) ? __ldg(A + (int64_t)k * lda + rb + r) : 0.f;
+      vb[t][j] = (cb + r < N && k < K) ? __ldg(B + (int64_t)(cb + r) * ldb + k) : 0.f;
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < PER; ++t) {
+    const int idx = threadIdx.x + t * THREADS;
+    const int r = idx % BM, g = idx / BM;
+    uint32_t ah[4], al[4], bh[4], bl[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      ah[j] = to_tf32(va[t][j]);
+      al[j] = to_tf32(va[t][j] - __uint_as_float(ah[j]));
+      bh[j] = to_tf32(vb[t][j]);
+      bl[j] = to_tf32(vb[t][j] - __uint_as_float(bh[j]));
+    }
+    const int off = g * KCORE_STRIDE + (r >> 3) * CORE_BYTES + (r & 7) * 16;
+    *reinterpret_cast<uint4*>(S.a_hi + off) = make_uint4(ah[0], ah[1], ah[2], ah[3]);
+    *reinterpret_cast<uint4*>(S.a_lo + off) = make_uint4(al[0], al[1], al[2], al[3]);
+    *reinterpret_cast<uint4*>(S.b_hi + off) = make_uint4(bh[0], bh[1], bh[2], bh[3]);
+    *reinterpret_cast<uint4*>(S.b_lo + off) = make_uint4(bl[0], bl[1], bl[2], bl[3]);
+  }
+}
+
+// C[rb.., cb..] -= A[rb.., 0:K] * B[0:K, cb..] for one 128 x 128 tile
+static __device__ void tile_update(Smem& sm, const float* A, int lda, const float* B, int ldb, float* C, int ldc,
+                                   int M, int N, int K, int rb, int cb, int* err) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm.tmem_base)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    mbar_init(&sm.bar[0], 1);
+    mbar_init(&sm.bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = sm.tmem_base;
+  constexpr uint32_t idesc = make_idesc(BM, BN);
+  uint32_t ph[2] = {0u, 0u};
+  bool ok = true;
+  const int nchunks = (K + KC - 1) / KC;
+  for (int ch = 0; ch < nchunks; ++ch) {
+    const int s = ch & 1;
+    bool w = true;
+    if (ch >= 2) {   // the MMAs of chunk ch - 2 read this stage: wait for them
+      w = mbar_wait(&sm.bar[s], ph[s]);
+      ph[s] ^= 1u;
+    }
+    if (!__syncthreads_and(w)) {
+      ok = false;
+      break;
+    }
+    stage_chunk(sm.st[s], A, lda, B, ldb, M, N, K, rb, cb, ch * KC);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t ah = smem_u32(sm.st[s].a_hi), al = smem_u32(sm.st[s].a_lo);
+      const uint32_t bh = smem_u32(sm.st[s].b_hi), bl = smem_u32(sm.st[s].b_lo);
+#pragma unroll
+      for (int q = 0; q < KC / 8; ++q) {
+        const uint32_t koff = (uint32_t)(2 * q * KCORE_STRIDE);   // 8 tf32 = 2 core matrices along K
+        const uint64_t dah = make_desc(ah + koff, KCORE_STRIDE, CORE_BYTES);
+        const uint64_t dal = make_desc(al + koff, KCORE_STRIDE, CORE_BYTES);
+        const uint64_t dbh = make_desc(bh + koff, KCORE_STRIDE, CORE_BYTES);
+        const uint64_t dbl = make_desc(bl + koff, KCORE_STRIDE, CORE_BYTES);
+        mma_tf32(tmem, dal, dbh, idesc, (ch > 0 || q > 0) ? 1u : 0u);   // small terms first
+        mma_tf32(tmem, dah, dbl, idesc, 1u);
+        mma_tf32(tmem, dah, dbh, idesc, 1u);
+      }
+      mma_commit(&sm.bar[s]);
+    }
+    __syncwarp();
+  }
+  if (ok) {   // drain the (at most two) outstanding commits
+    bool w = true;
+    for (int c = nchunks > 2 ? nchunks - 2 : 0; c < nchunks; ++c) {
+      const int s = c & 1;
+      w = mbar_wait(&sm.bar[s], ph[s]) && w;
+      ph[s] ^= 1u;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    ok = __syncthreads_and(w) != 0;
+  }
+  if (!ok) {
+    if (tid == 0) atomicExch(err, 1);
+  } else {
+    // epilogue: warp w reads accumulator lanes 32 (w % 4) .. (tile rows) and
+    // column half w / 4; each thread owns one row
+    const int quarter = warp & 3, half = warp >> 2;
+    const int r = rb + quarter * 32 + lane;
+    for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 32) {
+      uint32_t v[32];
+      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+            "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+            "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+            "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (r < M) {
+        // all 32 loads of C first, then the 32 stores: loads stay in flight together
+        float cv[32];
+        float* cr = C + (int64_t)(cb + c0) * ldc + r;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) cv[j] = (cb + c0 + j < N) ? cr[(int64_t)j * ldc] : 0.f;
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (cb + c0 + j < N) cr[(int64_t)j * ldc] = cv[j] - __uint_as_float(v[j]);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
+}  // namespace tc
+}  // namespace viv

@@ -57,11 +57,19 @@ constexpr int VOL_PAIRS = 1188;    // u rows x (u,x,p) + p rows x (u,x) + x rows
 constexpr int FACE_PAIRS = 120;    // u x lambda, lambda x (u, delta), delta x lambda
 
 // ----- blocked factorisation schedule ---------------------------------------
-enum LaunchKind { L_ASSEMBLE = 0, L_PANEL = 1, L_TRSM = 2, L_GEMM = 3, L_PANEL_CL = 4, L_LASWP = 5, L_PANEL_1 = 6 };
+enum LaunchKind {
+  L_ASSEMBLE = 0, L_PANEL = 1, L_TRSM = 2, L_GEMM = 3, L_PANEL_CL = 4, L_LASWP = 5, L_PANEL_1 = 6, L_TC_GEMM = 7
+};
+constexpr int WORK_STRIDE = 8;   // ints per work item
+// work items:  ASSEMBLE (f, c0)           PANEL* (f)              LASWP (f, c0)
+//              TRSM (f, c0, c_end, k)      GEMM (f, rb, cb, r_end, c_end, k_begin, k_len)
+//              TC_GEMM (f, rb, cb, k_begin, k_len)  [128 x 128 tiles, tensor cores]
+constexpr int BIG_FRONT = 512;   // fronts at least this large use 128-column outer blocks
+constexpr int OUTER_NB = 128;    // outer block width (K of the outer Schur update)
 struct Launch {
   int kind;
   int level;
-  int k;          // panel start (pivot index) for PANEL/TRSM/GEMM
+  int k;          // panel start (pivot index) for PANEL/LASWP
   int64_t item0;  // first work item
   int64_t count;  // work items
   int aux = 0;    // PANEL_CL: rows per CTA (shared-memory sizing)
@@ -134,6 +142,7 @@ struct Mesh {
   int64_t front_entries = 0, vec_entries = 0, piv_entries = 0;
   double factor_flops = 0;
   double gemm_flops = 0, panel_flops = 0, trsm_flops = 0;   // per numeric factorisation
+  double outer_flops = 0;   // part of gemm_flops done by the K = 128 outer updates (tensor cores)
   // device copies
   cudaStream_t stream = nullptr;
   bool on_device = false;
@@ -182,7 +191,7 @@ struct CaseState {
 // ----- launch accounting and per-kind event timing ----------------------------
 namespace viv {
 enum KernelKind {
-  K_RES = 0, K_JAC, K_FACE, K_FRONT_ASM, K_PANEL, K_TRSM, K_GEMM, K_FWD, K_BWD, K_SPMV, K_VEC, K_NKINDS
+  K_RES = 0, K_JAC, K_FACE, K_FRONT_ASM, K_PANEL, K_TRSM, K_GEMM, K_FWD, K_BWD, K_SPMV, K_VEC, K_TCGEMM, K_NKINDS
 };
 struct Profiler {
   bool on = false;

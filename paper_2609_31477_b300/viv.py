@@ -20,7 +20,7 @@ VIV_RES, VIV_JAC = 1, 2
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_PIVOT", 5: "ERR_NEWTON",
           6: "ERR_NONFINITE", 7: "ERR_TIMEOUT", 8: "ERR_ADMISSION", 9: "ERR_STATE"}
 KINDS = ("residual", "jacobian", "face_border", "front_assemble", "panel_lu", "trsm", "schur_gemm",
-         "fwd_solve", "bwd_solve", "spmv", "vector")
+         "fwd_solve", "bwd_solve", "spmv", "vector", "tc_schur_gemm")
 KINDS_N = len(KINDS)
 FIELD = {0: "ux", 1: "uy", 2: "xx", 3: "xy", 4: "p", 5: "lx", 6: "ly", 7: "dx", 8: "dy"}
 
@@ -42,7 +42,8 @@ class MeshInfo(C.Structure):
                 ("max_front", C.c_int64), ("n_levels", C.c_int64), ("factor_flops", C.c_double),
                 ("front_entries", C.c_size_t), ("device_bytes_fp64", C.c_size_t),
                 ("device_bytes_mixed", C.c_size_t), ("n_colors", C.c_int32),
-                ("gemm_flops", C.c_double), ("panel_flops", C.c_double), ("trsm_flops", C.c_double)]
+                ("gemm_flops", C.c_double), ("panel_flops", C.c_double), ("trsm_flops", C.c_double),
+                ("outer_flops", C.c_double)]
 
 
 class Params(C.Structure):
@@ -97,6 +98,7 @@ SIGNATURES = {
     "viv_solve_rhs": (C.c_int, [_P, C.c_int, _P, _P, C.POINTER(C.c_int)]),
     "viv_update": (C.c_int, [_P]),
     "viv_lu_solve_noalloc": (C.c_int, [_P, _P, _P]),
+    "viv_tc_schur_update": (C.c_int, [_P, C.c_int, _P, C.c_int, _P, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P]),
     "viv_step": (C.c_int, [_P, C.POINTER(StepInfo)]),
     "viv_step_host": (C.c_int, [_P, _P, _P, C.POINTER(StepInfo)]),
     "viv_state_size": (C.c_int64, [_P]),
@@ -340,6 +342,18 @@ class Case:
             self.close()
         except Exception:
             pass
+
+
+def tc_schur_update(a, b, c, err, stream=None):
+    """c -= a @ b with the tcgen05 3xTF32 kernel; a, b, c are column-major
+    FP32 CUDA tensors (stride(0) == 1), err a device int32 flag."""
+    import torch
+    M, K = a.shape
+    N = b.shape[1]
+    st = stream if stream is not None else torch.cuda.current_stream()
+    ld = lambda t: t.stride(1) if t.shape[1] > 1 else max(1, t.shape[0])   # any ld >= rows for one column
+    _check(load().viv_tc_schur_update(_dev_ptr(a), ld(a), _dev_ptr(b), ld(b), _dev_ptr(c), ld(c), M, N, K,
+                                      _dev_ptr(err), C.c_void_p(st.cuda_stream)))
 
 
 def kernel_launches():
