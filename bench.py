@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--autotune", action="store_true")
     return ap.parse_args()
 
 
@@ -189,10 +190,12 @@ def run_ours(args, wl, rank, world, local):
     viv.load()
     mesh = I.viv_cylinder_mesh(wl["m"])
     u0 = I.viv_initial_velocity(mesh, 1.0, 1e-3, 1 + rank)
-    stream = torch.cuda.current_stream()
     M = viv.Mesh(mesh)
     info = M.info
     case = viv.viv_case(M, wl["Re"], wl["Ustar"], wl["dt"], u0, precision=viv.VIV_MIXED)
+    stream = case.stream           # every kernel of the case runs on its own stream
+    if args.autotune:
+        tuned = case.autotune()
     for _ in range(args.warmup):
         case.step()
 
@@ -283,16 +286,19 @@ def run_ours(args, wl, rank, world, local):
            "kernels_ms": {k: round(v[0], 3) for k, v in kern.items()},
            "profiled": {"steps": args.steps, "ms_per_step": prof_ms / args.steps,
                         "note": "second pass with a CUDA event pair around every launch (kernels_ms, roofline)"},
-           "roofline": roof, "gpu_launches": launches, "clocks": clk}
+           "roofline": roof, "gpu_launches": launches, "clocks": clk,
+           "graphs": "residual, Jacobian, factorisation and refinement sweeps replayed as CUDA graphs"}
+    if args.autotune:
+        out["autotune"] = {"big_front": tuned[0], "factor_ms": tuned[1]}
 
     if not args.no_fp64 and rank == 0:
         c64 = viv.viv_case(M, wl["Re"], wl["Ustar"], wl["dt"], u0, precision=viv.VIV_FP64)
         c64.step()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+        e0.record(c64.stream)
         i64 = [c64.step() for _ in range(args.fp64_steps)]
-        e1.record(stream)
+        e1.record(c64.stream)
         torch.cuda.synchronize()
         ms64 = e0.elapsed_time(e1)
         out["fp64_path"] = {"value": args.fp64_steps / (ms64 / 1e3), "unit": "time steps/s",

@@ -237,6 +237,20 @@ vivStatus viv_step_host(vivCase* c, const double* state_in, double* state_out, v
 /* size in doubles of the packed host state used by viv_step_host */
 int64_t viv_state_size(const vivMesh* mesh);
 
+/* ---- launch batching and tuning ------------------------------------------ */
+/* Switch the per-case CUDA graphs on (default) or off.  With graphs on, the
+ * residual, Jacobian, factorisation and each refinement sweep of viv_step are
+ * captured once per case on its stream (which must not be the legacy default
+ * stream) and replayed as single graph launches; they are re-captured when the
+ * mesh schedule changes.  Profiling (viv_profile) bypasses the graphs. */
+vivStatus viv_case_graphs(vivCase* c, int on);
+/* Project autotuner: times the numeric factorisation of the case's current
+ * Jacobian for several large-front thresholds (fronts at least this large use
+ * 128-column outer blocks whose Schur updates run on the tensor cores) and
+ * keeps the fastest schedule for the mesh.  Affects every case of the mesh;
+ * call it while no other case of the mesh is running. */
+vivStatus viv_autotune(vivCase* c, int32_t* best_big_front, double* best_ms);
+
 /* ---- instrumentation ----------------------------------------------------- */
 /* kernel launches issued by this library in this process so far */
 int64_t viv_kernel_launches(void);

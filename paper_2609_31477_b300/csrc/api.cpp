@@ -13,12 +13,13 @@
 #include "viv_internal.h"
 
 namespace viv {
-int64_t launches();
 void tc_gemm_update(const float* A, int lda, const float* B, int ldb, float* C, int ldc, int M, int N, int K,
                     int* err, cudaStream_t s);
 void lu_solve_noalloc(vivCase* c, const double* b, double* x);
 void build_mesh(Mesh& m, const vivMeshDesc* d);
 void upload_mesh(Mesh& m, cudaStream_t s);
+void build_schedule(Mesh& m, int big_front);
+void upload_work(Mesh& m, cudaStream_t s);
 
 static thread_local std::string g_err;
 void set_error(const std::string& msg) { g_err = msg; }
@@ -69,6 +70,53 @@ double read_scalar(vivCase* c, const double* dptr) {
 double norm2(vivCase* c, const double* v, int64_t n) {
   launch_norm2(v, n, c->s.partial, c->s.scal, c->stream);
   return read_scalar(c, c->s.scal);
+}
+
+void drop_graphs(vivCase* c) {
+  for (vivCase::Graph* g : {&c->g_res, &c->g_upd_res, &c->g_jac, &c->g_fac, &c->g_sinit, &c->g_sweep})
+    if (g->exec) {
+      cudaGraphExecDestroy(g->exec);
+      g->exec = nullptr;
+      g->kernels = 0;
+    }
+}
+
+// Run `body` (a fixed sequence of launches on the case stream) through a CUDA
+// graph captured on first use; plain launches while profiling, on the legacy
+// default stream, or with graphs switched off.
+template <class F>
+void run_graph(vivCase* c, vivCase::Graph& g, F&& body) {
+  if (!c->graphs || c->stream == nullptr || c->prof.on) {
+    body();
+    return;
+  }
+  // kernel arguments are captured by value: the schedule version and the BDF
+  // coefficient (BDF1 on the first step, BDF2 after) key the graphs
+  if (c->graph_version != c->mesh->m.sched_version || c->graph_c0 != c->c0) {
+    drop_graphs(c);
+    c->graph_version = c->mesh->m.sched_version;
+    c->graph_c0 = c->c0;
+  }
+  if (!g.exec) {
+    cudaGraph_t graph = nullptr;
+    const int64_t before = launches();
+    VIV_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    try {
+      body();
+    } catch (...) {
+      cudaStreamEndCapture(c->stream, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      throw;
+    }
+    VIV_CUDA(cudaStreamEndCapture(c->stream, &graph));
+    g.kernels = launches() - before;
+    count_launches(-g.kernels);   // counted when the graph runs, not when it is captured
+    cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    VIV_CUDA(e);
+  }
+  VIV_CUDA(cudaGraphLaunch(g.exec, c->stream));
+  count_launches(g.kernels);
 }
 
 void copy_in(vivCase* c, double* dst, const double* src, size_t count) {
@@ -343,6 +391,10 @@ vivStatus viv_case_create(vivMesh* mesh, const vivParams* prm, const double* u0,
     VIV_CUDA(cudaMemsetAsync(s.u_nm1, 0, 2 * n * sizeof(double), st));
     VIV_CUDA(cudaMemsetAsync(s.x_nm1, 0, 2 * n * sizeof(double), st));
     VIV_CUDA(cudaMemsetAsync(s.stats, 0, 4 * sizeof(int32_t), st));
+    if (mixed(c))
+      prepare_kernels<float>();
+    else
+      prepare_kernels<double>();
     launch_element_areas(m, s.lame, c->prm.lame_scale, s.scal + 1, st);
     VIV_CUDA(cudaStreamSynchronize(st));
   } catch (...) {
@@ -358,6 +410,7 @@ vivStatus viv_case_destroy(vivCase* c) {
   API_BEGIN
   if (c) {
     cudaStreamSynchronize(c->stream);
+    drop_graphs(c);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     delete c;
   }
@@ -475,6 +528,52 @@ vivStatus viv_solve_rhs(vivCase* c, int, const double* b, double* y, int* sweeps
   API_END
 }
 
+vivStatus viv_case_graphs(vivCase* c, int on) {
+  API_BEGIN
+  VIV_CHECK(c, VIV_ERR_ARG, "NULL case");
+  c->graphs = on != 0;
+  if (!c->graphs) drop_graphs(c);
+  API_END
+}
+
+vivStatus viv_autotune(vivCase* c, int32_t* best_big_front, double* best_ms) {
+  API_BEGIN
+  ProfBind pb_(c);
+  VIV_CHECK(c, VIV_ERR_ARG, "NULL case");
+  Mesh& m = c->mesh->m;
+  if (!c->step_open) begin_step(c);
+  assemble(c, VIV_JAC, false);
+  const int cands[] = {256, 384, 512, 768, 1024, 1 << 30};
+  cudaEvent_t e0, e1;
+  VIV_CUDA(cudaEventCreate(&e0));
+  VIV_CUDA(cudaEventCreate(&e1));
+  int best = m.big_front;
+  double best_t = 1e300;
+  for (int bf : cands) {
+    build_schedule(m, bf);
+    upload_work(m, c->stream);
+    factor(c);   // warm-up
+    VIV_CUDA(cudaEventRecord(e0, c->stream));
+    for (int r = 0; r < 2; ++r) factor(c);
+    VIV_CUDA(cudaEventRecord(e1, c->stream));
+    VIV_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    VIV_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms / 2 < best_t) {
+      best_t = ms / 2;
+      best = bf;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  build_schedule(m, best);
+  upload_work(m, c->stream);
+  c->factored = false;
+  if (best_big_front) *best_big_front = best;
+  if (best_ms) *best_ms = best_t;
+  API_END
+}
+
 vivStatus viv_lu_solve_noalloc(vivCase* c, const double* b, double* x) {
   API_BEGIN
   VIV_CHECK(c && b && x, VIV_ERR_ARG, "NULL argument");
@@ -501,6 +600,37 @@ vivStatus viv_update(vivCase* c) {
   API_END
 }
 
+// one Newton linear solve J dU = -R with FP64 refinement, through graphs:
+// init (dU = 0, r = -R, ||R||) then sweeps (LU solve, dU += d, r = -R - J dU, ||r||)
+static int refined_solve_graphs(vivCase* c) {
+  const Mesh& m = c->mesh->m;
+  CaseState& s = c->s;
+  const int64_t n = m.n_dofs;
+  const int max_sweeps = 1 + (c->prm.refine_max > 0 ? c->prm.refine_max : (mixed(c) ? 10 : 1));
+  const double tol = c->prm.refine_tol > 0 ? c->prm.refine_tol : 1e-13;
+  run_graph(c, c->g_sinit, [&] {
+    launch_scale_copy(s.mR, s.R, -1.0, n, c->stream);
+    VIV_CUDA(cudaMemsetAsync(s.dU, 0, n * sizeof(double), c->stream));
+    VIV_CUDA(cudaMemcpyAsync(s.r, s.mR, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    launch_norm2(s.mR, n, s.partial, s.scal + 2, c->stream);
+  });
+  const double nb = read_scalar(c, s.scal + 2);
+  int sweeps = 0;
+  for (;;) {
+    run_graph(c, c->g_sweep, [&] {
+      lu_solve(c, s.r, s.d);
+      launch_axpy(s.dU, s.d, 1.0, n, c->stream);
+      launch_spmv_residual(m, s.J64, s.dU, s.mR, s.r, c->stream);
+      launch_norm2(s.r, n, s.partial, s.scal + 3, c->stream);
+    });
+    ++sweeps;
+    const double nr = read_scalar(c, s.scal + 3);
+    VIV_CHECK(std::isfinite(nr), VIV_ERR_NONFINITE, "refinement residual is not finite");
+    if (sweeps >= max_sweeps || nb == 0 || nr <= tol * nb) break;
+  }
+  return sweeps;
+}
+
 static void step_impl(vivCase* c, vivStepInfo* info) {
   const Mesh& m = c->mesh->m;
   begin_step(c);
@@ -509,25 +639,42 @@ static void step_impl(vivCase* c, vivStepInfo* info) {
   double n0 = 0, nr = 0;
   int32_t st_acc[2] = {0, 0};
   for (int it = 0;; ++it) {
-    nr = assemble(c, VIV_RES, true);
+    {
+      auto res = [&] {
+        launch_residual(m, c->s, c->prm, c->c0, c->stream);
+        launch_norm2(c->s.R, m.n_dofs, c->s.partial, c->s.scal, c->stream);
+      };
+      if (it == 0)
+        run_graph(c, c->g_res, res);
+      else
+        run_graph(c, c->g_upd_res, [&] {
+          launch_update(m, c->s, c->s.dU, c->stream);
+          res();
+        });
+      nr = read_scalar(c, c->s.scal);
+    }
     if (it == 0) n0 = nr;
     VIV_CHECK(std::isfinite(nr), VIV_ERR_NONFINITE, "residual norm is not finite");
     if (nr <= tol) break;
     VIV_CHECK(it < c->prm.max_newton, VIV_ERR_NEWTON,
               "Newton did not converge in " + std::to_string(c->prm.max_newton) + " iterations (|R| = " +
                   fmt_e(nr) + ", tolerance " + fmt_e(tol) + ")");
-    assemble(c, VIV_JAC, false);
-    factor(c);
-    launch_scale_copy(c->s.mR, c->s.R, -1.0, m.n_dofs, c->stream);
-    sweeps += refined_solve(c, c->s.mR, c->s.dU);
-    int32_t stv[2];
+    run_graph(c, c->g_jac, [&] {
+      launch_jacobian<double>(m, c->s, c->prm, c->c0, c->s.J64, c->stream);
+      if (mixed(c)) launch_f64_to_f32(c->s.J32, c->s.J64, m.row_ptr[m.n_dofs], c->stream);
+    });
+    run_graph(c, c->g_fac, [&] { factor(c); });
+    c->factored = true;
+    sweeps += refined_solve_graphs(c);
+    int32_t stv[3];
     VIV_CUDA(cudaMemcpyAsync(stv, c->s.stats, sizeof(stv), cudaMemcpyDeviceToHost, c->stream));
-    launch_update(m, c->s, c->s.dU, c->stream);
     VIV_CUDA(cudaStreamSynchronize(c->stream));
+    VIV_CHECK(stv[2] == 0, VIV_ERR_TIMEOUT, "a tensor-core wait expired during the factorisation");
     st_acc[0] += stv[0];
     st_acc[1] += stv[1];
     ++iters;
   }
+  // the loop ends on a converged residual of the updated state
   c->t += c->prm.dt;
   c->nstep += 1;
   c->step_open = false;

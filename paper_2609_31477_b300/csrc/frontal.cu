@@ -661,23 +661,30 @@ __global__ void __launch_bounds__(SOLVE_THREADS) bwd_kernel(FT ft, const int32_t
 
 }  // namespace
 
+// one-time kernel attributes (dynamic shared memory limits); called before
+// any launch, including before a stream capture
+template <class T>
+void prepare_kernels() {
+  static bool done = false;
+  if (done) return;
+  if constexpr (std::is_same<T, float>::value)
+    VIV_CUDA(cudaFuncSetAttribute(tc_front_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes()));
+  VIV_CUDA(cudaFuncSetAttribute(panel_smem_kernel<T, 1, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                PANEL_SMEM_BYTES));
+  VIV_CUDA(cudaFuncSetAttribute(panel_smem_kernel<T, PANEL_CLUSTER, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                PANEL_SMEM_BYTES));
+  VIV_CUDA(cudaFuncSetAttribute(fwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX));
+  VIV_CUDA(cudaFuncSetAttribute(bwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX));
+  done = true;
+}
+template void prepare_kernels<float>();
+template void prepare_kernels<double>();
+
 template <class T>
 void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* fronts, int32_t* piv,
                     int32_t* stats, double threshold, cudaStream_t s) {
   FT ft = make_ft(m);
-  static bool attr_set = false;
-  if (!attr_set) {
-    if constexpr (std::is_same<T, float>::value)
-      VIV_CUDA(cudaFuncSetAttribute(tc_front_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)tc_smem_bytes()));
-    VIV_CUDA(cudaFuncSetAttribute(panel_smem_kernel<T, 1, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  PANEL_SMEM_BYTES));
-    VIV_CUDA(cudaFuncSetAttribute(panel_smem_kernel<T, PANEL_CLUSTER, 256>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, PANEL_SMEM_BYTES));
-    VIV_CUDA(cudaFuncSetAttribute(fwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX));
-    VIV_CUDA(cudaFuncSetAttribute(bwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX));
-    attr_set = true;
-  }
+  prepare_kernels<T>();
   VIV_CUDA(cudaMemsetAsync(stats, 0, 3 * sizeof(int32_t), s));
   const int32_t* work = m.ft.work;
   for (const Launch& L : m.sched[sizeof(T) == 8]) {
@@ -741,12 +748,7 @@ template <class T>
 void solve_fronts(const Mesh& m, const T* fronts, const int32_t* piv, const double* b, double* x, T* vec,
                   T* yv, cudaStream_t s) {
   FT ft = make_ft(m);
-  static bool attr_set = false;
-  if (!attr_set) {
-    VIV_CUDA(cudaFuncSetAttribute(fwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX));
-    VIV_CUDA(cudaFuncSetAttribute(bwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX));
-    attr_set = true;
-  }
+  prepare_kernels<T>();
   for (int l = 0; l < m.n_levels; ++l) {
     const int n = m.level_off[l + 1] - m.level_off[l];
     const size_t need = (size_t)m.level_maxm[l] * sizeof(T);

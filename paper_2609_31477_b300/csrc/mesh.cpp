@@ -162,6 +162,8 @@ int greedy_colour(const std::vector<int32_t>& items, int per, int64_t count, int
 
 }  // namespace
 
+void build_schedule(Mesh& m, int big_front);
+
 // Build every host table of the mesh; see the file header.
 void build_mesh(Mesh& m, const vivMeshDesc* d) {
   VIV_CHECK(d && d->X && d->conn && d->tags, VIV_ERR_ARG, "mesh description has NULL arrays");
@@ -572,6 +574,13 @@ void build_mesh(Mesh& m, const vivMeshDesc* d) {
     int t = ((m.level_maxm[l] / 2 + 31) / 32) * 32;
     m.level_threads[l] = std::min(1024, std::max(64, t));
   }
+  build_schedule(m, BIG_FRONT);
+}
+
+// Launch schedules of the numeric factorisation for a large-front threshold
+// (fronts of order >= big_front use 128-column outer blocks).
+void build_schedule(Mesh& m, int big_front) {
+  m.big_front = big_front;
   // launch schedules of the numeric factorisation, one per front element size.
   // Fronts of order >= BIG_FRONT are factored in 128-column outer blocks: four
   // 32-column pivot panels update only the block's own columns; the outer
@@ -615,7 +624,7 @@ void build_mesh(Mesh& m, const vivMeshDesc* d) {
       close(L);
       for (int k = 0; k < maxp; k += PANEL_NB) {
         const int k2 = (k / OUTER_NB) * OUTER_NB;
-        auto big = [&](int f) { return m.f_m[f] >= BIG_FRONT; };
+        auto big = [&](int f) { return m.f_m[f] >= big_front; };
         auto block_end = [&](int f) { return std::min(k2 + OUTER_NB, m.f_p[f]); };
         // panel kind of a front: 0 one CTA, 1 cluster, 2 global-memory fallback
         auto kind = [&](int f) {
@@ -730,6 +739,19 @@ void build_mesh(Mesh& m, const vivMeshDesc* d) {
   }
 }
 
+// (re)upload the work-item array of the schedules
+void upload_work(Mesh& m, cudaStream_t s) {
+  const size_t need = m.work.size() ? m.work.size() : 1;
+  if (!m.ft.work || m.work_cap < need) {
+    m.ft.work = m.arena.make<int32_t>(need);
+    m.work_cap = need;
+  }
+  if (!m.work.empty())
+    VIV_CUDA(cudaMemcpyAsync(m.ft.work, m.work.data(), m.work.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  VIV_CUDA(cudaStreamSynchronize(s));
+  m.sched_version += 1;
+}
+
 void upload_mesh(Mesh& m, cudaStream_t s) {
   DeviceArena& A = m.arena;
   m.d_X = A.upload(m.X, s);
@@ -765,7 +787,7 @@ void upload_mesh(Mesh& m, cudaStream_t s) {
   t.piv_off = A.upload(m.f_piv_off, s);
   t.col_nz = A.upload(m.f_col_nz, s);
   t.col_nz_off = A.upload(m.f_col_nz_off, s);
-  t.work = A.upload(m.work, s);
+  upload_work(m, s);
   VIV_CUDA(cudaStreamSynchronize(s));
 }
 

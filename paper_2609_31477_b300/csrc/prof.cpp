@@ -9,6 +9,7 @@ static std::atomic<int64_t> g_launches{0};
 thread_local Profiler* g_prof = nullptr;
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 int64_t launches() { return g_launches.load(); }
 
 void Profiler::start(int k, cudaStream_t s) {

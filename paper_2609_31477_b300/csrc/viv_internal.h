@@ -64,7 +64,7 @@ constexpr int WORK_STRIDE = 8;   // ints per work item
 // work items:  ASSEMBLE (f, c0)           PANEL* (f)              LASWP (f, c0)
 //              TRSM (f, c0, c_end, k)      GEMM (f, rb, cb, r_end, c_end, k_begin, k_len)
 //              TC_GEMM (f, rb, cb, k_begin, k_len)  [128 x 128 tiles, tensor cores]
-constexpr int BIG_FRONT = 512;   // fronts at least this large use 128-column outer blocks
+constexpr int BIG_FRONT = 512;   // default: fronts at least this large use 128-column outer blocks
 constexpr int OUTER_NB = 128;    // outer block width (K of the outer Schur update)
 struct Launch {
   int kind;
@@ -141,6 +141,9 @@ struct Mesh {
   std::vector<int32_t> level_threads;  // solve threads per front at each level
   int64_t front_entries = 0, vec_entries = 0, piv_entries = 0;
   double factor_flops = 0;
+  int big_front = 0;          // large-front threshold of the current schedules
+  size_t work_cap = 0;        // device capacity of the work-item array
+  int sched_version = 0;      // bumped whenever the schedules are rebuilt
   double gemm_flops = 0, panel_flops = 0, trsm_flops = 0;   // per numeric factorisation
   double outer_flops = 0;   // part of gemm_flops done by the K = 128 outer updates (tensor cores)
   // device copies
@@ -205,6 +208,8 @@ struct Profiler {
 };
 extern thread_local Profiler* g_prof;
 void count_launch();
+void count_launches(int64_t n);
+int64_t launches();
 struct Launched {           // wraps one kernel launch: counts it and, when profiling, times it
   cudaStream_t s;
   bool timed;
@@ -237,6 +242,16 @@ struct vivCase {
   bool have_dU = false;
   double* h_pinned = nullptr;  // pinned scalars
   viv::Profiler prof;
+  // CUDA graphs of the per-iteration phases (captured on first use; re-captured
+  // when the mesh schedule changes; not used while profiling or on stream 0)
+  struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;   // kernel launches captured in the graph (added to the counter per replay)
+  };
+  bool graphs = true;
+  int graph_version = -1;
+  double graph_c0 = 0.0;   // BDF rate coefficient baked into the captured kernel arguments
+  Graph g_res, g_upd_res, g_jac, g_fac, g_sinit, g_sweep;
 };
 
 // kernels (defined in .cu files), all launched on the case stream
@@ -254,6 +269,8 @@ void launch_spmv_residual(const Mesh& m, const double* J, const double* x, const
 void launch_axpy(double* y, const double* x, double a, int64_t n, cudaStream_t s);
 void launch_scale_copy(double* y, const double* x, double a, int64_t n, cudaStream_t s);
 void launch_f64_to_f32(float* y, const double* x, int64_t n, cudaStream_t s);
+template <class T>
+void prepare_kernels();
 template <class T>
 void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* fronts, int32_t* piv,
                     int32_t* stats, double threshold, cudaStream_t s);

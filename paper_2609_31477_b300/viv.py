@@ -102,6 +102,8 @@ SIGNATURES = {
     "viv_step": (C.c_int, [_P, C.POINTER(StepInfo)]),
     "viv_step_host": (C.c_int, [_P, _P, _P, C.POINTER(StepInfo)]),
     "viv_state_size": (C.c_int64, [_P]),
+    "viv_case_graphs": (C.c_int, [_P, C.c_int]),
+    "viv_autotune": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
     "viv_kernel_launches": (C.c_int64, []),
     "viv_profile": (C.c_int, [_P, C.c_int]),
     "viv_profile_read": (C.c_int, [_P, _P, _P]),
@@ -242,15 +244,20 @@ class Case:
     """Device state of one cylinder case and its Newton/BDF driver."""
 
     def __init__(self, mesh: Mesh, u0, rho, mu, k, dt, precision=VIV_FP64, lame_scale=1.0,
-                 newton_tol=1e-10, max_newton=25, refine_tol=0.0, refine_max=0, pivot_threshold=0.01):
+                 newton_tol=1e-10, max_newton=25, refine_tol=0.0, refine_max=0, pivot_threshold=0.01,
+                 stream=None):
         lib = load()
         self.mesh = mesh
         self.params = Params(rho, mu, k, dt, lame_scale, newton_tol, max_newton, precision, refine_tol,
                              refine_max, pivot_threshold)
         u0 = np.ascontiguousarray(u0, dtype=np.float64)
+        import torch
+        # each case owns a non-default stream (graphs cannot capture the legacy stream)
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        torch.cuda.current_stream().synchronize()
         h = C.c_void_p()
         _check(lib.viv_case_create(mesh.h, C.byref(self.params), _ptr(u0),
-                                   C.c_void_p(mesh.stream.cuda_stream), C.byref(h)))
+                                   C.c_void_p(self.stream.cuda_stream), C.byref(h)))
         self.h = h
         self.n = mesh.n_nodes
 
@@ -323,6 +330,14 @@ class Case:
         _check(_lib.viv_step_host(self.h, _ptr(state_in), _ptr(state_out), C.byref(info)))
         return info.as_dict()
 
+    def graphs(self, on=True):
+        _check(_lib.viv_case_graphs(self.h, int(on)))
+
+    def autotune(self):
+        bf, ms = C.c_int32(), C.c_double()
+        _check(_lib.viv_autotune(self.h, C.byref(bf), C.byref(ms)))
+        return bf.value, ms.value
+
     def profile(self, on=True):
         _check(_lib.viv_profile(self.h, int(on)))
 
@@ -331,6 +346,9 @@ class Case:
         cnt = np.zeros(KINDS_N, np.int64)
         _check(_lib.viv_profile_read(self.h, _ptr(ms), _ptr(cnt)))
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KINDS)}
+
+    def synchronize(self):
+        self.stream.synchronize()
 
     def close(self):
         if self.h:

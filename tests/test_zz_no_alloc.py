@@ -32,7 +32,9 @@ def test_noalloc_solve_matches_regular_solve_on_two_calls():
         ref, _ = case.solve_rhs(b)
         bd = torch.tensor(b, device="cuda")
         xd = torch.full_like(bd, float("nan"))
+        torch.cuda.synchronize()          # inputs ready before the case stream reads them
         case.lu_solve_noalloc(bd, xd)
+        torch.cuda.synchronize()          # the solve ran on the case's own stream
         x = xd.cpu().numpy()
         assert np.all(np.isfinite(x))
         assert np.linalg.norm(x - ref) <= 1e-10 * np.linalg.norm(ref)
