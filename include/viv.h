@@ -251,6 +251,48 @@ vivStatus viv_case_graphs(vivCase* c, int on);
  * call it while no other case of the mesh is running. */
 vivStatus viv_autotune(vivCase* c, int32_t* best_big_front, double* best_ms);
 
+/* ---- serving: parameter sweeps with continuous admission ------------------ */
+typedef struct vivServer vivServer;
+typedef struct {
+  vivMesh* mesh;           /* device mesh (viv_mesh_create); may be shared by requests */
+  vivParams params;
+  const double* u0;        /* n_nodes x 2 host initial velocity; copied at submit */
+  int32_t n_steps;         /* BDF steps to run */
+  double arrival_time;     /* seconds after server creation when the request arrives */
+} vivRequest;
+typedef struct {
+  int64_t id;
+  vivStatus status;        /* VIV_ERR_ADMISSION if it can never fit the budget */
+  int32_t steps_done, newton_total;
+  double t, delta[2], force[2];
+  double submit_s, admit_s, finish_s;   /* server clock, seconds */
+  double step_ms_mean, step_ms_max;
+  char message[160];       /* error text when status != VIV_OK */
+} vivResult;
+typedef struct {
+  double step_ms_p50, step_ms_p99;      /* over every completed step of every case */
+  int64_t steps, cases_done;
+  double elapsed_s;
+  int32_t peak_active, active, pending;
+  size_t peak_bytes;                    /* peak of the admitted predicted device bytes */
+} vivServerStats;
+/* A serving loop: requests arrive over time, are admitted FIFO while the
+ * predicted device bytes of the admitted cases (viv_mesh_info) stay within
+ * mem_budget and fewer than max_active cases run; each admitted case runs on
+ * its own stream and worker thread, so cases overlap on the GPU, and its
+ * memory is returned when it finishes.  A failed case reports its status and
+ * does not affect the others.  Cases allocate with cudaMalloc. */
+vivStatus viv_server_create(size_t mem_budget, int32_t max_active, vivServer** out);
+vivStatus viv_server_submit(vivServer* s, const vivRequest* req, int64_t* id);
+/* finished results not yet polled (up to max); waits up to wait_ms for one */
+vivStatus viv_server_poll(vivServer* s, vivResult* out, int32_t max, int32_t* n, int32_t wait_ms);
+/* final state of a finished case: u, x, lam (n_nodes x 2), p (n_nodes), delta (2) */
+vivStatus viv_server_state(vivServer* s, int64_t id, double* u, double* p, double* x, double* lam,
+                           double* delta);
+vivStatus viv_server_stats(vivServer* s, vivServerStats* out);
+/* runs every submitted request to completion, then frees the server */
+vivStatus viv_server_destroy(vivServer* s);
+
 /* ---- instrumentation ----------------------------------------------------- */
 /* kernel launches issued by this library in this process so far */
 int64_t viv_kernel_launches(void);

@@ -332,7 +332,21 @@ vivStatus viv_mesh_destroy(vivMesh* mesh) {
   API_END
 }
 
+static vivStatus case_create_impl(vivMesh* mesh, const vivParams* prm, const double* u0, void* stream, vivCase** out,
+                                  bool default_alloc);
+
+// cases of the serving loop allocate with cudaMalloc (library-internal symbol)
+__attribute__((visibility("hidden"))) vivStatus viv_internal_case_create(vivMesh* mesh, const vivParams* prm,
+                                                                         const double* u0, void* s, vivCase** out) {
+  return case_create_impl(mesh, prm, u0, s, out, true);
+}
+
 vivStatus viv_case_create(vivMesh* mesh, const vivParams* prm, const double* u0, void* stream, vivCase** out) {
+  return case_create_impl(mesh, prm, u0, stream, out, false);
+}
+
+static vivStatus case_create_impl(vivMesh* mesh, const vivParams* prm, const double* u0, void* stream, vivCase** out,
+                                  bool default_alloc) {
   API_BEGIN
   VIV_CHECK(mesh && prm && u0 && out, VIV_ERR_ARG, "NULL argument");
   VIV_CHECK(prm->dt > 0 && prm->rho > 0 && prm->mu > 0, VIV_ERR_ARG, "rho, mu and dt must be positive");
@@ -348,7 +362,7 @@ vivStatus viv_case_create(vivMesh* mesh, const vivParams* prm, const double* u0,
     if (c->prm.max_newton <= 0) c->prm.max_newton = 25;
     c->stream = (cudaStream_t)stream;
     c->arena.alloc = mesh->m.arena.alloc;
-    c->arena.custom = mesh->m.arena.custom;
+    c->arena.custom = mesh->m.arena.custom && !default_alloc;
     const Mesh& m = mesh->m;
     const int64_t n = m.n_nodes, nd = m.n_dofs, nnz = m.row_ptr[m.n_dofs];
     DeviceArena& A = c->arena;

@@ -66,6 +66,31 @@ class StepInfo(C.Structure):
                     delta=list(self.delta), force=list(self.force))
 
 
+class Request(C.Structure):
+    _fields_ = [("mesh", C.c_void_p), ("params", Params), ("u0", C.c_void_p), ("n_steps", C.c_int32),
+                ("arrival_time", C.c_double)]
+
+
+class Result(C.Structure):
+    _fields_ = [("id", C.c_int64), ("status", C.c_int), ("steps_done", C.c_int32), ("newton_total", C.c_int32),
+                ("t", C.c_double), ("delta", C.c_double * 2), ("force", C.c_double * 2),
+                ("submit_s", C.c_double), ("admit_s", C.c_double), ("finish_s", C.c_double),
+                ("step_ms_mean", C.c_double), ("step_ms_max", C.c_double), ("message", C.c_char * 160)]
+
+    def as_dict(self):
+        return dict(id=self.id, status=STATUS.get(self.status, self.status), steps_done=self.steps_done,
+                    newton_total=self.newton_total, t=self.t, delta=list(self.delta), force=list(self.force),
+                    submit_s=self.submit_s, admit_s=self.admit_s, finish_s=self.finish_s,
+                    step_ms_mean=self.step_ms_mean, step_ms_max=self.step_ms_max,
+                    message=self.message.decode(errors="replace"))
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("step_ms_p50", C.c_double), ("step_ms_p99", C.c_double), ("steps", C.c_int64),
+                ("cases_done", C.c_int64), ("elapsed_s", C.c_double), ("peak_active", C.c_int32),
+                ("active", C.c_int32), ("pending", C.c_int32), ("peak_bytes", C.c_size_t)]
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
@@ -104,6 +129,12 @@ SIGNATURES = {
     "viv_state_size": (C.c_int64, [_P]),
     "viv_case_graphs": (C.c_int, [_P, C.c_int]),
     "viv_autotune": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
+    "viv_server_create": (C.c_int, [C.c_size_t, C.c_int32, C.POINTER(_P)]),
+    "viv_server_submit": (C.c_int, [_P, C.POINTER(Request), C.POINTER(C.c_int64)]),
+    "viv_server_poll": (C.c_int, [_P, _P, C.c_int32, C.POINTER(C.c_int32), C.c_int32]),
+    "viv_server_state": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, _P]),
+    "viv_server_stats": (C.c_int, [_P, C.POINTER(ServerStats)]),
+    "viv_server_destroy": (C.c_int, [_P]),
     "viv_kernel_launches": (C.c_int64, []),
     "viv_profile": (C.c_int, [_P, C.c_int]),
     "viv_profile_read": (C.c_int, [_P, _P, _P]),
@@ -353,6 +384,64 @@ class Case:
     def close(self):
         if self.h:
             _lib.viv_case_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Serving loop of the library (viv_server_*): continuous admission of
+    cases by predicted device memory, concurrent cases on their own streams."""
+
+    def __init__(self, mem_budget_bytes, max_active=8):
+        lib = load()
+        h = C.c_void_p()
+        _check(lib.viv_server_create(int(mem_budget_bytes), int(max_active), C.byref(h)))
+        self.h = h
+        self._keep = []
+
+    def submit(self, mesh: Mesh, u0, Re, Ustar, dt, n_steps, arrival_time=0.0, precision=VIV_MIXED,
+               U_inf=1.0, D=1.0, rho=1.0, newton_tol=1e-10, max_newton=25):
+        mu = rho * U_inf * D / Re
+        prm = Params(rho, mu, stiffness(rho, U_inf, Ustar), dt, 1.0, newton_tol, max_newton, precision, 0.0, 0,
+                     0.01)
+        u0 = np.ascontiguousarray(u0, dtype=np.float64)
+        req = Request(mesh.h.value, prm, u0.ctypes.data, int(n_steps), float(arrival_time))
+        rid = C.c_int64()
+        _check(_lib.viv_server_submit(self.h, C.byref(req), C.byref(rid)))
+        return rid.value
+
+    def poll(self, max_results=64, wait_ms=0):
+        buf = (Result * max_results)()
+        n = C.c_int32()
+        _check(_lib.viv_server_poll(self.h, buf, max_results, C.byref(n), int(wait_ms)))
+        return [buf[i].as_dict() for i in range(n.value)]
+
+    def state(self, rid, n_nodes):
+        u, p, x, lam, d = (np.empty((n_nodes, 2)), np.empty(n_nodes), np.empty((n_nodes, 2)),
+                           np.empty((n_nodes, 2)), np.empty(2))
+        _check(_lib.viv_server_state(self.h, rid, _ptr(u), _ptr(p), _ptr(x), _ptr(lam), _ptr(d)))
+        return dict(u=u, p=p, x=x, lam=lam, delta=d)
+
+    def stats(self):
+        st = ServerStats()
+        _check(_lib.viv_server_stats(self.h, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def wait_all(self, count, timeout_s=600.0):
+        import time
+        out, t0 = [], time.time()
+        while len(out) < count and time.time() - t0 < timeout_s:
+            out += self.poll(64, 200)
+        return out
+
+    def close(self):
+        if self.h:
+            _lib.viv_server_destroy(self.h)
             self.h = None
 
     def __del__(self):
