@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--sweep-cases", type=int, default=16)
+    ap.add_argument("--sweep-steps", type=int, default=10)
     return ap.parse_args()
 
 
@@ -159,6 +162,44 @@ def oracle_sample(wl, newton_iters):
 
 
 # ---------------------------------------------------------------------------------
+def run_sweep(viv, I, n_cases, n_steps, seed=7):
+    """Served parameter sweep (a sample of the 64-case, 200-step sweep): cases
+    with 2k-20k quads, Re ~ U[100, 300], U* log-uniform in [4, 20], Poisson
+    arrivals, a 24 GB device budget; every case runs n_steps BDF steps."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    ms_set = (14, 22, 30, 38, 43)                      # O-grid refinements: 2.1k .. 19.9k quads
+    meshes, dev = {}, {}
+    cases = []
+    for k in range(n_cases):
+        quads = rng.uniform(2000, 20000)
+        m = min(ms_set, key=lambda v: abs(1552 * (v / 12) ** 2 - quads))
+        Re = rng.uniform(100, 300)
+        Us = float(np.exp(rng.uniform(np.log(4), np.log(20))))
+        cases.append((m, Re, Us))
+    for m, _, _ in cases:
+        if m not in meshes:
+            meshes[m] = I.viv_cylinder_mesh(m)
+            dev[m] = viv.Mesh(meshes[m])
+    arrivals = np.cumsum(rng.exponential(0.05, size=n_cases))
+    srv = viv.Server(24 << 30, max_active=16)
+    for k, (m, Re, Us) in enumerate(cases):
+        srv.submit(dev[m], I.viv_initial_velocity(meshes[m], 1.0, 1e-3, 100 + k), Re=Re, Ustar=Us, dt=0.02,
+                   n_steps=n_steps, arrival_time=float(arrivals[k]))
+    res = srv.wait_all(n_cases, timeout_s=900)
+    st = srv.stats()
+    srv.close()
+    ok = sum(r["status"] == "OK" for r in res)
+    last = max(r["finish_s"] for r in res) if res else 0.0
+    return {"cases": n_cases, "ok": ok, "steps_per_case": n_steps, "step_ms_p50": st["step_ms_p50"],
+            "step_ms_p99": st["step_ms_p99"], "steps": st["steps"], "elapsed_s": last,
+            "steps_per_s": st["steps"] / last if last else None,
+            "cases_per_hour_at_200_steps": 3600.0 * ok / last * n_steps / 200.0 if last else None,
+            "peak_active": st["peak_active"], "peak_gb": st["peak_bytes"] / 1e9,
+            "quads": sorted({int(1552 * (m / 12) ** 2) for m, _, _ in cases}),
+            "sample": f"{n_cases} of 64 cases, {n_steps} of 200 steps each; cases/hour extrapolated"}
+
+
 def run_reference(args, wl, rank):
     if rank != 0:
         return
@@ -330,6 +371,9 @@ def run_ours(args, wl, rank, world, local):
         barrier()
         out["e2e"] = {"value": world * args.steps / el, "unit": "time steps/s",
                       "h2d_bytes_per_step": 8 * n_st, "d2h_bytes_per_step": 8 * n_st}
+
+    if rank == 0 and not args.no_sweep:
+        out["sweep"] = run_sweep(viv, I, args.sweep_cases, args.sweep_steps)
 
     if rank == 0 and not args.no_cpu_baseline:
         v, desc, secs = oracle_sample(wl, newton)
