@@ -133,7 +133,7 @@ typedef struct {
 } vivStepInfo;
 
 /* ---- mesh: numbering, sparsity, nested dissection, symbolic factorisation
- * (Section 4.3: the pattern is fixed because ALE moves nodes, not
+ * (Section 6: the pattern is fixed because ALE moves nodes, not
  * connectivity, so analysis runs once per mesh) --------------------------- */
 vivStatus viv_mesh_create(const vivMeshDesc* desc, const vivAllocator* alloc, void* stream,
                           vivMesh** out);

@@ -1,5 +1,5 @@
 // Multifrontal LU of the Jacobian on the GPU (replaces the sparse direct
-// solver of Section 4.4).  Fronts are dense column-major blocks in one pool;
+// solver of Section 4.3).  Fronts are dense column-major blocks in one pool;
 // each tree level is processed by batched launches over all of its fronts:
 //
 //   assemble : zero the front, place the original CSR entries, extend-add the

@@ -1,6 +1,6 @@
-// Mesh analysis, run once per mesh on the host (Section 4.3: ALE moves nodes,
-// never connectivity, so numbering, sparsity and the symbolic factorisation
-// are computed once and reused by every Newton iteration of every step).
+// Mesh analysis, run once per mesh on the host (Section 6, scaling study: the
+// mesh and therefore the nonzero pattern never change, so the symbolic
+// factorisation is computed once and reused by every Newton iteration).
 //
 //  1. unknown numbering (node-major inside nested-dissection supernodes)
 //  2. CSR pattern of the Jacobian with the structural zeros of the block
