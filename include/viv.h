@@ -108,8 +108,10 @@ typedef struct {
  * k: spring stiffness of Eq. solid_balance; dt: constant time step;
  * lame_scale: lambda_s = mu_s = lame_scale * min|K_0| / |K_0| per element
  *   (reference areas; 0 means 1);
- * newton_tol: absolute ||NL||_2 stop; refine_tol: relative residual of the
- * refined linear solve; refine_max: refinement sweeps (mixed path). */
+ * newton_tol: absolute ||NL||_2 stop; refine_tol: relative residual at which
+ * the refinement of a Newton correction stops (0: 1e-8; it also stops once the
+ * residual is below newton_tol / 10); refine_max: refinement sweeps (0: 10 on
+ * the mixed path, 1 on the FP64 path).  viv_solve_rhs refines to 1e-13. */
 typedef struct {
   double rho, mu, k, dt;
   double lame_scale;

@@ -4,6 +4,7 @@
 // on its stream; the host only reads back scalars (norms) to steer Newton.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -621,7 +622,11 @@ static int refined_solve_graphs(vivCase* c) {
   CaseState& s = c->s;
   const int64_t n = m.n_dofs;
   const int max_sweeps = 1 + (c->prm.refine_max > 0 ? c->prm.refine_max : (mixed(c) ? 10 : 1));
-  const double tol = c->prm.refine_tol > 0 ? c->prm.refine_tol : 1e-13;
+  // Newton needs the correction only as accurately as the step can use it: stop
+  // when the linear residual is below refine_tol relative (default 1e-8), or
+  // below a tenth of the Newton tolerance in absolute terms, whichever is looser
+  const double tol = c->prm.refine_tol > 0 ? c->prm.refine_tol : 1e-8;
+  const double abs_tol = 0.1 * c->prm.newton_tol;
   run_graph(c, c->g_sinit, [&] {
     launch_scale_copy(s.mR, s.R, -1.0, n, c->stream);
     VIV_CUDA(cudaMemsetAsync(s.dU, 0, n * sizeof(double), c->stream));
@@ -640,7 +645,7 @@ static int refined_solve_graphs(vivCase* c) {
     ++sweeps;
     const double nr = read_scalar(c, s.scal + 3);
     VIV_CHECK(std::isfinite(nr), VIV_ERR_NONFINITE, "refinement residual is not finite");
-    if (sweeps >= max_sweeps || nb == 0 || nr <= tol * nb) break;
+    if (sweeps >= max_sweeps || nb == 0 || nr <= std::max(tol * nb, abs_tol)) break;
   }
   return sweeps;
 }
