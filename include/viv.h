@@ -121,6 +121,10 @@ typedef struct {
   double refine_tol;
   int32_t refine_max;
   double pivot_threshold;  /* threshold u of partial pivoting in fronts (0.01) */
+  int32_t source;          /* 0: none (the physical problem); 1: steady manufactured
+                              solution of Section 5.1 on a mesh deformed by
+                              X + source_amp sin(pi X) sin(pi Y) (1, 1), for verification */
+  double source_amp;
 } vivParams;
 
 typedef struct {

@@ -30,7 +30,7 @@ namespace {
 constexpr int EPB = 8;              // elements per block
 constexpr int ROWS = 40;            // element rows: 18 u, 4 p, 18 x
 constexpr int ASM_THREADS = EPB * ROWS;
-constexpr int QP_DATA = 54;         // per quadrature point values kept in shared memory
+constexpr int QP_DATA = 59;         // per quadrature point values kept in shared memory
 
 __device__ __forceinline__ void lag2(double s, double* L, double* dL) {
   L[0] = (1 - s) * (1 - 2 * s);
@@ -83,11 +83,38 @@ struct ElemNodes {
 // qp data layout (offsets into a QP_DATA-sized record)
 enum {
   Q_WDET = 0, Q_G = 1, Q_UW = 19, Q_L = 21, Q_SIG = 25, Q_INERT = 28, Q_DIV = 30,
-  Q_WDET0 = 31, Q_G0 = 32, Q_EPS = 50, Q_TR = 53
+  Q_WDET0 = 31, Q_G0 = 32, Q_EPS = 50, Q_TR = 53,
+  Q_FU = 54, Q_GP = 56, Q_FX = 57   // manufactured source terms (zero unless enabled)
 };
 
+// Manufactured source of the steady 2-D test (Section 5.1's velocity and
+// pressure without their time factors, on a mesh deformed by
+// chi(X) = X + amp sin(pi X) sin(pi Y) (1, 1), lambda_s = mu_s = 1):
+//   f_u = rho (u.grad) u + grad p - mu (lap u + grad div u)   at x = chi(X_q)
+//   g_p = div u                                               at x = chi(X_q)
+//   f_x = -div_X sigma_s(chi) = amp (4 pi^2 s - 2 pi^2 cos pi X cos pi Y) (1, 1)
+__device__ void mms_source(double X, double Y, double amp, double rho, double mu, double* fu, double* gp,
+                           double* fx) {
+  const double pi = 3.14159265358979323846;
+  const double s = sin(pi * X) * sin(pi * Y);
+  const double x = X + amp * s, y = Y + amp * s;
+  const double sx = sin(pi * x), cx = cos(pi * x), sy = sin(pi * y), cy = cos(pi * y);
+  const double u1 = sx * cy, u2 = sx * sy;
+  const double u1x = pi * cx * cy, u1y = -pi * sx * sy, u2x = pi * cx * sy, u2y = pi * sx * cy;
+  const double lap1 = -2 * pi * pi * sx * cy, lap2 = -2 * pi * pi * sx * sy;
+  const double gd1 = -pi * pi * sx * cy + pi * pi * cx * cy, gd2 = -pi * pi * cx * sy - pi * pi * sx * sy;
+  const double px = -pi * sx * cy, py = -pi * cx * sy;
+  fu[0] = rho * (u1 * u1x + u2 * u1y) + px - mu * (lap1 + gd1);
+  fu[1] = rho * (u1 * u2x + u2 * u2y) + py - mu * (lap2 + gd2);
+  *gp = u1x + u2y;
+  const double f = amp * (4 * pi * pi * s - 2 * pi * pi * cos(pi * X) * cos(pi * Y));
+  fx[0] = f;
+  fx[1] = f;
+}
+
 template <class T>
-__device__ void qp_compute(const Tables<T>& tb, const ElemNodes<T>& en, int q, T rho, T mu, T* out) {
+__device__ void qp_compute(const Tables<T>& tb, const ElemNodes<T>& en, int q, T rho, T mu, int source,
+                           double amp, T* out) {
   // current configuration
   T J00 = 0, J01 = 0, J10 = 0, J11 = 0;
   T K00 = 0, K01 = 0, K10 = 0, K11 = 0;   // reference
@@ -143,6 +170,21 @@ __device__ void qp_compute(const Tables<T>& tb, const ElemNodes<T>& en, int q, T
   T e00 = F00, e11 = F11, e01 = T(0.5) * (F01 + F10);
   out[Q_EPS] = e00; out[Q_EPS + 1] = e01; out[Q_EPS + 2] = e11;
   out[Q_TR] = e00 + e11;
+  out[Q_FU] = out[Q_FU + 1] = out[Q_GP] = out[Q_FX] = out[Q_FX + 1] = T(0);
+  if (source == 1) {
+    double Xq = 0, Yq = 0;
+    for (int a = 0; a < 9; ++a) {
+      Xq += (double)tb.N[q][a] * (double)en.X[a][0];
+      Yq += (double)tb.N[q][a] * (double)en.X[a][1];
+    }
+    double fu[2], gp, fx[2];
+    mms_source(Xq, Yq, amp, (double)rho, (double)mu, fu, &gp, fx);
+    out[Q_FU] = (T)fu[0];
+    out[Q_FU + 1] = (T)fu[1];
+    out[Q_GP] = (T)gp;
+    out[Q_FX] = tb.W[q] * det0 * (T)fx[0];   // integrated over the reference element
+    out[Q_FX + 1] = tb.W[q] * det0 * (T)fx[1];
+  }
 }
 
 template <class T>
@@ -176,6 +218,8 @@ struct AsmArgs {
   const int32_t* node_dof;
   const int32_t* e2nz;
   double c0, rho, mu;
+  int source;        // 0 none, 1 the steady manufactured solution
+  double source_amp;
 };
 
 template <class T, bool JAC>
@@ -190,7 +234,7 @@ __global__ void __launch_bounds__(ASM_THREADS) element_kernel(AsmArgs A, double*
   const int e = live ? A.elems[gi] : 0;
   if (live) load_element<T>(A.conn, A.X, A.x, A.u, A.p, A.hu, A.hx, A.lame, A.c0, e, t, en[le]);
   __syncthreads();
-  if (live && t < 9) qp_compute<T>(tb, en[le], t, (T)A.rho, (T)A.mu, qd[le][t]);
+  if (live && t < 9) qp_compute<T>(tb, en[le], t, (T)A.rho, (T)A.mu, A.source, A.source_amp, qd[le][t]);
   __syncthreads();
   if (!live) return;
   const int* cn = A.conn + e * 9;
@@ -206,7 +250,7 @@ __global__ void __launch_bounds__(ASM_THREADS) element_kernel(AsmArgs A, double*
         T ga0 = Q[Q_G + 2 * a], ga1 = Q[Q_G + 2 * a + 1];
         T s0 = i == 0 ? Q[Q_SIG + 0] : Q[Q_SIG + 1];
         T s1 = i == 0 ? Q[Q_SIG + 1] : Q[Q_SIG + 2];
-        acc += Q[Q_WDET] * (tb.N[q][a] * Q[Q_INERT + i] + ga0 * s0 + ga1 * s1);
+        acc += Q[Q_WDET] * (tb.N[q][a] * (Q[Q_INERT + i] - Q[Q_FU + i]) + ga0 * s0 + ga1 * s1);
       }
       R[row] += (double)acc;
       return;
@@ -228,7 +272,7 @@ __global__ void __launch_bounds__(ASM_THREADS) element_kernel(AsmArgs A, double*
         const T si0 = i == 0 ? Q[Q_SIG + 0] : Q[Q_SIG + 1];
         const T si1 = i == 0 ? Q[Q_SIG + 1] : Q[Q_SIG + 2];
         const T sig_gb = si0 * gb0 + si1 * gb1;
-        const T rai = Na * Q[Q_INERT + i] + ga0 * si0 + ga1 * si1;
+        const T rai = Na * (Q[Q_INERT + i] - Q[Q_FU + i]) + ga0 * si0 + ga1 * si1;
         const T base = rho * Na * (c0 * Nb + uwg);
         for (int k = 0; k < 2; ++k) {
           const T Lik = k == 0 ? Li0 : Li1;
@@ -265,7 +309,7 @@ __global__ void __launch_bounds__(ASM_THREADS) element_kernel(AsmArgs A, double*
     if (row < 0) return;
     if (!JAC) {
       T acc = 0;
-      for (int q = 0; q < 9; ++q) acc -= qd[le][q][Q_WDET] * tb.M[q][c] * qd[le][q][Q_DIV];
+      for (int q = 0; q < 9; ++q) acc -= qd[le][q][Q_WDET] * tb.M[q][c] * (qd[le][q][Q_DIV] - qd[le][q][Q_GP]);
       R[row] += (double)acc;
       return;
     }
@@ -280,7 +324,7 @@ __global__ void __launch_bounds__(ASM_THREADS) element_kernel(AsmArgs A, double*
           const T gbk = k == 0 ? gb0 : gb1;
           au[k] -= wm * gbk;
           const T Lg = Q[Q_L + k] * gb0 + Q[Q_L + 2 + k] * gb1;   // sum_i L_ik g_b,i
-          ax[k] += wm * (Lg - Q[Q_DIV] * gbk);
+          ax[k] += wm * (Lg - (Q[Q_DIV] - Q[Q_GP]) * gbk);
         }
       }
       for (int k = 0; k < 2; ++k) {
@@ -303,7 +347,7 @@ __global__ void __launch_bounds__(ASM_THREADS) element_kernel(AsmArgs A, double*
         T gai = i == 0 ? ga0 : ga1;
         T e0 = i == 0 ? Q[Q_EPS] : Q[Q_EPS + 1];
         T e1 = i == 0 ? Q[Q_EPS + 1] : Q[Q_EPS + 2];
-        acc += Q[Q_WDET0] * (gai * Q[Q_TR] + 2 * (ga0 * e0 + ga1 * e1));
+        acc += Q[Q_WDET0] * (gai * Q[Q_TR] + 2 * (ga0 * e0 + ga1 * e1)) - tb.N[q][a] * Q[Q_FX + i];
       }
       R[row] += (double)acc;
       return;
@@ -537,6 +581,8 @@ static void run_assembly(const Mesh& m, const CaseState& st, const vivParams& pr
   A.c0 = c0;
   A.rho = prm.rho;
   A.mu = prm.mu;
+  A.source = prm.source;
+  A.source_amp = prm.source_amp;
   int ncol = (int)m.color_off.size() - 1;
   for (int c = 0; c < ncol; ++c) {
     A.elems = m.d_color_elems + m.color_off[c];
