@@ -125,7 +125,12 @@ typedef struct {
                               solution of Section 5.1 on a mesh deformed by
                               X + source_amp sin(pi X) sin(pi Y) (1, 1), for verification */
   double source_amp;
+  int32_t pivoting;        /* VIV_PIVOT_THRESHOLD (0): threshold partial pivoting over all
+                              fully summed rows of a front; VIV_PIVOT_WINDOW (1): partial
+                              pivoting inside each 32 x 32 diagonal block only (faster
+                              panels; the refinement recovers the accuracy) */
 } vivParams;
+enum { VIV_PIVOT_THRESHOLD = 0, VIV_PIVOT_WINDOW = 1 };
 
 typedef struct {
   int32_t newton_iters;    /* Jacobian factorisations this step */

@@ -170,10 +170,11 @@ double assemble(vivCase* c, int what, bool want_norm) {
 void factor(vivCase* c) {
   const Mesh& m = c->mesh->m;
   double thr = c->prm.pivot_threshold > 0 ? c->prm.pivot_threshold : 0.01;
+  const bool win = c->prm.pivoting == VIV_PIVOT_WINDOW;
   if (mixed(c))
-    factor_numeric<float>(m, nullptr, c->s.J32, (float*)c->s.fronts, c->s.piv, c->s.stats, thr, c->stream);
+    factor_numeric<float>(m, nullptr, c->s.J32, (float*)c->s.fronts, c->s.piv, c->s.stats, thr, win, c->stream);
   else
-    factor_numeric<double>(m, c->s.J64, nullptr, (double*)c->s.fronts, c->s.piv, c->s.stats, thr, c->stream);
+    factor_numeric<double>(m, c->s.J64, nullptr, (double*)c->s.fronts, c->s.piv, c->s.stats, thr, win, c->stream);
   c->factored = true;
 }
 
@@ -352,6 +353,8 @@ static vivStatus case_create_impl(vivMesh* mesh, const vivParams* prm, const dou
   VIV_CHECK(mesh && prm && u0 && out, VIV_ERR_ARG, "NULL argument");
   VIV_CHECK(prm->dt > 0 && prm->rho > 0 && prm->mu > 0, VIV_ERR_ARG, "rho, mu and dt must be positive");
   VIV_CHECK(prm->precision == VIV_FP64 || prm->precision == VIV_MIXED, VIV_ERR_ARG, "unknown precision");
+  VIV_CHECK(prm->pivoting == VIV_PIVOT_THRESHOLD || prm->pivoting == VIV_PIVOT_WINDOW, VIV_ERR_ARG,
+            "unknown pivoting");
   VIV_CHECK(mesh->m.on_device, VIV_ERR_STATE, "mesh was analysed on the host only");
   *out = nullptr;
   vivCase* c = new vivCase();

@@ -392,6 +392,151 @@ __global__ void __launch_bounds__(NT)
   grp.sync();   // no CTA leaves while another may still read its shared memory
 }
 
+// ---- windowed pivoting ---------------------------------------------------------
+// Pivots of a 32-column step are chosen inside the 32 x 32 diagonal block only
+// (partial pivoting within the window, a counted perturbation when the window
+// has no nonzero candidate).  The diagonal block is factored by one warp; the
+// rows below (L21 = A21 U11^{-1}) and the columns to the right
+// (U12 = L11^{-1} P A12) then need no cross-CTA reduction.
+template <class T>
+__global__ void __launch_bounds__(32) diag_lu_kernel(FT ft, const int32_t* work, int k, T* pool, int32_t* piv,
+                                                     int32_t* stats) {
+  const int f = work[WORK_STRIDE * blockIdx.x];
+  const int m = ft.m[f], p = ft.p[f];
+  const int nbe = min(PANEL_NB, p - k);
+  const int lane = threadIdx.x;
+  T* F = pool + ft.off[f];
+  __shared__ T s_row[PANEL_NB];
+  T a[PANEL_NB];
+#pragma unroll
+  for (int c = 0; c < PANEL_NB; ++c) a[c] = (lane < nbe && c < nbe) ? F[(int64_t)(k + c) * m + k + lane] : T(0);
+  T bmax = 0;   // largest entry of the block, the perturbation scale
+#pragma unroll
+  for (int c = 0; c < PANEL_NB; ++c) bmax = fmax(bmax, fabs(a[c]));
+  for (int o = 16; o > 0; o >>= 1) bmax = fmax(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+  int mypiv = lane;
+#pragma unroll
+  for (int jj = 0; jj < PANEL_NB; ++jj) {
+    if (jj < nbe) {
+      T v = (lane >= jj && lane < nbe) ? fabs(a[jj]) : T(-1);
+      int r = lane;
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int orr = __shfl_xor_sync(0xffffffffu, r, o);
+        if (ov > v || (ov == v && orr < r)) {
+          v = ov;
+          r = orr;
+        }
+      }
+      if (v <= 0) r = jj;   // empty window column: perturb the diagonal below
+      // interchange rows jj and r (lanes) in registers
+#pragma unroll
+      for (int c = 0; c < PANEL_NB; ++c) {
+        const T vr = __shfl_sync(0xffffffffu, a[c], r);
+        const T vj = __shfl_sync(0xffffffffu, a[c], jj);
+        if (lane == jj) a[c] = vr;
+        else if (lane == r) a[c] = vj;
+      }
+      if (lane == jj) {
+        mypiv = r;
+        if (v <= 0) {
+          a[jj] = sqrt(Eps<T>::v) * (bmax > 0 ? bmax : T(1));
+          atomicAdd(&stats[0], 1);
+        }
+#pragma unroll
+        for (int c = 0; c < PANEL_NB; ++c) s_row[c] = a[c];
+      }
+      __syncwarp();
+      if (lane > jj && lane < nbe) {
+        const T l = a[jj] / s_row[jj];
+        a[jj] = l;
+#pragma unroll
+        for (int c = jj + 1; c < PANEL_NB; ++c) a[c] -= l * s_row[c];
+      }
+      __syncwarp();
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < PANEL_NB; ++c)
+    if (lane < nbe && c < nbe) F[(int64_t)(k + c) * m + k + lane] = a[c];
+  if (lane < nbe) piv[ft.piv_off[f] + k + lane] = k + mypiv;
+}
+
+// One launch, two kinds of items.  Kind 0 (f, r0): rows [r0, r0 + 256) of the
+// panel below the diagonal block: L21 = A21 U11^{-1}.  Kind 1 (f, c0, c_end):
+// columns [c0, c0 + 256) outside the panel: the block's row permutation and,
+// for columns in [k + nbe, c_end), U12 = L11^{-1} P A12.
+template <class T>
+__global__ void __launch_bounds__(WINDOW_THREADS) window_kernel(FT ft, const int32_t* work, int k, T* pool,
+                                                     const int32_t* piv, int32_t* stats, T thresh) {
+  const int32_t* it = work + WORK_STRIDE * blockIdx.x;
+  const int f = it[1];
+  const int m = ft.m[f], p = ft.p[f];
+  const int nbe = min(PANEL_NB, p - k);
+  T* F = pool + ft.off[f];
+  __shared__ T D[PANEL_NB][PANEL_NB + 1];   // the factored diagonal block (L11 \ U11)
+  __shared__ int s_src[PANEL_NB];
+  for (int e = threadIdx.x; e < PANEL_NB * PANEL_NB; e += blockDim.x) {
+    const int i = e % PANEL_NB, c = e / PANEL_NB;
+    D[i][c] = (i < nbe && c < nbe) ? F[(int64_t)(k + c) * m + k + i] : T(0);
+  }
+  if (threadIdx.x == 0) {
+    // net permutation of the block rows: new row i takes old row s_src[i]
+    for (int i = 0; i < PANEL_NB; ++i) s_src[i] = i;
+    const int32_t* pv = piv + ft.piv_off[f];
+    for (int jj = 0; jj < nbe; ++jj) {
+      const int r = pv[k + jj] - k;
+      const int tmp = s_src[jj];
+      s_src[jj] = s_src[r];
+      s_src[r] = tmp;
+    }
+  }
+  __syncthreads();
+  if (it[0] == 0) {
+    const int g = it[2] + threadIdx.x;
+    const bool live = g < m;
+    bool big = false;
+    if (live) {
+      T x[PANEL_NB];
+#pragma unroll
+      for (int c = 0; c < PANEL_NB; ++c) x[c] = c < nbe ? F[(int64_t)(k + c) * m + g] : T(0);
+#pragma unroll
+      for (int c = 0; c < PANEL_NB; ++c) {
+        if (c < nbe) {
+          x[c] /= D[c][c];
+          big = big || fabs(x[c]) * thresh > T(1);
+#pragma unroll
+          for (int c2 = c + 1; c2 < PANEL_NB; ++c2) x[c2] -= x[c] * D[c][c2];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < PANEL_NB; ++c)
+        if (c < nbe) F[(int64_t)(k + c) * m + g] = x[c];
+    }
+    // a multiplier above 1/threshold: the window pivot missed the threshold test
+    // that pivoting over all fully summed rows would have applied
+    if (__syncthreads_or(big) && threadIdx.x == 0) atomicAdd(&stats[1], 1);
+  } else {
+    const int c = it[2] + threadIdx.x, c_end = it[3];
+    if (c >= m || (c >= k && c < k + nbe)) return;
+    T* col = F + (int64_t)c * m;
+    T x[PANEL_NB];
+#pragma unroll
+    for (int i = 0; i < PANEL_NB; ++i) x[i] = i < nbe ? col[k + s_src[i]] : T(0);
+    if (c >= k + nbe && c < c_end) {
+#pragma unroll
+      for (int l = 0; l < PANEL_NB - 1; ++l) {
+        const T xl = x[l];
+#pragma unroll
+        for (int i = l + 1; i < PANEL_NB; ++i) x[i] -= D[i][l] * xl;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < PANEL_NB; ++i)
+      if (i < nbe) col[k + i] = x[i];
+  }
+}
+
 // row interchanges of a cluster panel applied to the columns outside it
 template <class T>
 __global__ void laswp_kernel(FT ft, const int32_t* work, int k, T* pool, const int32_t* piv) {
@@ -682,15 +827,16 @@ template void prepare_kernels<double>();
 
 template <class T>
 void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* fronts, int32_t* piv,
-                    int32_t* stats, double threshold, cudaStream_t s) {
+                    int32_t* stats, double threshold, bool window, cudaStream_t s) {
   FT ft = make_ft(m);
   prepare_kernels<T>();
   VIV_CUDA(cudaMemsetAsync(stats, 0, 3 * sizeof(int32_t), s));
   const int32_t* work = m.ft.work;
-  for (const Launch& L : m.sched[sizeof(T) == 8]) {
+  for (const Launch& L : m.sched[(sizeof(T) == 8) + 2 * (window ? 1 : 0)]) {
     const int32_t* w = work + (int64_t)WORK_STRIDE * L.item0;
     const unsigned grid = (unsigned)L.count;
-    static const int kk[8] = {K_FRONT_ASM, K_PANEL, K_TRSM, K_GEMM, K_PANEL, K_TRSM, K_PANEL, K_TCGEMM};
+    static const int kk[10] = {K_FRONT_ASM, K_PANEL,  K_TRSM,  K_GEMM,  K_PANEL,
+                               K_TRSM,      K_PANEL,  K_TCGEMM, K_PANEL, K_TRSM};
     Launched LL(kk[L.kind], s);
     switch (L.kind) {
       case L_ASSEMBLE:
@@ -736,6 +882,12 @@ void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* front
                                     (T)threshold));
         break;
       }
+      case L_DIAG:
+        diag_lu_kernel<T><<<grid, 32, 0, s>>>(ft, w, L.k, fronts, piv, stats);
+        break;
+      case L_WINDOW:
+        window_kernel<T><<<grid, WINDOW_THREADS, 0, s>>>(ft, w, L.k, fronts, piv, stats, (T)threshold);
+        break;
       case L_LASWP:
         laswp_kernel<T><<<grid, LASWP_COLS, 0, s>>>(ft, w, L.k, fronts, piv);
         break;
@@ -769,9 +921,9 @@ void solve_fronts(const Mesh& m, const T* fronts, const int32_t* piv, const doub
 }
 
 template void factor_numeric<double>(const Mesh&, const double*, const float*, double*, int32_t*, int32_t*,
-                                     double, cudaStream_t);
+                                     double, bool, cudaStream_t);
 template void factor_numeric<float>(const Mesh&, const double*, const float*, float*, int32_t*, int32_t*,
-                                    double, cudaStream_t);
+                                    double, bool, cudaStream_t);
 template void solve_fronts<double>(const Mesh&, const double*, const int32_t*, const double*, double*, double*,
                                    double*, cudaStream_t);
 template void solve_fronts<float>(const Mesh&, const float*, const int32_t*, const double*, double*, float*,

@@ -597,11 +597,13 @@ void build_schedule(Mesh& m, int big_front) {
     for (; n < WORK_STRIDE; ++n) m.work.push_back(0);
   };
   auto items = [&]() { return (int64_t)m.work.size() / WORK_STRIDE; };
-  for (int prec = 0; prec < 2; ++prec) {
-    const bool count = prec == 0;
+  for (int var = 0; var < 4; ++var) {
+    const int prec = var & 1;          // FP64 fronts
+    const bool window = var >= 2;      // pivots restricted to the diagonal block
+    const bool count = var == 0;
     const int esz = prec ? 8 : 4;
     const int rows_cta = PANEL_SMEM_BYTES / (PANEL_NB * esz);   // panel rows one CTA holds
-    std::vector<Launch>& sched = m.sched[prec];
+    std::vector<Launch>& sched = m.sched[var];
     sched.clear();
     auto open = [&](int kind, int l, int k) { return Launch{kind, l, k, items(), 0}; };
     auto close = [&](Launch L) {
@@ -633,7 +635,28 @@ void build_schedule(Mesh& m, int big_front) {
           if ((rows + PANEL_CLUSTER - 1) / PANEL_CLUSTER <= rows_cta) return 1;
           return 2;
         };
-        for (int pk = 0; pk < 2; ++pk) {
+        if (window) {
+          // one warp per front factors the diagonal block; then, in one launch,
+          // the rows below it (L21) and the columns outside the panel (row
+          // permutation everywhere, U12 inside the block's column range)
+          Launch D = open(L_DIAG, l, k);
+          for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
+            int f = m.level_fronts[q];
+            if (m.f_p[f] > k) push({f});
+          }
+          close(D);
+          Launch W = open(L_WINDOW, l, k);
+          for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
+            int f = m.level_fronts[q];
+            if (m.f_p[f] <= k) continue;
+            const int nbe = std::min(PANEL_NB, m.f_p[f] - k);
+            const int c_end = big(f) ? block_end(f) : m.f_m[f];
+            for (int r0 = k + nbe; r0 < m.f_m[f]; r0 += WINDOW_THREADS) push({0, f, r0});
+            for (int c0 = 0; c0 < m.f_m[f]; c0 += WINDOW_THREADS) push({1, f, c0, c_end});
+          }
+          close(W);
+        }
+        for (int pk = 0; pk < 2 && !window; ++pk) {
           Launch PC = open(pk == 0 ? L_PANEL_1 : L_PANEL_CL, l, k);
           int rows = 0;
           for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
@@ -647,19 +670,21 @@ void build_schedule(Mesh& m, int big_front) {
           PC.aux = rows;
           close(PC);
         }
-        Launch SW = open(L_LASWP, l, k);
-        for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
-          int f = m.level_fronts[q];
-          if (m.f_p[f] > k && kind(f) < 2)
-            for (int c0 = 0; c0 < m.f_m[f]; c0 += LASWP_COLS) push({f, c0});
+        if (!window) {
+          Launch SW = open(L_LASWP, l, k);
+          for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
+            int f = m.level_fronts[q];
+            if (m.f_p[f] > k && kind(f) < 2)
+              for (int c0 = 0; c0 < m.f_m[f]; c0 += LASWP_COLS) push({f, c0});
+          }
+          close(SW);
+          Launch P = open(L_PANEL, l, k);
+          for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
+            int f = m.level_fronts[q];
+            if (m.f_p[f] > k && kind(f) == 2) push({f});
+          }
+          close(P);
         }
-        close(SW);
-        Launch P = open(L_PANEL, l, k);
-        for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
-          int f = m.level_fronts[q];
-          if (m.f_p[f] > k && kind(f) == 2) push({f});
-        }
-        close(P);
         // TRSM and GEMM of this panel (inside the outer block for large fronts)
         Launch T = open(L_TRSM, l, k);
         for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
@@ -667,7 +692,8 @@ void build_schedule(Mesh& m, int big_front) {
           if (m.f_p[f] <= k) continue;
           const int nbe = std::min(PANEL_NB, m.f_p[f] - k);
           const int c_end = big(f) ? block_end(f) : m.f_m[f];
-          for (int c0 = k + nbe; c0 < c_end; c0 += TRSM_COLS) push({f, c0, c_end, k});
+          if (!window)
+            for (int c0 = k + nbe; c0 < c_end; c0 += TRSM_COLS) push({f, c0, c_end, k});
           if (count) {
             m.trsm_flops += (double)nbe * (nbe - 1) * std::max(0, c_end - k - nbe);
             for (int j = k; j < k + nbe; ++j) {
@@ -721,8 +747,10 @@ void build_schedule(Mesh& m, int big_front) {
             for (int rb = be; rb < mm; rb += 128)
               for (int cb = be; cb < mm; cb += 128) push({f, rb, cb, k2, be - k2});
             const double rest = (double)(mm - be);
-            m.gemm_flops += 2.0 * rest * rest * (be - k2);
-            m.outer_flops += 2.0 * rest * rest * (be - k2);
+            if (count) {
+              m.gemm_flops += 2.0 * rest * rest * (be - k2);
+              m.outer_flops += 2.0 * rest * rest * (be - k2);
+            }
           }
           close(TC);
         } else {

@@ -58,12 +58,16 @@ constexpr int FACE_PAIRS = 120;    // u x lambda, lambda x (u, delta), delta x l
 
 // ----- blocked factorisation schedule ---------------------------------------
 enum LaunchKind {
-  L_ASSEMBLE = 0, L_PANEL = 1, L_TRSM = 2, L_GEMM = 3, L_PANEL_CL = 4, L_LASWP = 5, L_PANEL_1 = 6, L_TC_GEMM = 7
+  L_ASSEMBLE = 0, L_PANEL = 1, L_TRSM = 2, L_GEMM = 3, L_PANEL_CL = 4, L_LASWP = 5, L_PANEL_1 = 6, L_TC_GEMM = 7,
+  L_DIAG = 8,      // windowed pivoting: one warp factors the 32 x 32 diagonal block
+  L_WINDOW = 9     // windowed pivoting: L21 rows and permuted / solved columns
 };
 constexpr int WORK_STRIDE = 8;   // ints per work item
 // work items:  ASSEMBLE (f, c0)           PANEL* (f)              LASWP (f, c0)
 //              TRSM (f, c0, c_end, k)      GEMM (f, rb, cb, r_end, c_end, k_begin, k_len)
 //              TC_GEMM (f, rb, cb, k_begin, k_len)  [128 x 128 tiles, tensor cores]
+//              DIAG (f)   WINDOW (0, f, r0) rows of L21 | (1, f, c0, c_end) permuted / solved columns
+constexpr int WINDOW_THREADS = 256;   // rows or columns per WINDOW item
 constexpr int BIG_FRONT = 512;   // default: fronts at least this large use 128-column outer blocks
 constexpr int OUTER_NB = 128;    // outer block width (K of the outer Schur update)
 struct Launch {
@@ -134,7 +138,7 @@ struct Mesh {
   std::vector<int32_t> f_m, f_p, f_first, f_idx, f_nz_csr, f_nz_pos, f_child_off, f_child, f_ea,
       f_parent, f_piv_off, f_col_nz, f_level;
   std::vector<int32_t> work;
-  std::vector<Launch> sched[2];    // numeric factorisation launches in order ([0] FP32, [1] FP64 fronts)
+  std::vector<Launch> sched[4];    // numeric factorisation launches in order: [FP64 + 2 * windowed pivoting]
   std::vector<int32_t> level_off;  // fronts sorted by level
   std::vector<int32_t> level_fronts;
   std::vector<int32_t> level_maxm;   // largest front order per level
@@ -273,7 +277,7 @@ template <class T>
 void prepare_kernels();
 template <class T>
 void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* fronts, int32_t* piv,
-                    int32_t* stats, double threshold, cudaStream_t s);
+                    int32_t* stats, double threshold, bool window, cudaStream_t s);
 template <class T>
 void solve_fronts(const Mesh& m, const T* fronts, const int32_t* piv, const double* b, double* x,
                   T* vec, T* yv, cudaStream_t s);

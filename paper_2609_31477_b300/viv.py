@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "libviv.so")
 
 VIV_FP64, VIV_MIXED = 0, 1
 VIV_RES, VIV_JAC = 1, 2
+VIV_PIVOT_THRESHOLD, VIV_PIVOT_WINDOW = 0, 1
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_PIVOT", 5: "ERR_NEWTON",
           6: "ERR_NONFINITE", 7: "ERR_TIMEOUT", 8: "ERR_ADMISSION", 9: "ERR_STATE"}
 KINDS = ("residual", "jacobian", "face_border", "front_assemble", "panel_lu", "trsm", "schur_gemm",
@@ -50,7 +51,8 @@ class Params(C.Structure):
     _fields_ = [("rho", C.c_double), ("mu", C.c_double), ("k", C.c_double), ("dt", C.c_double),
                 ("lame_scale", C.c_double), ("newton_tol", C.c_double), ("max_newton", C.c_int32),
                 ("precision", C.c_int32), ("refine_tol", C.c_double), ("refine_max", C.c_int32),
-                ("pivot_threshold", C.c_double), ("source", C.c_int32), ("source_amp", C.c_double)]
+                ("pivot_threshold", C.c_double), ("source", C.c_int32), ("source_amp", C.c_double),
+                ("pivoting", C.c_int32)]
 
 
 class StepInfo(C.Structure):
@@ -276,11 +278,11 @@ class Case:
 
     def __init__(self, mesh: Mesh, u0, rho, mu, k, dt, precision=VIV_FP64, lame_scale=1.0,
                  newton_tol=1e-10, max_newton=25, refine_tol=0.0, refine_max=0, pivot_threshold=0.01,
-                 stream=None, source=0, source_amp=0.0):
+                 stream=None, source=0, source_amp=0.0, pivoting=0):
         lib = load()
         self.mesh = mesh
         self.params = Params(rho, mu, k, dt, lame_scale, newton_tol, max_newton, precision, refine_tol,
-                             refine_max, pivot_threshold, source, source_amp)
+                             refine_max, pivot_threshold, source, source_amp, pivoting)
         u0 = np.ascontiguousarray(u0, dtype=np.float64)
         import torch
         # each case owns a non-default stream (graphs cannot capture the legacy stream)

@@ -25,12 +25,12 @@ def viv():
     return V
 
 
-def _pair(viv, m, precision, seed=3):
+def _pair(viv, m, precision, seed=3, pivoting=0):
     mesh = I.viv_cylinder_mesh(m)
     u0 = I.viv_initial_velocity(mesh, 1.0, 1e-3, 1)
     oc = viv_oracle_case(mesh, RE, USTAR, DT, u0)
     M = viv.Mesh(mesh)
-    case = viv.viv_case(M, RE, USTAR, DT, u0, precision=precision)
+    case = viv.viv_case(M, RE, USTAR, DT, u0, precision=precision, pivoting=pivoting)
     return mesh, oc, M, case
 
 
@@ -79,11 +79,13 @@ def test_residual_and_jacobian_entrywise(viv, m):
     assert abs(np.abs(J_o).sum() - np.abs(J_g_in_o).sum()) <= 1e-9 * np.abs(J_o).sum()
 
 
+@pytest.mark.parametrize("pivoting", ["threshold", "window"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("m", [4, 12])
-def test_refined_multifrontal_solve(viv, m, precision):
+def test_refined_multifrontal_solve(viv, m, precision, pivoting):
     prec = viv.VIV_FP64 if precision == "fp64" else viv.VIV_MIXED
-    mesh, oc, M, case = _pair(viv, m, prec)
+    piv = viv.VIV_PIVOT_THRESHOLD if pivoting == "threshold" else viv.VIV_PIVOT_WINDOW
+    mesh, oc, M, case = _pair(viv, m, prec, pivoting=piv)
     c0, hu, hx = _mid_step_state(viv, oc, case, 21)
     perm = perm_oracle_to_lib(oc, M)
     case.assemble(viv.VIV_RES | viv.VIV_JAC)
@@ -133,13 +135,15 @@ def cylinder_reference():
     return mesh, oc, states
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_cylinder_ten_steps_match_oracle(viv, cylinder_reference, precision):
+@pytest.mark.parametrize("precision,pivoting", [("fp64", "threshold"), ("mixed", "threshold"),
+                                                ("fp64", "window"), ("mixed", "window")])
+def test_cylinder_ten_steps_match_oracle(viv, cylinder_reference, precision, pivoting):
     mesh, oc, states = cylinder_reference
     prec = viv.VIV_FP64 if precision == "fp64" else viv.VIV_MIXED
+    piv = viv.VIV_PIVOT_THRESHOLD if pivoting == "threshold" else viv.VIV_PIVOT_WINDOW
     u0 = I.viv_initial_velocity(mesh, 1.0, 1e-3, 1)
     M = viv.Mesh(mesh)
-    case = viv.viv_case(M, RE, USTAR, DT, u0, precision=prec)
+    case = viv.viv_case(M, RE, USTAR, DT, u0, precision=prec, pivoting=piv)
     for s in range(10):
         info = case.step()
         assert info["res_norm"] <= 1e-10
