@@ -172,19 +172,21 @@ void factor(vivCase* c) {
   double thr = c->prm.pivot_threshold > 0 ? c->prm.pivot_threshold : 0.01;
   const bool win = c->prm.pivoting == VIV_PIVOT_WINDOW;
   if (mixed(c))
-    factor_numeric<float>(m, nullptr, c->s.J32, (float*)c->s.fronts, c->s.piv, c->s.stats, thr, win, c->stream);
+    factor_numeric<float>(m, nullptr, c->s.J32, (float*)c->s.fronts, c->s.piv, c->s.perm, c->s.stats, thr, win,
+                          c->stream);
   else
-    factor_numeric<double>(m, c->s.J64, nullptr, (double*)c->s.fronts, c->s.piv, c->s.stats, thr, win, c->stream);
+    factor_numeric<double>(m, c->s.J64, nullptr, (double*)c->s.fronts, c->s.piv, c->s.perm, c->s.stats, thr, win,
+                           c->stream);
   c->factored = true;
 }
 
 void lu_solve(vivCase* c, const double* b, double* x) {
   const Mesh& m = c->mesh->m;
   if (mixed(c))
-    solve_fronts<float>(m, (const float*)c->s.fronts, c->s.piv, b, x, (float*)c->s.vec, (float*)c->s.yv,
+    solve_fronts<float>(m, (const float*)c->s.fronts, c->s.perm, b, x, (float*)c->s.vec, (float*)c->s.yv,
                         c->stream);
   else
-    solve_fronts<double>(m, (const double*)c->s.fronts, c->s.piv, b, x, (double*)c->s.vec,
+    solve_fronts<double>(m, (const double*)c->s.fronts, c->s.perm, b, x, (double*)c->s.vec,
                          (double*)c->s.yv, c->stream);
 }
 
@@ -286,7 +288,7 @@ vivStatus viv_mesh_info(const vivMesh* mesh, vivMeshInfo* info) {
   info->factor_flops = m.factor_flops;
   info->front_entries = (size_t)m.front_entries;
   size_t nodes = (size_t)m.n_nodes, nnz = (size_t)info->nnz, nd = (size_t)m.n_dofs;
-  size_t state = 8 * (17 * nodes + (size_t)m.n_elems + 3 * nd + 2 * 296 + 64) + 4 * (size_t)m.piv_entries;
+  size_t state = 8 * (17 * nodes + (size_t)m.n_elems + 3 * nd + 2 * 296 + 64) + 8 * (size_t)m.piv_entries;
   info->device_bytes_fp64 = state + 8 * (nnz + (size_t)m.front_entries + (size_t)m.vec_entries + nd);
   info->device_bytes_mixed =
       state + 8 * nnz + 4 * (nnz + (size_t)m.front_entries + (size_t)m.vec_entries + nd);
@@ -396,6 +398,7 @@ static vivStatus case_create_impl(vivMesh* mesh, const vivParams* prm, const dou
     s.vec = A.get(tsz * (size_t)m.vec_entries);
     s.yv = A.get(tsz * (size_t)nd);
     s.piv = A.make<int32_t>(m.piv_entries);
+    s.perm = A.make<int32_t>(m.piv_entries);
     s.stats = A.make<int32_t>(4);
     s.partial = A.make<double>(296);
     s.scal = A.make<double>(8);

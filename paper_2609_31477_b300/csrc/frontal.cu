@@ -652,156 +652,277 @@ __global__ void __launch_bounds__(tc::THREADS) tc_front_kernel(FT ft, const int3
 }
 
 // ---- solves -----------------------------------------------------------------------
-// Each front keeps its m-vector in shared memory when it fits (else global
-// memory), gathers its children's update vectors, and applies its triangular
-// factors in 32-column blocks: one warp solves the 32 x 32 diagonal block,
-// then every thread updates the remaining rows with that block.
+// After the numeric factorisation, every 32 x 32 diagonal block of a front is
+// replaced in place by the inverses of its unit-lower part L11 (strictly lower
+// entries) and of its upper part U11 (upper entries, diagonal included), and
+// the row interchanges of each front are composed into one permutation.
+// A solve then walks the tree level by level:
+//   forward, per level:  one CTA per front gathers the children's update
+//     vectors, permutes the pivot rows and runs the triangular chain over the
+//     pivot rows (x_blk = L11^{-1} w_blk, then the rows below the block); a
+//     second, multi-CTA launch forms L21 x for the non-pivot rows in column
+//     slices (partial sums per slice, summed in order by the parent);
+//   backward, per level: a multi-CTA launch forms U12 x2 in column slices,
+//     then one CTA per front subtracts the slices and runs the chain upwards
+//     (x_blk = U11^{-1} v_blk, then the rows above the block).
+// The chains are latency-bound (one barrier and one memory round trip per
+// 32 rows); the slice launches carry the bandwidth-bound part of the solve.
+
+// in-place inversion of the diagonal blocks; one warp per (front, block)
+constexpr int INV_WARPS = 4;
+template <class T>
+__global__ void __launch_bounds__(INV_WARPS * 32) diag_inv_kernel(FT ft, const int32_t* items, int n, T* pool) {
+  __shared__ T B[INV_WARPS][32][33];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int it = blockIdx.x * INV_WARPS + wid;
+  if (it >= n) return;   // warp-uniform; the kernel uses no block barrier
+  const int f = items[2 * it], jb = items[2 * it + 1];
+  const int m = ft.m[f], p = ft.p[f];
+  const int nb = min(32, p - jb);
+  T* F = pool + ft.off[f] + (int64_t)jb * m + jb;
+  T(*Bw)[33] = B[wid];
+#pragma unroll 4
+  for (int j = 0; j < 32; ++j) Bw[lane][j] = (lane < nb && j < nb) ? F[(int64_t)j * m + lane] : T(lane == j ? 1 : 0);
+  __syncwarp();
+  // column `lane` of L11^{-1} (unit lower): X[i] = -sum_{k<i} L[i][k] X[k] for i > lane
+  T X[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) X[i] = i == lane ? T(1) : T(0);
+#pragma unroll
+  for (int i = 1; i < 32; ++i) {
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < i; ++k) s += Bw[i][k] * X[k];
+    if (i > lane) X[i] = -s;
+  }
+  // column `lane` of U11^{-1}: Y[i] = (delta_i,lane - sum_{k>i} U[i][k] Y[k]) / U[i][i] for i <= lane
+  T Y[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) Y[i] = 0;
+#pragma unroll
+  for (int i = 31; i >= 0; --i) {
+    T s = i == lane ? T(1) : T(0);
+#pragma unroll
+    for (int k = i + 1; k < 32; ++k) s -= Bw[i][k] * Y[k];
+    if (i <= lane) Y[i] = s / Bw[i][i];
+  }
+  __syncwarp();
+#pragma unroll
+  for (int i = 0; i < 32; ++i) Bw[i][lane] = i > lane ? X[i] : Y[i];
+  __syncwarp();
+  if (lane < nb)
+    for (int j = 0; j < nb; ++j) F[(int64_t)j * m + lane] = Bw[lane][j];
+}
+
+// Composition of a front's row interchanges: new pivot row i holds old row
+// perm[i].  With windowed pivoting every interchange stays inside its
+// 32-row block and the blocks are composed in parallel.
+__global__ void perm_kernel(FT ft, const int32_t* piv, int32_t* perm, bool block_local) {
+  extern __shared__ int32_t s_perm[];
+  const int f = blockIdx.x;
+  const int p = ft.p[f];
+  const int32_t* pv = piv + ft.piv_off[f];
+  int32_t* sp = s_perm;
+  int32_t* sv = s_perm + p;
+  for (int i = threadIdx.x; i < p; i += blockDim.x) {
+    sp[i] = i;
+    sv[i] = pv[i];
+  }
+  __syncthreads();
+  if (block_local) {
+    for (int b = threadIdx.x; b * 32 < p; b += blockDim.x)
+      for (int j = b * 32; j < min(p, b * 32 + 32); ++j) {
+        const int r = sv[j];
+        const int32_t t = sp[j];
+        sp[j] = sp[r];
+        sp[r] = t;
+      }
+  } else if (threadIdx.x == 0) {
+    for (int j = 0; j < p; ++j) {
+      const int r = sv[j];
+      const int32_t t = sp[j];
+      sp[j] = sp[r];
+      sp[r] = t;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < p; i += blockDim.x) perm[ft.piv_off[f] + i] = sp[i];
+}
+
 constexpr int SOLVE_THREADS = 1024;
 constexpr int SOLVE_SMEM_MAX = 160 * 1024;
-
+// chain CTAs: up to 1024 threads for FP32 fronts, 512 for FP64 (two 32-entry
+// register rows per thread)
 template <class T>
-__global__ void __launch_bounds__(SOLVE_THREADS) fwd_kernel(FT ft, const int32_t* fronts, const T* pool,
-                                                            const int32_t* piv, const double* b, T* vec, T* yv,
-                                                            bool in_smem) {
+constexpr int solve_threads_max() {
+  return sizeof(T) == 8 ? 512 : 1024;
+}
+constexpr int GEMV_THREADS = SOLVE_ROWS;   // one row per thread, 32 rows per warp
+
+// slice partial sums of the non-pivot rows (FWD: L21 x) or of the pivot rows
+// (!FWD: U12 x2) for one item (f, r0, s)
+template <class T, bool FWD>
+__global__ void __launch_bounds__(GEMV_THREADS) solve_gemv_kernel(FT ft, const int32_t* items, const T* __restrict__ pool,
+                                                                  const T* __restrict__ yv,
+                                                                  const double* __restrict__ x, T* vec) {
+  __shared__ T xs[SOLVE_SLICE];
+  const int32_t* it = items + 4 * blockIdx.x;
+  const int f = it[0], r0 = it[1], sl = it[2];
+  const int m = ft.m[f], p = ft.p[f], first = ft.first[f];
+  const int row_lo = FWD ? p : 0, row_hi = FWD ? m : p;
+  const int col_lo = FWD ? 0 : p, col_hi = FWD ? p : m;
+  const int c0 = col_lo + sl * SOLVE_SLICE, c1 = min(col_hi, c0 + SOLVE_SLICE);
+  const int nrows = row_hi - row_lo;
+  if (FWD) {
+    for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) xs[c - c0] = yv[first + c];
+  } else {
+    const int32_t* idx = ft.idx + ft.idx_off[f];
+    for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) xs[c - c0] = (T)x[idx[c]];
+  }
+  __syncthreads();
+  const int i = row_lo + r0 + threadIdx.x;
+  if (i >= row_hi) return;
+  const T* col = pool + ft.off[f] + (int64_t)c0 * m + i;
+  T a[4] = {0, 0, 0, 0};
+  int c = 0;
+  const int nc = c1 - c0;
+  for (; c + 32 <= nc; c += 32) {
+    T v[32];
+#pragma unroll
+    for (int u = 0; u < 32; ++u) v[u] = __ldg(col + (int64_t)(c + u) * m);
+#pragma unroll
+    for (int u = 0; u < 32; ++u) a[u & 3] += v[u] * xs[c + u];
+  }
+  for (; c < nc; ++c) a[0] += __ldg(col + (int64_t)c * m) * xs[c];
+  T* part = vec + ft.vec_off[f] + m;
+  part[(int64_t)sl * nrows + (i - row_lo)] = (a[0] + a[1]) + (a[2] + a[3]);
+}
+
+// forward chain of one front: gather, permute, L11^{-1} blocks and the pivot
+// rows below them; the non-pivot rows keep the gathered values for the slices
+template <class T>
+__global__ void __launch_bounds__(solve_threads_max<T>(), 1) fwd_tri_kernel(FT ft, const int32_t* fronts, const T* __restrict__ pool,
+                                                                const int32_t* perm, const double* b, T* vec, T* yv,
+                                                                bool in_smem) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T xw[SOLVE_THREADS / 32][32];
   const int f = fronts[blockIdx.x];
   const int m = ft.m[f], p = ft.p[f], first = ft.first[f];
   T* gw = vec + ft.vec_off[f];
   T* w = in_smem ? reinterpret_cast<T*>(smem_raw) : gw;
+  T* tmp = in_smem ? w + m : yv + first;
   const T* F = pool + ft.off[f];
   for (int i = threadIdx.x; i < m; i += blockDim.x) w[i] = i < p ? (T)b[first + i] : T(0);
   __syncthreads();
   for (int cc = ft.child_off[f]; cc < ft.child_off[f + 1]; ++cc) {
     const int c = ft.child[cc];
-    const int nc = ft.m[c] - ft.p[c];
+    const int mc = ft.m[c], pc = ft.p[c], nc = mc - pc;
     const int32_t* ea = ft.ea + ft.ea_off[c];
-    const T* wc = vec + ft.vec_off[c] + ft.p[c];
-    for (int r = threadIdx.x; r < nc; r += blockDim.x) w[ea[r]] += wc[r];
+    const T* wc = vec + ft.vec_off[c];
+    const T* pc_part = wc + mc;
+    const int ns = (pc + SOLVE_SLICE - 1) / SOLVE_SLICE;
+    for (int r = threadIdx.x; r < nc; r += blockDim.x) {
+      T v = wc[pc + r];
+      for (int s = 0; s < ns; ++s) v -= pc_part[(int64_t)s * nc + r];
+      w[ea[r]] += v;
+    }
     __syncthreads();
   }
-  // row interchanges, in order; pivot indices staged through shared memory
-  __shared__ int s_pv[1024];
-  const int32_t* pv = piv + ft.piv_off[f];
-  for (int j0 = 0; j0 < p; j0 += 1024) {
-    const int nj = min(1024, p - j0);
-    for (int t = threadIdx.x; t < nj; t += blockDim.x) s_pv[t] = pv[j0 + t];
-    __syncthreads();
-    if (threadIdx.x == 0)
-      for (int t = 0; t < nj; ++t) {
-        const int j = j0 + t, r = s_pv[t];
-        if (r != j) {
-          const T tmp = w[j];
-          w[j] = w[r];
-          w[r] = tmp;
-        }
-      }
-    __syncthreads();
-  }
+  const int32_t* pm = perm + ft.piv_off[f];
+  for (int i = threadIdx.x; i < p; i += blockDim.x) tmp[i] = w[pm[i]];
+  __syncthreads();
+  for (int i = threadIdx.x; i < p; i += blockDim.x) w[i] = tmp[i];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __shared__ T Dg[32][33];
   for (int jb = 0; jb < p; jb += 32) {
     const int nb = min(32, p - jb);
-    for (int q = threadIdx.x; q < nb * 32; q += blockDim.x) {
-      const int i = q & 31, jj = q >> 5;
-      Dg[i][jj] = i < nb ? F[(int64_t)(jb + jj) * m + jb + i] : T(0);
-    }
-    __syncthreads();
-    if (wid == 0) {
-      T xv = lane < nb ? w[jb + lane] : T(0);
-      for (int jj = 0; jj < nb; ++jj) {
-        const T xj = __shfl_sync(0xffffffffu, xv, jj);
-        if (lane > jj && lane < nb) xv -= Dg[lane][jj] * xj;
-      }
-      if (lane < nb) w[jb + lane] = xv;
-    }
-    __syncthreads();
-    if (nb == 32) {
-      // 32 independent loads per row keep the memory pipeline full
-      for (int i = jb + 32 + threadIdx.x; i < m; i += blockDim.x) {
-        const T* col = F + (int64_t)jb * m + i;
-        T a[4] = {0, 0, 0, 0};
+    // row `lane` of L11^{-1} (strictly lower part), loaded before the barrier
+    T d[32];
+    const T* Db = F + (int64_t)jb * m + jb + lane;
 #pragma unroll
-        for (int jj = 0; jj < 32; ++jj) a[jj & 3] += col[(int64_t)jj * m] * w[jb + jj];
-        w[i] -= (a[0] + a[1]) + (a[2] + a[3]);
-      }
-    } else {
-      for (int i = jb + nb + threadIdx.x; i < m; i += blockDim.x) {
-        T acc = 0;
-        for (int jj = 0; jj < nb; ++jj) acc += F[(int64_t)(jb + jj) * m + i] * w[jb + jj];
-        w[i] -= acc;
+    for (int j = 0; j < 32; ++j) d[j] = (j < lane && lane < nb) ? Db[(int64_t)j * m] : T(0);
+    __syncthreads();
+    const T wl = lane < nb ? w[jb + lane] : T(0);
+    T xl = wl;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) xl += d[j] * __shfl_sync(0xffffffffu, wl, j);
+    xw[wid][lane] = xl;
+    __syncwarp();
+    if (wid == 0 && lane < nb) yv[first + jb + lane] = xl;
+    const T* xr = xw[wid];
+    if (nb == 32) {
+      for (int i = jb + 32 + threadIdx.x; i < p; i += blockDim.x) {
+        const T* col = F + (int64_t)jb * m + i;
+        T v[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = col[(int64_t)j * m];
+        T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+#pragma unroll
+        for (int j = 0; j < 32; j += 4) {
+          a0 += v[j] * xr[j];
+          a1 += v[j + 1] * xr[j + 1];
+          a2 += v[j + 2] * xr[j + 2];
+          a3 += v[j + 3] * xr[j + 3];
+        }
+        w[i] -= (a0 + a1) + (a2 + a3);
       }
     }
-    __syncthreads();
+    // (a short last block has no pivot rows below it)
   }
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    if (i < p)
-      yv[first + i] = w[i];
-    else if (in_smem)
-      gw[i] = w[i];
-  }
+  if (in_smem)
+    for (int i = p + threadIdx.x; i < m; i += blockDim.x) gw[i] = w[i];
 }
 
+// backward chain of one front: subtract the slice sums, U11^{-1} blocks from
+// the last one up, and the rows above each block
 template <class T>
-__global__ void __launch_bounds__(SOLVE_THREADS) bwd_kernel(FT ft, const int32_t* fronts, const T* pool,
-                                                            const T* yv, T* vec, double* x, bool in_smem) {
+__global__ void __launch_bounds__(solve_threads_max<T>(), 1) bwd_tri_kernel(FT ft, const int32_t* fronts, const T* __restrict__ pool,
+                                                                T* yv, const T* vec, double* x, bool in_smem) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T xw[SOLVE_THREADS / 32][32];
   const int f = fronts[blockIdx.x];
   const int m = ft.m[f], p = ft.p[f], first = ft.first[f];
-  T* v = in_smem ? reinterpret_cast<T*>(smem_raw) : vec + ft.vec_off[f];
+  T* v = in_smem ? reinterpret_cast<T*>(smem_raw) : yv + first;   // in place in yv otherwise
   const T* F = pool + ft.off[f];
-  const int32_t* idx = ft.idx + ft.idx_off[f];
-  for (int i = threadIdx.x; i < m; i += blockDim.x) v[i] = i < p ? yv[first + i] : (T)x[idx[i]];
-  __syncthreads();
+  const T* part = vec + ft.vec_off[f] + m;
+  const int ns = (m - p + SOLVE_SLICE - 1) / SOLVE_SLICE;
   for (int i = threadIdx.x; i < p; i += blockDim.x) {
-    // eight independent partial sums: eight loads in flight per thread
-    T a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    const T* row = F + i;
-    int c = p;
-    for (; c + 8 <= m; c += 8) {
-#pragma unroll
-      for (int u = 0; u < 8; ++u) a[u] += row[(int64_t)(c + u) * m] * v[c + u];
-    }
-    for (; c < m; ++c) a[0] += row[(int64_t)c * m] * v[c];
-    v[i] -= ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+    T a = yv[first + i];
+    for (int s = 0; s < ns; ++s) a -= part[(int64_t)s * p + i];
+    v[i] = a;
   }
-  __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __shared__ T Dg[32][33];
   for (int jb = ((p - 1) / 32) * 32; jb >= 0 && p > 0; jb -= 32) {
     const int nb = min(32, p - jb);
-    for (int q = threadIdx.x; q < nb * 32; q += blockDim.x) {
-      const int i = q & 31, jj = q >> 5;
-      Dg[i][jj] = i < nb ? F[(int64_t)(jb + jj) * m + jb + i] : T(0);
-    }
-    __syncthreads();
-    if (wid == 0) {
-      T xv = lane < nb ? v[jb + lane] : T(0);
-      for (int jj = nb - 1; jj >= 0; --jj) {
-        if (lane == jj) xv /= Dg[jj][jj];
-        const T xj = __shfl_sync(0xffffffffu, xv, jj);
-        if (lane < jj) xv -= Dg[lane][jj] * xj;
-      }
-      if (lane < nb) v[jb + lane] = xv;
-    }
-    __syncthreads();
-    if (nb == 32) {
-      for (int i = threadIdx.x; i < jb; i += blockDim.x) {
-        const T* col = F + (int64_t)jb * m + i;
-        T a[4] = {0, 0, 0, 0};
+    // row `lane` of U11^{-1} (upper part, diagonal included)
+    T d[32];
+    const T* Db = F + (int64_t)jb * m + jb + lane;
 #pragma unroll
-        for (int jj = 0; jj < 32; ++jj) a[jj & 3] += col[(int64_t)jj * m] * v[jb + jj];
-        v[i] -= (a[0] + a[1]) + (a[2] + a[3]);
-      }
-    } else {
-      for (int i = threadIdx.x; i < jb; i += blockDim.x) {
-        T acc = 0;
-        for (int jj = 0; jj < nb; ++jj) acc += F[(int64_t)(jb + jj) * m + i] * v[jb + jj];
-        v[i] -= acc;
-      }
-    }
+    for (int j = 0; j < 32; ++j) d[j] = (j >= lane && j < nb) ? Db[(int64_t)j * m] : T(0);
     __syncthreads();
+    const T vl = lane < nb ? v[jb + lane] : T(0);
+    T xl = 0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) xl += d[j] * __shfl_sync(0xffffffffu, vl, j);
+    xw[wid][lane] = xl;
+    __syncwarp();
+    if (wid == 0 && lane < nb) x[first + jb + lane] = (double)xl;
+    const T* xr = xw[wid];
+    for (int i = threadIdx.x; i < jb; i += blockDim.x) {
+      const T* col = F + (int64_t)jb * m + i;
+      T u[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) u[j] = j < nb ? col[(int64_t)j * m] : T(0);
+      T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+#pragma unroll
+      for (int j = 0; j < 32; j += 4) {
+        a0 += u[j] * xr[j];
+        a1 += u[j + 1] * xr[j + 1];
+        a2 += u[j + 2] * xr[j + 2];
+        a3 += u[j + 3] * xr[j + 3];
+      }
+      v[i] -= (a0 + a1) + (a2 + a3);
+    }
   }
-  for (int i = threadIdx.x; i < p; i += blockDim.x) x[first + i] = (double)v[i];
 }
 
 }  // namespace
@@ -818,15 +939,16 @@ void prepare_kernels() {
                                 PANEL_SMEM_BYTES));
   VIV_CUDA(cudaFuncSetAttribute(panel_smem_kernel<T, PANEL_CLUSTER, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 PANEL_SMEM_BYTES));
-  VIV_CUDA(cudaFuncSetAttribute(fwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX));
-  VIV_CUDA(cudaFuncSetAttribute(bwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX));
+  VIV_CUDA(cudaFuncSetAttribute(fwd_tri_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX));
+  VIV_CUDA(cudaFuncSetAttribute(bwd_tri_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX));
+  VIV_CUDA(cudaFuncSetAttribute(perm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, PERM_SMEM_MAX));
   done = true;
 }
 template void prepare_kernels<float>();
 template void prepare_kernels<double>();
 
 template <class T>
-void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* fronts, int32_t* piv,
+void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* fronts, int32_t* piv, int32_t* perm,
                     int32_t* stats, double threshold, bool window, cudaStream_t s) {
   FT ft = make_ft(m);
   prepare_kernels<T>();
@@ -894,35 +1016,60 @@ void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* front
     }
   }
   VIV_CUDA(cudaGetLastError());
+  // solve preparation: composed row permutations, inverted diagonal blocks
+  {
+    Launched LL(K_TRSM, s);
+    perm_kernel<<<m.n_fronts, 128, 2 * (size_t)std::max(1, m.max_p) * sizeof(int32_t), s>>>(ft, piv, perm, window);
+  }
+  if (!m.inv_items.empty()) {
+    Launched LL(K_TRSM, s);
+    const int n = (int)(m.inv_items.size() / 2);
+    diag_inv_kernel<T><<<(n + INV_WARPS - 1) / INV_WARPS, INV_WARPS * 32, 0, s>>>(ft, m.d_inv_items, n, fronts);
+  }
+  VIV_CUDA(cudaGetLastError());
 }
 
 template <class T>
-void solve_fronts(const Mesh& m, const T* fronts, const int32_t* piv, const double* b, double* x, T* vec,
-                  T* yv, cudaStream_t s) {
+void solve_fronts(const Mesh& m, const T* fronts, const int32_t* perm, const double* b, double* x, T* vec, T* yv,
+                  cudaStream_t s) {
   FT ft = make_ft(m);
   prepare_kernels<T>();
   for (int l = 0; l < m.n_levels; ++l) {
     const int n = m.level_off[l + 1] - m.level_off[l];
-    const size_t need = (size_t)m.level_maxm[l] * sizeof(T);
+    const size_t need = (size_t)(m.level_maxm[l] + m.level_maxp[l]) * sizeof(T);
     const bool sm = need <= (size_t)SOLVE_SMEM_MAX;
-    Launched L(K_FWD, s);
-    fwd_kernel<T><<<n, m.level_threads[l], sm ? need : 0, s>>>(ft, m.d_level_fronts + m.level_off[l], fronts, piv, b,
-                                                          vec, yv, sm);
+    {
+      Launched L(K_FWD, s);
+      fwd_tri_kernel<T><<<n, std::min(m.level_threads[l], solve_threads_max<T>()), sm ? need : 0, s>>>(ft, m.d_level_fronts + m.level_off[l], fronts,
+                                                                    perm, b, vec, yv, sm);
+    }
+    const int ng = m.fg_off[l + 1] - m.fg_off[l];
+    if (ng) {
+      Launched L(K_FWD, s);
+      solve_gemv_kernel<T, true><<<ng, GEMV_THREADS, 0, s>>>(ft, m.d_fg_items + 4 * (int64_t)m.fg_off[l], fronts, yv,
+                                                              x, vec);
+    }
   }
   for (int l = m.n_levels - 1; l >= 0; --l) {
+    const int ng = m.bg_off[l + 1] - m.bg_off[l];
+    if (ng) {
+      Launched L(K_BWD, s);
+      solve_gemv_kernel<T, false><<<ng, GEMV_THREADS, 0, s>>>(ft, m.d_bg_items + 4 * (int64_t)m.bg_off[l], fronts,
+                                                               yv, x, vec);
+    }
     const int n = m.level_off[l + 1] - m.level_off[l];
-    const size_t need = (size_t)m.level_maxm[l] * sizeof(T);
+    const size_t need = (size_t)m.level_maxp[l] * sizeof(T);
     const bool sm = need <= (size_t)SOLVE_SMEM_MAX;
     Launched L(K_BWD, s);
-    bwd_kernel<T><<<n, m.level_threads[l], sm ? need : 0, s>>>(ft, m.d_level_fronts + m.level_off[l], fronts, yv,
-                                                          vec, x, sm);
+    bwd_tri_kernel<T><<<n, std::min(m.level_threads[l], solve_threads_max<T>()), sm ? need : 0, s>>>(ft, m.d_level_fronts + m.level_off[l], fronts, yv,
+                                                                  vec, x, sm);
   }
   VIV_CUDA(cudaGetLastError());
 }
 
 template void factor_numeric<double>(const Mesh&, const double*, const float*, double*, int32_t*, int32_t*,
-                                     double, bool, cudaStream_t);
-template void factor_numeric<float>(const Mesh&, const double*, const float*, float*, int32_t*, int32_t*,
+                                     int32_t*, double, bool, cudaStream_t);
+template void factor_numeric<float>(const Mesh&, const double*, const float*, float*, int32_t*, int32_t*, int32_t*,
                                     double, bool, cudaStream_t);
 template void solve_fronts<double>(const Mesh&, const double*, const int32_t*, const double*, double*, double*,
                                    double*, cudaStream_t);

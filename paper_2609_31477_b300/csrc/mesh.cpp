@@ -449,6 +449,7 @@ void build_mesh(Mesh& m, const vivMeshDesc* d) {
   m.f_idx.clear();
   m.factor_flops = 0;
   m.max_front = 0;
+  m.max_p = 0;
   for (int i = 0; i < NF; ++i) {
     for (int32_t j = 0; j < m.f_p[i]; ++j) m.f_idx.push_back(m.f_first[i] + j);
     for (int b : cbn[i])
@@ -457,9 +458,15 @@ void build_mesh(Mesh& m, const vivMeshDesc* d) {
     VIV_CHECK(mm < 46000, VIV_ERR_ARG, "front order exceeds the 32-bit local index range");
     m.f_m[i] = (int32_t)mm;
     m.max_front = std::max<int>(m.max_front, (int)mm);
+    m.max_p = std::max<int>(m.max_p, m.f_p[i]);
+    VIV_CHECK(2 * (int64_t)m.f_p[i] * 4 <= PERM_SMEM_MAX, VIV_ERR_ARG, "front pivot count exceeds the solve tables");
     m.f_idx_off[i + 1] = m.f_idx.size();
     m.f_off[i + 1] = m.f_off[i] + mm * mm;
-    m.f_vec_off[i + 1] = m.f_vec_off[i] + mm;
+    // solve workspace: the front vector, then the slice partial sums
+    // (forward: ceil(p / SLICE) x (m - p); backward: ceil((m - p) / SLICE) x p)
+    const int64_t pp = m.f_p[i], nn = mm - pp;
+    const int64_t part = std::max((pp + SOLVE_SLICE - 1) / SOLVE_SLICE * nn, (nn + SOLVE_SLICE - 1) / SOLVE_SLICE * pp);
+    m.f_vec_off[i + 1] = m.f_vec_off[i] + mm + part;
     m.f_piv_off[i + 1] = m.f_piv_off[i] + m.f_p[i];
     double p = m.f_p[i];
     for (int64_t j = 0; j < m.f_p[i]; ++j) {
@@ -568,11 +575,36 @@ void build_mesh(Mesh& m, const vivMeshDesc* d) {
       m.level_maxm[m.f_level[i]] = std::max(m.level_maxm[m.f_level[i]], m.f_m[i]);
     }
   }
-  // solve threads per front, by level (small fronts get small blocks)
+  // solve threads per front, by level: the chains update pivot rows only
+  m.level_maxp.assign(m.n_levels, 0);
+  for (int i = 0; i < NF; ++i) m.level_maxp[m.f_level[i]] = std::max(m.level_maxp[m.f_level[i]], m.f_p[i]);
   m.level_threads.assign(m.n_levels, 64);
   for (int l = 0; l < m.n_levels; ++l) {
-    int t = ((m.level_maxm[l] / 2 + 31) / 32) * 32;
+    int t = ((m.level_maxp[l] + 31) / 32) * 32;
     m.level_threads[l] = std::min(1024, std::max(64, t));
+  }
+  // diagonal blocks to invert, and the slice items of the solves by level
+  m.inv_items.clear();
+  for (int i = 0; i < NF; ++i)
+    for (int jb = 0; jb < m.f_p[i]; jb += 32) {
+      m.inv_items.push_back(i);
+      m.inv_items.push_back(jb);
+    }
+  m.fg_items.clear();
+  m.bg_items.clear();
+  m.fg_off.assign(m.n_levels + 1, 0);
+  m.bg_off.assign(m.n_levels + 1, 0);
+  for (int l = 0; l < m.n_levels; ++l) {
+    for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
+      const int f = m.level_fronts[q];
+      const int pp = m.f_p[f], nn = m.f_m[f] - pp;
+      for (int s0 = 0; s0 * SOLVE_SLICE < pp; ++s0)
+        for (int r0 = 0; r0 < nn; r0 += SOLVE_ROWS) m.fg_items.insert(m.fg_items.end(), {f, r0, s0, 0});
+      for (int s0 = 0; s0 * SOLVE_SLICE < nn; ++s0)
+        for (int r0 = 0; r0 < pp; r0 += SOLVE_ROWS) m.bg_items.insert(m.bg_items.end(), {f, r0, s0, 0});
+    }
+    m.fg_off[l + 1] = (int32_t)(m.fg_items.size() / 4);
+    m.bg_off[l + 1] = (int32_t)(m.bg_items.size() / 4);
   }
   build_schedule(m, BIG_FRONT);
 }
@@ -795,6 +827,9 @@ void upload_mesh(Mesh& m, cudaStream_t s) {
   m.d_color_elems = A.upload(m.color_elems, s);
   m.d_fcolor_faces = A.upload(m.fcolor_faces, s);
   m.d_level_fronts = A.upload(m.level_fronts, s);
+  m.d_inv_items = A.upload(m.inv_items, s);
+  m.d_fg_items = A.upload(m.fg_items, s);
+  m.d_bg_items = A.upload(m.bg_items, s);
   FrontTables& t = m.ft;
   t.n_fronts = m.n_fronts;
   t.off = A.upload(m.f_off, s);

@@ -62,10 +62,10 @@ void lu_solve_noalloc(vivCase* c, const double* b, double* x) {
                 "-byte array; use viv_solve_rhs");
   unsigned char* base = static_cast<unsigned char*>(scratch_address());
   if (f32)
-    solve_fronts<float>(m, (const float*)c->s.fronts, c->s.piv, b, x, (float*)base, (float*)(base + vec_bytes),
+    solve_fronts<float>(m, (const float*)c->s.fronts, c->s.perm, b, x, (float*)base, (float*)(base + vec_bytes),
                         c->stream);
   else
-    solve_fronts<double>(m, (const double*)c->s.fronts, c->s.piv, b, x, (double*)base,
+    solve_fronts<double>(m, (const double*)c->s.fronts, c->s.perm, b, x, (double*)base,
                          (double*)(base + vec_bytes), c->stream);
 }
 

@@ -68,6 +68,11 @@ constexpr int WORK_STRIDE = 8;   // ints per work item
 //              TC_GEMM (f, rb, cb, k_begin, k_len)  [128 x 128 tiles, tensor cores]
 //              DIAG (f)   WINDOW (0, f, r0) rows of L21 | (1, f, c0, c_end) permuted / solved columns
 constexpr int WINDOW_THREADS = 256;   // rows or columns per WINDOW item
+// solves: the bandwidth-bound products with the off-diagonal factor blocks run
+// as items of SOLVE_ROWS rows x SOLVE_SLICE columns (one partial sum per slice)
+constexpr int SOLVE_ROWS = 256;
+constexpr int SOLVE_SLICE = 256;
+constexpr int PERM_SMEM_MAX = 200 * 1024;   // composed permutation of one front (2 ints per pivot)
 constexpr int BIG_FRONT = 512;   // default: fronts at least this large use 128-column outer blocks
 constexpr int OUTER_NB = 128;    // outer block width (K of the outer Schur update)
 struct Launch {
@@ -143,6 +148,11 @@ struct Mesh {
   std::vector<int32_t> level_fronts;
   std::vector<int32_t> level_maxm;   // largest front order per level
   std::vector<int32_t> level_threads;  // solve threads per front at each level
+  std::vector<int32_t> level_maxp;     // largest pivot count per level
+  int max_p = 0;                       // largest pivot count of any front
+  std::vector<int32_t> inv_items;      // (front, first row) of every 32 x 32 diagonal block
+  std::vector<int32_t> fg_items, fg_off;   // forward slice items (f, r0, slice, 0) by level
+  std::vector<int32_t> bg_items, bg_off;   // backward slice items by level
   int64_t front_entries = 0, vec_entries = 0, piv_entries = 0;
   double factor_flops = 0;
   int big_front = 0;          // large-front threshold of the current schedules
@@ -167,6 +177,9 @@ struct Mesh {
   int32_t* d_color_elems = nullptr;
   int32_t* d_fcolor_faces = nullptr;
   int32_t* d_level_fronts = nullptr;
+  int32_t* d_inv_items = nullptr;
+  int32_t* d_fg_items = nullptr;
+  int32_t* d_bg_items = nullptr;
   FrontTables ft;
 };
 
@@ -188,6 +201,7 @@ struct CaseState {
   void* vec;                            // solve workspace (double or float)
   void* yv;                             // forward-solve vector (n_dofs)
   int32_t* piv;                         // row pivots of all fronts
+  int32_t* perm;                        // composed row permutation of each front (solves)
   int32_t* stats;                       // [0] perturbed, [1] threshold misses
   double* partial;                      // norm partial sums
   double* scal;                         // host-visible scalars (device side)
@@ -276,10 +290,10 @@ void launch_f64_to_f32(float* y, const double* x, int64_t n, cudaStream_t s);
 template <class T>
 void prepare_kernels();
 template <class T>
-void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* fronts, int32_t* piv,
+void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* fronts, int32_t* piv, int32_t* perm,
                     int32_t* stats, double threshold, bool window, cudaStream_t s);
 template <class T>
-void solve_fronts(const Mesh& m, const T* fronts, const int32_t* piv, const double* b, double* x,
+void solve_fronts(const Mesh& m, const T* fronts, const int32_t* perm, const double* b, double* x,
                   T* vec, T* yv, cudaStream_t s);
 }  // namespace viv
 
