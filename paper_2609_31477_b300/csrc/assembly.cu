@@ -93,7 +93,7 @@ enum {
 //   f_u = rho (u.grad) u + grad p - mu (lap u + grad div u)   at x = chi(X_q)
 //   g_p = div u                                               at x = chi(X_q)
 //   f_x = -div_X sigma_s(chi) = amp (4 pi^2 s - 2 pi^2 cos pi X cos pi Y) (1, 1)
-__device__ void mms_source(double X, double Y, double amp, double rho, double mu, double* fu, double* gp,
+__device__ __noinline__ void mms_source(double X, double Y, double amp, double rho, double mu, double* fu, double* gp,
                            double* fx) {
   const double pi = 3.14159265358979323846;
   const double s = sin(pi * X) * sin(pi * Y);
@@ -191,7 +191,7 @@ template <class T>
 __device__ void load_element(const int32_t* conn, const double* X, const double* x,
                              const double* u, const double* p, const double* hu, const double* hx,
                              const double* lame, double c0, int e, int t, ElemNodes<T>& en) {
-  // t in [0, 40): cooperative load by the element's row threads
+  // t in [0, 14): cooperative load by 14 threads of the element
   if (t < 9) {
     int nd = conn[e * 9 + t];
     for (int i = 0; i < 2; ++i) {
@@ -222,21 +222,42 @@ struct AsmArgs {
   double source_amp;
 };
 
+// Threads are laid out by row kind so that a warp runs one kind of row:
+// [0, 18 EPB) momentum rows, [18 EPB, 22 EPB) continuity rows, [22 EPB, 40 EPB)
+// pseudo-solid rows (element le = offset / rows of the kind).  Node loads use
+// threads [0, 14 EPB), quadrature-point data threads [0, 9 EPB).
 template <class T, bool JAC>
-__global__ void __launch_bounds__(ASM_THREADS) element_kernel(AsmArgs A, double* R, T* vals) {
+__global__ void __launch_bounds__(ASM_THREADS, 2) element_kernel(AsmArgs A, double* R, T* vals) {
   __shared__ Tables<T> tb;
   __shared__ ElemNodes<T> en[EPB];
   __shared__ T qd[EPB][9][QP_DATA];
   build_tables(tb);
-  const int le = threadIdx.x / ROWS, t = threadIdx.x % ROWS;
+  const int tid = threadIdx.x;
+  if (tid < 14 * EPB) {
+    const int le = tid / 14, gi = blockIdx.x * EPB + le;
+    if (gi < A.n)
+      load_element<T>(A.conn, A.X, A.x, A.u, A.p, A.hu, A.hx, A.lame, A.c0, A.elems[gi], tid % 14, en[le]);
+  }
+  __syncthreads();
+  if (tid < 9 * EPB) {
+    const int le = tid / 9, q = tid % 9;
+    if (blockIdx.x * EPB + le < A.n) qp_compute<T>(tb, en[le], q, (T)A.rho, (T)A.mu, A.source, A.source_amp, qd[le][q]);
+  }
+  __syncthreads();
+  int le, t;
+  if (tid < 18 * EPB) {
+    le = tid / 18;
+    t = tid % 18;
+  } else if (tid < 22 * EPB) {
+    le = (tid - 18 * EPB) / 4;
+    t = 18 + (tid - 18 * EPB) % 4;
+  } else {
+    le = (tid - 22 * EPB) / 18;
+    t = 22 + (tid - 22 * EPB) % 18;
+  }
   const int gi = blockIdx.x * EPB + le;
-  const bool live = gi < A.n;
-  const int e = live ? A.elems[gi] : 0;
-  if (live) load_element<T>(A.conn, A.X, A.x, A.u, A.p, A.hu, A.hx, A.lame, A.c0, e, t, en[le]);
-  __syncthreads();
-  if (live && t < 9) qp_compute<T>(tb, en[le], t, (T)A.rho, (T)A.mu, A.source, A.source_amp, qd[le][t]);
-  __syncthreads();
-  if (!live) return;
+  if (gi >= A.n) return;
+  const int e = A.elems[gi];
   const int* cn = A.conn + e * 9;
   const T c0 = (T)A.c0, rho = (T)A.rho, mu = (T)A.mu;
   if (t < 18) {  // momentum row (a, i)
