@@ -51,6 +51,13 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--sweep-cases", type=int, default=16)
     ap.add_argument("--sweep-steps", type=int, default=10)
+    ap.add_argument("--pivoting", default="window", choices=["window", "threshold"],
+                    help="front pivoting: partial pivoting inside each 32-row diagonal block (window) or "
+                         "threshold pivoting over all fully summed rows")
+    ap.add_argument("--no-threshold-path", action="store_true")
+    ap.add_argument("--jacobian", default="fp32", choices=["fp32", "fp64"],
+                    help="mixed path: volume element Jacobians in FP32 (faces, border rows, residual and "
+                         "refinement stay FP64) or everything in FP64")
     return ap.parse_args()
 
 
@@ -162,7 +169,7 @@ def oracle_sample(wl, newton_iters):
 
 
 # ---------------------------------------------------------------------------------
-def run_sweep(viv, I, n_cases, n_steps, seed=7):
+def run_sweep(viv, I, n_cases, n_steps, pivoting, jacobian_fp32, seed=7):
     """Served parameter sweep (a sample of the 64-case, 200-step sweep): cases
     with 2k-20k quads, Re ~ U[100, 300], U* log-uniform in [4, 20], Poisson
     arrivals, a 24 GB device budget; every case runs n_steps BDF steps."""
@@ -185,7 +192,8 @@ def run_sweep(viv, I, n_cases, n_steps, seed=7):
     srv = viv.Server(24 << 30, max_active=16)
     for k, (m, Re, Us) in enumerate(cases):
         srv.submit(dev[m], I.viv_initial_velocity(meshes[m], 1.0, 1e-3, 100 + k), Re=Re, Ustar=Us, dt=0.02,
-                   n_steps=n_steps, arrival_time=float(arrivals[k]))
+                   n_steps=n_steps, arrival_time=float(arrivals[k]), pivoting=pivoting,
+                   jacobian_fp32=jacobian_fp32)
     res = srv.wait_all(n_cases, timeout_s=900)
     st = srv.stats()
     srv.close()
@@ -233,7 +241,10 @@ def run_ours(args, wl, rank, world, local):
     u0 = I.viv_initial_velocity(mesh, 1.0, 1e-3, 1 + rank)
     M = viv.Mesh(mesh)
     info = M.info
-    case = viv.viv_case(M, wl["Re"], wl["Ustar"], wl["dt"], u0, precision=viv.VIV_MIXED)
+    piv = viv.VIV_PIVOT_WINDOW if args.pivoting == "window" else viv.VIV_PIVOT_THRESHOLD
+    j32 = 1 if args.jacobian == "fp32" else 0
+    case = viv.viv_case(M, wl["Re"], wl["Ustar"], wl["dt"], u0, precision=viv.VIV_MIXED, pivoting=piv,
+                        jacobian_fp32=j32)
     stream = case.stream           # every kernel of the case runs on its own stream
     if args.autotune:
         tuned = case.autotune()
@@ -321,6 +332,7 @@ def run_ours(args, wl, rank, world, local):
            "config": {"workload": args.workload, "quads": len(mesh["conn"]), "dofs": info["n_dofs"],
                       "nnz": info["nnz"], "fronts": info["n_fronts"], "max_front": info["max_front"],
                       "factor_gflop": info["factor_flops"] / 1e9, **wl, "precision": "mixed",
+                      "pivoting": args.pivoting, "jacobian": args.jacobian,
                       "l2": f"inputs larger than L2 (front pool {4 * info['front_entries'] / 1e9:.1f} GB)",
                       "parallelism": "replicas" if world > 1 else "single"},
            "newton_iters_per_step": newton, "refine_sweeps_per_step": sweeps,
@@ -333,7 +345,7 @@ def run_ours(args, wl, rank, world, local):
         out["autotune"] = {"big_front": tuned[0], "factor_ms": tuned[1]}
 
     if not args.no_fp64 and rank == 0:
-        c64 = viv.viv_case(M, wl["Re"], wl["Ustar"], wl["dt"], u0, precision=viv.VIV_FP64)
+        c64 = viv.viv_case(M, wl["Re"], wl["Ustar"], wl["dt"], u0, precision=viv.VIV_FP64, pivoting=piv)
         c64.step()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -347,6 +359,24 @@ def run_ours(args, wl, rank, world, local):
                             "newton_iters_per_step": sum(i["newton_iters"] for i in i64) / len(i64)}
         out["speedup_mixed_vs_fp64"] = value / world / out["fp64_path"]["value"]
         c64.close()
+
+    if not args.no_threshold_path and args.pivoting == "window" and rank == 0:
+        # the same mixed path with threshold pivoting over all fully summed rows
+        ct = viv.viv_case(M, wl["Re"], wl["Ustar"], wl["dt"], u0, precision=viv.VIV_MIXED,
+                          pivoting=viv.VIV_PIVOT_THRESHOLD, jacobian_fp32=j32)
+        ct.step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ct.stream)
+        it_ = [ct.step() for _ in range(3)]
+        e1.record(ct.stream)
+        torch.cuda.synchronize()
+        mst = e0.elapsed_time(e1)
+        out["threshold_pivoting_path"] = {"value": 3 / (mst / 1e3), "unit": "time steps/s", "ms_per_step": mst / 3,
+                                          "steps": 3,
+                                          "newton_iters_per_step": sum(i["newton_iters"] for i in it_) / 3,
+                                          "refine_sweeps_per_step": sum(i["refine_sweeps"] for i in it_) / 3}
+        ct.close()
 
     if not args.no_e2e:
         # end to end through viv_step_host: the packed state crosses the bus every step
@@ -373,7 +403,7 @@ def run_ours(args, wl, rank, world, local):
                       "h2d_bytes_per_step": 8 * n_st, "d2h_bytes_per_step": 8 * n_st}
 
     if rank == 0 and not args.no_sweep:
-        out["sweep"] = run_sweep(viv, I, args.sweep_cases, args.sweep_steps)
+        out["sweep"] = run_sweep(viv, I, args.sweep_cases, args.sweep_steps, piv, j32)
 
     if rank == 0 and not args.no_cpu_baseline:
         v, desc, secs = oracle_sample(wl, newton)

@@ -129,6 +129,10 @@ typedef struct {
                               fully summed rows of a front; VIV_PIVOT_WINDOW (1): partial
                               pivoting inside each 32 x 32 diagonal block only (faster
                               panels; the refinement recovers the accuracy) */
+  int32_t jacobian_fp32;   /* mixed path only: 1 evaluates the volume element Jacobians in
+                              FP32 arithmetic (Gamma-face and border rows, the residual, the
+                              Newton test and the refinement products stay FP64); 0 (default)
+                              evaluates every Jacobian entry in FP64 */
 } vivParams;
 enum { VIV_PIVOT_THRESHOLD = 0, VIV_PIVOT_WINDOW = 1 };
 
@@ -316,6 +320,10 @@ int64_t viv_kernel_launches(void);
 enum { VIV_NKINDS = 12 };
 vivStatus viv_profile(vivCase* c, int on);
 vivStatus viv_profile_read(vivCase* c, double* ms, int64_t* count);
+/* Factorisation kernel time of the last viv_profile_read split by elimination
+ * tree level (0 = leaves): ms[l] for l < min(max_levels, *n_levels);
+ * *n_levels receives the number of levels recorded.  Host buffer. */
+vivStatus viv_profile_levels(const vivCase* c, double* ms, int32_t max_levels, int32_t* n_levels);
 
 const char* viv_last_error(void);
 const char* viv_version(void);

@@ -151,6 +151,21 @@ void begin_step(vivCase* c) {
   c->have_dU = false;
 }
 
+// Jacobian values: FP64 element arithmetic (rounded to FP32 for the mixed
+// fronts), or, with jacobian_fp32 on the mixed path, FP32 arithmetic for the
+// volume elements and FP64 for the Gamma faces and border rows (widened to
+// FP64 for the refinement products)
+void jacobian(vivCase* c) {
+  const Mesh& m = c->mesh->m;
+  const int64_t nnz = m.row_ptr[m.n_dofs];
+  if (mixed(c) && c->prm.jacobian_fp32) {
+    launch_jacobian_split(m, c->s, c->prm, c->c0, c->s.J32, c->s.J64, c->stream);
+  } else {
+    launch_jacobian<double>(m, c->s, c->prm, c->c0, c->s.J64, c->stream);
+    if (mixed(c)) launch_f64_to_f32(c->s.J32, c->s.J64, nnz, c->stream);
+  }
+}
+
 double assemble(vivCase* c, int what, bool want_norm) {
   const Mesh& m = c->mesh->m;
   VIV_CHECK(c->step_open, VIV_ERR_STATE, "viv_assemble before viv_begin_step");
@@ -160,8 +175,7 @@ double assemble(vivCase* c, int what, bool want_norm) {
     if (want_norm) nr = norm2(c, c->s.R, m.n_dofs);
   }
   if (what & VIV_JAC) {
-    launch_jacobian<double>(m, c->s, c->prm, c->c0, c->s.J64, c->stream);
-    if (mixed(c)) launch_f64_to_f32(c->s.J32, c->s.J64, m.row_ptr[m.n_dofs], c->stream);
+    jacobian(c);
     c->factored = false;
   }
   return nr;
@@ -236,6 +250,15 @@ vivStatus viv_profile_read(vivCase* c, double* ms, int64_t* count) {
   API_BEGIN
   VIV_CHECK(c && ms && count, VIV_ERR_ARG, "NULL argument");
   c->prof.read(ms, count);
+  API_END
+}
+
+vivStatus viv_profile_levels(const vivCase* c, double* ms, int32_t max_levels, int32_t* n_levels) {
+  API_BEGIN
+  VIV_CHECK(c && n_levels && (max_levels <= 0 || ms), VIV_ERR_ARG, "NULL argument");
+  const std::vector<double>& lv = c->prof.level_ms;
+  *n_levels = (int32_t)lv.size();
+  for (int32_t l = 0; l < max_levels && l < (int32_t)lv.size(); ++l) ms[l] = lv[l];
   API_END
 }
 
@@ -357,6 +380,7 @@ static vivStatus case_create_impl(vivMesh* mesh, const vivParams* prm, const dou
   VIV_CHECK(prm->precision == VIV_FP64 || prm->precision == VIV_MIXED, VIV_ERR_ARG, "unknown precision");
   VIV_CHECK(prm->pivoting == VIV_PIVOT_THRESHOLD || prm->pivoting == VIV_PIVOT_WINDOW, VIV_ERR_ARG,
             "unknown pivoting");
+  VIV_CHECK(prm->jacobian_fp32 == 0 || prm->jacobian_fp32 == 1, VIV_ERR_ARG, "jacobian_fp32 must be 0 or 1");
   VIV_CHECK(mesh->m.on_device, VIV_ERR_STATE, "mesh was analysed on the host only");
   *out = nullptr;
   vivCase* c = new vivCase();
@@ -684,10 +708,7 @@ static void step_impl(vivCase* c, vivStepInfo* info) {
     VIV_CHECK(it < c->prm.max_newton, VIV_ERR_NEWTON,
               "Newton did not converge in " + std::to_string(c->prm.max_newton) + " iterations (|R| = " +
                   fmt_e(nr) + ", tolerance " + fmt_e(tol) + ")");
-    run_graph(c, c->g_jac, [&] {
-      launch_jacobian<double>(m, c->s, c->prm, c->c0, c->s.J64, c->stream);
-      if (mixed(c)) launch_f64_to_f32(c->s.J32, c->s.J64, m.row_ptr[m.n_dofs], c->stream);
-    });
+    run_graph(c, c->g_jac, [&] { jacobian(c); });
     run_graph(c, c->g_fac, [&] { factor(c); });
     c->factored = true;
     sweeps += refined_solve_graphs(c);

@@ -585,9 +585,10 @@ void launch_element_areas(const Mesh& m, double* lame, double scale, double* scr
   VIV_CUDA(cudaGetLastError());
 }
 
+// parts: 1 volume elements, 2 Gamma faces and border rows, 3 both
 template <class T, bool JAC>
 static void run_assembly(const Mesh& m, const CaseState& st, const vivParams& prm, double c0, double* R,
-                         T* vals, cudaStream_t s) {
+                         T* vals, cudaStream_t s, int parts = 3) {
   AsmArgs A;
   A.conn = m.d_conn;
   A.X = m.d_X;
@@ -604,7 +605,7 @@ static void run_assembly(const Mesh& m, const CaseState& st, const vivParams& pr
   A.mu = prm.mu;
   A.source = prm.source;
   A.source_amp = prm.source_amp;
-  int ncol = (int)m.color_off.size() - 1;
+  int ncol = (parts & 1) ? (int)m.color_off.size() - 1 : 0;
   for (int c = 0; c < ncol; ++c) {
     A.elems = m.d_color_elems + m.color_off[c];
     A.n = m.color_off[c + 1] - m.color_off[c];
@@ -621,6 +622,10 @@ static void run_assembly(const Mesh& m, const CaseState& st, const vivParams& pr
   Fa.node_dof = m.d_node_dof;
   Fa.f2nz = m.d_f2nz;
   Fa.c0 = c0;
+  if (!(parts & 2)) {
+    VIV_CUDA(cudaGetLastError());
+    return;
+  }
   int nfc = (int)m.fcolor_off.size() - 1;
   for (int c = 0; c < nfc; ++c) {
     Fa.list = m.d_fcolor_faces + m.fcolor_off[c];
@@ -649,6 +654,19 @@ void launch_jacobian(const Mesh& m, const CaseState& st, const vivParams& prm, d
   run_assembly<T, true>(m, st, prm, c0, nullptr, vals, s);
 }
 template void launch_jacobian<double>(const Mesh&, const CaseState&, const vivParams&, double, double*, cudaStream_t);
+
+// Volume element Jacobians in FP32 arithmetic; the Gamma-face and border
+// (multiplier and cylinder position) entries in FP64.  Both arrays end up
+// holding the same values (J64 exact widenings of the FP32 volume entries).
+void launch_jacobian_split(const Mesh& m, const CaseState& st, const vivParams& prm, double c0, float* J32,
+                           double* J64, cudaStream_t s) {
+  const int64_t nnz = m.row_ptr[m.n_dofs];
+  VIV_CUDA(cudaMemsetAsync(J32, 0, sizeof(float) * nnz, s));
+  run_assembly<float, true>(m, st, prm, c0, nullptr, J32, s, 1);
+  launch_f32_to_f64(J64, J32, nnz, s);
+  run_assembly<double, true>(m, st, prm, c0, nullptr, J64, s, 2);
+  launch_f64_to_f32(J32, J64, nnz, s);
+}
 template void launch_jacobian<float>(const Mesh&, const CaseState&, const vivParams&, double, float*, cudaStream_t);
 
 }  // namespace viv

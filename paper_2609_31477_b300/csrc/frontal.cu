@@ -398,68 +398,78 @@ __global__ void __launch_bounds__(NT)
 // has no nonzero candidate).  The diagonal block is factored by one warp; the
 // rows below (L21 = A21 U11^{-1}) and the columns to the right
 // (U12 = L11^{-1} P A12) then need no cross-CTA reduction.
+// ordered bits of |x|: the IEEE bits of a nonnegative float, or the high word
+// of a nonnegative double (sign, exponent and 20 leading mantissa bits)
+__device__ __forceinline__ uint32_t mag_bits(float x) { return __float_as_uint(x) & 0x7FFFFFFFu; }
+__device__ __forceinline__ uint32_t mag_bits(double x) {
+  return (uint32_t)(__double_as_longlong(x) >> 32) & 0x7FFFFFFFu;
+}
+
+// Factor the 32 x 32 diagonal block of front f at pivot index k with partial
+// pivoting inside the block (one warp, lane = threadIdx.x & 31).  The block
+// lives in shared memory (A[row][col], padded so that a row and a column are
+// both conflict-free) and the elimination loop stays rolled: a fully unrolled
+// 32-step elimination is too long for the instruction cache.
+template <class T>
+__device__ void diag_block_lu(const FT& ft, int f, int k, T* pool, int32_t* piv, int32_t* stats) {
+  __shared__ T A[PANEL_NB][PANEL_NB + 1];
+  __shared__ int s_piv[PANEL_NB];
+  const int m = ft.m[f], p = ft.p[f];
+  const int nbe = min(PANEL_NB, p - k);
+  const int lane = threadIdx.x & 31;
+  T* F = pool + ft.off[f] + (int64_t)k * m + k;
+  T v[PANEL_NB];   // all 32 loads in flight together
+#pragma unroll
+  for (int c = 0; c < PANEL_NB; ++c) v[c] = (lane < nbe && c < nbe) ? F[(int64_t)c * m + lane] : T(0);
+  T bmax = 0;   // largest entry of the block, the perturbation scale
+#pragma unroll
+  for (int c = 0; c < PANEL_NB; ++c) {
+    A[lane][c] = v[c];
+    bmax = fmax(bmax, fabs(v[c]));
+  }
+  for (int o = 16; o > 0; o >>= 1) bmax = fmax(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+  __syncwarp();
+  for (int jj = 0; jj < nbe; ++jj) {
+    // pivot search in one warp reduction: the key is the magnitude's leading
+    // bits (five low bits dropped) with the lane in the low bits, so the
+    // largest magnitude wins and, among equal keys, the lowest lane
+    const uint32_t key = (lane >= jj && lane < nbe) ? ((mag_bits(A[lane][jj]) & ~31u) | (31u - lane)) : 0u;
+    const uint32_t best = __reduce_max_sync(0xffffffffu, key);
+    const bool empty = (best & ~31u) == 0u;   // no nonzero candidate in the window column
+    const int r = empty ? jj : (int)(31u - (best & 31u));
+    if (r != jj) {   // warp-uniform: lane c exchanges column c of rows jj and r
+      const T t1 = A[jj][lane], t2 = A[r][lane];
+      A[jj][lane] = t2;
+      A[r][lane] = t1;
+    }
+    if (lane == 0) {
+      s_piv[jj] = r;
+      if (empty) {
+        A[jj][jj] = sqrt(Eps<T>::v) * (bmax > 0 ? bmax : T(1));
+        atomicAdd(&stats[0], 1);
+      }
+    }
+    __syncwarp();
+    if (lane > jj && lane < nbe) {
+      const T l = A[lane][jj] / A[jj][jj];
+      A[lane][jj] = l;
+#pragma unroll 8
+      for (int c = jj + 1; c < nbe; ++c) A[lane][c] -= l * A[jj][c];
+    }
+    __syncwarp();
+  }
+#pragma unroll 8
+  for (int c = 0; c < PANEL_NB; ++c)
+    if (lane < nbe && c < nbe) F[(int64_t)c * m + lane] = A[lane][c];
+  if (lane < nbe) piv[ft.piv_off[f] + k + lane] = k + s_piv[lane];
+}
+
+// the diagonal blocks of the fronts of one launch (those not factored by the
+// previous panel's Schur update)
 template <class T>
 __global__ void __launch_bounds__(32) diag_lu_kernel(FT ft, const int32_t* work, int k, T* pool, int32_t* piv,
                                                      int32_t* stats) {
-  const int f = work[WORK_STRIDE * blockIdx.x];
-  const int m = ft.m[f], p = ft.p[f];
-  const int nbe = min(PANEL_NB, p - k);
-  const int lane = threadIdx.x;
-  T* F = pool + ft.off[f];
-  __shared__ T s_row[PANEL_NB];
-  T a[PANEL_NB];
-#pragma unroll
-  for (int c = 0; c < PANEL_NB; ++c) a[c] = (lane < nbe && c < nbe) ? F[(int64_t)(k + c) * m + k + lane] : T(0);
-  T bmax = 0;   // largest entry of the block, the perturbation scale
-#pragma unroll
-  for (int c = 0; c < PANEL_NB; ++c) bmax = fmax(bmax, fabs(a[c]));
-  for (int o = 16; o > 0; o >>= 1) bmax = fmax(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
-  int mypiv = lane;
-#pragma unroll
-  for (int jj = 0; jj < PANEL_NB; ++jj) {
-    if (jj < nbe) {
-      T v = (lane >= jj && lane < nbe) ? fabs(a[jj]) : T(-1);
-      int r = lane;
-      for (int o = 16; o > 0; o >>= 1) {
-        const T ov = __shfl_xor_sync(0xffffffffu, v, o);
-        const int orr = __shfl_xor_sync(0xffffffffu, r, o);
-        if (ov > v || (ov == v && orr < r)) {
-          v = ov;
-          r = orr;
-        }
-      }
-      if (v <= 0) r = jj;   // empty window column: perturb the diagonal below
-      // interchange rows jj and r (lanes) in registers
-#pragma unroll
-      for (int c = 0; c < PANEL_NB; ++c) {
-        const T vr = __shfl_sync(0xffffffffu, a[c], r);
-        const T vj = __shfl_sync(0xffffffffu, a[c], jj);
-        if (lane == jj) a[c] = vr;
-        else if (lane == r) a[c] = vj;
-      }
-      if (lane == jj) {
-        mypiv = r;
-        if (v <= 0) {
-          a[jj] = sqrt(Eps<T>::v) * (bmax > 0 ? bmax : T(1));
-          atomicAdd(&stats[0], 1);
-        }
-#pragma unroll
-        for (int c = 0; c < PANEL_NB; ++c) s_row[c] = a[c];
-      }
-      __syncwarp();
-      if (lane > jj && lane < nbe) {
-        const T l = a[jj] / s_row[jj];
-        a[jj] = l;
-#pragma unroll
-        for (int c = jj + 1; c < PANEL_NB; ++c) a[c] -= l * s_row[c];
-      }
-      __syncwarp();
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < PANEL_NB; ++c)
-    if (lane < nbe && c < nbe) F[(int64_t)(k + c) * m + k + lane] = a[c];
-  if (lane < nbe) piv[ft.piv_off[f] + k + lane] = k + mypiv;
+  diag_block_lu<T>(ft, work[WORK_STRIDE * blockIdx.x], k, pool, piv, stats);
 }
 
 // One launch, two kinds of items.  Kind 0 (f, r0): rows [r0, r0 + 256) of the
@@ -594,9 +604,12 @@ __global__ void trsm_kernel(FT ft, const int32_t* work, T* pool) {
 }
 
 // F[rb.., cb..] -= F[rows, k_begin : k_begin + k_len] * F[k_begin : k_begin + k_len, cols]
-// for one 64 x 64 tile clipped to rows < r_end and columns < c_end (SIMT)
+// for one 64 x 64 tile clipped to rows < r_end and columns < c_end (SIMT).
+// With item[7] set (windowed pivoting) the tile holds the next panel's
+// diagonal block at (rb, rb): once the tile is updated, one warp factors it.
 template <class T>
-__global__ void __launch_bounds__(256) gemm_kernel(FT ft, const int32_t* work, T* pool) {
+__global__ void __launch_bounds__(256) gemm_kernel(FT ft, const int32_t* work, T* pool, int32_t* piv,
+                                                   int32_t* stats) {
   const int32_t* it = work + WORK_STRIDE * blockIdx.x;
   const int f = it[0], rb = it[1], cb = it[2], r_end = it[3], c_end = it[4], kb = it[5], kl = it[6];
   const int m = ft.m[f];
@@ -604,44 +617,60 @@ __global__ void __launch_bounds__(256) gemm_kernel(FT ft, const int32_t* work, T
   __shared__ T As[PANEL_NB][GEMM_TILE + 1];   // [kk][row]
   __shared__ T Bs[PANEL_NB][GEMM_TILE + 1];   // [kk][col]
   const int tr = threadIdx.x % 16, tc = threadIdx.x / 16;
+  constexpr int LD = PANEL_NB * GEMM_TILE / 256;   // operand entries per thread and chunk = 8
   T acc[4][4] = {};
   for (int k0 = 0; k0 < kl; k0 += PANEL_NB) {
     const int kn = min(PANEL_NB, kl - k0);
-    for (int q = threadIdx.x; q < PANEL_NB * GEMM_TILE; q += blockDim.x) {
-      int r = q % GEMM_TILE, kk = q / GEMM_TILE;
-      T a = 0, b = 0;
-      if (kk < kn) {
-        if (rb + r < r_end) a = F[(int64_t)(kb + k0 + kk) * m + rb + r];
-        if (cb + r < c_end) b = F[(int64_t)(cb + r) * m + kb + k0 + kk];
-      }
-      As[kk][r] = a;
-      Bs[kk][r] = b;
+    // A: rows vary fastest; B: k varies fastest (each column is contiguous in k)
+    T ra[LD], rbv[LD];
+#pragma unroll
+    for (int t = 0; t < LD; ++t) {
+      const int q = threadIdx.x + 256 * t;
+      const int r = q % GEMM_TILE, kk = q / GEMM_TILE;
+      const int kk2 = q % PANEL_NB, c2 = q / PANEL_NB;
+      ra[t] = (kk < kn && rb + r < r_end) ? F[(int64_t)(kb + k0 + kk) * m + rb + r] : T(0);
+      rbv[t] = (kk2 < kn && cb + c2 < c_end) ? F[(int64_t)(cb + c2) * m + kb + k0 + kk2] : T(0);
+    }
+#pragma unroll
+    for (int t = 0; t < LD; ++t) {
+      const int q = threadIdx.x + 256 * t;
+      As[q / GEMM_TILE][q % GEMM_TILE] = ra[t];
+      Bs[q % PANEL_NB][q / PANEL_NB] = rbv[t];
     }
     __syncthreads();
+#pragma unroll 4
     for (int kk = 0; kk < kn; ++kk) {
       T a[4], b[4];
+#pragma unroll
       for (int u = 0; u < 4; ++u) {
         a[u] = As[kk][tr + 16 * u];
         b[u] = Bs[kk][tc + 16 * u];
       }
+#pragma unroll
       for (int u = 0; u < 4; ++u)
+#pragma unroll
         for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
     }
     __syncthreads();
   }
+#pragma unroll
   for (int v = 0; v < 4; ++v) {
     const int c = cb + tc + 16 * v;
-    if (c >= c_end) continue;
+#pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int r = rb + tr + 16 * u;
-      if (r < r_end) F[(int64_t)c * m + r] -= acc[u][v];
+      if (c < c_end && r < r_end) F[(int64_t)c * m + r] -= acc[u][v];
     }
+  }
+  if (it[7]) {
+    __syncthreads();   // the whole tile is updated (block-scope visibility of its stores)
+    if (threadIdx.x < 32) diag_block_lu<T>(ft, f, rb, pool, piv, stats);
   }
 }
 
 // outer Schur update of a large front on the tensor cores: one 128 x 128 tile
 // F[rb.., cb..] -= F[.., k_begin : k_begin + k_len] * F[k_begin : .., ..]
-__global__ void __launch_bounds__(tc::THREADS) tc_front_kernel(FT ft, const int32_t* work, float* pool, int* err) {
+__global__ void __launch_bounds__(tc::THREADS, 3) tc_front_kernel(FT ft, const int32_t* work, float* pool, int* err) {
   extern __shared__ __align__(1024) unsigned char raw[];
   tc::Smem& sm = *reinterpret_cast<tc::Smem*>(raw);
   const int32_t* it = work + WORK_STRIDE * blockIdx.x;
@@ -955,6 +984,7 @@ void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* front
   VIV_CUDA(cudaMemsetAsync(stats, 0, 3 * sizeof(int32_t), s));
   const int32_t* work = m.ft.work;
   for (const Launch& L : m.sched[(sizeof(T) == 8) + 2 * (window ? 1 : 0)]) {
+    prof_level(L.level);
     const int32_t* w = work + (int64_t)WORK_STRIDE * L.item0;
     const unsigned grid = (unsigned)L.count;
     static const int kk[10] = {K_FRONT_ASM, K_PANEL,  K_TRSM,  K_GEMM,  K_PANEL,
@@ -974,7 +1004,7 @@ void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* front
         trsm_kernel<T><<<grid, TRSM_COLS, 0, s>>>(ft, w, fronts);
         break;
       case L_GEMM:
-        gemm_kernel<T><<<grid, 256, 0, s>>>(ft, w, fronts);
+        gemm_kernel<T><<<grid, 256, 0, s>>>(ft, w, fronts, piv, stats);
         break;
       case L_TC_GEMM:
         if constexpr (std::is_same<T, float>::value) {
@@ -1016,6 +1046,7 @@ void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* front
     }
   }
   VIV_CUDA(cudaGetLastError());
+  prof_level(-1);
   // solve preparation: composed row permutations, inverted diagonal blocks
   {
     Launched LL(K_TRSM, s);

@@ -642,10 +642,18 @@ void build_schedule(Mesh& m, int big_front) {
       L.count = items() - L.item0;
       if (L.count) sched.push_back(L);
     };
-    auto gemm_tiles = [&](int f, int r0, int r_end, int c0, int c_end, int kb, int kl) {
+    // diag_tile: the tile at (r0, c0) also factors the next panel's diagonal block
+    auto gemm_tiles = [&](int f, int r0, int r_end, int c0, int c_end, int kb, int kl, bool diag_tile = false) {
       for (int rb = r0; rb < r_end; rb += GEMM_TILE)
-        for (int cb = c0; cb < c_end; cb += GEMM_TILE) push({f, rb, cb, r_end, c_end, kb, kl});
+        for (int cb = c0; cb < c_end; cb += GEMM_TILE)
+          push({f, rb, cb, r_end, c_end, kb, kl, (diag_tile && rb == r0 && cb == c0) ? 1 : 0});
       if (count) m.gemm_flops += 2.0 * std::max(0, r_end - r0) * std::max(0, c_end - c0) * kl;
+    };
+    // windowed pivoting: the diagonal block of panel k of front f is factored by
+    // the Schur update of panel k - 32 when that update covers it (every panel
+    // but the first, and but the first of each outer block of a large front)
+    auto diag_fused = [&](int f, int k) {
+      return window && k > 0 && k < m.f_p[f] && (m.f_m[f] < big_front || k % OUTER_NB != 0);
     };
     for (int l = 0; l < m.n_levels; ++l) {
       Launch L = open(L_ASSEMBLE, l, 0);
@@ -674,7 +682,7 @@ void build_schedule(Mesh& m, int big_front) {
           Launch D = open(L_DIAG, l, k);
           for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
             int f = m.level_fronts[q];
-            if (m.f_p[f] > k) push({f});
+            if (m.f_p[f] > k && !diag_fused(f, k)) push({f});
           }
           close(D);
           Launch W = open(L_WINDOW, l, k);
@@ -682,9 +690,10 @@ void build_schedule(Mesh& m, int big_front) {
             int f = m.level_fronts[q];
             if (m.f_p[f] <= k) continue;
             const int nbe = std::min(PANEL_NB, m.f_p[f] - k);
-            const int c_end = big(f) ? block_end(f) : m.f_m[f];
+            // U12 for every column right of the panel, the outer columns of a
+            // large front included (their in-block rows are updated below)
             for (int r0 = k + nbe; r0 < m.f_m[f]; r0 += WINDOW_THREADS) push({0, f, r0});
-            for (int c0 = 0; c0 < m.f_m[f]; c0 += WINDOW_THREADS) push({1, f, c0, c_end});
+            for (int c0 = 0; c0 < m.f_m[f]; c0 += WINDOW_THREADS) push({1, f, c0, m.f_m[f]});
           }
           close(W);
         }
@@ -742,7 +751,9 @@ void build_schedule(Mesh& m, int big_front) {
           const int nbe = std::min(PANEL_NB, m.f_p[f] - k);
           const int r0 = k + nbe;
           const int c_end = big(f) ? block_end(f) : m.f_m[f];
-          gemm_tiles(f, r0, m.f_m[f], r0, c_end, k, nbe);
+          gemm_tiles(f, r0, m.f_m[f], r0, c_end, k, nbe, diag_fused(f, r0));
+          // windowed schedule: the outer columns' rows inside the block, panel by panel
+          if (window && big(f) && c_end < m.f_m[f]) gemm_tiles(f, r0, c_end, c_end, m.f_m[f], k, nbe);
         }
         close(G);
         // large fronts whose outer block ends with this panel: the outer columns
@@ -754,7 +765,7 @@ void build_schedule(Mesh& m, int big_front) {
           if (k + nbe == block_end(f) && block_end(f) < m.f_m[f]) done.push_back(f);
         }
         if (done.empty()) continue;
-        for (int s0 = k2; s0 <= k; s0 += PANEL_NB) {
+        for (int s0 = k2; s0 <= k && !window; s0 += PANEL_NB) {
           Launch OT = open(L_TRSM, l, s0);
           for (int f : done) {
             const int be = block_end(f);

@@ -20,8 +20,10 @@ void Profiler::start(int k, cudaStream_t s) {
       ev.push_back(e);
     }
     kind.resize(ev.size() / 2 + 1);
+    level.resize(ev.size() / 2 + 1);
   }
   kind[used / 2] = k;
+  level[used / 2] = cur_level;
   VIV_CUDA(cudaEventRecord(ev[used], s));
   ++used;
 }
@@ -37,13 +39,23 @@ void Profiler::read(double* ms, int64_t* count) {
     count[k] = 0;
   }
   if (used) VIV_CUDA(cudaEventSynchronize(ev[used - 1]));
+  level_ms.clear();
   for (size_t i = 0; i + 1 < used; i += 2) {
     float t = 0;
     VIV_CUDA(cudaEventElapsedTime(&t, ev[i], ev[i + 1]));
     ms[kind[i / 2]] += t;
     count[kind[i / 2]] += 1;
+    const int l = level[i / 2];
+    if (l >= 0) {
+      if ((int)level_ms.size() <= l) level_ms.resize(l + 1, 0.0);
+      level_ms[l] += t;
+    }
   }
   used = 0;
+}
+
+void prof_level(int l) {
+  if (g_prof) g_prof->cur_level = l;
 }
 
 Profiler::~Profiler() {

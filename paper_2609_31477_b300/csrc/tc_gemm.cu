@@ -8,7 +8,7 @@
 namespace viv {
 namespace tc {
 
-__global__ void __launch_bounds__(THREADS) gemm_standalone_kernel(const float* A, int lda, const float* B, int ldb,
+__global__ void __launch_bounds__(THREADS, 3) gemm_standalone_kernel(const float* A, int lda, const float* B, int ldb,
                                                                    float* C, int ldc, int M, int N, int K, int* err) {
   extern __shared__ __align__(1024) unsigned char raw[];
   Smem& sm = *reinterpret_cast<Smem*>(raw);

@@ -95,21 +95,24 @@ struct Stage {
   alignas(1024) unsigned char b_lo[OPERAND_BYTES];
 };
 
+// One operand stage (64 KB) so that three CTAs fit on an SM; the next K
+// chunk waits in registers while the MMAs of the current one run.
 struct Smem {
-  Stage st[2];          // two-stage pipeline: stage K-chunk c+1 while the MMAs of chunk c run
-  uint64_t bar[2];      // one mbarrier per stage, completed by tcgen05.commit
+  Stage st;
+  uint64_t bar;         // completed by tcgen05.commit of the stage's MMAs
   uint32_t tmem_base;
 };
 
-// stage K-chunk [k0, k0 + KC) of A (rows rb..) and B (columns cb..) as hi/lo
-// TF32 pairs.  All global loads of a thread are issued before any conversion
-// or shared-memory store (read-only path: A and B are never written by the
-// update), and every thread writes whole 16-byte core-matrix rows.
-__device__ __forceinline__ void stage_chunk(Stage& S, const float* __restrict__ A, int lda,
-                                            const float* __restrict__ B, int ldb, int M, int N, int K, int rb,
-                                            int cb, int k0) {
-  constexpr int PER = BM * (KC / 4) / THREADS;   // (row, k-group) pairs per thread = 4
+constexpr int PER = BM * (KC / 4) / THREADS;   // (row, k-group) pairs per thread = 4
+struct ChunkRegs {
   float va[PER][4], vb[PER][4];
+};
+
+// global loads of K-chunk [k0, k0 + KC) of A (rows rb..) and B (columns
+// cb..), read-only path (A and B are never written by the update)
+__device__ __forceinline__ void load_chunk(ChunkRegs& R, const float* __restrict__ A, int lda,
+                                           const float* __restrict__ B, int ldb, int M, int N, int K, int rb, int cb,
+                                           int k0) {
 #pragma unroll
   for (int t = 0; t < PER; ++t) {
     const int idx = threadIdx.x + t * THREADS;
@@ -117,10 +120,15 @@ __device__ __forceinline__ void stage_chunk(Stage& S, const float* __restrict__ 
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int k = k0 + 4 * g + j;
-      va[t][j] = (rb + r < M && k < K) ? __ldg(A + (int64_t)k * lda + rb + r) : 0.f;
-      vb[t][j] = (cb + r < N && k < K) ? __ldg(B + (int64_t)(cb + r) * ldb + k) : 0.f;
+      R.va[t][j] = (rb + r < M && k < K) ? __ldg(A + (int64_t)k * lda + rb + r) : 0.f;
+      R.vb[t][j] = (cb + r < N && k < K) ? __ldg(B + (int64_t)(cb + r) * ldb + k) : 0.f;
     }
   }
+}
+
+// hi/lo TF32 split of a loaded chunk into the stage; every thread writes
+// whole 16-byte core-matrix rows
+__device__ __forceinline__ void store_chunk(Stage& S, const ChunkRegs& R) {
 #pragma unroll
   for (int t = 0; t < PER; ++t) {
     const int idx = threadIdx.x + t * THREADS;
@@ -128,10 +136,10 @@ __device__ __forceinline__ void stage_chunk(Stage& S, const float* __restrict__ 
     uint32_t ah[4], al[4], bh[4], bl[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      ah[j] = to_tf32(va[t][j]);
-      al[j] = to_tf32(va[t][j] - __uint_as_float(ah[j]));
-      bh[j] = to_tf32(vb[t][j]);
-      bl[j] = to_tf32(vb[t][j] - __uint_as_float(bh[j]));
+      ah[j] = to_tf32(R.va[t][j]);
+      al[j] = to_tf32(R.va[t][j] - __uint_as_float(ah[j]));
+      bh[j] = to_tf32(R.vb[t][j]);
+      bl[j] = to_tf32(R.vb[t][j] - __uint_as_float(bh[j]));
     }
     const int off = g * KCORE_STRIDE + (r >> 3) * CORE_BYTES + (r & 7) * 16;
     *reinterpret_cast<uint4*>(S.a_hi + off) = make_uint4(ah[0], ah[1], ah[2], ah[3]);
@@ -151,8 +159,7 @@ static __device__ void tile_update(Smem& sm, const float* A, int lda, const floa
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    mbar_init(&sm.bar[0], 1);
-    mbar_init(&sm.bar[1], 1);
+    mbar_init(&sm.bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -160,27 +167,27 @@ static __device__ void tile_update(Smem& sm, const float* A, int lda, const floa
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = sm.tmem_base;
   constexpr uint32_t idesc = make_idesc(BM, BN);
-  uint32_t ph[2] = {0u, 0u};
+  uint32_t ph = 0u;
   bool ok = true;
   const int nchunks = (K + KC - 1) / KC;
+  ChunkRegs R;
+  load_chunk(R, A, lda, B, ldb, M, N, K, rb, cb, 0);
   for (int ch = 0; ch < nchunks; ++ch) {
-    const int s = ch & 1;
-    bool w = true;
-    if (ch >= 2) {   // the MMAs of chunk ch - 2 read this stage: wait for them
-      w = mbar_wait(&sm.bar[s], ph[s]);
-      ph[s] ^= 1u;
+    if (ch > 0) {   // the MMAs of chunk ch - 1 still read the stage: wait for them
+      const bool w = mbar_wait(&sm.bar, ph);
+      ph ^= 1u;
+      if (!__syncthreads_and(w)) {
+        ok = false;
+        break;
+      }
     }
-    if (!__syncthreads_and(w)) {
-      ok = false;
-      break;
-    }
-    stage_chunk(sm.st[s], A, lda, B, ldb, M, N, K, rb, cb, ch * KC);
+    store_chunk(sm.st, R);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t ah = smem_u32(sm.st[s].a_hi), al = smem_u32(sm.st[s].a_lo);
-      const uint32_t bh = smem_u32(sm.st[s].b_hi), bl = smem_u32(sm.st[s].b_lo);
+      const uint32_t ah = smem_u32(sm.st.a_hi), al = smem_u32(sm.st.a_lo);
+      const uint32_t bh = smem_u32(sm.st.b_hi), bl = smem_u32(sm.st.b_lo);
 #pragma unroll
       for (int q = 0; q < KC / 8; ++q) {
         const uint32_t koff = (uint32_t)(2 * q * KCORE_STRIDE);   // 8 tf32 = 2 core matrices along K
@@ -192,17 +199,13 @@ static __device__ void tile_update(Smem& sm, const float* A, int lda, const floa
         mma_tf32(tmem, dah, dbl, idesc, 1u);
         mma_tf32(tmem, dah, dbh, idesc, 1u);
       }
-      mma_commit(&sm.bar[s]);
+      mma_commit(&sm.bar);
     }
     __syncwarp();
+    if (ch + 1 < nchunks) load_chunk(R, A, lda, B, ldb, M, N, K, rb, cb, (ch + 1) * KC);   // overlaps the MMAs
   }
-  if (ok) {   // drain the (at most two) outstanding commits
-    bool w = true;
-    for (int c = nchunks > 2 ? nchunks - 2 : 0; c < nchunks; ++c) {
-      const int s = c & 1;
-      w = mbar_wait(&sm.bar[s], ph[s]) && w;
-      ph[s] ^= 1u;
-    }
+  if (ok) {   // the last commit
+    bool w = nchunks == 0 || mbar_wait(&sm.bar, ph);
     asm volatile("tcgen05.fence::after_thread_sync;");
     ok = __syncthreads_and(w) != 0;
   }
@@ -213,27 +216,24 @@ static __device__ void tile_update(Smem& sm, const float* A, int lda, const floa
     // column half w / 4; each thread owns one row
     const int quarter = warp & 3, half = warp >> 2;
     const int r = rb + quarter * 32 + lane;
-    for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 32) {
-      uint32_t v[32];
+    for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 16) {
+      uint32_t v[16];
       const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
       asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
           : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
             "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-            "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-            "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-            "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            "=r"(v[15])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       if (r < M) {
-        // all 32 loads of C first, then the 32 stores: loads stay in flight together
-        float cv[32];
+        // all 16 loads of C first, then the 16 stores: loads stay in flight together
+        float cv[16];
         float* cr = C + (int64_t)(cb + c0) * ldc + r;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) cv[j] = (cb + c0 + j < N) ? cr[(int64_t)j * ldc] : 0.f;
+        for (int j = 0; j < 16; ++j) cv[j] = (cb + c0 + j < N) ? cr[(int64_t)j * ldc] : 0.f;
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
+        for (int j = 0; j < 16; ++j)
           if (cb + c0 + j < N) cr[(int64_t)j * ldc] = cv[j] - __uint_as_float(v[j]);
       }
     }

@@ -105,6 +105,11 @@ __global__ void f64_to_f32_kernel(float* y, const double* x, int64_t n) {
   if (i < n) y[i] = (float)x[i];
 }
 
+__global__ void f32_to_f64_kernel(double* y, const float* x, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (double)x[i];
+}
+
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -166,6 +171,12 @@ void launch_scale_copy(double* y, const double* x, double a, int64_t n, cudaStre
 void launch_f64_to_f32(float* y, const double* x, int64_t n, cudaStream_t s) {
   Launched L(K_VEC, s);
   f64_to_f32_kernel<<<blocks_for(n, 256), 256, 0, s>>>(y, x, n);
+  VIV_CUDA(cudaGetLastError());
+}
+
+void launch_f32_to_f64(double* y, const float* x, int64_t n, cudaStream_t s) {
+  Launched L(K_VEC, s);
+  f32_to_f64_kernel<<<blocks_for(n, 256), 256, 0, s>>>(y, x, n);
   VIV_CUDA(cudaGetLastError());
 }
 

@@ -217,13 +217,17 @@ enum KernelKind {
 struct Profiler {
   bool on = false;
   std::vector<cudaEvent_t> ev;
-  std::vector<int> kind;
+  std::vector<int> kind, level;
   size_t used = 0;
+  int cur_level = -1;                 // tree level of the factorisation launches being issued (-1: none)
+  std::vector<double> level_ms;       // per-level factorisation time of the last read
   void start(int k, cudaStream_t s);
   void stop(cudaStream_t s);
   void read(double* ms, int64_t* count);   // synchronises on the recorded events
   ~Profiler();
 };
+// tag the factorisation launches that follow with their tree level (profiling only)
+void prof_level(int l);
 extern thread_local Profiler* g_prof;
 void count_launch();
 void count_launches(int64_t n);
@@ -287,6 +291,9 @@ void launch_spmv_residual(const Mesh& m, const double* J, const double* x, const
 void launch_axpy(double* y, const double* x, double a, int64_t n, cudaStream_t s);
 void launch_scale_copy(double* y, const double* x, double a, int64_t n, cudaStream_t s);
 void launch_f64_to_f32(float* y, const double* x, int64_t n, cudaStream_t s);
+void launch_f32_to_f64(double* y, const float* x, int64_t n, cudaStream_t s);
+void launch_jacobian_split(const Mesh& m, const CaseState& st, const vivParams& prm, double c0, float* J32,
+                           double* J64, cudaStream_t s);
 template <class T>
 void prepare_kernels();
 template <class T>

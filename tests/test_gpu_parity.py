@@ -25,12 +25,13 @@ def viv():
     return V
 
 
-def _pair(viv, m, precision, seed=3, pivoting=0):
+def _pair(viv, m, precision, seed=3, pivoting=0, jacobian_fp32=0):
     mesh = I.viv_cylinder_mesh(m)
     u0 = I.viv_initial_velocity(mesh, 1.0, 1e-3, 1)
     oc = viv_oracle_case(mesh, RE, USTAR, DT, u0)
     M = viv.Mesh(mesh)
-    case = viv.viv_case(M, RE, USTAR, DT, u0, precision=precision, pivoting=pivoting)
+    case = viv.viv_case(M, RE, USTAR, DT, u0, precision=precision, pivoting=pivoting,
+                        jacobian_fp32=jacobian_fp32)
     return mesh, oc, M, case
 
 
@@ -77,6 +78,36 @@ def test_residual_and_jacobian_entrywise(viv, m):
     assert err.max() <= 1e-11 * jscale, (err.max(), jscale, rows[err.argmax()], col[err.argmax()])
     # every oracle entry is inside the library's pattern (checked on the host too)
     assert abs(np.abs(J_o).sum() - np.abs(J_g_in_o).sum()) <= 1e-9 * np.abs(J_o).sum()
+
+
+@pytest.mark.parametrize("m", [4, 12])
+def test_jacobian_fp32_volume_entrywise(viv, m):
+    """Mixed path with FP32 volume-element Jacobians: the Gamma-face and border
+    entries (multiplier and cylinder-position rows and columns) stay FP64; the
+    volume entries carry FP32 evaluation error only."""
+    mesh, oc, M, case = _pair(viv, m, viv.VIV_MIXED, jacobian_fp32=1)
+    c0, hu, hx = _mid_step_state(viv, oc, case, 11)
+    perm = perm_oracle_to_lib(oc, M)
+    case.assemble(viv.VIV_RES | viv.VIV_JAC)
+    J_o = oc.jacobian(c0, hu, hx, DT).tocsr()
+    rp, col = M.pattern()
+    vals = case.jacobian_values()
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(len(perm))
+    rows = np.repeat(np.arange(M.n_dofs), np.diff(rp))
+    J_g_in_o = np.asarray(J_o[inv[rows], inv[col]]).ravel()
+    _, field = M.dof_labels()
+    # face and border entries: multiplier and cylinder-position rows, multiplier
+    # columns (the position columns of velocity and pressure rows are volume
+    # shape-derivative entries)
+    fb = np.isin(field[rows], [5, 6, 7, 8]) | np.isin(field[col], [5, 6])
+    err = np.abs(vals - J_g_in_o)
+    jscale = np.abs(J_o.data).max()
+    assert err[fb].max() <= 1e-11 * jscale
+    row_scale = np.maximum(np.maximum.reduceat(np.abs(J_g_in_o), rp[:-1]), 1e-300)[rows]
+    rel = err[~fb] / row_scale[~fb]
+    assert rel.max() <= 1e-4, rel.max()
+    assert np.median(rel) <= 1e-6, np.median(rel)
 
 
 @pytest.mark.parametrize("pivoting", ["threshold", "window"])
@@ -135,15 +166,16 @@ def cylinder_reference():
     return mesh, oc, states
 
 
-@pytest.mark.parametrize("precision,pivoting", [("fp64", "threshold"), ("mixed", "threshold"),
-                                                ("fp64", "window"), ("mixed", "window")])
-def test_cylinder_ten_steps_match_oracle(viv, cylinder_reference, precision, pivoting):
+@pytest.mark.parametrize("precision,pivoting,jac32", [("fp64", "threshold", 0), ("mixed", "threshold", 0),
+                                                      ("fp64", "window", 0), ("mixed", "window", 0),
+                                                      ("mixed", "window", 1)])
+def test_cylinder_ten_steps_match_oracle(viv, cylinder_reference, precision, pivoting, jac32):
     mesh, oc, states = cylinder_reference
     prec = viv.VIV_FP64 if precision == "fp64" else viv.VIV_MIXED
     piv = viv.VIV_PIVOT_THRESHOLD if pivoting == "threshold" else viv.VIV_PIVOT_WINDOW
     u0 = I.viv_initial_velocity(mesh, 1.0, 1e-3, 1)
     M = viv.Mesh(mesh)
-    case = viv.viv_case(M, RE, USTAR, DT, u0, precision=prec, pivoting=piv)
+    case = viv.viv_case(M, RE, USTAR, DT, u0, precision=prec, pivoting=piv, jacobian_fp32=jac32)
     for s in range(10):
         info = case.step()
         assert info["res_norm"] <= 1e-10
