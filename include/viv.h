@@ -265,6 +265,10 @@ vivStatus viv_case_graphs(vivCase* c, int on);
  * keeps the fastest schedule for the mesh.  Affects every case of the mesh;
  * call it while no other case of the mesh is running. */
 vivStatus viv_autotune(vivCase* c, int32_t* best_big_front, double* best_ms);
+/* Set the large-front threshold by hand (a front of order >= big_front uses
+ * 128-column outer blocks); rebuilds the mesh's schedules when it changes.
+ * Same scope rules as viv_autotune.  VIV_ERR_ARG if big_front <= 0. */
+vivStatus viv_set_big_front(vivCase* c, int32_t big_front);
 
 /* ---- serving: parameter sweeps with continuous admission ------------------ */
 typedef struct vivServer vivServer;
@@ -321,8 +325,9 @@ enum { VIV_NKINDS = 12 };
 vivStatus viv_profile(vivCase* c, int on);
 vivStatus viv_profile_read(vivCase* c, double* ms, int64_t* count);
 /* Factorisation kernel time of the last viv_profile_read split by elimination
- * tree level (0 = leaves): ms[l] for l < min(max_levels, *n_levels);
- * *n_levels receives the number of levels recorded.  Host buffer. */
+ * tree level (0 = leaves) and kind: ms[l * VIV_NKINDS + k] for
+ * l < min(max_levels, *n_levels); *n_levels receives the number of levels
+ * recorded.  Host buffer of max_levels * VIV_NKINDS doubles. */
 vivStatus viv_profile_levels(const vivCase* c, double* ms, int32_t max_levels, int32_t* n_levels);
 
 const char* viv_last_error(void);

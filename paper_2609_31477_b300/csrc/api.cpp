@@ -257,8 +257,10 @@ vivStatus viv_profile_levels(const vivCase* c, double* ms, int32_t max_levels, i
   API_BEGIN
   VIV_CHECK(c && n_levels && (max_levels <= 0 || ms), VIV_ERR_ARG, "NULL argument");
   const std::vector<double>& lv = c->prof.level_ms;
-  *n_levels = (int32_t)lv.size();
-  for (int32_t l = 0; l < max_levels && l < (int32_t)lv.size(); ++l) ms[l] = lv[l];
+  const int32_t nl = (int32_t)(lv.size() / K_NKINDS);
+  *n_levels = nl;
+  for (int32_t l = 0; l < max_levels && l < nl; ++l)
+    for (int k = 0; k < K_NKINDS; ++k) ms[(int64_t)l * K_NKINDS + k] = lv[(int64_t)l * K_NKINDS + k];
   API_END
 }
 
@@ -588,7 +590,7 @@ vivStatus viv_autotune(vivCase* c, int32_t* best_big_front, double* best_ms) {
   Mesh& m = c->mesh->m;
   if (!c->step_open) begin_step(c);
   assemble(c, VIV_JAC, false);
-  const int cands[] = {256, 384, 512, 768, 1024, 1 << 30};
+  const int cands[] = {96, 128, 192, 256, 384, 512, 768, 1024, 1 << 30};
   cudaEvent_t e0, e1;
   VIV_CUDA(cudaEventCreate(&e0));
   VIV_CUDA(cudaEventCreate(&e1));
@@ -616,6 +618,18 @@ vivStatus viv_autotune(vivCase* c, int32_t* best_big_front, double* best_ms) {
   c->factored = false;
   if (best_big_front) *best_big_front = best;
   if (best_ms) *best_ms = best_t;
+  API_END
+}
+
+vivStatus viv_set_big_front(vivCase* c, int32_t big_front) {
+  API_BEGIN
+  VIV_CHECK(c && big_front > 0, VIV_ERR_ARG, "viv_set_big_front: bad arguments");
+  Mesh& m = c->mesh->m;
+  if (m.big_front != big_front) {
+    build_schedule(m, big_front);
+    upload_work(m, c->stream);
+    c->factored = false;
+  }
   API_END
 }
 

@@ -104,12 +104,33 @@ __global__ void assemble_kernel(FT ft, const int32_t* work, const S* J, T* pool)
     if (nc == 0) continue;
     const int32_t* ea = ft.ea + ft.ea_off[c];
     const int lo = lower_bound_i(ea, nc, c0), hi = lower_bound_i(ea, nc, c1);
-    const T* C = pool + ft.off[c];
-    const int64_t cnt = (int64_t)(hi - lo) * nc;
-    for (int64_t q = threadIdx.x; q < cnt; q += blockDim.x) {
-      const int r = (int)(q % nc), k = lo + (int)(q / nc);
-      F[ea[r] + (int64_t)ea[k] * m] += C[(pc + r) + (int64_t)(pc + k) * mc];
-    }
+    const T* C = pool + ft.off[c] + pc + (int64_t)pc * mc;   // the child's contribution block
+    // threads as (row, column group): R rows per pass, G groups of the (at
+    // most ASM_COLS) child columns that map into this chunk; four columns at
+    // a time per thread, all loads before the stores
+    const int R = min(nc, (int)blockDim.x), G = blockDim.x / R;
+    const int g = threadIdx.x / R;
+    if (g < G)
+      for (int r = threadIdx.x % R; r < nc; r += R) {
+        const int er = ea[r];
+        const T* Cr = C + r;
+        for (int k0 = lo + g; k0 < hi; k0 += 4 * G) {
+          T cv[4], fv[4];
+          int64_t fo[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int k = k0 + u * G;
+            if (k < hi) {
+              fo[u] = er + (int64_t)ea[k] * m;
+              cv[u] = Cr[(int64_t)k * mc];
+              fv[u] = F[fo[u]];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (k0 + u * G < hi) F[fo[u]] = fv[u] + cv[u];
+        }
+      }
     __syncthreads();
   }
 }
@@ -993,9 +1014,9 @@ void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* front
     switch (L.kind) {
       case L_ASSEMBLE:
         if (J32)
-          assemble_kernel<T, float><<<grid, 256, 0, s>>>(ft, w, J32, fronts);
+          assemble_kernel<T, float><<<grid, L.aux, 0, s>>>(ft, w, J32, fronts);
         else
-          assemble_kernel<T, double><<<grid, 256, 0, s>>>(ft, w, J64, fronts);
+          assemble_kernel<T, double><<<grid, L.aux, 0, s>>>(ft, w, J64, fronts);
         break;
       case L_PANEL:
         panel_kernel<T><<<grid, PANEL_THREADS, 0, s>>>(ft, w, L.k, fronts, piv, stats, (T)threshold);

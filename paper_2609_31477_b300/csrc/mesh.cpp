@@ -657,6 +657,7 @@ void build_schedule(Mesh& m, int big_front) {
     };
     for (int l = 0; l < m.n_levels; ++l) {
       Launch L = open(L_ASSEMBLE, l, 0);
+      L.aux = m.level_maxm[l] >= 1024 ? 512 : 256;   // assembly threads per item
       int maxp = 0;
       for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
         int f = m.level_fronts[q];

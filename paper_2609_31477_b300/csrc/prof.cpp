@@ -47,8 +47,8 @@ void Profiler::read(double* ms, int64_t* count) {
     count[kind[i / 2]] += 1;
     const int l = level[i / 2];
     if (l >= 0) {
-      if ((int)level_ms.size() <= l) level_ms.resize(l + 1, 0.0);
-      level_ms[l] += t;
+      if ((int)level_ms.size() < (l + 1) * K_NKINDS) level_ms.resize((l + 1) * K_NKINDS, 0.0);
+      level_ms[l * K_NKINDS + kind[i / 2]] += t;
     }
   }
   used = 0;

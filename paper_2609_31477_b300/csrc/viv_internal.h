@@ -73,7 +73,7 @@ constexpr int WINDOW_THREADS = 256;   // rows or columns per WINDOW item
 constexpr int SOLVE_ROWS = 256;
 constexpr int SOLVE_SLICE = 256;
 constexpr int PERM_SMEM_MAX = 200 * 1024;   // composed permutation of one front (2 ints per pivot)
-constexpr int BIG_FRONT = 512;   // default: fronts at least this large use 128-column outer blocks
+constexpr int BIG_FRONT = 96;    // default: fronts at least this large use 128-column outer blocks
 constexpr int OUTER_NB = 128;    // outer block width (K of the outer Schur update)
 struct Launch {
   int kind;
@@ -81,7 +81,7 @@ struct Launch {
   int k;          // panel start (pivot index) for PANEL/LASWP
   int64_t item0;  // first work item
   int64_t count;  // work items
-  int aux = 0;    // PANEL_CL: rows per CTA (shared-memory sizing)
+  int aux = 0;    // PANEL_CL: rows per CTA (shared-memory sizing); ASSEMBLE: threads per item
 };
 
 constexpr int PANEL_NB = 32;    // pivot block
@@ -220,7 +220,7 @@ struct Profiler {
   std::vector<int> kind, level;
   size_t used = 0;
   int cur_level = -1;                 // tree level of the factorisation launches being issued (-1: none)
-  std::vector<double> level_ms;       // per-level factorisation time of the last read
+  std::vector<double> level_ms;       // [level][kind] factorisation time of the last read
   void start(int k, cudaStream_t s);
   void stop(cudaStream_t s);
   void read(double* ms, int64_t* count);   // synchronises on the recorded events

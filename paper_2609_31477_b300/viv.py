@@ -141,6 +141,7 @@ SIGNATURES = {
     "viv_profile": (C.c_int, [_P, C.c_int]),
     "viv_profile_read": (C.c_int, [_P, _P, _P]),
     "viv_profile_levels": (C.c_int, [_P, _P, C.c_int32, _P]),
+    "viv_set_big_front": (C.c_int, [_P, C.c_int32]),
     "viv_last_error": (C.c_char_p, []),
     "viv_version": (C.c_char_p, []),
 }
@@ -372,6 +373,9 @@ class Case:
         _check(_lib.viv_autotune(self.h, C.byref(bf), C.byref(ms)))
         return bf.value, ms.value
 
+    def set_big_front(self, big_front):
+        _check(_lib.viv_set_big_front(self.h, int(big_front)))
+
     def profile(self, on=True):
         _check(_lib.viv_profile(self.h, int(on)))
 
@@ -382,11 +386,13 @@ class Case:
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KINDS)}
 
     def profile_levels(self):
-        """Factorisation time (ms) per elimination-tree level at the last profile_read."""
+        """Factorisation time (ms) per elimination-tree level and kernel kind at the
+        last profile_read: a list (one entry per level) of {kind: ms}."""
         n = C.c_int32()
-        ms = np.zeros(256)
+        ms = np.zeros(256 * KINDS_N)
         _check(_lib.viv_profile_levels(self.h, _ptr(ms), 256, C.byref(n)))
-        return ms[:n.value].tolist()
+        ms = ms[:n.value * KINDS_N].reshape(n.value, KINDS_N)
+        return [{k: float(row[i]) for i, k in enumerate(KINDS) if row[i] > 0} for row in ms]
 
     def synchronize(self):
         self.stream.synchronize()
