@@ -131,8 +131,10 @@ typedef struct {
                               panels; the refinement recovers the accuracy) */
   int32_t jacobian_fp32;   /* mixed path only: 1 evaluates the volume element Jacobians in
                               FP32 arithmetic (Gamma-face and border rows, the residual, the
-                              Newton test and the refinement products stay FP64); 0 (default)
-                              evaluates every Jacobian entry in FP64 */
+                              Newton test and the refinement products stay FP64) and, once
+                              ||NL|| passes the test, applies one more correction with the
+                              current factors (no new Jacobian); 0 (default) evaluates every
+                              Jacobian entry in FP64 */
 } vivParams;
 enum { VIV_PIVOT_THRESHOLD = 0, VIV_PIVOT_WINDOW = 1 };
 

@@ -108,6 +108,20 @@ struct ChunkRegs {
   float va[PER][4], vb[PER][4];
 };
 
+// (row, k-group) pair t of this thread for A (rows contiguous in memory: the
+// row index runs fastest across a warp) and for B (k contiguous: the k-group
+// runs fastest, so eight lanes read one 128-byte column segment)
+__device__ __forceinline__ void pair_a(int t, int& r, int& g) {
+  const int idx = threadIdx.x + t * THREADS;
+  r = idx % BM;
+  g = idx / BM;
+}
+__device__ __forceinline__ void pair_b(int t, int& r, int& g) {
+  const int idx = threadIdx.x + t * THREADS;
+  g = idx % (KC / 4);
+  r = idx / (KC / 4);
+}
+
 // global loads of K-chunk [k0, k0 + KC) of A (rows rb..) and B (columns
 // cb..), read-only path (A and B are never written by the update)
 __device__ __forceinline__ void load_chunk(ChunkRegs& R, const float* __restrict__ A, int lda,
@@ -115,12 +129,17 @@ __device__ __forceinline__ void load_chunk(ChunkRegs& R, const float* __restrict
                                            int k0) {
 #pragma unroll
   for (int t = 0; t < PER; ++t) {
-    const int idx = threadIdx.x + t * THREADS;
-    const int r = idx % BM, g = idx / BM;
+    int r, g;
+    pair_a(t, r, g);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int k = k0 + 4 * g + j;
       R.va[t][j] = (rb + r < M && k < K) ? __ldg(A + (int64_t)k * lda + rb + r) : 0.f;
+    }
+    pair_b(t, r, g);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = k0 + 4 * g + j;
       R.vb[t][j] = (cb + r < N && k < K) ? __ldg(B + (int64_t)(cb + r) * ldb + k) : 0.f;
     }
   }
@@ -131,21 +150,26 @@ __device__ __forceinline__ void load_chunk(ChunkRegs& R, const float* __restrict
 __device__ __forceinline__ void store_chunk(Stage& S, const ChunkRegs& R) {
 #pragma unroll
   for (int t = 0; t < PER; ++t) {
-    const int idx = threadIdx.x + t * THREADS;
-    const int r = idx % BM, g = idx / BM;
-    uint32_t ah[4], al[4], bh[4], bl[4];
+    uint32_t h[4], l[4];
+    int r, g;
+    pair_a(t, r, g);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      ah[j] = to_tf32(R.va[t][j]);
-      al[j] = to_tf32(R.va[t][j] - __uint_as_float(ah[j]));
-      bh[j] = to_tf32(R.vb[t][j]);
-      bl[j] = to_tf32(R.vb[t][j] - __uint_as_float(bh[j]));
+      h[j] = to_tf32(R.va[t][j]);
+      l[j] = to_tf32(R.va[t][j] - __uint_as_float(h[j]));
     }
-    const int off = g * KCORE_STRIDE + (r >> 3) * CORE_BYTES + (r & 7) * 16;
-    *reinterpret_cast<uint4*>(S.a_hi + off) = make_uint4(ah[0], ah[1], ah[2], ah[3]);
-    *reinterpret_cast<uint4*>(S.a_lo + off) = make_uint4(al[0], al[1], al[2], al[3]);
-    *reinterpret_cast<uint4*>(S.b_hi + off) = make_uint4(bh[0], bh[1], bh[2], bh[3]);
-    *reinterpret_cast<uint4*>(S.b_lo + off) = make_uint4(bl[0], bl[1], bl[2], bl[3]);
+    int off = g * KCORE_STRIDE + (r >> 3) * CORE_BYTES + (r & 7) * 16;
+    *reinterpret_cast<uint4*>(S.a_hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(S.a_lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+    pair_b(t, r, g);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      h[j] = to_tf32(R.vb[t][j]);
+      l[j] = to_tf32(R.vb[t][j] - __uint_as_float(h[j]));
+    }
+    off = g * KCORE_STRIDE + (r >> 3) * CORE_BYTES + (r & 7) * 16;
+    *reinterpret_cast<uint4*>(S.b_hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(S.b_lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
   }
 }
 
