@@ -292,43 +292,53 @@ def run_ours(args, wl, rank, world, local):
     n_fact = sum(i["newton_iters"] for i in pinfos)
     sweeps_p = sum(i["refine_sweeps"] for i in pinfos)
 
-    # roofline of the dominant kernel class, from the events of the timed region
-    dom = max(kern, key=lambda k: kern[k][0])
-    dom_ms, dom_n = kern[dom]
+    # roofline of every kernel class from the events of the profiled pass;
+    # the dominant class (most time) is the headline
     peaks, src = measured_peaks()
-    if dom == "tc_schur_gemm":
-        # tensor-core kind::tf32 issues three products per FP32 multiply-add (3xTF32):
-        # achieved = algorithmic FP32 flops / time; peak = TF32 dense = BF16 measured / 2 (nominal ratio), / 3
-        flops = info["outer_flops"] * n_fact
-        achieved = flops / (dom_ms / 1e3) / 1e12
-        key = "bf16_tflops_sustained" if "bf16_tflops_sustained" in peaks else "bf16_tflops"
-        peak = peaks[key] / 2.0 / 3.0
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": dom,
-                "peak_source": f"{src} {key} / 2 (TF32:BF16 nominal) / 3 (3xTF32 products)",
-                "launches": dom_n, "ms_total": dom_ms}
-    elif dom in ("schur_gemm", "panel_lu", "trsm"):
-        flops = {"schur_gemm": info["gemm_flops"], "panel_lu": info["panel_flops"],
-                 "trsm": info["trsm_flops"]}[dom] * n_fact
-        achieved = flops / (dom_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_SIMT_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_SIMT_TFLOPS, "traffic": None, "kernel": dom,
-                "peak_source": "FP32 SIMT: 148 SMs x 128 lanes x 2 flop x 2.032 GHz (derived)",
-                "launches": dom_n, "ms_total": dom_ms}
-    else:
-        # bytes: front factors read once per solve sweep (fwd/bwd) or the CSR matrix per SpMV
-        fbytes = 4 * info["front_entries"]
-        per = {"fwd_solve": fbytes, "bwd_solve": fbytes, "front_assemble": 2 * fbytes,
-               "spmv": 12 * info["nnz"], "residual": 0, "jacobian": 8 * info["nnz"]}.get(dom, 0)
-        n_calls = sweeps_p if dom in ("fwd_solve", "bwd_solve", "spmv") else n_fact
-        achieved = per * n_calls / (dom_ms / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": dom,
-                "peak_source": src, "launches": dom_n, "ms_total": dom_ms}
+    bf16_key = "bf16_tflops_sustained" if "bf16_tflops_sustained" in peaks else "bf16_tflops"
+    tc_peak = peaks[bf16_key] / 2.0 / 3.0
+    fbytes = 4 * info["front_entries"]
+
+    def roofline_of(kind):
+        k_ms, k_n = kern[kind]
+        if k_ms <= 0:
+            return None
+        sec = k_ms / 1e3
+        if kind == "tc_schur_gemm":
+            # kind::tf32 with three products per FP32 multiply-add (3xTF32): algorithmic
+            # FP32 flops / time against TF32 dense (BF16 measured / 2, nominal) / 3
+            a = info["outer_flops"] * n_fact / sec / 1e12
+            return {"bound": "tensor", "achieved": a, "peak": tc_peak, "unit": "TFLOP/s", "frac": a / tc_peak,
+                    "peak_source": f"{src} {bf16_key} / 2 (TF32:BF16 nominal) / 3 (3xTF32 products)"}
+        if kind in ("schur_gemm", "panel_lu", "trsm"):
+            fl = {"schur_gemm": info["gemm_flops"] - info["outer_flops"],
+                  "panel_lu": info["panel_flops"], "trsm": info["trsm_flops"]}[kind]
+            a = fl * n_fact / sec / 1e12
+            return {"bound": "alu", "achieved": a, "peak": FP32_SIMT_TFLOPS, "unit": "TFLOP/s",
+                    "frac": a / FP32_SIMT_TFLOPS,
+                    "peak_source": "FP32 SIMT: 148 SMs x 128 lanes x 2 flop x 2.032 GHz (derived)"}
+        per = {"fwd_solve": fbytes / 2, "bwd_solve": fbytes / 2, "front_assemble": 2 * fbytes,
+               "spmv": 12 * info["nnz"] + 24 * info["n_dofs"], "jacobian": 12 * info["nnz"]}.get(kind)
+        if per is None:
+            return None
+        calls = sweeps_p if kind in ("fwd_solve", "bwd_solve", "spmv") else n_fact
+        a = per * calls / sec / 1e9
+        return {"bound": "hbm", "achieved": a, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": a / peaks["hbm_gbs"],
+                "peak_source": src}
+
+    rooflines = {}
+    for kind in kern:
+        r = roofline_of(kind)
+        if r is not None:
+            rooflines[kind] = {"achieved": round(r["achieved"], 3), "unit": r["unit"], "frac": round(r["frac"], 4)}
+    dom = max((k for k in kern if roofline_of(k) is not None), key=lambda k: kern[k][0])
+    roof = roofline_of(dom)
+    roof.update({"traffic": None, "kernel": dom, "launches": kern[dom][1], "ms_total": kern[dom][0]})
 
     out = {"metric": METRIC, "value": value, "unit": "time steps/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32 fronts + f64 residual/refinement", "data": "synthetic",
+           "vs_baseline": None, "dtype": ("f32 fronts and volume Jacobians + f64 residual/border/refinement" if j32 else
+                     "f32 fronts + f64 residual/Jacobian/refinement"), "data": "synthetic",
            "config": {"workload": args.workload, "quads": len(mesh["conn"]), "dofs": info["n_dofs"],
                       "nnz": info["nnz"], "fronts": info["n_fronts"], "max_front": info["max_front"],
                       "factor_gflop": info["factor_flops"] / 1e9, **wl, "precision": "mixed",
@@ -339,7 +349,7 @@ def run_ours(args, wl, rank, world, local):
            "kernels_ms": {k: round(v[0], 3) for k, v in kern.items()},
            "profiled": {"steps": args.steps, "ms_per_step": prof_ms / args.steps,
                         "note": "second pass with a CUDA event pair around every launch (kernels_ms, roofline)"},
-           "roofline": roof, "gpu_launches": launches, "clocks": clk,
+           "roofline": roof, "rooflines_by_kind": rooflines, "gpu_launches": launches, "clocks": clk,
            "graphs": "residual, Jacobian, factorisation and refinement sweeps replayed as CUDA graphs"}
     if args.autotune:
         out["autotune"] = {"big_front": tuned[0], "factor_ms": tuned[1]}

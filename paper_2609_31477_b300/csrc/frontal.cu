@@ -432,9 +432,10 @@ __device__ __forceinline__ uint32_t mag_bits(double x) {
 // both conflict-free) and the elimination loop stays rolled: a fully unrolled
 // 32-step elimination is too long for the instruction cache.
 template <class T>
-__device__ void diag_block_lu(const FT& ft, int f, int k, T* pool, int32_t* piv, int32_t* stats) {
+__device__ void diag_block_lu(const FT& ft, int f, int k, T* pool, int32_t* piv, int32_t* perm, int32_t* stats) {
   __shared__ T A[PANEL_NB][PANEL_NB + 1];
   __shared__ int s_piv[PANEL_NB];
+  __shared__ int s_src[PANEL_NB];
   const int m = ft.m[f], p = ft.p[f];
   const int nbe = min(PANEL_NB, p - k);
   const int lane = threadIdx.x & 31;
@@ -472,7 +473,7 @@ __device__ void diag_block_lu(const FT& ft, int f, int k, T* pool, int32_t* piv,
     }
     __syncwarp();
     if (lane > jj && lane < nbe) {
-      const T l = A[lane][jj] / A[jj][jj];
+      const T l = A[lane][jj] * (T(1) / A[jj][jj]);
       A[lane][jj] = l;
 #pragma unroll 8
       for (int c = jj + 1; c < nbe; ++c) A[lane][c] -= l * A[jj][c];
@@ -482,15 +483,29 @@ __device__ void diag_block_lu(const FT& ft, int f, int k, T* pool, int32_t* piv,
 #pragma unroll 8
   for (int c = 0; c < PANEL_NB; ++c)
     if (lane < nbe && c < nbe) F[(int64_t)c * m + lane] = A[lane][c];
-  if (lane < nbe) piv[ft.piv_off[f] + k + lane] = k + s_piv[lane];
+  // the block's interchanges composed: new row i of the block holds old row
+  // s_src[i] (all interchanges of this pivoting stay inside the block)
+  s_src[lane] = lane;
+  __syncwarp();
+  if (lane == 0)
+    for (int jj = 0; jj < nbe; ++jj) {
+      const int r = s_piv[jj], t = s_src[jj];
+      s_src[jj] = s_src[r];
+      s_src[r] = t;
+    }
+  __syncwarp();
+  if (lane < nbe) {
+    piv[ft.piv_off[f] + k + lane] = k + s_piv[lane];
+    perm[ft.piv_off[f] + k + lane] = k + s_src[lane];
+  }
 }
 
 // the diagonal blocks of the fronts of one launch (those not factored by the
 // previous panel's Schur update)
 template <class T>
 __global__ void __launch_bounds__(32) diag_lu_kernel(FT ft, const int32_t* work, int k, T* pool, int32_t* piv,
-                                                     int32_t* stats) {
-  diag_block_lu<T>(ft, work[WORK_STRIDE * blockIdx.x], k, pool, piv, stats);
+                                                     int32_t* perm, int32_t* stats) {
+  diag_block_lu<T>(ft, work[WORK_STRIDE * blockIdx.x], k, pool, piv, perm, stats);
 }
 
 // One launch, two kinds of items.  Kind 0 (f, r0): rows [r0, r0 + 256) of the
@@ -499,29 +514,25 @@ __global__ void __launch_bounds__(32) diag_lu_kernel(FT ft, const int32_t* work,
 // for columns in [k + nbe, c_end), U12 = L11^{-1} P A12.
 template <class T>
 __global__ void __launch_bounds__(WINDOW_THREADS) window_kernel(FT ft, const int32_t* work, int k, T* pool,
-                                                     const int32_t* piv, int32_t* stats, T thresh) {
+                                                     const int32_t* perm, int32_t* stats, T thresh) {
   const int32_t* it = work + WORK_STRIDE * blockIdx.x;
   const int f = it[1];
   const int m = ft.m[f], p = ft.p[f];
   const int nbe = min(PANEL_NB, p - k);
   T* F = pool + ft.off[f];
   __shared__ T D[PANEL_NB][PANEL_NB + 1];   // the factored diagonal block (L11 \ U11)
+  __shared__ T Dinv[PANEL_NB];              // reciprocals of U11's diagonal
   __shared__ int s_src[PANEL_NB];
   for (int e = threadIdx.x; e < PANEL_NB * PANEL_NB; e += blockDim.x) {
     const int i = e % PANEL_NB, c = e / PANEL_NB;
     D[i][c] = (i < nbe && c < nbe) ? F[(int64_t)(k + c) * m + k + i] : T(0);
   }
-  if (threadIdx.x == 0) {
-    // net permutation of the block rows: new row i takes old row s_src[i]
-    for (int i = 0; i < PANEL_NB; ++i) s_src[i] = i;
-    const int32_t* pv = piv + ft.piv_off[f];
-    for (int jj = 0; jj < nbe; ++jj) {
-      const int r = pv[k + jj] - k;
-      const int tmp = s_src[jj];
-      s_src[jj] = s_src[r];
-      s_src[r] = tmp;
-    }
-  }
+  if (threadIdx.x < PANEL_NB)
+    Dinv[threadIdx.x] = threadIdx.x < nbe ? T(1) / F[(int64_t)(k + threadIdx.x) * m + k + threadIdx.x] : T(0);
+  // the block's composed interchanges (written by its diagonal LU): new row i
+  // takes old row s_src[i]
+  if (threadIdx.x < PANEL_NB)
+    s_src[threadIdx.x] = threadIdx.x < nbe ? perm[ft.piv_off[f] + k + threadIdx.x] - k : threadIdx.x;
   __syncthreads();
   if (it[0] == 0) {
     const int g = it[2] + threadIdx.x;
@@ -534,7 +545,7 @@ __global__ void __launch_bounds__(WINDOW_THREADS) window_kernel(FT ft, const int
 #pragma unroll
       for (int c = 0; c < PANEL_NB; ++c) {
         if (c < nbe) {
-          x[c] /= D[c][c];
+          x[c] *= Dinv[c];
           big = big || fabs(x[c]) * thresh > T(1);
 #pragma unroll
           for (int c2 = c + 1; c2 < PANEL_NB; ++c2) x[c2] -= x[c] * D[c][c2];
@@ -630,7 +641,7 @@ __global__ void trsm_kernel(FT ft, const int32_t* work, T* pool) {
 // diagonal block at (rb, rb): once the tile is updated, one warp factors it.
 template <class T>
 __global__ void __launch_bounds__(256) gemm_kernel(FT ft, const int32_t* work, T* pool, int32_t* piv,
-                                                   int32_t* stats) {
+                                                   int32_t* perm, int32_t* stats) {
   const int32_t* it = work + WORK_STRIDE * blockIdx.x;
   const int f = it[0], rb = it[1], cb = it[2], r_end = it[3], c_end = it[4], kb = it[5], kl = it[6];
   const int m = ft.m[f];
@@ -685,7 +696,7 @@ __global__ void __launch_bounds__(256) gemm_kernel(FT ft, const int32_t* work, T
   }
   if (it[7]) {
     __syncthreads();   // the whole tile is updated (block-scope visibility of its stores)
-    if (threadIdx.x < 32) diag_block_lu<T>(ft, f, rb, pool, piv, stats);
+    if (threadIdx.x < 32) diag_block_lu<T>(ft, f, rb, pool, piv, perm, stats);
   }
 }
 
@@ -764,10 +775,10 @@ __global__ void __launch_bounds__(INV_WARPS * 32) diag_inv_kernel(FT ft, const i
     for (int j = 0; j < nb; ++j) F[(int64_t)j * m + lane] = Bw[lane][j];
 }
 
-// Composition of a front's row interchanges: new pivot row i holds old row
-// perm[i].  With windowed pivoting every interchange stays inside its
-// 32-row block and the blocks are composed in parallel.
-__global__ void perm_kernel(FT ft, const int32_t* piv, int32_t* perm, bool block_local) {
+// Composition of a front's row interchanges (threshold pivoting): new pivot
+// row i holds old row perm[i].  (With windowed pivoting each diagonal LU
+// writes its block's composition itself.)
+__global__ void perm_kernel(FT ft, const int32_t* piv, int32_t* perm) {
   extern __shared__ int32_t s_perm[];
   const int f = blockIdx.x;
   const int p = ft.p[f];
@@ -779,22 +790,13 @@ __global__ void perm_kernel(FT ft, const int32_t* piv, int32_t* perm, bool block
     sv[i] = pv[i];
   }
   __syncthreads();
-  if (block_local) {
-    for (int b = threadIdx.x; b * 32 < p; b += blockDim.x)
-      for (int j = b * 32; j < min(p, b * 32 + 32); ++j) {
-        const int r = sv[j];
-        const int32_t t = sp[j];
-        sp[j] = sp[r];
-        sp[r] = t;
-      }
-  } else if (threadIdx.x == 0) {
+  if (threadIdx.x == 0)
     for (int j = 0; j < p; ++j) {
       const int r = sv[j];
       const int32_t t = sp[j];
       sp[j] = sp[r];
       sp[r] = t;
     }
-  }
   __syncthreads();
   for (int i = threadIdx.x; i < p; i += blockDim.x) perm[ft.piv_off[f] + i] = sp[i];
 }
@@ -1025,7 +1027,7 @@ void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* front
         trsm_kernel<T><<<grid, TRSM_COLS, 0, s>>>(ft, w, fronts);
         break;
       case L_GEMM:
-        gemm_kernel<T><<<grid, 256, 0, s>>>(ft, w, fronts, piv, stats);
+        gemm_kernel<T><<<grid, 256, 0, s>>>(ft, w, fronts, piv, perm, stats);
         break;
       case L_TC_GEMM:
         if constexpr (std::is_same<T, float>::value) {
@@ -1056,10 +1058,10 @@ void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* front
         break;
       }
       case L_DIAG:
-        diag_lu_kernel<T><<<grid, 32, 0, s>>>(ft, w, L.k, fronts, piv, stats);
+        diag_lu_kernel<T><<<grid, 32, 0, s>>>(ft, w, L.k, fronts, piv, perm, stats);
         break;
       case L_WINDOW:
-        window_kernel<T><<<grid, WINDOW_THREADS, 0, s>>>(ft, w, L.k, fronts, piv, stats, (T)threshold);
+        window_kernel<T><<<grid, WINDOW_THREADS, 0, s>>>(ft, w, L.k, fronts, perm, stats, (T)threshold);
         break;
       case L_LASWP:
         laswp_kernel<T><<<grid, LASWP_COLS, 0, s>>>(ft, w, L.k, fronts, piv);
@@ -1069,9 +1071,9 @@ void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* front
   VIV_CUDA(cudaGetLastError());
   prof_level(-1);
   // solve preparation: composed row permutations, inverted diagonal blocks
-  {
+  if (!window) {   // (windowed pivoting: the diagonal LUs wrote the permutations)
     Launched LL(K_TRSM, s);
-    perm_kernel<<<m.n_fronts, 128, 2 * (size_t)std::max(1, m.max_p) * sizeof(int32_t), s>>>(ft, piv, perm, window);
+    perm_kernel<<<m.n_fronts, 128, 2 * (size_t)std::max(1, m.max_p) * sizeof(int32_t), s>>>(ft, piv, perm);
   }
   if (!m.inv_items.empty()) {
     Launched LL(K_TRSM, s);
