@@ -55,6 +55,8 @@ def parse():
                     help="front pivoting: partial pivoting inside each 32-row diagonal block (window) or "
                          "threshold pivoting over all fully summed rows")
     ap.add_argument("--no-threshold-path", action="store_true")
+    ap.add_argument("--predictor", default="extrapolate", choices=["extrapolate", "previous"],
+                    help="Newton starting point of a BDF2 step: 2 U^n - U^(n-1) or U^n")
     ap.add_argument("--jacobian", default="fp32", choices=["fp32", "fp64"],
                     help="mixed path: volume element Jacobians in FP32 (faces, border rows, residual and "
                          "refinement stay FP64) or everything in FP64")
@@ -169,7 +171,7 @@ def oracle_sample(wl, newton_iters):
 
 
 # ---------------------------------------------------------------------------------
-def run_sweep(viv, I, n_cases, n_steps, pivoting, jacobian_fp32, seed=7):
+def run_sweep(viv, I, n_cases, n_steps, pivoting, jacobian_fp32, predictor, seed=7):
     """Served parameter sweep (a sample of the 64-case, 200-step sweep): cases
     with 2k-20k quads, Re ~ U[100, 300], U* log-uniform in [4, 20], Poisson
     arrivals, a 24 GB device budget; every case runs n_steps BDF steps."""
@@ -193,7 +195,7 @@ def run_sweep(viv, I, n_cases, n_steps, pivoting, jacobian_fp32, seed=7):
     for k, (m, Re, Us) in enumerate(cases):
         srv.submit(dev[m], I.viv_initial_velocity(meshes[m], 1.0, 1e-3, 100 + k), Re=Re, Ustar=Us, dt=0.02,
                    n_steps=n_steps, arrival_time=float(arrivals[k]), pivoting=pivoting,
-                   jacobian_fp32=jacobian_fp32)
+                   jacobian_fp32=jacobian_fp32, predictor=predictor)
     res = srv.wait_all(n_cases, timeout_s=900)
     st = srv.stats()
     srv.close()
@@ -243,8 +245,9 @@ def run_ours(args, wl, rank, world, local):
     info = M.info
     piv = viv.VIV_PIVOT_WINDOW if args.pivoting == "window" else viv.VIV_PIVOT_THRESHOLD
     j32 = 1 if args.jacobian == "fp32" else 0
+    pred = 1 if args.predictor == "extrapolate" else 0
     case = viv.viv_case(M, wl["Re"], wl["Ustar"], wl["dt"], u0, precision=viv.VIV_MIXED, pivoting=piv,
-                        jacobian_fp32=j32)
+                        jacobian_fp32=j32, predictor=pred)
     stream = case.stream           # every kernel of the case runs on its own stream
     if args.autotune:
         tuned = case.autotune()
@@ -342,7 +345,7 @@ def run_ours(args, wl, rank, world, local):
            "config": {"workload": args.workload, "quads": len(mesh["conn"]), "dofs": info["n_dofs"],
                       "nnz": info["nnz"], "fronts": info["n_fronts"], "max_front": info["max_front"],
                       "factor_gflop": info["factor_flops"] / 1e9, **wl, "precision": "mixed",
-                      "pivoting": args.pivoting, "jacobian": args.jacobian,
+                      "pivoting": args.pivoting, "jacobian": args.jacobian, "predictor": args.predictor,
                       "l2": f"inputs larger than L2 (front pool {4 * info['front_entries'] / 1e9:.1f} GB)",
                       "parallelism": "replicas" if world > 1 else "single"},
            "newton_iters_per_step": newton, "refine_sweeps_per_step": sweeps,
@@ -355,7 +358,8 @@ def run_ours(args, wl, rank, world, local):
         out["autotune"] = {"big_front": tuned[0], "factor_ms": tuned[1]}
 
     if not args.no_fp64 and rank == 0:
-        c64 = viv.viv_case(M, wl["Re"], wl["Ustar"], wl["dt"], u0, precision=viv.VIV_FP64, pivoting=piv)
+        c64 = viv.viv_case(M, wl["Re"], wl["Ustar"], wl["dt"], u0, precision=viv.VIV_FP64, pivoting=piv,
+                           predictor=pred)
         c64.step()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -373,7 +377,7 @@ def run_ours(args, wl, rank, world, local):
     if not args.no_threshold_path and args.pivoting == "window" and rank == 0:
         # the same mixed path with threshold pivoting over all fully summed rows
         ct = viv.viv_case(M, wl["Re"], wl["Ustar"], wl["dt"], u0, precision=viv.VIV_MIXED,
-                          pivoting=viv.VIV_PIVOT_THRESHOLD, jacobian_fp32=j32)
+                          pivoting=viv.VIV_PIVOT_THRESHOLD, jacobian_fp32=j32, predictor=pred)
         ct.step()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -413,7 +417,7 @@ def run_ours(args, wl, rank, world, local):
                       "h2d_bytes_per_step": 8 * n_st, "d2h_bytes_per_step": 8 * n_st}
 
     if rank == 0 and not args.no_sweep:
-        out["sweep"] = run_sweep(viv, I, args.sweep_cases, args.sweep_steps, piv, j32)
+        out["sweep"] = run_sweep(viv, I, args.sweep_cases, args.sweep_steps, piv, j32, pred)
 
     if rank == 0 and not args.no_cpu_baseline:
         v, desc, secs = oracle_sample(wl, newton)

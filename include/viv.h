@@ -135,6 +135,11 @@ typedef struct {
                               ||NL|| passes the test, applies one more correction with the
                               current factors (no new Jacobian); 0 (default) evaluates every
                               Jacobian entry in FP64 */
+  int32_t predictor;       /* Newton starting point of a BDF2 step: 0 (default) the previous
+                              time level U^n; 1 the linear extrapolation 2 U^n - U^{n-1} of
+                              velocity and position (and so of delta); p and lambda start
+                              from U^n either way.  The converged state does not depend on it
+                              beyond the Newton tolerance. */
 } vivParams;
 enum { VIV_PIVOT_THRESHOLD = 0, VIV_PIVOT_WINDOW = 1 };
 
@@ -190,7 +195,8 @@ vivStatus viv_get_state(const vivCase* c, int device, double* u, double* p, doub
                         double* delta, double* t);
 
 /* Begin a time step: shift the BDF history and form the nodal rate
- * coefficients (BDF1 on the first step, BDF2 after). */
+ * coefficients (BDF1 on the first step, BDF2 after).  With predictor = 1 a
+ * BDF2 step's Newton iterate starts from 2 U^n - U^{n-1} (u, x, delta). */
 vivStatus viv_begin_step(vivCase* c);
 
 /* Residual NL(U) (Eq. nonlinear_functional_discrete) and/or Jacobian

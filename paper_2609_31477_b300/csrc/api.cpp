@@ -142,6 +142,7 @@ void begin_step(vivCase* c) {
   if (bdf2) {
     c->c0 = 1.5 / dt;
     launch_bdf_history(m, s, -2.0 / dt, 0.5 / dt, false, c->stream);
+    if (c->prm.predictor == 1) launch_extrapolate(m, s, c->stream);
   } else {
     c->c0 = 1.0 / dt;
     launch_bdf_history(m, s, -1.0 / dt, 0.0, false, c->stream);
@@ -383,6 +384,7 @@ static vivStatus case_create_impl(vivMesh* mesh, const vivParams* prm, const dou
   VIV_CHECK(prm->pivoting == VIV_PIVOT_THRESHOLD || prm->pivoting == VIV_PIVOT_WINDOW, VIV_ERR_ARG,
             "unknown pivoting");
   VIV_CHECK(prm->jacobian_fp32 == 0 || prm->jacobian_fp32 == 1, VIV_ERR_ARG, "jacobian_fp32 must be 0 or 1");
+  VIV_CHECK(prm->predictor == 0 || prm->predictor == 1, VIV_ERR_ARG, "predictor must be 0 or 1");
   VIV_CHECK(mesh->m.on_device, VIV_ERR_STATE, "mesh was analysed on the host only");
   *out = nullptr;
   vivCase* c = new vivCase();

@@ -53,6 +53,20 @@ __global__ void bdf_kernel(int64_t n2, const double* u_n, const double* u_nm1, c
   hx[i] = sx;
 }
 
+// Newton starting point 2 U^n - U^{n-1} for u and x (all nodal entries)
+__global__ void extrapolate_kernel(int64_t n2, const double* u_n, const double* u_nm1, const double* x_n,
+                                   const double* x_nm1, double* u, double* x) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n2) return;
+  u[i] = 2.0 * u_n[i] - u_nm1[i];
+  x[i] = 2.0 * x_n[i] - x_nm1[i];
+}
+
+// delta read back from a Gamma node's position (x = X + delta on Gamma)
+__global__ void delta_from_x_kernel(int64_t a, const double* X, const double* x, double* delta) {
+  if (threadIdx.x < 2) delta[threadIdx.x] = x[2 * a + threadIdx.x] - X[2 * a + threadIdx.x];
+}
+
 // U += dU for every nodal field; Gamma nodes follow x = X + delta_new
 __global__ void update_kernel(int64_t n, const int32_t* node_dof, const int32_t* tags, const double* X,
                               const int32_t* delta_dof, const double* delta, const double* dU, double* u,
@@ -131,6 +145,19 @@ void launch_bdf_history(const Mesh& m, CaseState& st, double a_n, double a_nm1, 
   Launched L(K_VEC, s);
   bdf_kernel<<<blocks_for(n2, 256), 256, 0, s>>>(n2, st.u_n, st.u_nm1, st.x_n, st.x_nm1, a_n, a_nm1, st.hu,
                                                    st.hx);
+  VIV_CUDA(cudaGetLastError());
+}
+
+void launch_extrapolate(const Mesh& m, CaseState& st, cudaStream_t s) {
+  const int64_t n2 = 2 * m.n_nodes;
+  {
+    Launched L(K_VEC, s);
+    extrapolate_kernel<<<blocks_for(n2, 256), 256, 0, s>>>(n2, st.u_n, st.u_nm1, st.x_n, st.x_nm1, st.u, st.x);
+  }
+  if (m.n_faces > 0) {
+    Launched L(K_VEC, s);
+    delta_from_x_kernel<<<1, 32, 0, s>>>(m.faces[0], m.d_X, st.x, st.delta);
+  }
   VIV_CUDA(cudaGetLastError());
 }
 

@@ -285,6 +285,7 @@ void launch_jacobian(const Mesh& m, const CaseState& st, const vivParams& prm, d
                      cudaStream_t s);
 void launch_norm2(const double* v, int64_t n, double* partial, double* out, cudaStream_t s);
 void launch_bdf_history(const Mesh& m, CaseState& st, double a_n, double a_nm1, bool shift, cudaStream_t s);
+void launch_extrapolate(const Mesh& m, CaseState& st, cudaStream_t s);
 void launch_update(const Mesh& m, CaseState& st, const double* dU, cudaStream_t s);
 void launch_spmv_residual(const Mesh& m, const double* J, const double* x, const double* b, double* r,
                           cudaStream_t s);

@@ -52,7 +52,7 @@ class Params(C.Structure):
                 ("lame_scale", C.c_double), ("newton_tol", C.c_double), ("max_newton", C.c_int32),
                 ("precision", C.c_int32), ("refine_tol", C.c_double), ("refine_max", C.c_int32),
                 ("pivot_threshold", C.c_double), ("source", C.c_int32), ("source_amp", C.c_double),
-                ("pivoting", C.c_int32), ("jacobian_fp32", C.c_int32)]
+                ("pivoting", C.c_int32), ("jacobian_fp32", C.c_int32), ("predictor", C.c_int32)]
 
 
 class StepInfo(C.Structure):
@@ -280,11 +280,12 @@ class Case:
 
     def __init__(self, mesh: Mesh, u0, rho, mu, k, dt, precision=VIV_FP64, lame_scale=1.0,
                  newton_tol=1e-10, max_newton=25, refine_tol=0.0, refine_max=0, pivot_threshold=0.01,
-                 stream=None, source=0, source_amp=0.0, pivoting=0, jacobian_fp32=0):
+                 stream=None, source=0, source_amp=0.0, pivoting=0, jacobian_fp32=0, predictor=0):
         lib = load()
         self.mesh = mesh
         self.params = Params(rho, mu, k, dt, lame_scale, newton_tol, max_newton, precision, refine_tol,
-                             refine_max, pivot_threshold, source, source_amp, pivoting, jacobian_fp32)
+                             refine_max, pivot_threshold, source, source_amp, pivoting, jacobian_fp32,
+                             predictor)
         u0 = np.ascontiguousarray(u0, dtype=np.float64)
         import torch
         # each case owns a non-default stream (graphs cannot capture the legacy stream)
@@ -422,10 +423,10 @@ class Server:
 
     def submit(self, mesh: Mesh, u0, Re, Ustar, dt, n_steps, arrival_time=0.0, precision=VIV_MIXED,
                U_inf=1.0, D=1.0, rho=1.0, newton_tol=1e-10, max_newton=25, pivoting=VIV_PIVOT_THRESHOLD,
-               jacobian_fp32=0):
+               jacobian_fp32=0, predictor=0):
         mu = rho * U_inf * D / Re
         prm = Params(rho, mu, stiffness(rho, U_inf, Ustar), dt, 1.0, newton_tol, max_newton, precision, 0.0, 0,
-                     0.01, 0, 0.0, pivoting, jacobian_fp32)
+                     0.01, 0, 0.0, pivoting, jacobian_fp32, predictor)
         u0 = np.ascontiguousarray(u0, dtype=np.float64)
         req = Request(mesh.h.value, prm, u0.ctypes.data, int(n_steps), float(arrival_time))
         rid = C.c_int64()
