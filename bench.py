@@ -34,6 +34,9 @@ WORKLOADS = {
     "viv_re100_m24": dict(m=24, Re=100.0, Ustar=8.0, dt=0.05),
 }
 FP32_SIMT_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12      # 148 SMs x 128 FP32 lanes x FMA x 2.032 GHz
+# DRAM bytes (read + write) per 128 x 128 tile of the tensor-core Schur update, from one ncu capture on the
+# 6,208-quad member of the mesh family (profiles/tc_front_kernel_viv_re100_m24.md); scaled by tiles per launch
+TC_DRAM_BYTES_PER_TILE = 73.4e3
 
 
 def parse():
@@ -336,7 +339,14 @@ def run_ours(args, wl, rank, world, local):
             rooflines[kind] = {"achieved": round(r["achieved"], 3), "unit": r["unit"], "frac": round(r["frac"], 4)}
     dom = max((k for k in kern if roofline_of(k) is not None), key=lambda k: kern[k][0])
     roof = roofline_of(dom)
-    roof.update({"traffic": None, "kernel": dom, "launches": kern[dom][1], "ms_total": kern[dom][0]})
+    traffic = None
+    if dom == "tc_schur_gemm" and kern[dom][1]:
+        # tiles per launch from the outer-update flops (K = 128 per outer block)
+        tiles = info["outer_flops"] * n_fact / (2.0 * 128 * 128 * 128) / kern[dom][1]
+        traffic = TC_DRAM_BYTES_PER_TILE * tiles
+        roof["traffic_note"] = (f"ncu DRAM bytes per tile (6,208-quad capture) x {tiles:.0f} tiles per launch; "
+                                "algorithmic operand + C bytes per tile without reuse: 262144")
+    roof.update({"traffic": traffic, "kernel": dom, "launches": kern[dom][1], "ms_total": kern[dom][0]})
 
     out = {"metric": METRIC, "value": value, "unit": "time steps/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
