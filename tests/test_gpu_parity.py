@@ -184,3 +184,33 @@ def test_cylinder_ten_steps_match_oracle(viv, cylinder_reference, precision, piv
         for k, v in ref.items():
             setattr(oc, k, v)
         _compare_fields(oc, st)
+
+
+def test_large_front_threshold_and_level_profile(viv):
+    """The same refined solution whatever the large-front threshold (outer
+    blocks on the tensor cores for every front of order >= 96, for fronts of
+    order >= 256, or for none), and a per-level profile that splits the
+    factorisation time by tree level and kind."""
+    mesh, oc, M, case = _pair(viv, 12, viv.VIV_MIXED, pivoting=viv.VIV_PIVOT_WINDOW)
+    _mid_step_state(viv, oc, case, 31)
+    case.assemble(viv.VIV_RES | viv.VIV_JAC)
+    b = np.random.default_rng(9).standard_normal(M.n_dofs)
+    levels = int(M.fronts()["level"].max()) + 1
+    fact_kinds = ("front_assemble", "panel_lu", "trsm", "schur_gemm", "tc_schur_gemm")
+    ys = {}
+    for bf in (96, 1 << 30, 256):
+        case.set_big_front(bf)
+        case.profile(True)
+        case.factor()
+        ys[bf], _ = case.solve_rhs(b)
+        kinds = case.profile_read()
+        lv = case.profile_levels()
+        case.profile(False)
+        assert len(lv) == levels
+        per_level = sum(sum(d.values()) for d in lv)
+        per_kind = sum(kinds[k][0] for k in fact_kinds)
+        assert 0 < per_level <= per_kind * (1 + 1e-9) + 1e-9
+        uses_tc = any("tc_schur_gemm" in d for d in lv)
+        assert uses_tc == (bf != 1 << 30)
+    for bf in (1 << 30, 256):
+        assert rel_l2(ys[bf], ys[96]) <= 1e-10, (bf, rel_l2(ys[bf], ys[96]))
