@@ -41,7 +41,7 @@ typedef enum {
   VIV_ERR_PIVOT = 4,           /* a front met an exactly zero pivot column */
   VIV_ERR_NEWTON = 5,          /* Newton did not reach the tolerance in max_newton */
   VIV_ERR_NONFINITE = 6,       /* a residual or correction norm is NaN/Inf */
-  VIV_ERR_TIMEOUT = 7,         /* reserved for bounded device waits */
+  VIV_ERR_TIMEOUT = 7,         /* a bounded device wait expired (tensor-core mbarrier) */
   VIV_ERR_ADMISSION = 8,       /* server: request exceeds the memory budget */
   VIV_ERR_STATE = 9            /* call out of order (e.g. solve before factor) */
 } vivStatus;
@@ -55,7 +55,8 @@ enum {
   VIV_TAG_P_FIX = 64                           /* pressure held (all-Dirichlet problems) */
 };
 
-/* precision of the Jacobian and factors; residual, refinement, state: FP64 always */
+/* precision of the factors (and of the Jacobian; see jacobian_fp32); residual,
+ * refinement, state: FP64 always */
 enum { VIV_FP64 = 0, VIV_MIXED = 1 };
 /* what viv_assemble builds */
 enum { VIV_RES = 1, VIV_JAC = 2 };
@@ -209,10 +210,14 @@ vivStatus viv_get_residual(const vivCase* c, double* r);
 vivStatus viv_get_jacobian(const vivCase* c, double* vals);
 
 /* Numeric multifrontal LU of the Jacobian with threshold partial pivoting
- * inside fronts; delta is eliminated last in the root front. */
+ * inside fronts, or windowed pivoting (vivParams.pivoting); delta is
+ * eliminated last in the root front.  The factors keep each 32 x 32 diagonal
+ * block's L and U inverted (for the solves) and are read only by this
+ * library's solves. */
 vivStatus viv_factor(vivCase* c);
 /* Solve J dU = -NL for the Newton correction with iterative refinement
- * against the FP64 Jacobian; sweeps (nullable) receives the sweep count. */
+ * against the FP64 Jacobian values (with jacobian_fp32: the widened FP32
+ * volume entries); sweeps (nullable) receives the sweep count. */
 vivStatus viv_solve(vivCase* c, int* sweeps);
 /* Solve J y = b for a host or device right-hand side b (n_dofs, FP64). */
 vivStatus viv_solve_rhs(vivCase* c, int device, const double* b, double* y, int* sweeps);
@@ -229,9 +234,9 @@ vivStatus viv_solve_rhs(vivCase* c, int device, const double* b, double* y, int*
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) and caches it; make that first call before any
  *    stream capture.
- *  - A mesh whose workspace ((sum of front orders) + n_dofs, times 4 bytes on
- *    the mixed path or 8 on the FP64 path) exceeds 8 MiB is rejected with
- *    VIV_ERR_ARG.
+ *  - A mesh whose workspace (every front's solve vector with its slice
+ *    partial sums, plus n_dofs; 4 bytes per entry on the mixed path, 8 on the
+ *    FP64 path) exceeds 8 MiB is rejected with VIV_ERR_ARG.
  *  - All calls share the array and it keeps the last call's contents; the
  *    solve writes every workspace entry before reading it, so no clearing is
  *    needed.  Calls whose GPU work overlaps (other streams or threads) race on
