@@ -208,7 +208,10 @@ def run_sweep(viv, I, n_cases, n_steps, pivoting, jacobian_fp32, predictor, seed
     ok = sum(r["status"] == "OK" for r in res)
     last = max(r["finish_s"] for r in res) if res else 0.0
     return {"cases": n_cases, "ok": ok, "steps_per_case": n_steps, "step_ms_p50": st["step_ms_p50"],
-            "step_ms_p99": st["step_ms_p99"], "steps": st["steps"], "elapsed_s": last,
+            "step_ms_p99": st["step_ms_p99"], "steady_step_ms_p50": st["steady_ms_p50"],
+            "steady_step_ms_p99": st["steady_ms_p99"],
+            "steady_note": "without each case's first two steps (they capture its CUDA graphs)",
+            "steps": st["steps"], "elapsed_s": last,
             "steps_per_s": st["steps"] / last if last else None,
             "cases_per_hour_at_200_steps": 3600.0 * ok / last * n_steps / 200.0 if last else None,
             "peak_active": st["peak_active"], "peak_gb": st["peak_bytes"] / 1e9,

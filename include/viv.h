@@ -307,6 +307,8 @@ typedef struct {
   double elapsed_s;
   int32_t peak_active, active, pending;
   size_t peak_bytes;                    /* peak of the admitted predicted device bytes */
+  double steady_ms_p50, steady_ms_p99;  /* the same without each case's first two steps, which
+                                           capture the case's CUDA graphs (BDF1, then BDF2) */
 } vivServerStats;
 /* A serving loop: requests arrive over time, are admitted FIFO while the
  * predicted device bytes of the admitted cases (viv_mesh_info) stay within

@@ -59,6 +59,7 @@ struct vivServer {
   std::map<int64_t, Done> finished;
   std::deque<int64_t> unpolled;
   std::vector<double> step_ms;
+  std::vector<double> steady_ms;    // without each case's first two (graph-capturing) steps
   int64_t steps_total = 0, cases_done = 0;
   bool stop = false;
   std::thread sched;
@@ -122,6 +123,7 @@ void run_case(vivServer* S, Req q, double admit_s) {
   S->used -= q.bytes;
   S->active -= 1;
   S->step_ms.insert(S->step_ms.end(), lat.begin(), lat.end());
+  if (lat.size() > 2) S->steady_ms.insert(S->steady_ms.end(), lat.begin() + 2, lat.end());
   S->steps_total += (int64_t)lat.size();
   S->cases_done += 1;
   S->finished[q.id] = std::move(d);
@@ -270,11 +272,15 @@ vivStatus viv_server_stats(vivServer* S, vivServerStats* out) {
     return VIV_ERR_ARG;
   }
   std::lock_guard<std::mutex> lk(S->mu);
-  std::vector<double> v = S->step_ms;
-  std::sort(v.begin(), v.end());
-  auto pct = [&](double q) { return v.empty() ? 0.0 : v[std::min(v.size() - 1, (size_t)(q * (v.size() - 1) + 0.5))]; };
-  out->step_ms_p50 = pct(0.50);
-  out->step_ms_p99 = pct(0.99);
+  auto pct = [](std::vector<double> v, double q) {
+    if (v.empty()) return 0.0;
+    std::sort(v.begin(), v.end());
+    return v[std::min(v.size() - 1, (size_t)(q * (v.size() - 1) + 0.5))];
+  };
+  out->step_ms_p50 = pct(S->step_ms, 0.50);
+  out->step_ms_p99 = pct(S->step_ms, 0.99);
+  out->steady_ms_p50 = pct(S->steady_ms, 0.50);
+  out->steady_ms_p99 = pct(S->steady_ms, 0.99);
   out->steps = S->steps_total;
   out->cases_done = S->cases_done;
   out->elapsed_s = S->now();

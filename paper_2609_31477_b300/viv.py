@@ -90,7 +90,8 @@ class Result(C.Structure):
 class ServerStats(C.Structure):
     _fields_ = [("step_ms_p50", C.c_double), ("step_ms_p99", C.c_double), ("steps", C.c_int64),
                 ("cases_done", C.c_int64), ("elapsed_s", C.c_double), ("peak_active", C.c_int32),
-                ("active", C.c_int32), ("pending", C.c_int32), ("peak_bytes", C.c_size_t)]
+                ("active", C.c_int32), ("pending", C.c_int32), ("peak_bytes", C.c_size_t),
+                ("steady_ms_p50", C.c_double), ("steady_ms_p99", C.c_double)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)

@@ -83,4 +83,5 @@ def test_poisson_arrivals_report_latency(env):
     srv.close()
     assert len(res) == 8 and all(r["status"] == "OK" for r in res)
     assert st["steps"] == 24 and 0 < st["step_ms_p50"] <= st["step_ms_p99"]
+    assert 0 < st["steady_ms_p50"] <= st["steady_ms_p99"] <= st["step_ms_p99"]
     assert all(r["admit_s"] >= r["submit_s"] - 1e-6 for r in res)
