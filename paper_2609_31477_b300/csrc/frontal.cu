@@ -1,24 +1,35 @@
 // Multifrontal LU of the Jacobian on the GPU (replaces the sparse direct
 // solver of Section 4.3).  Fronts are dense column-major blocks in one pool;
-// each tree level is processed by batched launches over all of its fronts:
+// each tree level is processed by batched launches over all of its fronts, in
+// 32-column panel steps:
 //
 //   assemble : zero the front, place the original CSR entries, extend-add the
 //              children's contribution blocks (children in a fixed order, so
 //              the sums are deterministic)
-//   panel    : partial LU of PANEL_NB pivot columns with threshold partial
+//   threshold pivoting (vivParams.pivoting = 0):
+//     panel  : partial LU of PANEL_NB pivot columns with threshold partial
 //              pivoting restricted to the fully summed rows; a pivot below the
 //              threshold is counted, an empty fully summed column is replaced
-//              by a small static perturbation and counted.  A front's whole
-//              m x PANEL_NB panel is held in the distributed shared memory of
-//              a cluster of PANEL_CLUSTER CTAs; pivot choice is a cluster-wide
-//              reduction read through DSMEM, and the row interchanges of the
-//              columns outside the panel are applied afterwards (laswp)
-//   trsm     : U12 = L11^{-1} A12 for the panel rows
-//   gemm     : A22 -= L21 U12 (the Schur-complement update)
+//              by a small static perturbation and counted.  The m x PANEL_NB
+//              panel is held in shared memory (one CTA, or the distributed
+//              shared memory of a PANEL_CLUSTER-CTA cluster with a DSMEM pivot
+//              reduction); row interchanges outside the panel follow (laswp)
+//     trsm   : U12 = L11^{-1} A12 for the panel rows
+//   windowed pivoting (vivParams.pivoting = 1):
+//     diag   : one warp factors the 32 x 32 diagonal block with partial
+//              pivoting inside it (run inside the previous panel's gemm tile
+//              that covers the block when there is one)
+//     window : L21 = A21 U11^{-1} and U12 = L11^{-1} P A12 in one launch
+//   gemm     : A22 -= L21 U12 inside the front's 128-column outer block (SIMT)
+//   tc       : the outer block's K = 128 Schur update of large fronts on the
+//              tcgen05 tensor cores (3xTF32, tc_mma.cuh)
 //
-// The forward and backward solves walk the same tree: each front gathers
-// its children's update vectors (extend-add on vectors), so no global atomics
-// are used and results do not depend on the launch order.
+// After the factorisation every diagonal block's L11 and U11 are inverted in
+// place and each front's interchanges are composed into one permutation.  The
+// forward and backward solves walk the same tree: a CTA per front runs the
+// triangular chain over its pivot rows, and multi-CTA slice products handle
+// the off-diagonal blocks; each front gathers its children's update vectors,
+// so no global atomics are used and results do not depend on launch order.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
