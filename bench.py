@@ -71,6 +71,20 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def replica_throughput(ms_local, steps, world, device=None):
+    """Whole-job throughput of `world` independent replicas that each ran
+    `steps` steps in `ms_local` ms: the job time is the slowest rank's (a MAX
+    all-reduce over the process group); returns (job ms, steps/s)."""
+    t_max = float(ms_local)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([t_max], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    return t_max, world * steps / (t_max / 1e3)
+
+
 # ---------------------------------------------------------------------------------
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
@@ -293,12 +307,7 @@ def run_ours(args, wl, rank, world, local):
     kern = case.profile_read()
     case.profile(False)
     prof_ms = ep0.elapsed_time(ep1)
-    t_max = ms
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * args.steps / (t_max / 1e3)
+    t_max, value = replica_throughput(ms, args.steps, world, torch.device("cuda", local))
     newton = sum(i["newton_iters"] for i in infos) / len(infos)
     sweeps = sum(i["refine_sweeps"] for i in infos) / len(infos)
     n_fact = sum(i["newton_iters"] for i in pinfos)
