@@ -34,6 +34,13 @@ EDGE_NODES = ((0, 3, 6), (2, 5, 8), (0, 1, 2), (6, 7, 8))
 H_CS = 1e-30
 
 
+def sparse_lu(J):
+    """Library sparse LU (SuperLU) of the Jacobian, with a minimum-degree
+    ordering of A^T + A: the same exact factorisation up to rounding as any
+    other ordering, with a fraction of COLAMD's fill on these matrices."""
+    return spla.splu(J.tocsc(), permc_spec="MMD_AT_PLUS_A")
+
+
 def stiffness_from_reduced_velocity(rho, U_inf, Ustar, L=1.0):
     """U_r = pi U sqrt(pi rho L / k) (Section 1) solved for k."""
     return math.pi ** 3 * rho * L * U_inf ** 2 / Ustar ** 2
@@ -316,7 +323,7 @@ class OracleCase:
             if it == max_newton:
                 raise RuntimeError(f"Newton did not converge: {norms}")
             J = self.jacobian(c0, hu, hx, t_new)
-            dU = spla.splu(J.tocsc()).solve(-R)
+            dU = sparse_lu(J).solve(-R)
             self.scatter(self.gather() + dU)
         self.hist = (self.u_n, self.x_n)
         self.t = t_new

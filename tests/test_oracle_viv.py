@@ -81,3 +81,21 @@ def test_lame_scale_invariance():
     b.mu_s = 37.0 * b.mu_s
     a.step(); b.step()
     assert np.abs(a.u - b.u).max() < 1e-9 and np.abs(a.x - b.x).max() < 1e-10
+
+
+def test_stiffness_from_reduced_velocity_pins():
+    """Section 1 defines the reduced velocity of a massless cylinder as
+    U_r = pi U sqrt(pi rho L / k).  The oracle's k must give back U_r = U* through
+    that definition, and for the cylinder workloads (rho = U = L = 1) take the
+    values the mathematics fixes: U* = 8 -> pi^3/64 = 0.484473..., U* = 10 ->
+    pi^3/100 = 0.310063... (a pi^2 for pi^3 slip would give 0.154 and 0.0987)."""
+    from oracle.solver import stiffness_from_reduced_velocity as kfun
+    assert abs(kfun(1.0, 1.0, 8.0) - 0.48447307) < 5e-9
+    assert abs(kfun(1.0, 1.0, 10.0) - 0.31006277) < 5e-9
+    for rho, U, Us, L in [(1.0, 1.0, 8.0, 1.0), (2.5, 0.7, 5.5, 6.283185307179586), (1.0, 3.0, 17.0, 2.0)]:
+        k = kfun(rho, U, Us, L)
+        Ur = np.pi * U * np.sqrt(np.pi * rho * L / k)
+        assert abs(Ur - Us) <= 1e-12 * Us
+    mesh = I.viv_cylinder_mesh(4)
+    c = viv_oracle_case(mesh, 100.0, 8.0, 0.1, I.viv_initial_velocity(mesh, 1.0, 0.0, 1))
+    assert abs(c.k - 0.48447307) < 5e-9 and abs(c.mu - 0.01) < 1e-15
