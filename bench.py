@@ -35,8 +35,8 @@ WORKLOADS = {
     "viv_re100_m24": dict(m=24, Re=100.0, Ustar=8.0, dt=0.05),
 }
 FP32_SIMT_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12      # 148 SMs x 128 FP32 lanes x FMA x 2.032 GHz
-# DRAM bytes (read + write) per 128 x 128 tile of the tensor-core Schur update, from one ncu capture on the
-# 6,208-quad member of the mesh family (profiles/tc_front_kernel_viv_re100_m24.md); scaled by tiles per launch
+# DRAM bytes (read + write) per 128 x 128 tile of the tensor-core Schur update, from one ncu capture of that
+# kernel on the 6,208-quad member of the mesh family; scaled by the tiles of an average launch
 TC_DRAM_BYTES_PER_TILE = 73.4e3
 
 
@@ -47,7 +47,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="viv_re200_m60", choices=sorted(WORKLOADS))
-    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--oracle-full-steps", type=int, default=10,
+                    help="steps of the fully timed oracle run on the 1,552-quad case (0: skip)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -148,9 +150,8 @@ def oracle_sample(wl, newton_iters):
     mesh family (x (N/N_6208)^1.5, the 2-D nested-dissection cost law).
     Returns (steps/s, description, seconds of CPU work)."""
     import numpy as np
-    import scipy.sparse.linalg as spla
     from paper_2609_31477_b300 import inputs as I
-    from oracle.solver import viv_oracle_case
+    from oracle.solver import sparse_lu, viv_oracle_case
     t_all = time.perf_counter()
     mesh = I.viv_cylinder_mesh(wl["m"])
     u0 = I.viv_initial_velocity(mesh, 1.0, 1e-3, 1)
@@ -180,7 +181,7 @@ def oracle_sample(wl, newton_iters):
     c0l, hul, hxl = lc.bdf_coefficients()
     J24 = lc.jacobian(c0l, hul, hxl, wl["dt"]).tocsc()
     t0 = time.perf_counter()
-    spla.splu(J24)
+    sparse_lu(J24)
     t_lu24 = time.perf_counter() - t0
     t_lu = t_lu24 * (oc.ndof / lc.ndof) ** 1.5
     per_step = newton_iters * (t_res + t_jac + t_lu) + t_res
@@ -188,6 +189,37 @@ def oracle_sample(wl, newton_iters):
             f"elements x32 ({t_jac:.1f}s), SuperLU of the {len(m24['conn'])}-quad mesh scaled by (N ratio)^1.5 "
             f"({t_lu24:.1f}s -> {t_lu:.0f}s); {newton_iters:.2f} Newton iterations per step; extrapolated")
     return 1.0 / per_step, desc, time.perf_counter() - t_all
+
+
+def host_info():
+    model = "unknown"
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model,
+            "threads_used": 1, "note": "the oracle's element loops and SuperLU run on one core"}
+
+
+def oracle_full_run(steps):
+    """The oracle as it stands, fully timed (no extrapolation) on the 1,552-quad
+    cylinder case (Re 100, U* 8, dt 0.1, seed 1): `steps` BDF steps, each
+    Newton-converged to ||NL|| <= 1e-10.  Returns steps/s and the seconds."""
+    from paper_2609_31477_b300 import inputs as I
+    from oracle.solver import viv_oracle_case
+    mesh = I.viv_cylinder_mesh(12)
+    oc = viv_oracle_case(mesh, 100.0, 8.0, 0.1, I.viv_initial_velocity(mesh, 1.0, 1e-3, 1))
+    t0 = time.perf_counter()
+    newton = 0
+    for _ in range(steps):
+        newton += len(oc.step()) - 1
+    el = time.perf_counter() - t0
+    return {"value": steps / el, "unit": "time steps/s", "steps": steps, "seconds": round(el, 2),
+            "newton_iters_per_step": newton / steps, "workload": "viv_re100_m12 (1,552 quads, 26,554 unknowns)",
+            "kind": "oracle, fully timed"}
 
 
 # ---------------------------------------------------------------------------------
@@ -246,7 +278,8 @@ def run_reference(args, wl, rank):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": args.workload, **wl},
-           "cpu_baseline": {"value": value, "unit": "time steps/s", "cores": 1, "kind": "oracle", "sample": desc},
+           "cpu_baseline": {"value": value, "unit": "time steps/s", "cores": 1, "kind": "oracle", "sample": desc,
+                            "host": host_info()},
            "e2e": {"value": value, "unit": "time steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -374,6 +407,10 @@ def run_ours(args, wl, rank, world, local):
                       "l2": f"inputs larger than L2 (front pool {4 * info['front_entries'] / 1e9:.1f} GB)",
                       "parallelism": "replicas" if world > 1 else "single"},
            "newton_iters_per_step": newton, "refine_sweeps_per_step": sweeps,
+           "pivoting_record": {"threshold_misses": sum(i["threshold_misses"] for i in infos),
+                               "perturbed_pivots": sum(i["perturbed_pivots"] for i in infos),
+                               "note": "summed over the timed steps' factorisations; a miss is a multiplier "
+                                       "above 1/u (u = 0.01), i.e. a pivot the threshold test would reject"},
            "kernels_ms": {k: round(v[0], 3) for k, v in kern.items()},
            "profiled": {"steps": args.steps, "ms_per_step": prof_ms / args.steps,
                         "note": "second pass with a CUDA event pair around every launch (kernels_ms, roofline)"},
@@ -385,7 +422,8 @@ def run_ours(args, wl, rank, world, local):
     if not args.no_fp64 and rank == 0:
         c64 = viv.viv_case(M, wl["Re"], wl["Ustar"], wl["dt"], u0, precision=viv.VIV_FP64, pivoting=piv,
                            predictor=pred)
-        c64.step()
+        for _ in range(max(2, args.warmup)):     # BDF1, then BDF2: both graph sets captured before timing
+            c64.step()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(c64.stream)
@@ -395,6 +433,7 @@ def run_ours(args, wl, rank, world, local):
         ms64 = e0.elapsed_time(e1)
         out["fp64_path"] = {"value": args.fp64_steps / (ms64 / 1e3), "unit": "time steps/s",
                             "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps,
+                            "warmup": max(2, args.warmup),
                             "newton_iters_per_step": sum(i["newton_iters"] for i in i64) / len(i64)}
         out["speedup_mixed_vs_fp64"] = value / world / out["fp64_path"]["value"]
         c64.close()
@@ -403,18 +442,22 @@ def run_ours(args, wl, rank, world, local):
         # the same mixed path with threshold pivoting over all fully summed rows
         ct = viv.viv_case(M, wl["Re"], wl["Ustar"], wl["dt"], u0, precision=viv.VIV_MIXED,
                           pivoting=viv.VIV_PIVOT_THRESHOLD, jacobian_fp32=j32, predictor=pred)
-        ct.step()
+        for _ in range(max(2, args.warmup)):
+            ct.step()
         torch.cuda.synchronize()
+        nt = max(3, args.steps)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(ct.stream)
-        it_ = [ct.step() for _ in range(3)]
+        it_ = [ct.step() for _ in range(nt)]
         e1.record(ct.stream)
         torch.cuda.synchronize()
         mst = e0.elapsed_time(e1)
-        out["threshold_pivoting_path"] = {"value": 3 / (mst / 1e3), "unit": "time steps/s", "ms_per_step": mst / 3,
-                                          "steps": 3,
-                                          "newton_iters_per_step": sum(i["newton_iters"] for i in it_) / 3,
-                                          "refine_sweeps_per_step": sum(i["refine_sweeps"] for i in it_) / 3}
+        out["threshold_pivoting_path"] = {"value": nt / (mst / 1e3), "unit": "time steps/s", "ms_per_step": mst / nt,
+                                          "steps": nt, "warmup": max(2, args.warmup),
+                                          "newton_iters_per_step": sum(i["newton_iters"] for i in it_) / nt,
+                                          "refine_sweeps_per_step": sum(i["refine_sweeps"] for i in it_) / nt,
+                                          "threshold_misses": sum(i["threshold_misses"] for i in it_),
+                                          "perturbed_pivots": sum(i["perturbed_pivots"] for i in it_)}
         ct.close()
 
     if not args.no_e2e:
@@ -449,7 +492,9 @@ def run_ours(args, wl, rank, world, local):
         # count with the same starting point)
         v, desc, secs = oracle_sample(wl, 3.0)
         out["cpu_baseline"] = {"value": v, "unit": "time steps/s", "cores": 1, "kind": "oracle", "sample": desc,
-                               "sample_seconds": round(secs, 1)}
+                               "sample_seconds": round(secs, 1), "host": host_info()}
+        if args.oracle_full_steps > 0:
+            out["cpu_baseline"]["full_run_small_case"] = oracle_full_run(args.oracle_full_steps)
     if rank == 0:
         print(json.dumps(out), flush=True)
     case.close()

@@ -106,7 +106,8 @@ typedef struct {
 } vivMeshInfo;
 
 /* Physical and solver parameters.  rho, mu: fluid density and viscosity;
- * k: spring stiffness of Eq. solid_balance; dt: constant time step;
+ * k: spring stiffness of Eq. solid_balance (mu and k may instead come from Re
+ * and Ustar, see the last fields); dt: constant time step;
  * lame_scale: lambda_s = mu_s = lame_scale * min|K_0| / |K_0| per element
  *   (reference areas; 0 means 1);
  * newton_tol: absolute ||NL||_2 stop; refine_tol: relative residual at which
@@ -132,15 +133,24 @@ typedef struct {
                               panels; the refinement recovers the accuracy) */
   int32_t jacobian_fp32;   /* mixed path only: 1 evaluates the volume element Jacobians in
                               FP32 arithmetic (Gamma-face and border rows, the residual, the
-                              Newton test and the refinement products stay FP64) and, once
-                              ||NL|| passes the test, applies one more correction with the
-                              current factors (no new Jacobian); 0 (default) evaluates every
-                              Jacobian entry in FP64 */
+                              Newton test and the refinement products stay FP64); 0 (default)
+                              evaluates every Jacobian entry in FP64 */
   int32_t predictor;       /* Newton starting point of a BDF2 step: 0 (default) the previous
                               time level U^n; 1 the linear extrapolation 2 U^n - U^{n-1} of
                               velocity and position (and so of delta); p and lambda start
                               from U^n either way.  The converged state does not depend on it
                               beyond the Newton tolerance. */
+  /* Dimensionless inputs, converted by viv_case_create (and by the server at
+   * admission) when the corresponding dimensional value is not given:
+   *   mu <= 0 and Re > 0:    mu = rho U_inf D / Re;
+   *   k <= 0 and Ustar > 0:  k = pi^3 rho L U_inf^2 / Ustar^2, the stiffness at
+   *                          which the reduced velocity of a massless cylinder,
+   *                          U_r = pi U_inf sqrt(pi rho L / k) (Section 1), equals
+   *                          Ustar; L = span_L, the length that carries the force
+   *                          (1 for a 2-D section).
+   * U_inf, D and span_L default to 1 when 0.  k = 0 with Ustar = 0 is a problem
+   * without a cylinder (no border unknowns). */
+  double Re, Ustar, U_inf, D, span_L;
 } vivParams;
 enum { VIV_PIVOT_THRESHOLD = 0, VIV_PIVOT_WINDOW = 1 };
 
@@ -181,6 +191,24 @@ vivStatus viv_mesh_destroy(vivMesh* mesh);
 vivStatus viv_case_create(vivMesh* mesh, const vivParams* params, const double* u0,
                           void* stream, vivCase** out);
 vivStatus viv_case_destroy(vivCase* c);
+
+/* The parameters the case runs with, after the Re / Ustar conversions of
+ * viv_case_create (mu and k as used by the residual and the border rows). */
+vivStatus viv_case_params(const vivCase* c, vivParams* out);
+
+/* Checkpoint / resume of a case between time steps.  viv_case_save writes
+ * the current state (u, p, x, lambda, delta), the previous time level that
+ * the next BDF2 step needs, the time, the step count and dt into a host
+ * buffer of *bytes bytes (caller-owned); with buf == NULL it only stores the
+ * required size in *bytes.  viv_case_load restores such a buffer into a case
+ * created on the same mesh with the same dt (VIV_ERR_ARG otherwise); the
+ * next viv_step then computes exactly what the saved case would have
+ * computed (same kernels, same inputs, deterministic reductions).  Saving
+ * inside an open step (after viv_begin_step) returns VIV_ERR_STATE.  Factors
+ * are not saved: the next step assembles and factors anew.  The format is
+ * native-endian and tied to the mesh's node count. */
+vivStatus viv_case_save(const vivCase* c, void* buf, size_t* bytes);
+vivStatus viv_case_load(vivCase* c, const void* buf, size_t bytes);
 
 /* Overwrite the state.  Each pointer may be NULL (left unchanged); pointers
  * may be host or device memory (the `device` flag documents which; copies use
@@ -228,12 +256,13 @@ vivStatus viv_solve_rhs(vivCase* c, int device, const double* b, double* y, int*
  * synchronisation of cudaMalloc/cudaFree.  This entry point performs one
  * forward + backward multifrontal solve J x = b with the case's current
  * factors (no refinement) and allocates nothing: its workspace is a fixed
- * 8 MiB device array inside the library that every GPU loading the library
- * holds until the process exits.  b and x are device pointers to n_dofs
- * doubles (caller-owned); work is ordered on the case's stream.
- *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) and caches it; make that first call before any
- *    stream capture.
+ * 8 MiB device array inside the library.  A GPU holds the array from the
+ * first viv_case_create on it until the process exits: case creation looks
+ * up the array's device address (cudaGetSymbolAddress), which loads the
+ * library module that holds it, and caches the address per device; so the
+ * allocation-free call itself never triggers that load.  b and x are device
+ * pointers to n_dofs doubles (caller-owned); work is ordered on the case's
+ * stream.
  *  - A mesh whose workspace (every front's solve vector with its slice
  *    partial sums, plus n_dofs; 4 bytes per entry on the mixed path, 8 on the
  *    FP64 path) exceeds 8 MiB is rejected with VIV_ERR_ARG.
@@ -257,7 +286,13 @@ vivStatus viv_tc_schur_update(const float* A, int lda, const float* B, int ldb, 
 vivStatus viv_update(vivCase* c);
 
 /* One BDF step: begin_step, then Newton (Eq. NR_iteration) until
- * ||NL||_2 <= newton_tol. info nullable. */
+ * ||NL||_2 <= newton_tol.  On the mixed path, once ||NL|| passes the test, one
+ * closing correction is applied with the factors at hand (no new Jacobian),
+ * with at least two refinement sweeps and then to a linear residual of 1e-6
+ * of its right-hand side (counted in refine_sweeps), and ||NL|| is evaluated
+ * again: it removes the error the FP32 factors leave in directions the
+ * residual norm barely sees (a near-constant pressure offset), so the mixed
+ * state agrees with the FP64 path's to round-off.  info nullable. */
 vivStatus viv_step(vivCase* c, vivStepInfo* info);
 /* Same step with host buffers: uploads the state and history, steps, and
  * downloads the new state (the end-to-end form of one step). */

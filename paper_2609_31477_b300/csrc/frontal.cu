@@ -35,6 +35,7 @@
 
 #include <cfloat>
 #include <climits>
+#include <mutex>
 #include <type_traits>
 
 #include "tc_mma.cuh"
@@ -990,12 +991,9 @@ __global__ void __launch_bounds__(solve_threads_max<T>(), 1) bwd_tri_kernel(FT f
 
 }  // namespace
 
-// one-time kernel attributes (dynamic shared memory limits); called before
-// any launch, including before a stream capture
+// kernel attributes (dynamic shared memory limits) of one precision
 template <class T>
-void prepare_kernels() {
-  static bool done = false;
-  if (done) return;
+static void set_kernel_attributes() {
   if constexpr (std::is_same<T, float>::value)
     VIV_CUDA(cudaFuncSetAttribute(tc_front_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes()));
   VIV_CUDA(cudaFuncSetAttribute(panel_smem_kernel<T, 1, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1005,7 +1003,19 @@ void prepare_kernels() {
   VIV_CUDA(cudaFuncSetAttribute(fwd_tri_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX));
   VIV_CUDA(cudaFuncSetAttribute(bwd_tri_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX));
   VIV_CUDA(cudaFuncSetAttribute(perm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, PERM_SMEM_MAX));
-  done = true;
+}
+
+// set once per device and precision, before any launch (including before a
+// stream capture); the serving loop's worker threads get here concurrently,
+// hence call_once (an exception leaves the flag unset, so a later call retries)
+template <class T>
+void prepare_kernels() {
+  constexpr int MAX_DEV = 64;
+  static std::once_flag once[MAX_DEV];
+  int dev = 0;
+  VIV_CUDA(cudaGetDevice(&dev));
+  VIV_CHECK(dev >= 0 && dev < MAX_DEV, VIV_ERR_ARG, "device index out of range");
+  std::call_once(once[dev], [] { set_kernel_attributes<T>(); });
 }
 template void prepare_kernels<float>();
 template void prepare_kernels<double>();

@@ -10,9 +10,13 @@
 // instead of memory from the case's allocator.  The caller still provides
 // the right-hand side and the solution buffers.
 //
-// The array is a module global: every GPU that loads this library holds its
-// NOALLOC_SCRATCH_BYTES until the process exits, all calls share it, and it
-// keeps whatever the last call left in it.  The solve kernels write every
+// The array is a module global: a GPU holds its NOALLOC_SCRATCH_BYTES from
+// the moment this file's module is loaded on it until the process exits.
+// Under lazy module loading (the CUDA default) that moment would be the first
+// address lookup, which would make the first allocation-free call allocate;
+// so every viv_case_create looks the address up (noalloc_prepare), once per
+// device, while allocating is still allowed.  All calls share the array, and
+// it keeps whatever the last call left in it.  The solve kernels write every
 // workspace entry before reading it, so nothing needs clearing between
 // calls.  Calls whose GPU work overlaps in time (different streams or
 // threads) race on the array; callers must order them.
@@ -49,6 +53,9 @@ void* scratch_address() {
   return g_scratch_addr[dev];
 }
 }  // namespace
+
+// called by viv_case_create: commits the array on the current device
+void noalloc_prepare() { (void)scratch_address(); }
 
 void lu_solve_noalloc(vivCase* c, const double* b, double* x) {
   const Mesh& m = c->mesh->m;

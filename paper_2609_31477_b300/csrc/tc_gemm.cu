@@ -2,6 +2,8 @@
 // the device code is in tc_mma.cuh.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "tc_mma.cuh"
 #include "viv_internal.h"
 
@@ -23,12 +25,15 @@ size_t tc_smem_bytes() { return sizeof(tc::Smem) + 1024; }
 
 void tc_gemm_update(const float* A, int lda, const float* B, int ldb, float* C, int ldc, int M, int N, int K,
                     int* err, cudaStream_t s) {
-  static bool attr = false;
+  constexpr int MAX_DEV = 64;
+  static std::once_flag once[MAX_DEV];   // per device; callers may be concurrent threads
   const int smem = (int)tc_smem_bytes();
-  if (!attr) {
+  int dev = 0;
+  VIV_CUDA(cudaGetDevice(&dev));
+  VIV_CHECK(dev >= 0 && dev < MAX_DEV, VIV_ERR_ARG, "device index out of range");
+  std::call_once(once[dev], [&] {
     VIV_CUDA(cudaFuncSetAttribute(tc::gemm_standalone_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    attr = true;
-  }
+  });
   const int tiles = ((M + tc::BM - 1) / tc::BM) * ((N + tc::BN - 1) / tc::BN);
   if (tiles == 0 || K <= 0) return;
   Launched L(K_TCGEMM, s);

@@ -191,19 +191,21 @@ static __device__ void tile_update(Smem& sm, const float* A, int lda, const floa
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = sm.tmem_base;
   constexpr uint32_t idesc = make_idesc(BM, BN);
-  uint32_t ph = 0u;
+  uint32_t ph = 0u;        // parity of the barrier phase the next wait is for
   bool ok = true;
+  bool pending = false;     // a commit (the MMAs of one chunk) not yet seen complete
   const int nchunks = (K + KC - 1) / KC;
   ChunkRegs R;
   load_chunk(R, A, lda, B, ldb, M, N, K, rb, cb, 0);
   for (int ch = 0; ch < nchunks; ++ch) {
     if (ch > 0) {   // the MMAs of chunk ch - 1 still read the stage: wait for them
       const bool w = mbar_wait(&sm.bar, ph);
-      ph ^= 1u;
       if (!__syncthreads_and(w)) {
-        ok = false;
+        ok = false;   // the commit of chunk ch - 1 is still pending (phase ph)
         break;
       }
+      ph ^= 1u;
+      pending = false;
     }
     store_chunk(sm.st, R);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -225,16 +227,28 @@ static __device__ void tile_update(Smem& sm, const float* A, int lda, const floa
       }
       mma_commit(&sm.bar);
     }
+    pending = true;
     __syncwarp();
     if (ch + 1 < nchunks) load_chunk(R, A, lda, B, ldb, M, N, K, rb, cb, (ch + 1) * KC);   // overlaps the MMAs
   }
-  if (ok) {   // the last commit
-    bool w = nchunks == 0 || mbar_wait(&sm.bar, ph);
+  if (ok && pending) {   // the last commit
+    const bool w = mbar_wait(&sm.bar, ph);
     asm volatile("tcgen05.fence::after_thread_sync;");
     ok = __syncthreads_and(w) != 0;
+    if (ok) pending = false;
   }
   if (!ok) {
+    // Expired wait: flag the tile, then wait once more (bounded) for the MMAs
+    // still in flight - a commit tracks every earlier MMA of the issuing
+    // thread, so the pending phase completing means none is left - before
+    // the accumulator is released below.  A commit that never completes
+    // means the tensor core stopped; the tile is then abandoned as well.
     if (tid == 0) atomicExch(err, 1);
+    if (pending) {
+      const bool w = mbar_wait(&sm.bar, ph);
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      (void)__syncthreads_and(w);
+    }
   } else {
     // epilogue: warp w reads accumulator lanes 32 (w % 4) .. (tile rows) and
     // column half w / 4; each thread owns one row

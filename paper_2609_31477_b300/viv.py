@@ -52,7 +52,9 @@ class Params(C.Structure):
                 ("lame_scale", C.c_double), ("newton_tol", C.c_double), ("max_newton", C.c_int32),
                 ("precision", C.c_int32), ("refine_tol", C.c_double), ("refine_max", C.c_int32),
                 ("pivot_threshold", C.c_double), ("source", C.c_int32), ("source_amp", C.c_double),
-                ("pivoting", C.c_int32), ("jacobian_fp32", C.c_int32), ("predictor", C.c_int32)]
+                ("pivoting", C.c_int32), ("jacobian_fp32", C.c_int32), ("predictor", C.c_int32),
+                ("Re", C.c_double), ("Ustar", C.c_double), ("U_inf", C.c_double), ("D", C.c_double),
+                ("span_L", C.c_double)]
 
 
 class StepInfo(C.Structure):
@@ -114,6 +116,9 @@ SIGNATURES = {
     "viv_mesh_destroy": (C.c_int, [_P]),
     "viv_case_create": (C.c_int, [_P, C.POINTER(Params), _P, _P, C.POINTER(_P)]),
     "viv_case_destroy": (C.c_int, [_P]),
+    "viv_case_params": (C.c_int, [_P, C.POINTER(Params)]),
+    "viv_case_save": (C.c_int, [_P, _P, C.POINTER(C.c_size_t)]),
+    "viv_case_load": (C.c_int, [_P, _P, C.c_size_t]),
     "viv_set_state": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P, C.c_double]),
     "viv_set_history": (C.c_int, [_P, C.c_int, _P, _P]),
     "viv_get_state": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P, C.POINTER(C.c_double)]),
@@ -281,12 +286,13 @@ class Case:
 
     def __init__(self, mesh: Mesh, u0, rho, mu, k, dt, precision=VIV_FP64, lame_scale=1.0,
                  newton_tol=1e-10, max_newton=25, refine_tol=0.0, refine_max=0, pivot_threshold=0.01,
-                 stream=None, source=0, source_amp=0.0, pivoting=0, jacobian_fp32=0, predictor=0):
+                 stream=None, source=0, source_amp=0.0, pivoting=0, jacobian_fp32=0, predictor=0,
+                 Re=0.0, Ustar=0.0, U_inf=0.0, D=0.0, span_L=0.0):
         lib = load()
         self.mesh = mesh
         self.params = Params(rho, mu, k, dt, lame_scale, newton_tol, max_newton, precision, refine_tol,
                              refine_max, pivot_threshold, source, source_amp, pivoting, jacobian_fp32,
-                             predictor)
+                             predictor, Re, Ustar, U_inf, D, span_L)
         u0 = np.ascontiguousarray(u0, dtype=np.float64)
         import torch
         # each case owns a non-default stream (graphs cannot capture the legacy stream)
@@ -299,6 +305,24 @@ class Case:
         self.n = mesh.n_nodes
 
     # state ---------------------------------------------------------------------
+    def resolved_params(self):
+        """The parameters as the library runs them (mu and k after Re / U*)."""
+        p = Params()
+        _check(_lib.viv_case_params(self.h, C.byref(p)))
+        return {f: getattr(p, f) for f, _ in Params._fields_}
+
+    def save(self):
+        """Checkpoint of the case between steps (bytes)."""
+        n = C.c_size_t()
+        _check(_lib.viv_case_save(self.h, None, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        _check(_lib.viv_case_save(self.h, buf, C.byref(n)))
+        return buf.raw[:n.value]
+
+    def load(self, data: bytes):
+        buf = C.create_string_buffer(data, len(data))
+        _check(_lib.viv_case_load(self.h, buf, len(data)))
+
     def set_state(self, u=None, p=None, x=None, lam=None, delta=None, t=0.0):
         arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float64) for a in (u, p, x, lam, delta)]
         _check(_lib.viv_set_state(self.h, 0, *[_ptr(a) for a in arrs], C.c_double(t)))
@@ -425,9 +449,9 @@ class Server:
     def submit(self, mesh: Mesh, u0, Re, Ustar, dt, n_steps, arrival_time=0.0, precision=VIV_MIXED,
                U_inf=1.0, D=1.0, rho=1.0, newton_tol=1e-10, max_newton=25, pivoting=VIV_PIVOT_THRESHOLD,
                jacobian_fp32=0, predictor=0):
-        mu = rho * U_inf * D / Re
-        prm = Params(rho, mu, stiffness(rho, U_inf, Ustar), dt, 1.0, newton_tol, max_newton, precision, 0.0, 0,
-                     0.01, 0, 0.0, pivoting, jacobian_fp32, predictor)
+        # mu and k are derived from Re and U* by the library (vivParams)
+        prm = Params(rho, 0.0, 0.0, dt, 1.0, newton_tol, max_newton, precision, 0.0, 0,
+                     0.01, 0, 0.0, pivoting, jacobian_fp32, predictor, Re, Ustar, U_inf, D, 0.0)
         u0 = np.ascontiguousarray(u0, dtype=np.float64)
         req = Request(mesh.h.value, prm, u0.ctypes.data, int(n_steps), float(arrival_time))
         rid = C.c_int64()
@@ -486,13 +510,7 @@ def kernel_launches():
     return int(load().viv_kernel_launches())
 
 
-def stiffness(rho, U_inf, Ustar, L=1.0):
-    """Spring stiffness from the reduced velocity of a massless cylinder,
-    U* = pi U sqrt(pi rho L / k) (Section 1)."""
-    import math
-    return math.pi ** 3 * rho * L * U_inf ** 2 / Ustar ** 2
-
-
 def viv_case(mesh_obj, Re, Ustar, dt, u0, precision=VIV_FP64, U_inf=1.0, D=1.0, rho=1.0, **kw):
-    mu = rho * U_inf * D / Re
-    return Case(mesh_obj, u0, rho, mu, stiffness(rho, U_inf, Ustar), dt, precision=precision, **kw)
+    """A cylinder case given by Reynolds number and reduced velocity; the
+    library derives mu and the spring stiffness from them (vivParams)."""
+    return Case(mesh_obj, u0, rho, 0.0, 0.0, dt, precision=precision, Re=Re, Ustar=Ustar, U_inf=U_inf, D=D, **kw)

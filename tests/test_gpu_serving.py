@@ -85,3 +85,47 @@ def test_poisson_arrivals_report_latency(env):
     assert st["steps"] == 24 and 0 < st["step_ms_p50"] <= st["step_ms_p99"]
     assert 0 < st["steady_ms_p50"] <= st["steady_ms_p99"] <= st["step_ms_p99"]
     assert all(r["admit_s"] >= r["submit_s"] - 1e-6 for r in res)
+
+
+def test_served_cases_match_the_oracle(env):
+    """Cases of a served mix (different meshes, Re and U*, overlapping on the
+    device) each equal the oracle's run of the same case: fields to 1e-9
+    relative L2, delta to 1e-8."""
+    from oracle.solver import viv_oracle_case
+    viv, meshes, dev = env
+    cases = [(4, 120.0, 5.0, 21), (6, 260.0, 15.0, 22), (4, 180.0, 9.0, 23)]
+    srv = viv.Server(4 << 30, max_active=3)
+    ids = [srv.submit(dev[m], _u0(meshes[m], seed), Re=Re, Ustar=Us, dt=0.05, n_steps=3,
+                      pivoting=viv.VIV_PIVOT_WINDOW, jacobian_fp32=1, predictor=1)
+           for m, Re, Us, seed in cases]
+    res = {r["id"]: r for r in srv.wait_all(len(cases))}
+    st = srv.stats()
+    got = [srv.state(i, len(meshes[m]["X"])) for i, (m, _, _, _) in zip(ids, cases)]
+    srv.close()
+    assert all(res[i]["status"] == "OK" for i in ids), res
+    assert st["peak_active"] >= 2
+    for (m, Re, Us, seed), g in zip(cases, got):
+        oc = viv_oracle_case(meshes[m], Re, Us, 0.05, _u0(meshes[m], seed))
+        for _ in range(3):
+            oc.step()
+        v = oc.is_vertex
+        rel = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)
+        errs = (rel(g["u"], oc.u), rel(g["p"][v], oc.p[v]), rel(g["x"], oc.x), rel(g["lam"][oc.cyl], oc.lam[oc.cyl]))
+        assert max(errs) <= 1e-9, (m, Re, Us, errs)
+        assert np.abs(g["delta"] - oc.delta).max() <= 1e-8
+
+
+def test_newton_failure_stays_inside_its_case(env):
+    """A case whose Newton iteration cannot reach the tolerance in its
+    iteration limit (max_newton = 1 from the previous time level) fails with
+    VIV_ERR_NEWTON; the cases served beside it finish normally."""
+    viv, meshes, dev = env
+    srv = viv.Server(4 << 30, max_active=4)
+    good = [srv.submit(dev[m], _u0(meshes[m], 30 + m), Re=150.0, Ustar=7.0, dt=0.05, n_steps=3) for m in (4, 6)]
+    bad = srv.submit(dev[6], _u0(meshes[6], 40), Re=150.0, Ustar=7.0, dt=0.05, n_steps=3, max_newton=1)
+    res = {r["id"]: r for r in srv.wait_all(3)}
+    srv.close()
+    assert res[bad]["status"] == "ERR_NEWTON" and res[bad]["steps_done"] == 0, res[bad]
+    assert "Newton did not converge" in res[bad]["message"]
+    for i in good:
+        assert res[i]["status"] == "OK" and res[i]["steps_done"] == 3, res[i]

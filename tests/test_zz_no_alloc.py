@@ -5,7 +5,16 @@ memory pool is already committed, or a latency-bound loop that cannot take the
 device-wide synchronisation of cudaMalloc - use viv_lu_solve_noalloc, whose
 workspace is a fixed array inside the library.  This checks, through the C
 ABI, that it returns the same solution as the regular viv_solve_rhs, on two
-calls in a row (the shared workspace keeps the previous call's contents)."""
+calls in a row (the shared workspace keeps the previous call's contents), on
+the FP64 path and on the mixed path.
+
+The allocation-free solve is one unrefined forward + backward solve with the
+case's factors.  On the FP64 path that already meets the refined solve to
+1e-10.  On the mixed path the factors are FP32, so the unrefined solution
+differs from the FP64-refined one by the FP32 factorisation error: it must
+agree to 1e-3 relative (the first refinement sweep's contraction on these
+matrices is far below that), and two calls on the same right-hand side must
+agree bit for bit."""
 import numpy as np
 import pytest
 
@@ -13,8 +22,11 @@ from paper_2609_31477_b300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
+TOL = {"fp64": 1e-10, "mixed": 1e-3}
 
-def test_noalloc_solve_matches_regular_solve_on_two_calls():
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_noalloc_solve_matches_regular_solve_on_two_calls(precision):
     import torch
     from paper_2609_31477_b300 import build, viv
     build.build()
@@ -22,13 +34,15 @@ def test_noalloc_solve_matches_regular_solve_on_two_calls():
     mesh = I.viv_cylinder_mesh(4)
     u0 = I.viv_initial_velocity(mesh, 1.0, 1e-3, 1)
     M = viv.Mesh(mesh)
-    case = viv.viv_case(M, 100.0, 8.0, 0.1, u0, precision=viv.VIV_FP64)
+    prec = viv.VIV_FP64 if precision == "fp64" else viv.VIV_MIXED
+    case = viv.viv_case(M, 100.0, 8.0, 0.1, u0, precision=prec)
     case.begin_step()
     case.assemble(viv.VIV_RES | viv.VIV_JAC)
     case.factor()
     rng = np.random.default_rng(7)
-    for _ in range(2):
-        b = rng.standard_normal(M.n_dofs)
+    first = None
+    for call in range(2):
+        b = rng.standard_normal(M.n_dofs) if call == 0 else first[0]
         ref, _ = case.solve_rhs(b)
         bd = torch.tensor(b, device="cuda")
         xd = torch.full_like(bd, float("nan"))
@@ -37,6 +51,12 @@ def test_noalloc_solve_matches_regular_solve_on_two_calls():
         torch.cuda.synchronize()          # the solve ran on the case's own stream
         x = xd.cpu().numpy()
         assert np.all(np.isfinite(x))
-        assert np.linalg.norm(x - ref) <= 1e-10 * np.linalg.norm(ref)
+        err = np.linalg.norm(x - ref) / np.linalg.norm(ref)
+        print(f"{precision} call {call}: relative difference to the refined solve {err:.2e}")
+        assert err <= TOL[precision], err
+        if call == 0:
+            first = (b, x)
+        else:                             # same right-hand side, same factors: same bits
+            assert np.array_equal(x, first[1])
     case.close()
     M.close()
