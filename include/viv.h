@@ -103,6 +103,10 @@ typedef struct {
   double panel_flops;      /* in-panel LU flops of one factorisation */
   double trsm_flops;       /* panel TRSM flops of one factorisation */
   double outer_flops;      /* part of gemm_flops in K = 128 outer updates (tensor cores, mixed path) */
+  int64_t tc_split_chunks; /* mixed path, per factorisation: 128 x 32 operand chunks split into hi/lo
+                              TF32 images (16 KB read, 32 KB written each) */
+  int64_t tc_tiles;        /* mixed path, per factorisation: 128 x 128 tiles of the outer updates */
+  size_t tc_image_bytes;   /* the operand-image buffer a mixed case holds (in device_bytes_mixed) */
 } vivMeshInfo;
 
 /* Physical and solver parameters.  rho, mu: fluid density and viscosity;
@@ -369,9 +373,9 @@ int64_t viv_kernel_launches(void);
  * 0 residual elements, 1 Jacobian elements, 2 Gamma faces and border rows,
  * 3 front assembly, 4 panel LU, 5 TRSM, 6 Schur GEMM, 7 forward solve,
  * 8 backward solve, 9 refinement SpMV, 10 vector kernels, 11 tensor-core
- * (tcgen05) Schur updates.
- * viv_profile_read(ms[12], count[12]) synchronises and resets. */
-enum { VIV_NKINDS = 12 };
+ * (tcgen05) Schur updates, 12 their operand split (hi/lo TF32 images).
+ * viv_profile_read(ms[13], count[13]) synchronises and resets. */
+enum { VIV_NKINDS = 13 };
 vivStatus viv_profile(vivCase* c, int on);
 vivStatus viv_profile_read(vivCase* c, double* ms, int64_t* count);
 /* Factorisation kernel time of the last viv_profile_read split by elimination

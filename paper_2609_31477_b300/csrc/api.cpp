@@ -189,10 +189,10 @@ void factor(vivCase* c) {
   const bool win = c->prm.pivoting == VIV_PIVOT_WINDOW;
   if (mixed(c))
     factor_numeric<float>(m, nullptr, c->s.J32, (float*)c->s.fronts, c->s.piv, c->s.perm, c->s.stats, thr, win,
-                          c->stream);
+                          c->s.tc_img, c->stream);
   else
     factor_numeric<double>(m, c->s.J64, nullptr, (double*)c->s.fronts, c->s.piv, c->s.perm, c->s.stats, thr, win,
-                           c->stream);
+                           nullptr, c->stream);
   c->factored = true;
 }
 
@@ -317,13 +317,16 @@ vivStatus viv_mesh_info(const vivMesh* mesh, vivMeshInfo* info) {
   size_t nodes = (size_t)m.n_nodes, nnz = (size_t)info->nnz, nd = (size_t)m.n_dofs;
   size_t state = 8 * (17 * nodes + (size_t)m.n_elems + 3 * nd + 2 * 296 + 64) + 8 * (size_t)m.piv_entries;
   info->device_bytes_fp64 = state + 8 * (nnz + (size_t)m.front_entries + (size_t)m.vec_entries + nd);
-  info->device_bytes_mixed =
-      state + 8 * nnz + 4 * (nnz + (size_t)m.front_entries + (size_t)m.vec_entries + nd);
+  info->device_bytes_mixed = state + 8 * nnz + 4 * (nnz + (size_t)m.front_entries + (size_t)m.vec_entries + nd) +
+                             (size_t)m.tc_img_chunks * TC_IMG_CHUNK_BYTES;
   info->n_colors = (int32_t)m.color_off.size() - 1;
   info->gemm_flops = m.gemm_flops;
   info->panel_flops = m.panel_flops;
   info->trsm_flops = m.trsm_flops;
   info->outer_flops = m.outer_flops;
+  info->tc_split_chunks = m.tc_split_chunks;
+  info->tc_tiles = m.tc_tiles;
+  info->tc_image_bytes = (size_t)m.tc_img_chunks * TC_IMG_CHUNK_BYTES;
   API_END
 }
 
@@ -446,6 +449,9 @@ static vivStatus case_create_impl(vivMesh* mesh, const vivParams* prm_in, const 
     s.piv = A.make<int32_t>(m.piv_entries);
     s.perm = A.make<int32_t>(m.piv_entries);
     s.stats = A.make<int32_t>(4);
+    s.tc_img = mixed(c) && m.tc_img_chunks > 0
+                   ? static_cast<unsigned char*>(A.get((size_t)m.tc_img_chunks * TC_IMG_CHUNK_BYTES))
+                   : nullptr;
     s.partial = A.make<double>(296);
     s.scal = A.make<double>(8);
     VIV_CUDA(cudaMallocHost(&c->h_pinned, 8 * sizeof(double)));

@@ -33,16 +33,16 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cfloat>
 #include <climits>
 #include <mutex>
 #include <type_traits>
 
-#include "tc_mma.cuh"
+#include "tc_pipe.cuh"
 #include "viv_internal.h"
 
 namespace viv {
-size_t tc_smem_bytes();
 namespace {
 
 template <class T>
@@ -712,18 +712,6 @@ __global__ void __launch_bounds__(256) gemm_kernel(FT ft, const int32_t* work, T
   }
 }
 
-// outer Schur update of a large front on the tensor cores: one 128 x 128 tile
-// F[rb.., cb..] -= F[.., k_begin : k_begin + k_len] * F[k_begin : .., ..]
-__global__ void __launch_bounds__(tc::THREADS, 3) tc_front_kernel(FT ft, const int32_t* work, float* pool, int* err) {
-  extern __shared__ __align__(1024) unsigned char raw[];
-  tc::Smem& sm = *reinterpret_cast<tc::Smem*>(raw);
-  const int32_t* it = work + WORK_STRIDE * blockIdx.x;
-  const int f = it[0], rb = it[1], cb = it[2], kb = it[3], kl = it[4];
-  const int m = ft.m[f];
-  float* F = pool + ft.off[f];
-  tc::tile_update(sm, F + (int64_t)kb * m, m, F + kb, m, F, m, m, m, kl, rb, cb, err);
-}
-
 // ---- solves -----------------------------------------------------------------------
 // After the numeric factorisation, every 32 x 32 diagonal block of a front is
 // replaced in place by the inverses of its unit-lower part L11 (strictly lower
@@ -994,8 +982,7 @@ __global__ void __launch_bounds__(solve_threads_max<T>(), 1) bwd_tri_kernel(FT f
 // kernel attributes (dynamic shared memory limits) of one precision
 template <class T>
 static void set_kernel_attributes() {
-  if constexpr (std::is_same<T, float>::value)
-    VIV_CUDA(cudaFuncSetAttribute(tc_front_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes()));
+  if constexpr (std::is_same<T, float>::value) tcp::prepare();
   VIV_CUDA(cudaFuncSetAttribute(panel_smem_kernel<T, 1, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 PANEL_SMEM_BYTES));
   VIV_CUDA(cudaFuncSetAttribute(panel_smem_kernel<T, PANEL_CLUSTER, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1022,7 +1009,7 @@ template void prepare_kernels<double>();
 
 template <class T>
 void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* fronts, int32_t* piv, int32_t* perm,
-                    int32_t* stats, double threshold, bool window, cudaStream_t s) {
+                    int32_t* stats, double threshold, bool window, unsigned char* tc_img, cudaStream_t s) {
   FT ft = make_ft(m);
   prepare_kernels<T>();
   VIV_CUDA(cudaMemsetAsync(stats, 0, 3 * sizeof(int32_t), s));
@@ -1031,8 +1018,8 @@ void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* front
     prof_level(L.level);
     const int32_t* w = work + (int64_t)WORK_STRIDE * L.item0;
     const unsigned grid = (unsigned)L.count;
-    static const int kk[10] = {K_FRONT_ASM, K_PANEL,  K_TRSM,  K_GEMM,  K_PANEL,
-                               K_TRSM,      K_PANEL,  K_TCGEMM, K_PANEL, K_TRSM};
+    static const int kk[11] = {K_FRONT_ASM, K_PANEL,  K_TRSM,   K_GEMM,  K_PANEL,  K_TRSM,
+                               K_PANEL,     K_TCGEMM, K_PANEL, K_TRSM, K_TCSPLIT};
     Launched LL(kk[L.kind], s);
     switch (L.kind) {
       case L_ASSEMBLE:
@@ -1050,10 +1037,12 @@ void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* front
       case L_GEMM:
         gemm_kernel<T><<<grid, 256, 0, s>>>(ft, w, fronts, piv, perm, stats);
         break;
+      case L_TC_SPLIT:
+        if constexpr (std::is_same<T, float>::value) tcp::split_launch(w, (int)L.count, fronts, ft.off, ft.m, tc_img, s);
+        break;
       case L_TC_GEMM:
-        if constexpr (std::is_same<T, float>::value) {
-          tc_front_kernel<<<grid, tc::THREADS, tc_smem_bytes(), s>>>(ft, w, fronts, stats + 2);
-        }
+        if constexpr (std::is_same<T, float>::value)
+          tcp::pipe_launch(w, (int)L.count, tc_img, fronts, ft.off, ft.m, stats + 2, s);
         break;
       case L_PANEL_1: {
         const size_t smem = (size_t)L.aux * PANEL_NB * sizeof(T);
@@ -1143,9 +1132,9 @@ void solve_fronts(const Mesh& m, const T* fronts, const int32_t* perm, const dou
 }
 
 template void factor_numeric<double>(const Mesh&, const double*, const float*, double*, int32_t*, int32_t*,
-                                     int32_t*, double, bool, cudaStream_t);
+                                     int32_t*, double, bool, unsigned char*, cudaStream_t);
 template void factor_numeric<float>(const Mesh&, const double*, const float*, float*, int32_t*, int32_t*, int32_t*,
-                                    double, bool, cudaStream_t);
+                                    double, bool, unsigned char*, cudaStream_t);
 template void solve_fronts<double>(const Mesh&, const double*, const int32_t*, const double*, double*, double*,
                                    double*, cudaStream_t);
 template void solve_fronts<float>(const Mesh&, const float*, const int32_t*, const double*, double*, float*,

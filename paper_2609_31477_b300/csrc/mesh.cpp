@@ -606,6 +606,30 @@ void build_mesh(Mesh& m, const vivMeshDesc* d) {
     m.fg_off[l + 1] = (int32_t)(m.fg_items.size() / 4);
     m.bg_off[l + 1] = (int32_t)(m.bg_items.size() / 4);
   }
+  // image chunks of the tensor-core operand split that a mixed case holds: an
+  // upper bound for every schedule (each outer-block step of a level at most
+  // splits the blocks of all its fronts; a smaller large-front threshold only
+  // adds fronts), capped at TC_IMG_MAX_CHUNKS unless one front alone needs more
+  {
+    int64_t bound = 0, single = 0;
+    for (int l = 0; l < m.n_levels; ++l) {
+      int maxp = 0;
+      for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) maxp = std::max(maxp, m.f_p[m.level_fronts[q]]);
+      for (int k2 = 0; k2 < maxp; k2 += OUTER_NB) {
+        int64_t sum = 0;
+        for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
+          const int f = m.level_fronts[q];
+          const int be = std::min(k2 + OUTER_NB, m.f_p[f]);
+          if (m.f_p[f] <= k2 || be >= m.f_m[f]) continue;
+          const int64_t need = 2 * (int64_t)((m.f_m[f] - be + 127) / 128) * ((be - k2 + 31) / 32);
+          sum += need;
+          single = std::max(single, need);
+        }
+        bound = std::max(bound, sum);
+      }
+    }
+    m.tc_img_chunks = std::min(bound, std::max(TC_IMG_MAX_CHUNKS, single));
+  }
   build_schedule(m, BIG_FRONT);
 }
 
@@ -620,6 +644,7 @@ void build_schedule(Mesh& m, int big_front) {
   // K = 128 Schur update (tensor cores on the FP32 path).
   m.work.clear();
   m.gemm_flops = m.trsm_flops = m.panel_flops = m.outer_flops = 0;
+  m.tc_split_chunks = m.tc_tiles = 0;
   auto push = [&](std::initializer_list<int> v) {
     int n = 0;
     for (int x : v) {
@@ -785,18 +810,61 @@ void build_schedule(Mesh& m, int big_front) {
           close(OG);
         }
         if (prec == 0) {
-          Launch TC = open(L_TC_GEMM, l, k2);
+          // tensor cores: the fronts' L21 / U12 chunks are split into hi/lo
+          // TF32 images (one launch), then the 128 x 128 tiles are updated from
+          // them (one persistent launch); fronts are grouped so that a group's
+          // images fit the case's image buffer
+          std::vector<int> group;
+          int64_t group_chunks = 0;
+          auto flush = [&]() {
+            if (group.empty()) return;
+            std::vector<int64_t> a_base(group.size()), b_base(group.size());
+            int64_t blk = 0;
+            Launch SP = open(L_TC_SPLIT, l, k2);
+            for (size_t g = 0; g < group.size(); ++g) {
+              const int f = group[g], be = block_end(f), mm = m.f_m[f], kl = be - k2;
+              const int nch = (kl + 31) / 32;
+              a_base[g] = blk;
+              for (int rb = be; rb < mm; rb += 128)
+                for (int ch = 0; ch < nch; ++ch)
+                  push({f, rb, 0, k2 + 32 * ch, std::min(32, kl - 32 * ch), (int)blk++, mm});
+              b_base[g] = blk;
+              for (int cb = be; cb < mm; cb += 128)
+                for (int ch = 0; ch < nch; ++ch)
+                  push({f, cb, 1, k2 + 32 * ch, std::min(32, kl - 32 * ch), (int)blk++, mm});
+            }
+            close(SP);
+            VIV_CHECK(blk <= m.tc_img_chunks, VIV_ERR_ARG, "tensor-core operand images exceed the case buffer");
+            if (count) m.tc_split_chunks += blk;
+            // tiles row block by row block: a CTA takes a contiguous range, so
+            // its consecutive tiles mostly share the row block's A chunks
+            Launch TC = open(L_TC_GEMM, l, k2);
+            for (size_t g = 0; g < group.size(); ++g) {
+              const int f = group[g], be = block_end(f), mm = m.f_m[f];
+              const int nch = (be - k2 + 31) / 32, nb = (mm - be + 127) / 128;
+              for (int i = 0; i < nb; ++i)
+                for (int j = 0; j < nb; ++j)
+                  push({f, be + 128 * i, be + 128 * j, mm, mm, (int)(a_base[g] + (int64_t)i * nch),
+                        (int)(b_base[g] + (int64_t)j * nch), nch});
+              if (count) m.tc_tiles += (int64_t)nb * nb;
+            }
+            close(TC);
+            group.clear();
+            group_chunks = 0;
+          };
           for (int f : done) {
             const int be = block_end(f), mm = m.f_m[f];
-            for (int rb = be; rb < mm; rb += 128)
-              for (int cb = be; cb < mm; cb += 128) push({f, rb, cb, k2, be - k2});
+            const int64_t need = 2 * (int64_t)((mm - be + 127) / 128) * ((be - k2 + 31) / 32);
+            if (group_chunks + need > m.tc_img_chunks) flush();
+            group.push_back(f);
+            group_chunks += need;
             const double rest = (double)(mm - be);
             if (count) {
               m.gemm_flops += 2.0 * rest * rest * (be - k2);
               m.outer_flops += 2.0 * rest * rest * (be - k2);
             }
           }
-          close(TC);
+          flush();
         } else {
           Launch OG = open(L_GEMM, l, k2);
           for (int f : done) {

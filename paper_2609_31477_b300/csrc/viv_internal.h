@@ -60,12 +60,14 @@ constexpr int FACE_PAIRS = 120;    // u x lambda, lambda x (u, delta), delta x l
 enum LaunchKind {
   L_ASSEMBLE = 0, L_PANEL = 1, L_TRSM = 2, L_GEMM = 3, L_PANEL_CL = 4, L_LASWP = 5, L_PANEL_1 = 6, L_TC_GEMM = 7,
   L_DIAG = 8,      // windowed pivoting: one warp factors the 32 x 32 diagonal block
-  L_WINDOW = 9     // windowed pivoting: L21 rows and permuted / solved columns
+  L_WINDOW = 9,    // windowed pivoting: L21 rows and permuted / solved columns
+  L_TC_SPLIT = 10  // tensor-core operands: hi/lo TF32 images of the outer block's L21 and U12 chunks
 };
 constexpr int WORK_STRIDE = 8;   // ints per work item
 // work items:  ASSEMBLE (f, c0)           PANEL* (f)              LASWP (f, c0)
 //              TRSM (f, c0, c_end, k)      GEMM (f, rb, cb, r_end, c_end, k_begin, k_len)
-//              TC_GEMM (f, rb, cb, k_begin, k_len)  [128 x 128 tiles, tensor cores]
+//              TC_SPLIT (f, start, kind, k0, klen, block, limit)  [one 128 x 32 operand chunk]
+//              TC_GEMM (f, rb, cb, r_end, c_end, a_block, b_block, nchunks)  [128 x 128 tiles, tensor cores]
 //              DIAG (f)   WINDOW (0, f, r0) rows of L21 | (1, f, c0, c_end) permuted / solved columns
 constexpr int WINDOW_THREADS = 256;   // rows or columns per WINDOW item
 // solves: the bandwidth-bound products with the off-diagonal factor blocks run
@@ -75,6 +77,11 @@ constexpr int SOLVE_SLICE = 256;
 constexpr int PERM_SMEM_MAX = 200 * 1024;   // composed permutation of one front (2 ints per pivot)
 constexpr int BIG_FRONT = 96;    // default: fronts at least this large use 128-column outer blocks
 constexpr int OUTER_NB = 128;    // outer block width (K of the outer Schur update)
+// operand images of the tensor-core updates: 32 KB per 128 x 32 chunk (hi + lo);
+// the launches of one outer-block step are cut into groups of at most this
+// many chunks, which bounds each mixed case's image buffer (256 MB)
+constexpr int64_t TC_IMG_CHUNK_BYTES = 32 * 1024;
+constexpr int64_t TC_IMG_MAX_CHUNKS = 8192;
 struct Launch {
   int kind;
   int level;
@@ -160,6 +167,8 @@ struct Mesh {
   int sched_version = 0;      // bumped whenever the schedules are rebuilt
   double gemm_flops = 0, panel_flops = 0, trsm_flops = 0;   // per numeric factorisation
   double outer_flops = 0;   // part of gemm_flops done by the K = 128 outer updates (tensor cores)
+  int64_t tc_img_chunks = 0;   // image chunks a mixed case holds: the largest group of any schedule
+  int64_t tc_split_chunks = 0, tc_tiles = 0;   // per numeric factorisation: chunks split, tiles updated
   // device copies
   cudaStream_t stream = nullptr;
   bool on_device = false;
@@ -202,7 +211,8 @@ struct CaseState {
   void* yv;                             // forward-solve vector (n_dofs)
   int32_t* piv;                         // row pivots of all fronts
   int32_t* perm;                        // composed row permutation of each front (solves)
-  int32_t* stats;                       // [0] perturbed, [1] threshold misses
+  int32_t* stats;                       // [0] perturbed, [1] threshold misses, [2] tensor-core wait expired
+  unsigned char* tc_img;                // operand images of the tensor-core updates (mixed path)
   double* partial;                      // norm partial sums
   double* scal;                         // host-visible scalars (device side)
 };
@@ -212,7 +222,8 @@ struct CaseState {
 // ----- launch accounting and per-kind event timing ----------------------------
 namespace viv {
 enum KernelKind {
-  K_RES = 0, K_JAC, K_FACE, K_FRONT_ASM, K_PANEL, K_TRSM, K_GEMM, K_FWD, K_BWD, K_SPMV, K_VEC, K_TCGEMM, K_NKINDS
+  K_RES = 0, K_JAC, K_FACE, K_FRONT_ASM, K_PANEL, K_TRSM, K_GEMM, K_FWD, K_BWD, K_SPMV, K_VEC, K_TCGEMM, K_TCSPLIT,
+  K_NKINDS
 };
 struct Profiler {
   bool on = false;
@@ -299,7 +310,7 @@ template <class T>
 void prepare_kernels();
 template <class T>
 void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* fronts, int32_t* piv, int32_t* perm,
-                    int32_t* stats, double threshold, bool window, cudaStream_t s);
+                    int32_t* stats, double threshold, bool window, unsigned char* tc_img, cudaStream_t s);
 template <class T>
 void solve_fronts(const Mesh& m, const T* fronts, const int32_t* perm, const double* b, double* x,
                   T* vec, T* yv, cudaStream_t s);

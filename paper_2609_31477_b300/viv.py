@@ -21,7 +21,7 @@ VIV_PIVOT_THRESHOLD, VIV_PIVOT_WINDOW = 0, 1
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_PIVOT", 5: "ERR_NEWTON",
           6: "ERR_NONFINITE", 7: "ERR_TIMEOUT", 8: "ERR_ADMISSION", 9: "ERR_STATE"}
 KINDS = ("residual", "jacobian", "face_border", "front_assemble", "panel_lu", "trsm", "schur_gemm",
-         "fwd_solve", "bwd_solve", "spmv", "vector", "tc_schur_gemm")
+         "fwd_solve", "bwd_solve", "spmv", "vector", "tc_schur_gemm", "tc_split")
 KINDS_N = len(KINDS)
 FIELD = {0: "ux", 1: "uy", 2: "xx", 3: "xy", 4: "p", 5: "lx", 6: "ly", 7: "dx", 8: "dy"}
 
@@ -44,7 +44,8 @@ class MeshInfo(C.Structure):
                 ("front_entries", C.c_size_t), ("device_bytes_fp64", C.c_size_t),
                 ("device_bytes_mixed", C.c_size_t), ("n_colors", C.c_int32),
                 ("gemm_flops", C.c_double), ("panel_flops", C.c_double), ("trsm_flops", C.c_double),
-                ("outer_flops", C.c_double)]
+                ("outer_flops", C.c_double), ("tc_split_chunks", C.c_int64), ("tc_tiles", C.c_int64),
+                ("tc_image_bytes", C.c_size_t)]
 
 
 class Params(C.Structure):

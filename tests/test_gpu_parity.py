@@ -196,7 +196,7 @@ def test_large_front_threshold_and_level_profile(viv):
     case.assemble(viv.VIV_RES | viv.VIV_JAC)
     b = np.random.default_rng(9).standard_normal(M.n_dofs)
     levels = int(M.fronts()["level"].max()) + 1
-    fact_kinds = ("front_assemble", "panel_lu", "trsm", "schur_gemm", "tc_schur_gemm")
+    fact_kinds = ("front_assemble", "panel_lu", "trsm", "schur_gemm", "tc_schur_gemm", "tc_split")
     ys = {}
     for bf in (96, 1 << 30, 256):
         case.set_big_front(bf)
@@ -212,5 +212,6 @@ def test_large_front_threshold_and_level_profile(viv):
         assert 0 < per_level <= per_kind * (1 + 1e-9) + 1e-9
         uses_tc = any("tc_schur_gemm" in d for d in lv)
         assert uses_tc == (bf != 1 << 30)
+        assert uses_tc == any("tc_split" in d for d in lv)   # every tensor-core update splits its operands
     for bf in (1 << 30, 256):
         assert rel_l2(ys[bf], ys[96]) <= 1e-10, (bf, rel_l2(ys[bf], ys[96]))

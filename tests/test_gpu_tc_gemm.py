@@ -5,7 +5,7 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("M,N,K", [(128, 128, 32), (200, 300, 128), (257, 129, 20), (64, 64, 8),
+@pytest.mark.parametrize("M,N,K", [(128, 128, 32), (200, 300, 128), (257, 129, 20), (64, 64, 8), (300, 1100, 200),
                                    (1000, 777, 96), (129, 1, 33)])
 def test_tc_schur_update_matches_reference(M, N, K):
     import torch
