@@ -241,12 +241,21 @@ vivStatus viv_assemble(vivCase* c, int what, double* res_norm);
 vivStatus viv_get_residual(const vivCase* c, double* r);
 vivStatus viv_get_jacobian(const vivCase* c, double* vals);
 
-/* Numeric multifrontal LU of the Jacobian with threshold partial pivoting
- * inside fronts, or windowed pivoting (vivParams.pivoting); delta is
- * eliminated last in the root front.  The factors keep each 32 x 32 diagonal
- * block's L and U inverted (for the solves) and are read only by this
- * library's solves. */
+/* Numeric factorisation of the Jacobian J = [A B; C D], delta last.  A (every
+ * unknown but delta) is factored by the multifrontal LU with threshold partial
+ * pivoting inside fronts, or windowed pivoting (vivParams.pivoting), in the
+ * case's precision.  The force-position border (Eq. coupling_constraint) is
+ * then eliminated as a dense FP64 Schur block: Y = A^{-1} B (two solves with
+ * the factors), S_b = D - C Y, and S_b^{-1}, all in FP64; every solve then
+ * takes delta = S_b^{-1} (b_delta - C A^{-1} b_A).  A singular S_b returns
+ * VIV_ERR_PIVOT from viv_step.  The factors keep each 32 x 32 diagonal block's
+ * L and U inverted (for the solves) and are read only by this library's
+ * solves. */
 vivStatus viv_factor(vivCase* c);
+/* The FP64 border Schur block S_b = D - C A^{-1} B of the last factorisation,
+ * row major (4 doubles, host).  VIV_ERR_STATE before viv_factor or on a mesh
+ * without a cylinder. */
+vivStatus viv_border_block(const vivCase* c, double* S);
 /* Solve J dU = -NL for the Newton correction with iterative refinement
  * against the FP64 Jacobian values (with jacobian_fp32: the widened FP32
  * volume entries); sweeps (nullable) receives the sweep count. */
@@ -269,7 +278,10 @@ vivStatus viv_solve_rhs(vivCase* c, int device, const double* b, double* y, int*
  * stream.
  *  - A mesh whose workspace (every front's solve vector with its slice
  *    partial sums, plus n_dofs; 4 bytes per entry on the mixed path, 8 on the
- *    FP64 path) exceeds 8 MiB is rejected with VIV_ERR_ARG.
+ *    FP64 path; plus 256 bytes for the cylinder position) exceeds 8 MiB is
+ *    rejected with VIV_ERR_ARG.
+ *  - The cylinder position is solved through the FP64 border block of the
+ *    last factorisation, as in every other solve.
  *  - All calls share the array and it keeps the last call's contents; the
  *    solve writes every workspace entry before reading it, so no clearing is
  *    needed.  Calls whose GPU work overlaps (other streams or threads) race on

@@ -183,6 +183,23 @@ double assemble(vivCase* c, int what, bool want_norm) {
   return nr;
 }
 
+bool has_border(const Mesh& m) { return m.n_front_dofs < m.n_dofs; }
+
+// x[0 : n_front_dofs] = A^{-1} b[0 : n_front_dofs] with the fronts' factors
+void front_solve(vivCase* c, const double* b, double* x) {
+  const Mesh& m = c->mesh->m;
+  if (mixed(c))
+    solve_fronts<float>(m, (const float*)c->s.fronts, c->s.perm, b, x, (float*)c->s.vec, (float*)c->s.yv,
+                        c->stream);
+  else
+    solve_fronts<double>(m, (const double*)c->s.fronts, c->s.perm, b, x, (double*)c->s.vec,
+                         (double*)c->s.yv, c->stream);
+}
+
+// Numeric factorisation of A (the Jacobian without the delta rows and
+// columns) in the fronts, then the border: Y = A^{-1} B with those factors
+// and the 2 x 2 Schur block S_b = D - C Y formed and inverted in FP64
+// (Eq. coupling_constraint: the force-position rows eliminated last).
 void factor(vivCase* c) {
   const Mesh& m = c->mesh->m;
   double thr = c->prm.pivot_threshold > 0 ? c->prm.pivot_threshold : 0.01;
@@ -193,17 +210,22 @@ void factor(vivCase* c) {
   else
     factor_numeric<double>(m, c->s.J64, nullptr, (double*)c->s.fronts, c->s.piv, c->s.perm, c->s.stats, thr, win,
                            nullptr, c->stream);
+  if (has_border(m)) {
+    for (int j = 0; j < 2; ++j) {
+      launch_border_column(m, c->s.J64, j, c->s.Bcol, c->stream);
+      front_solve(c, c->s.Bcol, c->s.Y + (int64_t)j * m.n_dofs);
+    }
+    launch_border_schur(m, c->s.J64, c->s.Y, c->s.Sb, c->s.stats + 3, c->stream);
+  }
   c->factored = true;
 }
 
+// x = J^{-1} b for the factored J = [A B; C D]: z = A^{-1} b_A from the
+// fronts, delta = S_b^{-1} (b_delta - C z), x_A = z - Y delta
 void lu_solve(vivCase* c, const double* b, double* x) {
   const Mesh& m = c->mesh->m;
-  if (mixed(c))
-    solve_fronts<float>(m, (const float*)c->s.fronts, c->s.perm, b, x, (float*)c->s.vec, (float*)c->s.yv,
-                        c->stream);
-  else
-    solve_fronts<double>(m, (const double*)c->s.fronts, c->s.perm, b, x, (double*)c->s.vec,
-                         (double*)c->s.yv, c->stream);
+  front_solve(c, b, x);
+  if (has_border(m)) launch_border_solve(m, c->s.J64, b, x, c->s.Y, c->s.Sb, c->s.btmp, c->stream);
 }
 
 // y = J^{-1} b with refinement against the FP64 Jacobian; b, y device
@@ -449,6 +471,12 @@ static vivStatus case_create_impl(vivMesh* mesh, const vivParams* prm_in, const 
     s.piv = A.make<int32_t>(m.piv_entries);
     s.perm = A.make<int32_t>(m.piv_entries);
     s.stats = A.make<int32_t>(4);
+    if (has_border(m)) {
+      s.Y = A.make<double>(2 * (size_t)nd);
+      s.Bcol = A.make<double>(nd);
+      s.Sb = A.make<double>(8);
+      s.btmp = A.make<double>(4);
+    }
     s.tc_img = mixed(c) && m.tc_img_chunks > 0
                    ? static_cast<unsigned char*>(A.get((size_t)m.tc_img_chunks * TC_IMG_CHUNK_BYTES))
                    : nullptr;
@@ -574,6 +602,16 @@ vivStatus viv_factor(vivCase* c) {
   ProfBind pb_(c);
   VIV_CHECK(c, VIV_ERR_ARG, "NULL case");
   factor(c);
+  API_END
+}
+
+vivStatus viv_border_block(const vivCase* cc, double* S) {
+  API_BEGIN
+  VIV_CHECK(cc && S, VIV_ERR_ARG, "NULL argument");
+  vivCase* c = const_cast<vivCase*>(cc);
+  VIV_CHECK(c->factored && has_border(c->mesh->m), VIV_ERR_STATE, "no factored border block");
+  VIV_CUDA(cudaMemcpyAsync(S, c->s.Sb, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  VIV_CUDA(cudaStreamSynchronize(c->stream));
   API_END
 }
 
@@ -781,10 +819,11 @@ static void step_impl(vivCase* c, vivStepInfo* info) {
     run_graph(c, c->g_fac, [&] { factor(c); });
     c->factored = true;
     sweeps += refined_solve_graphs(c);
-    int32_t stv[3];
+    int32_t stv[4];
     VIV_CUDA(cudaMemcpyAsync(stv, c->s.stats, sizeof(stv), cudaMemcpyDeviceToHost, c->stream));
     VIV_CUDA(cudaStreamSynchronize(c->stream));
     VIV_CHECK(stv[2] == 0, VIV_ERR_TIMEOUT, "a tensor-core wait expired during the factorisation");
+    VIV_CHECK(stv[3] == 0, VIV_ERR_PIVOT, "the border Schur block of the cylinder position is singular");
     st_acc[0] += stv[0];
     st_acc[1] += stv[1];
     ++iters;

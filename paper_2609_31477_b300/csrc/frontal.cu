@@ -1012,7 +1012,7 @@ void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* front
                     int32_t* stats, double threshold, bool window, unsigned char* tc_img, cudaStream_t s) {
   FT ft = make_ft(m);
   prepare_kernels<T>();
-  VIV_CUDA(cudaMemsetAsync(stats, 0, 3 * sizeof(int32_t), s));
+  VIV_CUDA(cudaMemsetAsync(stats, 0, 4 * sizeof(int32_t), s));
   const int32_t* work = m.ft.work;
   for (const Launch& L : m.sched[(sizeof(T) == 8) + 2 * (window ? 1 : 0)]) {
     prof_level(L.level);

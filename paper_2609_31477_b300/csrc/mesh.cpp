@@ -216,7 +216,8 @@ void build_mesh(Mesh& m, const vivMeshDesc* d) {
     while (p >= 0 && !kept[p]) p = sns[p].parent;
     keep_parent[s] = p;
   }
-  if (has_body) sns[root0].nodes.push_back((int)n);   // delta pseudo-node, eliminated last
+  // (delta is not a front unknown: it is numbered last and eliminated through
+  // the FP64 border Schur complement after the fronts, see the border tables)
   // postorder over kept supernodes
   std::vector<std::vector<int>> kids(S0);
   for (int s = 0; s < S0; ++s)
@@ -279,6 +280,13 @@ void build_mesh(Mesh& m, const vivMeshDesc* d) {
     }
     m.f_p[i] = next - m.f_first[i];
     if (s != root0) m.f_parent[i] = pos_of[keep_parent[s]];
+  }
+  m.n_front_dofs = next;   // unknowns of the fronts (everything but delta)
+  if (has_body) {
+    node_first[n] = next;
+    m.delta_dof[0] = next++;
+    m.delta_dof[1] = next++;
+    node_cnt[n] = 2;
   }
   m.n_dofs = next;
   m.dof_node.assign(next, -1);
@@ -397,15 +405,9 @@ void build_mesh(Mesh& m, const vivMeshDesc* d) {
   // ---- symbolic factorisation on the node quotient graph ------------------------
   std::vector<std::vector<int32_t>> adj(n + 1);
   for (int64_t e = 0; e < E; ++e) {
-    bool touches = false;
-    for (int a = 0; a < 9; ++a) touches |= (bool)cyl[m.conn[e * 9 + a]];
     for (int a = 0; a < 9; ++a) {
       int na = m.conn[e * 9 + a];
       for (int b = 0; b < 9; ++b) adj[na].push_back(m.conn[e * 9 + b]);
-      if (touches && has_body) {
-        adj[na].push_back((int)n);
-        adj[n].push_back(na);
-      }
     }
   }
   for (auto& v : adj) {
@@ -486,23 +488,27 @@ void build_mesh(Mesh& m, const vivMeshDesc* d) {
   // original entries -> fronts (bucketed by the front of min(row, col))
   {
     const int64_t nnz = m.row_ptr[m.n_dofs];
+    const int32_t nA = (int32_t)m.n_front_dofs;   // entries in a delta row or column are border entries
     std::vector<int64_t> cnt(NF + 1, 0);
-    for (int64_t r = 0; r < m.n_dofs; ++r)
-      for (int64_t q = m.row_ptr[r]; q < m.row_ptr[r + 1]; ++q) cnt[front_of_dof[std::min<int32_t>(r, m.col[q])] + 1]++;
+    for (int64_t r = 0; r < nA; ++r)
+      for (int64_t q = m.row_ptr[r]; q < m.row_ptr[r + 1]; ++q)
+        if (m.col[q] < nA) cnt[front_of_dof[std::min<int32_t>(r, m.col[q])] + 1]++;
     for (int i = 0; i < NF; ++i) cnt[i + 1] += cnt[i];
     m.f_nz_off.assign(cnt.begin(), cnt.end());
     std::vector<int32_t> nz_row(nnz), nz_colv(nnz), nz_q(nnz);
     std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
-    for (int64_t r = 0; r < m.n_dofs; ++r)
+    for (int64_t r = 0; r < nA; ++r)
       for (int64_t q = m.row_ptr[r]; q < m.row_ptr[r + 1]; ++q) {
+        if (m.col[q] >= nA) continue;
         int f = front_of_dof[std::min<int32_t>(r, m.col[q])];
         int64_t at = fill[f]++;
         nz_row[at] = (int32_t)r;
         nz_colv[at] = m.col[q];
         nz_q[at] = (int32_t)q;
       }
-    m.f_nz_csr.resize(nnz);
-    m.f_nz_pos.resize(nnz);
+    const int64_t nnz_fronts = m.f_nz_off[NF];
+    m.f_nz_csr.resize(nnz_fronts);
+    m.f_nz_pos.resize(nnz_fronts);
     m.f_col_nz_off.assign(NF + 1, 0);
     for (int i = 0; i < NF; ++i) {
       int mm = m.f_m[i];
@@ -554,6 +560,39 @@ void build_mesh(Mesh& m, const vivMeshDesc* d) {
         m.f_ea[m.f_ea_off[i] + (j - m.f_p[i])] = l;
       }
       for (int j = 0; j < pm; ++j) loc[m.f_idx[m.f_idx_off[par] + j]] = -1;
+    }
+  }
+  // border tables: delta rows C (entries in front columns), delta columns B
+  // (entries in front rows) and D, as CSR slots
+  m.bc_off.assign(3, 0);
+  m.bb_off.assign(3, 0);
+  m.bc_col.clear();
+  m.bc_q.clear();
+  m.bb_row.clear();
+  m.bb_q.clear();
+  for (int i = 0; i < 4; ++i) m.bd_q[i] = -1;
+  if (has_body) {
+    const int32_t nA = (int32_t)m.n_front_dofs;
+    for (int i = 0; i < 2; ++i) {
+      const int32_t r = m.delta_dof[i];
+      for (int64_t q = m.row_ptr[r]; q < m.row_ptr[r + 1]; ++q) {
+        if (m.col[q] < nA) {
+          m.bc_col.push_back(m.col[q]);
+          m.bc_q.push_back((int32_t)q);
+        } else {
+          m.bd_q[2 * i + (m.col[q] - nA)] = (int32_t)q;
+        }
+      }
+      m.bc_off[i + 1] = (int32_t)m.bc_col.size();
+    }
+    for (int j = 0; j < 2; ++j) {
+      for (int32_t r = 0; r < nA; ++r)
+        for (int64_t q = m.row_ptr[r]; q < m.row_ptr[r + 1]; ++q)
+          if (m.col[q] == m.delta_dof[j]) {
+            m.bb_row.push_back(r);
+            m.bb_q.push_back((int32_t)q);
+          }
+      m.bb_off[j + 1] = (int32_t)m.bb_row.size();
     }
   }
   // levels (height above the leaves)
@@ -910,6 +949,10 @@ void upload_mesh(Mesh& m, cudaStream_t s) {
   m.d_inv_items = A.upload(m.inv_items, s);
   m.d_fg_items = A.upload(m.fg_items, s);
   m.d_bg_items = A.upload(m.bg_items, s);
+  m.d_bc_col = A.upload(m.bc_col, s);
+  m.d_bc_q = A.upload(m.bc_q, s);
+  m.d_bb_row = A.upload(m.bb_row, s);
+  m.d_bb_q = A.upload(m.bb_q, s);
   FrontTables& t = m.ft;
   t.n_fronts = m.n_fronts;
   t.off = A.upload(m.f_off, s);

@@ -62,7 +62,9 @@ void lu_solve_noalloc(vivCase* c, const double* b, double* x) {
   const bool f32 = c->prm.precision == VIV_MIXED;
   const size_t tsz = f32 ? sizeof(float) : sizeof(double);
   const size_t vec_bytes = ((size_t)m.vec_entries * tsz + 255) & ~size_t(255);
-  const size_t need = vec_bytes + (size_t)m.n_dofs * tsz;
+  const size_t yv_bytes = ((size_t)m.n_dofs * tsz + 255) & ~size_t(255);
+  const bool border = m.n_front_dofs < m.n_dofs;
+  const size_t need = vec_bytes + yv_bytes + (border ? 256 : 0);   // + the border's delta
   VIV_CHECK(need <= NOALLOC_SCRATCH_BYTES, VIV_ERR_ARG,
             "viv_lu_solve_noalloc: this mesh needs " + std::to_string(need) +
                 " bytes of solve workspace, more than the fixed " + std::to_string(NOALLOC_SCRATCH_BYTES) +
@@ -74,6 +76,9 @@ void lu_solve_noalloc(vivCase* c, const double* b, double* x) {
   else
     solve_fronts<double>(m, (const double*)c->s.fronts, c->s.perm, b, x, (double*)base,
                          (double*)(base + vec_bytes), c->stream);
+  // the cylinder position through the FP64 border Schur block formed at factorisation
+  if (border)
+    launch_border_solve(m, c->s.J64, b, x, c->s.Y, c->s.Sb, (double*)(base + vec_bytes + yv_bytes), c->stream);
 }
 
 }  // namespace viv

@@ -126,6 +126,97 @@ __global__ void f32_to_f64_kernel(double* y, const float* x, int64_t n) {
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// ---- border: the two delta unknowns eliminated after the fronts -------------
+// (J = [A B; C D]; Y = A^{-1} B from the factors, S_b = D - C Y in FP64)
+
+// column j of B as a dense front-row vector (dst zeroed beforehand)
+__global__ void border_scatter_kernel(int n, const int32_t* __restrict__ row, const int32_t* __restrict__ q,
+                                      const double* __restrict__ J, double* dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[row[i]] = J[q[i]];
+}
+
+constexpr int BORDER_THREADS = 256;
+
+// deterministic block sum of one value per thread
+__device__ double block_sum(double v, double* red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = BORDER_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// S_b = D - C Y and its inverse: Sb[0..3] = S (row major), Sb[4..7] = S^{-1};
+// a singular S_b sets *flag
+__global__ void __launch_bounds__(BORDER_THREADS) border_schur_kernel(int c0_end, int c1_end, const int32_t* col,
+                                                                      const int32_t* q, int4 dq, const double* J,
+                                                                      const double* Y, int64_t ldy, double* Sb,
+                                                                      int32_t* flag) {
+  __shared__ double red[BORDER_THREADS];
+  double S[4];
+  for (int i = 0; i < 2; ++i) {
+    const int b0 = i == 0 ? 0 : c0_end, b1 = i == 0 ? c0_end : c1_end;
+    double a0 = 0, a1 = 0;
+    for (int k = b0 + threadIdx.x; k < b1; k += BORDER_THREADS) {
+      const double c = J[q[k]];
+      a0 += c * Y[col[k]];
+      a1 += c * Y[ldy + col[k]];
+    }
+    const int d0 = i == 0 ? dq.x : dq.z, d1 = i == 0 ? dq.y : dq.w;
+    S[2 * i] = (d0 >= 0 ? J[d0] : 0.0) - block_sum(a0, red);
+    S[2 * i + 1] = (d1 >= 0 ? J[d1] : 0.0) - block_sum(a1, red);
+  }
+  if (threadIdx.x == 0) {
+    const double det = S[0] * S[3] - S[1] * S[2];
+    const double scale = fabs(S[0] * S[3]) + fabs(S[1] * S[2]);
+    for (int k = 0; k < 4; ++k) Sb[k] = S[k];
+    if (!(fabs(det) > 1e-300 && fabs(det) > 1e-14 * scale)) {
+      atomicExch(flag, 1);
+      for (int k = 4; k < 8; ++k) Sb[k] = 0.0;
+    } else {
+      Sb[4] = S[3] / det;
+      Sb[5] = -S[1] / det;
+      Sb[6] = -S[2] / det;
+      Sb[7] = S[0] / det;
+    }
+  }
+}
+
+// delta = S_b^{-1} (b_delta - C z) with z = x[0 : nA] (the front solve), into
+// x[nA], x[nA + 1] and dtmp[0..1]
+__global__ void __launch_bounds__(BORDER_THREADS) border_delta_kernel(int c0_end, int c1_end, const int32_t* col,
+                                                                      const int32_t* q, const double* J,
+                                                                      const double* b, double* x, int64_t nA,
+                                                                      const double* Sb, double* dtmp) {
+  __shared__ double red[BORDER_THREADS];
+  double t[2];
+  for (int i = 0; i < 2; ++i) {
+    const int b0 = i == 0 ? 0 : c0_end, b1 = i == 0 ? c0_end : c1_end;
+    double a = 0;
+    for (int k = b0 + threadIdx.x; k < b1; k += BORDER_THREADS) a += J[q[k]] * x[col[k]];
+    t[i] = b[nA + i] - block_sum(a, red);
+  }
+  if (threadIdx.x == 0) {
+    const double d0 = Sb[4] * t[0] + Sb[5] * t[1], d1 = Sb[6] * t[0] + Sb[7] * t[1];
+    x[nA] = d0;
+    x[nA + 1] = d1;
+    dtmp[0] = d0;
+    dtmp[1] = d1;
+  }
+}
+
+// x[0 : nA] -= Y delta
+__global__ void border_back_kernel(int64_t nA, const double* Y, int64_t ldy, const double* dtmp, double* x) {
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= nA) return;
+  x[r] -= Y[r] * dtmp[0] + Y[ldy + r] * dtmp[1];
+}
+
 }  // namespace
 
 void launch_norm2(const double* v, int64_t n, double* partial, double* out, cudaStream_t s) {
@@ -204,6 +295,40 @@ void launch_f64_to_f32(float* y, const double* x, int64_t n, cudaStream_t s) {
 void launch_f32_to_f64(double* y, const float* x, int64_t n, cudaStream_t s) {
   Launched L(K_VEC, s);
   f32_to_f64_kernel<<<blocks_for(n, 256), 256, 0, s>>>(y, x, n);
+  VIV_CUDA(cudaGetLastError());
+}
+
+// ---- border launchers --------------------------------------------------------
+void launch_border_column(const Mesh& m, const double* J, int j, double* dst, cudaStream_t s) {
+  VIV_CUDA(cudaMemsetAsync(dst, 0, (size_t)m.n_dofs * sizeof(double), s));
+  const int b0 = m.bb_off[j], n = m.bb_off[j + 1] - b0;
+  if (n > 0) {
+    Launched L(K_VEC, s);
+    border_scatter_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, m.d_bb_row + b0, m.d_bb_q + b0, J, dst);
+  }
+  VIV_CUDA(cudaGetLastError());
+}
+
+void launch_border_schur(const Mesh& m, const double* J, const double* Y, double* Sb, int32_t* flag,
+                         cudaStream_t s) {
+  Launched L(K_VEC, s);
+  border_schur_kernel<<<1, BORDER_THREADS, 0, s>>>(m.bc_off[1], m.bc_off[2], m.d_bc_col, m.d_bc_q,
+                                                   make_int4(m.bd_q[0], m.bd_q[1], m.bd_q[2], m.bd_q[3]), J, Y,
+                                                   m.n_dofs, Sb, flag);
+  VIV_CUDA(cudaGetLastError());
+}
+
+void launch_border_solve(const Mesh& m, const double* J, const double* b, double* x, const double* Y,
+                         const double* Sb, double* dtmp, cudaStream_t s) {
+  {
+    Launched L(K_VEC, s);
+    border_delta_kernel<<<1, BORDER_THREADS, 0, s>>>(m.bc_off[1], m.bc_off[2], m.d_bc_col, m.d_bc_q, J, b, x,
+                                                     m.n_front_dofs, Sb, dtmp);
+  }
+  {
+    Launched L(K_VEC, s);
+    border_back_kernel<<<blocks_for(m.n_front_dofs, 256), 256, 0, s>>>(m.n_front_dofs, Y, m.n_dofs, dtmp, x);
+  }
   VIV_CUDA(cudaGetLastError());
 }
 

@@ -133,11 +133,18 @@ struct Mesh {
   std::vector<int32_t> node_dof;   // n x 7
   std::vector<int32_t> delta_dof;  // 2 (or -1)
   int64_t n_dofs = 0;
+  int64_t n_front_dofs = 0;        // unknowns the fronts hold: all but delta (numbered last)
   std::vector<int64_t> row_ptr;
   std::vector<int32_t> col;
   std::vector<int32_t> e2nz;       // E x VOL_PAIRS
   std::vector<int32_t> f2nz;       // F x FACE_PAIRS
   int32_t dd_nz[2] = {-1, -1};     // CSR slots of (delta_i, delta_i)
+  // border of the Jacobian, J = [A B; C D] with the two delta unknowns last:
+  // C = delta rows in front columns (bc_col / bc_q, rows split at bc_off),
+  // B = delta columns in front rows (bb_row / bb_q, columns split at bb_off),
+  // D slots bd_q[2 i + j] (-1 where structurally zero)
+  std::vector<int32_t> bc_off, bc_col, bc_q, bb_off, bb_row, bb_q;
+  int32_t bd_q[4] = {-1, -1, -1, -1};
   std::vector<int32_t> color_off;  // element colours: elements sorted by colour
   std::vector<int32_t> color_elems;
   std::vector<int32_t> fcolor_off;
@@ -189,6 +196,7 @@ struct Mesh {
   int32_t* d_inv_items = nullptr;
   int32_t* d_fg_items = nullptr;
   int32_t* d_bg_items = nullptr;
+  int32_t *d_bc_col = nullptr, *d_bc_q = nullptr, *d_bb_row = nullptr, *d_bb_q = nullptr;
   FrontTables ft;
 };
 
@@ -213,6 +221,10 @@ struct CaseState {
   int32_t* perm;                        // composed row permutation of each front (solves)
   int32_t* stats;                       // [0] perturbed, [1] threshold misses, [2] tensor-core wait expired
   unsigned char* tc_img;                // operand images of the tensor-core updates (mixed path)
+  double* Y;                            // border: A^{-1} B (2 columns of n_dofs; rows < n_front_dofs used)
+  double* Sb;                           // border: S_b = D - C Y (4) and its inverse (4), FP64
+  double* btmp;                         // border: delta of the current solve (2) and scratch
+  double* Bcol;                         // border: one column of B as a dense vector (n_dofs)
   double* partial;                      // norm partial sums
   double* scal;                         // host-visible scalars (device side)
 };
@@ -306,6 +318,12 @@ void launch_f64_to_f32(float* y, const double* x, int64_t n, cudaStream_t s);
 void launch_f32_to_f64(double* y, const float* x, int64_t n, cudaStream_t s);
 void launch_jacobian_split(const Mesh& m, const CaseState& st, const vivParams& prm, double c0, float* J32,
                            double* J64, cudaStream_t s);
+// border of the Jacobian (the two delta unknowns, eliminated after the fronts)
+void launch_border_column(const Mesh& m, const double* J, int j, double* dst, cudaStream_t s);
+void launch_border_schur(const Mesh& m, const double* J, const double* Y, double* Sb, int32_t* flag,
+                         cudaStream_t s);
+void launch_border_solve(const Mesh& m, const double* J, const double* b, double* x, const double* Y,
+                         const double* Sb, double* dtmp, cudaStream_t s);
 template <class T>
 void prepare_kernels();
 template <class T>

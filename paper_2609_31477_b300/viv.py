@@ -128,6 +128,7 @@ SIGNATURES = {
     "viv_get_residual": (C.c_int, [_P, _P]),
     "viv_get_jacobian": (C.c_int, [_P, _P]),
     "viv_factor": (C.c_int, [_P]),
+    "viv_border_block": (C.c_int, [_P, _P]),
     "viv_solve": (C.c_int, [_P, C.POINTER(C.c_int)]),
     "viv_solve_rhs": (C.c_int, [_P, C.c_int, _P, _P, C.POINTER(C.c_int)]),
     "viv_update": (C.c_int, [_P]),
@@ -361,6 +362,12 @@ class Case:
 
     def factor(self):
         _check(_lib.viv_factor(self.h))
+
+    def border_block(self):
+        """FP64 border Schur block S_b = D - C A^{-1} B of the last factorisation (2 x 2)."""
+        S = np.empty(4)
+        _check(_lib.viv_border_block(self.h, _ptr(S)))
+        return S.reshape(2, 2)
 
     def solve(self):
         sw = C.c_int()

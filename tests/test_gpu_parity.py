@@ -130,6 +130,35 @@ def test_refined_multifrontal_solve(viv, m, precision, pivoting):
         assert sweeps >= 2
 
 
+@pytest.mark.parametrize("precision,pivoting", [("fp64", "threshold"), ("mixed", "window"), ("mixed", "threshold")])
+@pytest.mark.parametrize("m", [4, 12])
+def test_border_schur_block(viv, m, precision, pivoting):
+    """The cylinder position is eliminated after the fronts as a dense FP64
+    block (Eq. coupling_constraint): S_b = D - C A^{-1} B, with A the Jacobian
+    without the two delta rows and columns.  Reference: the definition, with
+    the oracle's Jacobian and a library sparse LU of its A.  The FP64 path
+    agrees to 1e-10; the mixed path's A^{-1} B comes from FP32 factors, so
+    its block carries their error (<= 1e-4), and the refined solve (tested
+    above) recovers full accuracy."""
+    prec = viv.VIV_FP64 if precision == "fp64" else viv.VIV_MIXED
+    piv = viv.VIV_PIVOT_THRESHOLD if pivoting == "threshold" else viv.VIV_PIVOT_WINDOW
+    mesh, oc, M, case = _pair(viv, m, prec, pivoting=piv)
+    c0, hu, hx = _mid_step_state(viv, oc, case, 41)
+    case.assemble(viv.VIV_RES | viv.VIV_JAC)
+    case.factor()
+    S = case.border_block()
+    J = oc.jacobian(c0, hu, hx, DT).tocsr()
+    d = np.asarray(oc.dof_d)
+    a = np.setdiff1d(np.arange(oc.ndof), d)
+    A = J[a][:, a].tocsc()
+    B = J[a][:, d].toarray()
+    C = J[d][:, a].toarray()
+    D = J[d][:, d].toarray()
+    S_o = D - C @ spla.splu(A).solve(B)
+    err = np.abs(S - S_o).max() / np.abs(S_o).max()
+    assert err <= (1e-10 if precision == "fp64" else 1e-4), (err, S, S_o)
+
+
 def _compare_fields(oc, st, tol_field=1e-9, tol_delta=1e-8):
     verts = oc.is_vertex
     errs = dict(u=rel_l2(st["u"], oc.u), p=rel_l2(st["p"][verts], oc.p[verts]), x=rel_l2(st["x"], oc.x),
