@@ -211,10 +211,14 @@ void factor(vivCase* c) {
     factor_numeric<double>(m, c->s.J64, nullptr, (double*)c->s.fronts, c->s.piv, c->s.perm, c->s.stats, thr, win,
                            nullptr, c->stream);
   if (has_border(m)) {
-    for (int j = 0; j < 2; ++j) {
-      launch_border_column(m, c->s.J64, j, c->s.Bcol, c->stream);
-      front_solve(c, c->s.Bcol, c->s.Y + (int64_t)j * m.n_dofs);
-    }
+    // both columns of B through the fronts in one pass
+    for (int j = 0; j < 2; ++j) launch_border_column(m, c->s.J64, j, c->s.Bcol + (int64_t)j * m.n_dofs, c->stream);
+    if (mixed(c))
+      solve_fronts2<float>(m, (const float*)c->s.fronts, c->s.perm, c->s.Bcol, c->s.Y, (float*)c->s.vec2,
+                           (float*)c->s.yv2, c->stream);
+    else
+      solve_fronts2<double>(m, (const double*)c->s.fronts, c->s.perm, c->s.Bcol, c->s.Y, (double*)c->s.vec2,
+                            (double*)c->s.yv2, c->stream);
     launch_border_schur(m, c->s.J64, c->s.Y, c->s.Sb, c->s.stats + 3, c->stream);
   }
   c->factored = true;
@@ -338,8 +342,10 @@ vivStatus viv_mesh_info(const vivMesh* mesh, vivMeshInfo* info) {
   info->front_entries = (size_t)m.front_entries;
   size_t nodes = (size_t)m.n_nodes, nnz = (size_t)info->nnz, nd = (size_t)m.n_dofs;
   size_t state = 8 * (17 * nodes + (size_t)m.n_elems + 3 * nd + 2 * 296 + 64) + 8 * (size_t)m.piv_entries;
-  info->device_bytes_fp64 = state + 8 * (nnz + (size_t)m.front_entries + (size_t)m.vec_entries + nd);
-  info->device_bytes_mixed = state + 8 * nnz + 4 * (nnz + (size_t)m.front_entries + (size_t)m.vec_entries + nd) +
+  if (m.n_front_dofs < m.n_dofs) state += 8 * 4 * nd;   // border: Y and the columns of B
+  const size_t nv = m.n_front_dofs < m.n_dofs ? 3 : 1;   // solve workspaces: one, plus two for the border columns
+  info->device_bytes_fp64 = state + 8 * (nnz + (size_t)m.front_entries + nv * ((size_t)m.vec_entries + nd));
+  info->device_bytes_mixed = state + 8 * nnz + 4 * (nnz + (size_t)m.front_entries + nv * ((size_t)m.vec_entries + nd)) +
                              (size_t)m.tc_img_chunks * TC_IMG_CHUNK_BYTES;
   info->n_colors = (int32_t)m.color_off.size() - 1;
   info->gemm_flops = m.gemm_flops;
@@ -473,7 +479,10 @@ static vivStatus case_create_impl(vivMesh* mesh, const vivParams* prm_in, const 
     s.stats = A.make<int32_t>(4);
     if (has_border(m)) {
       s.Y = A.make<double>(2 * (size_t)nd);
-      s.Bcol = A.make<double>(nd);
+      s.Bcol = A.make<double>(2 * (size_t)nd);
+      const size_t tsz2 = mixed(c) ? sizeof(float) : sizeof(double);
+      s.vec2 = A.get(2 * tsz2 * (size_t)m.vec_entries);
+      s.yv2 = A.get(2 * tsz2 * (size_t)nd);
       s.Sb = A.make<double>(8);
       s.btmp = A.make<double>(4);
     }

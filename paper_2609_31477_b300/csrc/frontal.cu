@@ -811,13 +811,19 @@ constexpr int solve_threads_max() {
 }
 constexpr int GEMV_THREADS = SOLVE_ROWS;   // one row per thread, 32 rows per warp
 
+// Every solve kernel handles NR right-hand sides at once (NR = 1 for the
+// refinement sweeps, 2 for the border columns Y = A^{-1} B): vector r of b
+// and x starts at r * ldv (doubles), of yv at r * ldv (T) and of the
+// workspace at r * vstride (T); the factor entries are loaded once for all NR.
+
 // slice partial sums of the non-pivot rows (FWD: L21 x) or of the pivot rows
 // (!FWD: U12 x2) for one item (f, r0, s)
-template <class T, bool FWD>
+template <class T, bool FWD, int NR>
 __global__ void __launch_bounds__(GEMV_THREADS) solve_gemv_kernel(FT ft, const int32_t* items, const T* __restrict__ pool,
                                                                   const T* __restrict__ yv,
-                                                                  const double* __restrict__ x, T* vec) {
-  __shared__ T xs[SOLVE_SLICE];
+                                                                  const double* __restrict__ x, T* vec, int64_t ldv,
+                                                                  int64_t vstride) {
+  __shared__ T xs[NR][SOLVE_SLICE];
   const int32_t* it = items + 4 * blockIdx.x;
   const int f = it[0], r0 = it[1], sl = it[2];
   const int m = ft.m[f], p = ft.p[f], first = ft.first[f];
@@ -826,16 +832,22 @@ __global__ void __launch_bounds__(GEMV_THREADS) solve_gemv_kernel(FT ft, const i
   const int c0 = col_lo + sl * SOLVE_SLICE, c1 = min(col_hi, c0 + SOLVE_SLICE);
   const int nrows = row_hi - row_lo;
   if (FWD) {
-    for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) xs[c - c0] = yv[first + c];
+    for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x)
+#pragma unroll
+      for (int r = 0; r < NR; ++r) xs[r][c - c0] = yv[r * ldv + first + c];
   } else {
     const int32_t* idx = ft.idx + ft.idx_off[f];
-    for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) xs[c - c0] = (T)x[idx[c]];
+    for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x)
+#pragma unroll
+      for (int r = 0; r < NR; ++r) xs[r][c - c0] = (T)x[r * ldv + idx[c]];
   }
   __syncthreads();
   const int i = row_lo + r0 + threadIdx.x;
   if (i >= row_hi) return;
   const T* col = pool + ft.off[f] + (int64_t)c0 * m + i;
-  T a[4] = {0, 0, 0, 0};
+  T a[NR][4];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) a[r][0] = a[r][1] = a[r][2] = a[r][3] = T(0);
   int c = 0;
   const int nc = c1 - c0;
   for (; c + 32 <= nc; c += 32) {
@@ -843,47 +855,72 @@ __global__ void __launch_bounds__(GEMV_THREADS) solve_gemv_kernel(FT ft, const i
 #pragma unroll
     for (int u = 0; u < 32; ++u) v[u] = __ldg(col + (int64_t)(c + u) * m);
 #pragma unroll
-    for (int u = 0; u < 32; ++u) a[u & 3] += v[u] * xs[c + u];
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+      for (int u = 0; u < 32; ++u) a[r][u & 3] += v[u] * xs[r][c + u];
   }
-  for (; c < nc; ++c) a[0] += __ldg(col + (int64_t)c * m) * xs[c];
-  T* part = vec + ft.vec_off[f] + m;
-  part[(int64_t)sl * nrows + (i - row_lo)] = (a[0] + a[1]) + (a[2] + a[3]);
+  for (; c < nc; ++c) {
+    const T v = __ldg(col + (int64_t)c * m);
+#pragma unroll
+    for (int r = 0; r < NR; ++r) a[r][0] += v * xs[r][c];
+  }
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    T* part = vec + r * vstride + ft.vec_off[f] + m;
+    part[(int64_t)sl * nrows + (i - row_lo)] = (a[r][0] + a[r][1]) + (a[r][2] + a[r][3]);
+  }
 }
 
 // forward chain of one front: gather, permute, L11^{-1} blocks and the pivot
 // rows below them; the non-pivot rows keep the gathered values for the slices
-template <class T>
+template <class T, int NR>
 __global__ void __launch_bounds__(solve_threads_max<T>(), 1) fwd_tri_kernel(FT ft, const int32_t* fronts, const T* __restrict__ pool,
                                                                 const int32_t* perm, const double* b, T* vec, T* yv,
-                                                                bool in_smem) {
+                                                                bool in_smem, int64_t ldv, int64_t vstride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ T xw[SOLVE_THREADS / 32][32];
+  __shared__ T xw[NR][SOLVE_THREADS / 32][32];
   const int f = fronts[blockIdx.x];
   const int m = ft.m[f], p = ft.p[f], first = ft.first[f];
-  T* gw = vec + ft.vec_off[f];
-  T* w = in_smem ? reinterpret_cast<T*>(smem_raw) : gw;
-  T* tmp = in_smem ? w + m : yv + first;
+  // vector r: w[r] (m entries) and tmp[r] (p entries)
+  T* const wsm = reinterpret_cast<T*>(smem_raw);
+  T* w[NR];
+  T* tmp[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    w[r] = in_smem ? wsm + (int64_t)r * m : vec + r * vstride + ft.vec_off[f];
+    tmp[r] = in_smem ? wsm + (int64_t)NR * m + (int64_t)r * p : yv + r * ldv + first;
+  }
   const T* F = pool + ft.off[f];
-  for (int i = threadIdx.x; i < m; i += blockDim.x) w[i] = i < p ? (T)b[first + i] : T(0);
+  for (int i = threadIdx.x; i < m; i += blockDim.x)
+#pragma unroll
+    for (int r = 0; r < NR; ++r) w[r][i] = i < p ? (T)b[r * ldv + first + i] : T(0);
   __syncthreads();
   for (int cc = ft.child_off[f]; cc < ft.child_off[f + 1]; ++cc) {
     const int c = ft.child[cc];
     const int mc = ft.m[c], pc = ft.p[c], nc = mc - pc;
     const int32_t* ea = ft.ea + ft.ea_off[c];
-    const T* wc = vec + ft.vec_off[c];
-    const T* pc_part = wc + mc;
     const int ns = (pc + SOLVE_SLICE - 1) / SOLVE_SLICE;
-    for (int r = threadIdx.x; r < nc; r += blockDim.x) {
-      T v = wc[pc + r];
-      for (int s = 0; s < ns; ++s) v -= pc_part[(int64_t)s * nc + r];
-      w[ea[r]] += v;
+    for (int rr = threadIdx.x; rr < nc; rr += blockDim.x) {
+      const int e = ea[rr];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        const T* wc = vec + r * vstride + ft.vec_off[c];
+        const T* pc_part = wc + mc;
+        T v = wc[pc + rr];
+        for (int s2 = 0; s2 < ns; ++s2) v -= pc_part[(int64_t)s2 * nc + rr];
+        w[r][e] += v;
+      }
     }
     __syncthreads();
   }
   const int32_t* pm = perm + ft.piv_off[f];
-  for (int i = threadIdx.x; i < p; i += blockDim.x) tmp[i] = w[pm[i]];
+  for (int i = threadIdx.x; i < p; i += blockDim.x)
+#pragma unroll
+    for (int r = 0; r < NR; ++r) tmp[r][i] = w[r][pm[i]];
   __syncthreads();
-  for (int i = threadIdx.x; i < p; i += blockDim.x) w[i] = tmp[i];
+  for (int i = threadIdx.x; i < p; i += blockDim.x)
+#pragma unroll
+    for (int r = 0; r < NR; ++r) w[r][i] = tmp[r][i];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int jb = 0; jb < p; jb += 32) {
     const int nb = min(32, p - jb);
@@ -893,55 +930,69 @@ __global__ void __launch_bounds__(solve_threads_max<T>(), 1) fwd_tri_kernel(FT f
 #pragma unroll
     for (int j = 0; j < 32; ++j) d[j] = (j < lane && lane < nb) ? Db[(int64_t)j * m] : T(0);
     __syncthreads();
-    const T wl = lane < nb ? w[jb + lane] : T(0);
-    T xl = wl;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) xl += d[j] * __shfl_sync(0xffffffffu, wl, j);
-    xw[wid][lane] = xl;
+    for (int r = 0; r < NR; ++r) {
+      const T wl = lane < nb ? w[r][jb + lane] : T(0);
+      T xl = wl;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) xl += d[j] * __shfl_sync(0xffffffffu, wl, j);
+      xw[r][wid][lane] = xl;
+      if (wid == 0 && lane < nb) yv[r * ldv + first + jb + lane] = xl;
+    }
     __syncwarp();
-    if (wid == 0 && lane < nb) yv[first + jb + lane] = xl;
-    const T* xr = xw[wid];
     if (nb == 32) {
       for (int i = jb + 32 + threadIdx.x; i < p; i += blockDim.x) {
         const T* col = F + (int64_t)jb * m + i;
         T v[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) v[j] = col[(int64_t)j * m];
-        T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
 #pragma unroll
-        for (int j = 0; j < 32; j += 4) {
-          a0 += v[j] * xr[j];
-          a1 += v[j + 1] * xr[j + 1];
-          a2 += v[j + 2] * xr[j + 2];
-          a3 += v[j + 3] * xr[j + 3];
+        for (int r = 0; r < NR; ++r) {
+          const T* xr = xw[r][wid];
+          T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+#pragma unroll
+          for (int j = 0; j < 32; j += 4) {
+            a0 += v[j] * xr[j];
+            a1 += v[j + 1] * xr[j + 1];
+            a2 += v[j + 2] * xr[j + 2];
+            a3 += v[j + 3] * xr[j + 3];
+          }
+          w[r][i] -= (a0 + a1) + (a2 + a3);
         }
-        w[i] -= (a0 + a1) + (a2 + a3);
       }
     }
     // (a short last block has no pivot rows below it)
   }
   if (in_smem)
-    for (int i = p + threadIdx.x; i < m; i += blockDim.x) gw[i] = w[i];
+    for (int i = p + threadIdx.x; i < m; i += blockDim.x)
+#pragma unroll
+      for (int r = 0; r < NR; ++r) vec[r * vstride + ft.vec_off[f] + i] = w[r][i];
 }
 
 // backward chain of one front: subtract the slice sums, U11^{-1} blocks from
 // the last one up, and the rows above each block
-template <class T>
+template <class T, int NR>
 __global__ void __launch_bounds__(solve_threads_max<T>(), 1) bwd_tri_kernel(FT ft, const int32_t* fronts, const T* __restrict__ pool,
-                                                                T* yv, const T* vec, double* x, bool in_smem) {
+                                                                T* yv, const T* vec, double* x, bool in_smem,
+                                                                int64_t ldv, int64_t vstride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ T xw[SOLVE_THREADS / 32][32];
+  __shared__ T xw[NR][SOLVE_THREADS / 32][32];
   const int f = fronts[blockIdx.x];
   const int m = ft.m[f], p = ft.p[f], first = ft.first[f];
-  T* v = in_smem ? reinterpret_cast<T*>(smem_raw) : yv + first;   // in place in yv otherwise
+  T* const vsm = reinterpret_cast<T*>(smem_raw);
+  T* v[NR];   // in place in yv when not in shared memory
+#pragma unroll
+  for (int r = 0; r < NR; ++r) v[r] = in_smem ? vsm + (int64_t)r * p : yv + r * ldv + first;
   const T* F = pool + ft.off[f];
-  const T* part = vec + ft.vec_off[f] + m;
   const int ns = (m - p + SOLVE_SLICE - 1) / SOLVE_SLICE;
-  for (int i = threadIdx.x; i < p; i += blockDim.x) {
-    T a = yv[first + i];
-    for (int s = 0; s < ns; ++s) a -= part[(int64_t)s * p + i];
-    v[i] = a;
-  }
+  for (int i = threadIdx.x; i < p; i += blockDim.x)
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const T* part = vec + r * vstride + ft.vec_off[f] + m;
+      T a = yv[r * ldv + first + i];
+      for (int s2 = 0; s2 < ns; ++s2) a -= part[(int64_t)s2 * p + i];
+      v[r][i] = a;
+    }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int jb = ((p - 1) / 32) * 32; jb >= 0 && p > 0; jb -= 32) {
     const int nb = min(32, p - jb);
@@ -951,28 +1002,34 @@ __global__ void __launch_bounds__(solve_threads_max<T>(), 1) bwd_tri_kernel(FT f
 #pragma unroll
     for (int j = 0; j < 32; ++j) d[j] = (j >= lane && j < nb) ? Db[(int64_t)j * m] : T(0);
     __syncthreads();
-    const T vl = lane < nb ? v[jb + lane] : T(0);
-    T xl = 0;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) xl += d[j] * __shfl_sync(0xffffffffu, vl, j);
-    xw[wid][lane] = xl;
+    for (int r = 0; r < NR; ++r) {
+      const T vl = lane < nb ? v[r][jb + lane] : T(0);
+      T xl = 0;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) xl += d[j] * __shfl_sync(0xffffffffu, vl, j);
+      xw[r][wid][lane] = xl;
+      if (wid == 0 && lane < nb) x[r * ldv + first + jb + lane] = (double)xl;
+    }
     __syncwarp();
-    if (wid == 0 && lane < nb) x[first + jb + lane] = (double)xl;
-    const T* xr = xw[wid];
     for (int i = threadIdx.x; i < jb; i += blockDim.x) {
       const T* col = F + (int64_t)jb * m + i;
       T u[32];
 #pragma unroll
       for (int j = 0; j < 32; ++j) u[j] = j < nb ? col[(int64_t)j * m] : T(0);
-      T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
 #pragma unroll
-      for (int j = 0; j < 32; j += 4) {
-        a0 += u[j] * xr[j];
-        a1 += u[j + 1] * xr[j + 1];
-        a2 += u[j + 2] * xr[j + 2];
-        a3 += u[j + 3] * xr[j + 3];
+      for (int r = 0; r < NR; ++r) {
+        const T* xr = xw[r][wid];
+        T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+#pragma unroll
+        for (int j = 0; j < 32; j += 4) {
+          a0 += u[j] * xr[j];
+          a1 += u[j + 1] * xr[j + 1];
+          a2 += u[j + 2] * xr[j + 2];
+          a3 += u[j + 3] * xr[j + 3];
+        }
+        v[r][i] -= (a0 + a1) + (a2 + a3);
       }
-      v[i] -= (a0 + a1) + (a2 + a3);
     }
   }
 }
@@ -987,8 +1044,10 @@ static void set_kernel_attributes() {
                                 PANEL_SMEM_BYTES));
   VIV_CUDA(cudaFuncSetAttribute(panel_smem_kernel<T, PANEL_CLUSTER, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 PANEL_SMEM_BYTES));
-  VIV_CUDA(cudaFuncSetAttribute(fwd_tri_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX));
-  VIV_CUDA(cudaFuncSetAttribute(bwd_tri_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX));
+  VIV_CUDA(cudaFuncSetAttribute(fwd_tri_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX));
+  VIV_CUDA(cudaFuncSetAttribute(bwd_tri_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX));
+  VIV_CUDA(cudaFuncSetAttribute(fwd_tri_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX));
+  VIV_CUDA(cudaFuncSetAttribute(bwd_tri_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_SMEM_MAX));
   VIV_CUDA(cudaFuncSetAttribute(perm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, PERM_SMEM_MAX));
 }
 
@@ -1093,42 +1152,58 @@ void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* front
   VIV_CUDA(cudaGetLastError());
 }
 
-template <class T>
-void solve_fronts(const Mesh& m, const T* fronts, const int32_t* perm, const double* b, double* x, T* vec, T* yv,
-                  cudaStream_t s) {
+// NR right-hand sides: vector r of b and x at r * ldv (doubles), of yv at
+// r * ldv (T), of the workspace vec at r * vstride (T)
+template <class T, int NR>
+void solve_fronts_nr(const Mesh& m, const T* fronts, const int32_t* perm, const double* b, double* x, T* vec, T* yv,
+                     int64_t ldv, int64_t vstride, cudaStream_t s) {
   FT ft = make_ft(m);
   prepare_kernels<T>();
   for (int l = 0; l < m.n_levels; ++l) {
     const int n = m.level_off[l + 1] - m.level_off[l];
-    const size_t need = (size_t)(m.level_maxm[l] + m.level_maxp[l]) * sizeof(T);
+    const size_t need = (size_t)NR * (m.level_maxm[l] + m.level_maxp[l]) * sizeof(T);
     const bool sm = need <= (size_t)SOLVE_SMEM_MAX;
     {
       Launched L(K_FWD, s);
-      fwd_tri_kernel<T><<<n, std::min(m.level_threads[l], solve_threads_max<T>()), sm ? need : 0, s>>>(ft, m.d_level_fronts + m.level_off[l], fronts,
-                                                                    perm, b, vec, yv, sm);
+      fwd_tri_kernel<T, NR><<<n, std::min(m.level_threads[l], solve_threads_max<T>()), sm ? need : 0, s>>>(
+          ft, m.d_level_fronts + m.level_off[l], fronts, perm, b, vec, yv, sm, ldv, vstride);
     }
     const int ng = m.fg_off[l + 1] - m.fg_off[l];
     if (ng) {
       Launched L(K_FWD, s);
-      solve_gemv_kernel<T, true><<<ng, GEMV_THREADS, 0, s>>>(ft, m.d_fg_items + 4 * (int64_t)m.fg_off[l], fronts, yv,
-                                                              x, vec);
+      solve_gemv_kernel<T, true, NR><<<ng, GEMV_THREADS, 0, s>>>(ft, m.d_fg_items + 4 * (int64_t)m.fg_off[l], fronts,
+                                                                  yv, x, vec, ldv, vstride);
     }
   }
   for (int l = m.n_levels - 1; l >= 0; --l) {
     const int ng = m.bg_off[l + 1] - m.bg_off[l];
     if (ng) {
       Launched L(K_BWD, s);
-      solve_gemv_kernel<T, false><<<ng, GEMV_THREADS, 0, s>>>(ft, m.d_bg_items + 4 * (int64_t)m.bg_off[l], fronts,
-                                                               yv, x, vec);
+      solve_gemv_kernel<T, false, NR><<<ng, GEMV_THREADS, 0, s>>>(ft, m.d_bg_items + 4 * (int64_t)m.bg_off[l],
+                                                                   fronts, yv, x, vec, ldv, vstride);
     }
     const int n = m.level_off[l + 1] - m.level_off[l];
-    const size_t need = (size_t)m.level_maxp[l] * sizeof(T);
+    const size_t need = (size_t)NR * m.level_maxp[l] * sizeof(T);
     const bool sm = need <= (size_t)SOLVE_SMEM_MAX;
     Launched L(K_BWD, s);
-    bwd_tri_kernel<T><<<n, std::min(m.level_threads[l], solve_threads_max<T>()), sm ? need : 0, s>>>(ft, m.d_level_fronts + m.level_off[l], fronts, yv,
-                                                                  vec, x, sm);
+    bwd_tri_kernel<T, NR><<<n, std::min(m.level_threads[l], solve_threads_max<T>()), sm ? need : 0, s>>>(
+        ft, m.d_level_fronts + m.level_off[l], fronts, yv, vec, x, sm, ldv, vstride);
   }
   VIV_CUDA(cudaGetLastError());
+}
+
+template <class T>
+void solve_fronts(const Mesh& m, const T* fronts, const int32_t* perm, const double* b, double* x, T* vec, T* yv,
+                  cudaStream_t s) {
+  solve_fronts_nr<T, 1>(m, fronts, perm, b, x, vec, yv, m.n_dofs, m.vec_entries, s);
+}
+
+// two right-hand sides in one pass (the border columns): b, x, yv hold two
+// vectors of m.n_dofs, vec two workspaces of m.vec_entries
+template <class T>
+void solve_fronts2(const Mesh& m, const T* fronts, const int32_t* perm, const double* b, double* x, T* vec, T* yv,
+                   cudaStream_t s) {
+  solve_fronts_nr<T, 2>(m, fronts, perm, b, x, vec, yv, m.n_dofs, m.vec_entries, s);
 }
 
 template void factor_numeric<double>(const Mesh&, const double*, const float*, double*, int32_t*, int32_t*,
@@ -1139,5 +1214,9 @@ template void solve_fronts<double>(const Mesh&, const double*, const int32_t*, c
                                    double*, cudaStream_t);
 template void solve_fronts<float>(const Mesh&, const float*, const int32_t*, const double*, double*, float*,
                                   float*, cudaStream_t);
+template void solve_fronts2<double>(const Mesh&, const double*, const int32_t*, const double*, double*, double*,
+                                    double*, cudaStream_t);
+template void solve_fronts2<float>(const Mesh&, const float*, const int32_t*, const double*, double*, float*,
+                                   float*, cudaStream_t);
 
 }  // namespace viv

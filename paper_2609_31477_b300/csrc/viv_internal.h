@@ -224,7 +224,9 @@ struct CaseState {
   double* Y;                            // border: A^{-1} B (2 columns of n_dofs; rows < n_front_dofs used)
   double* Sb;                           // border: S_b = D - C Y (4) and its inverse (4), FP64
   double* btmp;                         // border: delta of the current solve (2) and scratch
-  double* Bcol;                         // border: one column of B as a dense vector (n_dofs)
+  double* Bcol;                         // border: the two columns of B as dense vectors (2 x n_dofs)
+  void* vec2;                           // border: solve workspaces of the two columns (2 x vec_entries, T)
+  void* yv2;                            // border: forward-solve vectors of the two columns (2 x n_dofs, T)
   double* partial;                      // norm partial sums
   double* scal;                         // host-visible scalars (device side)
 };
@@ -332,6 +334,9 @@ void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* front
 template <class T>
 void solve_fronts(const Mesh& m, const T* fronts, const int32_t* perm, const double* b, double* x,
                   T* vec, T* yv, cudaStream_t s);
+template <class T>
+void solve_fronts2(const Mesh& m, const T* fronts, const int32_t* perm, const double* b, double* x, T* vec, T* yv,
+                   cudaStream_t s);
 }  // namespace viv
 
 // ----- canonical order of the element matrix pairs scattered through e2nz ----
