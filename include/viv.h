@@ -129,7 +129,12 @@ typedef struct {
   double pivot_threshold;  /* threshold u of partial pivoting in fronts (0.01) */
   int32_t source;          /* 0: none (the physical problem); 1: steady manufactured
                               solution of Section 5.1 on a mesh deformed by
-                              X + source_amp sin(pi X) sin(pi Y) (1, 1), for verification */
+                              X + source_amp sin(pi X) sin(pi Y) (1, 1); 2: Section 5.1's
+                              time-dependent solution (u = t^3 (sin pi x cos pi y,
+                              sin pi x sin pi y), p = t^2 cos pi x cos pi y) on a mesh moved by
+                              X + source_amp sin(pi t) sin(pi X) sin(pi Y) (1, 1), whose
+                              Dirichlet data the library sets at each step's time; for
+                              verification on the unit square */
   double source_amp;
   int32_t pivoting;        /* VIV_PIVOT_THRESHOLD (0): threshold partial pivoting over all
                               fully summed rows of a front; VIV_PIVOT_WINDOW (1): partial
@@ -302,13 +307,14 @@ vivStatus viv_tc_schur_update(const float* A, int lda, const float* B, int ldb, 
 vivStatus viv_update(vivCase* c);
 
 /* One BDF step: begin_step, then Newton (Eq. NR_iteration) until
- * ||NL||_2 <= newton_tol.  On the mixed path, once ||NL|| passes the test, one
- * closing correction is applied with the factors at hand (no new Jacobian),
- * with at least two refinement sweeps and then to a linear residual of 1e-6
- * of its right-hand side (counted in refine_sweeps), and ||NL|| is evaluated
- * again: it removes the error the FP32 factors leave in directions the
- * residual norm barely sees (a near-constant pressure offset), so the mixed
- * state agrees with the FP64 path's to round-off.  info nullable. */
+ * ||NL||_2 <= newton_tol.  Once ||NL|| passes the test (after at least one
+ * Newton iteration), one closing correction is applied with the factors at
+ * hand (no new Jacobian), with at least two refinement sweeps and then to a
+ * linear residual of 1e-6 of its right-hand side (counted in refine_sweeps),
+ * and ||NL|| is evaluated again.  It takes a state that only just passed the
+ * test to round-off, and on the mixed path removes the error the FP32 factors
+ * leave in directions the residual norm barely sees (a near-constant pressure
+ * offset), so both paths land on the same discrete solution.  info nullable. */
 vivStatus viv_step(vivCase* c, vivStepInfo* info);
 /* Same step with host buffers: uploads the state and history, steps, and
  * downloads the new state (the end-to-end form of one step). */

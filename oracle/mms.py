@@ -16,6 +16,10 @@ families are built here with sympy:
     factors) on a unit square whose mesh is statically deformed by
     x = X + A sin(pi X) sin(pi Y) (1, 1), run with a very large time step so the
     converged step is the steady problem; errors must fall at the optimal rates.
+  * UnsteadyMMS - the same fields with Section 5.1's time factors (t^3 for the
+    velocity, t^2 for the pressure) on a mesh moved by
+    x = X + A sin(pi t) sin(pi X) sin(pi Y) (1, 1): BDF2 must be second order in
+    time and the spatial rates optimal.
 
 Each provides: volume(Xq, t) -> (f_u, g_p, f_x), gamma(Xq, t) -> g_lambda,
 border(t) -> F, exact nodal values and a Dirichlet setter.
@@ -173,6 +177,21 @@ def steady_mms(rho=9.876, mu=1.234, amp=0.05):
     ux = sy.sin(pi * x_) * sy.cos(pi * y_)
     uy = sy.sin(pi * x_) * sy.sin(pi * y_)
     p = sy.cos(pi * x_) * sy.cos(pi * y_)
+    return _Manufactured((ux, uy), p, chi, rho, mu, 1.0, 1.0)
+
+
+def unsteady_mms(rho=9.876, mu=1.234, amp=0.05):
+    """Section 5.1's time-dependent 2-D manufactured solution:
+    u = t^3 (sin pi x cos pi y, sin pi x sin pi y), p = t^2 cos pi x cos pi y
+    on the unit square, with the mesh moved by
+    x = X + amp sin(pi t) sin(pi X) sin(pi Y) (1, 1) (zero on the boundary),
+    lambda_s = mu_s = 1; all-Dirichlet velocity and position."""
+    pi = sy.pi
+    bump = amp * sy.sin(pi * t_) * sy.sin(pi * X_) * sy.sin(pi * Y_)
+    chi = (X_ + bump, Y_ + bump)
+    ux = t_ ** 3 * sy.sin(pi * x_) * sy.cos(pi * y_)
+    uy = t_ ** 3 * sy.sin(pi * x_) * sy.sin(pi * y_)
+    p = t_ ** 2 * sy.cos(pi * x_) * sy.cos(pi * y_)
     return _Manufactured((ux, uy), p, chi, rho, mu, 1.0, 1.0)
 
 

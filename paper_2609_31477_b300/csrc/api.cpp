@@ -148,6 +148,10 @@ void begin_step(vivCase* c) {
     c->c0 = 1.0 / dt;
     launch_bdf_history(m, s, -1.0 / dt, 0.0, false, c->stream);
   }
+  launch_step_time(s, c->t + dt, c->stream);
+  // time-dependent manufactured solution: the Dirichlet data of the new time
+  // level (the history keeps the previous level's)
+  if (c->prm.source == 2) launch_mms_dirichlet(m, s, c->prm, c->stream);
   c->step_open = true;
   c->factored = false;
   c->have_dU = false;
@@ -434,6 +438,7 @@ static vivStatus case_create_impl(vivMesh* mesh, const vivParams* prm_in, const 
             "unknown pivoting");
   VIV_CHECK(prm->jacobian_fp32 == 0 || prm->jacobian_fp32 == 1, VIV_ERR_ARG, "jacobian_fp32 must be 0 or 1");
   VIV_CHECK(prm->predictor == 0 || prm->predictor == 1, VIV_ERR_ARG, "predictor must be 0 or 1");
+  VIV_CHECK(prm->source >= 0 && prm->source <= 2, VIV_ERR_ARG, "source must be 0, 1 or 2");
   VIV_CHECK(mesh->m.on_device, VIV_ERR_STATE, "mesh was analysed on the host only");
   *out = nullptr;
   vivCase* c = new vivCase();
@@ -491,6 +496,7 @@ static vivStatus case_create_impl(vivMesh* mesh, const vivParams* prm_in, const 
                    : nullptr;
     s.partial = A.make<double>(296);
     s.scal = A.make<double>(8);
+    s.t_src = A.make<double>(1);
     VIV_CUDA(cudaMallocHost(&c->h_pinned, 8 * sizeof(double)));
     cudaStream_t st = c->stream;
     VIV_CUDA(cudaMemcpyAsync(s.u, u0, 2 * n * sizeof(double), cudaMemcpyDefault, st));
@@ -803,8 +809,10 @@ static void step_impl(vivCase* c, vivStepInfo* info) {
     if (it == 0) n0 = nr;
     VIV_CHECK(std::isfinite(nr), VIV_ERR_NONFINITE, "residual norm is not finite");
     if (nr <= tol) {
-      // Closing correction of the mixed path, with the factors at hand (no new
-      // Jacobian).  With FP32 volume Jacobians Newton converges linearly
+      // Closing correction, with the factors at hand (no new Jacobian), on
+      // both paths: a state that only just passed the test can be ~1e-8 off
+      // the discrete solution in the pressure (all-Dirichlet problems), and the
+      // correction takes it to round-off.  With FP32 volume Jacobians Newton converges linearly
       // (contraction ~1e-4 here) and stops just under the tolerance; and on
       // every mixed path the FP32 factors leave errors in directions the
       // residual barely sees - at 38,800 quads a near-constant pressure offset
@@ -814,7 +822,7 @@ static void step_impl(vivCase* c, vivStepInfo* info) {
       // leaves the 1.8e-9, two bring the pressure to 3e-11..9e-11 of the FP64
       // path's, and more sweeps change nothing beyond that noise.  Hence at
       // least two sweeps, then to 1e-6 of the right-hand side.
-      if (mixed(c) && it > 0 && !polished) {
+      if (it > 0 && !polished) {
         polished = true;
         sweeps += refined_solve_graphs(c, true);
         continue;   // the next pass applies the correction and re-evaluates ||NL||

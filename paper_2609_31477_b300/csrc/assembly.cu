@@ -112,9 +112,37 @@ __device__ __noinline__ void mms_source(double X, double Y, double amp, double r
   fx[1] = f;
 }
 
+// Manufactured source of the time-dependent 2-D test (Section 5.1's fields
+// with their time factors, u = t^3 U, p = t^2 P with U, P the steady fields
+// above, on a mesh moved by chi(X, t) = X + amp sin(pi t) sin(pi X) sin(pi Y) (1, 1),
+// lambda_s = mu_s = 1):
+//   f_u = rho (d_t u + (u.grad) u) + grad p - mu (lap u + grad div u)
+//       = rho (3 t^2 U + t^6 (U.grad) U) + t^2 grad P - mu t^3 (lap U + grad div U)
+//   g_p = t^3 div U,  f_x = sin(pi t) times the steady f_x   (at x = chi(X_q, t))
+__device__ __noinline__ void mms_source_unsteady(double X, double Y, double t, double amp, double rho, double mu,
+                                                 double* fu, double* gp, double* fx) {
+  const double pi = 3.14159265358979323846;
+  const double st = sin(pi * t);
+  const double s = sin(pi * X) * sin(pi * Y);
+  const double x = X + amp * st * s, y = Y + amp * st * s;
+  const double sx = sin(pi * x), cx = cos(pi * x), sy = sin(pi * y), cy = cos(pi * y);
+  const double U1 = sx * cy, U2 = sx * sy;
+  const double U1x = pi * cx * cy, U1y = -pi * sx * sy, U2x = pi * cx * sy, U2y = pi * sx * cy;
+  const double lap1 = -2 * pi * pi * sx * cy, lap2 = -2 * pi * pi * sx * sy;
+  const double gd1 = -pi * pi * sx * cy + pi * pi * cx * cy, gd2 = -pi * pi * cx * sy - pi * pi * sx * sy;
+  const double Px = -pi * sx * cy, Py = -pi * cx * sy;
+  const double t2 = t * t, t3 = t2 * t, t6 = t3 * t3;
+  fu[0] = rho * (3 * t2 * U1 + t6 * (U1 * U1x + U2 * U1y)) + t2 * Px - mu * t3 * (lap1 + gd1);
+  fu[1] = rho * (3 * t2 * U2 + t6 * (U1 * U2x + U2 * U2y)) + t2 * Py - mu * t3 * (lap2 + gd2);
+  *gp = t3 * (U1x + U2y);
+  const double f = amp * st * (4 * pi * pi * s - 2 * pi * pi * cos(pi * X) * cos(pi * Y));
+  fx[0] = f;
+  fx[1] = f;
+}
+
 template <class T>
 __device__ void qp_compute(const Tables<T>& tb, const ElemNodes<T>& en, int q, T rho, T mu, int source,
-                           double amp, T* out) {
+                           double amp, double t_src, T* out) {
   // current configuration
   T J00 = 0, J01 = 0, J10 = 0, J11 = 0;
   T K00 = 0, K01 = 0, K10 = 0, K11 = 0;   // reference
@@ -171,14 +199,17 @@ __device__ void qp_compute(const Tables<T>& tb, const ElemNodes<T>& en, int q, T
   out[Q_EPS] = e00; out[Q_EPS + 1] = e01; out[Q_EPS + 2] = e11;
   out[Q_TR] = e00 + e11;
   out[Q_FU] = out[Q_FU + 1] = out[Q_GP] = out[Q_FX] = out[Q_FX + 1] = T(0);
-  if (source == 1) {
+  if (source == 1 || source == 2) {
     double Xq = 0, Yq = 0;
     for (int a = 0; a < 9; ++a) {
       Xq += (double)tb.N[q][a] * (double)en.X[a][0];
       Yq += (double)tb.N[q][a] * (double)en.X[a][1];
     }
     double fu[2], gp, fx[2];
-    mms_source(Xq, Yq, amp, (double)rho, (double)mu, fu, &gp, fx);
+    if (source == 1)
+      mms_source(Xq, Yq, amp, (double)rho, (double)mu, fu, &gp, fx);
+    else
+      mms_source_unsteady(Xq, Yq, t_src, amp, (double)rho, (double)mu, fu, &gp, fx);
     out[Q_FU] = (T)fu[0];
     out[Q_FU + 1] = (T)fu[1];
     out[Q_GP] = (T)gp;
@@ -218,8 +249,9 @@ struct AsmArgs {
   const int32_t* node_dof;
   const int32_t* e2nz;
   double c0, rho, mu;
-  int source;        // 0 none, 1 the steady manufactured solution
+  int source;        // 0 none, 1 the steady, 2 the time-dependent manufactured solution
   double source_amp;
+  const double* t_src;   // device: time of the step being solved (source 2)
 };
 
 // Threads are laid out by row kind so that a warp runs one kind of row:
@@ -241,7 +273,9 @@ __global__ void __launch_bounds__(ASM_THREADS, 2) element_kernel(AsmArgs A, doub
   __syncthreads();
   if (tid < 9 * EPB) {
     const int le = tid / 9, q = tid % 9;
-    if (blockIdx.x * EPB + le < A.n) qp_compute<T>(tb, en[le], q, (T)A.rho, (T)A.mu, A.source, A.source_amp, qd[le][q]);
+    if (blockIdx.x * EPB + le < A.n)
+      qp_compute<T>(tb, en[le], q, (T)A.rho, (T)A.mu, A.source, A.source_amp, A.source == 2 ? *A.t_src : 0.0,
+                    qd[le][q]);
   }
   __syncthreads();
   int le, t;
@@ -605,6 +639,7 @@ static void run_assembly(const Mesh& m, const CaseState& st, const vivParams& pr
   A.mu = prm.mu;
   A.source = prm.source;
   A.source_amp = prm.source_amp;
+  A.t_src = st.t_src;
   int ncol = (parts & 1) ? (int)m.color_off.size() - 1 : 0;
   for (int c = 0; c < ncol; ++c) {
     A.elems = m.d_color_elems + m.color_off[c];
@@ -668,5 +703,39 @@ void launch_jacobian_split(const Mesh& m, const CaseState& st, const vivParams& 
   launch_f64_to_f32(J32, J64, nnz, s);
 }
 template void launch_jacobian<float>(const Mesh&, const CaseState&, const vivParams&, double, float*, cudaStream_t);
+
+// Exact Dirichlet data of the time-dependent manufactured solution at the
+// step's time: prescribed velocity, position and pressure components
+__global__ void mms_dirichlet_kernel(int64_t n, const int32_t* tags, const double* X, const double* t_src, double amp,
+                                     double* u, double* x, double* p) {
+  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (a >= n) return;
+  const double pi = 3.14159265358979323846, t = *t_src;
+  const double Xa = X[2 * a], Ya = X[2 * a + 1];
+  const double b = amp * sin(pi * t) * sin(pi * Xa) * sin(pi * Ya);
+  const double xa = Xa + b, ya = Ya + b;
+  const int32_t tg = tags[a];
+  const double t3 = t * t * t;
+  if (tg & VIV_TAG_U_FIX_X) u[2 * a] = t3 * sin(pi * xa) * cos(pi * ya);
+  if (tg & VIV_TAG_U_FIX_Y) u[2 * a + 1] = t3 * sin(pi * xa) * sin(pi * ya);
+  if (tg & VIV_TAG_X_FIX_X) x[2 * a] = xa;
+  if (tg & VIV_TAG_X_FIX_Y) x[2 * a + 1] = ya;
+  if (tg & VIV_TAG_P_FIX) p[a] = t * t * cos(pi * xa) * cos(pi * ya);
+}
+
+__global__ void set_scalar_kernel(double* dst, double v) { *dst = v; }
+
+void launch_step_time(const CaseState& st, double t_new, cudaStream_t s) {
+  Launched L(K_VEC, s);
+  set_scalar_kernel<<<1, 1, 0, s>>>(st.t_src, t_new);
+  VIV_CUDA(cudaGetLastError());
+}
+
+void launch_mms_dirichlet(const Mesh& m, const CaseState& st, const vivParams& prm, cudaStream_t s) {
+  Launched L(K_VEC, s);
+  mms_dirichlet_kernel<<<(unsigned)((m.n_nodes + 255) / 256), 256, 0, s>>>(m.n_nodes, m.d_tags, m.d_X, st.t_src,
+                                                                           prm.source_amp, st.u, st.x, st.p);
+  VIV_CUDA(cudaGetLastError());
+}
 
 }  // namespace viv

@@ -229,6 +229,7 @@ struct CaseState {
   void* yv2;                            // border: forward-solve vectors of the two columns (2 x n_dofs, T)
   double* partial;                      // norm partial sums
   double* scal;                         // host-visible scalars (device side)
+  double* t_src;                        // time of the step being solved (manufactured sources)
 };
 
 }  // namespace viv
@@ -309,6 +310,8 @@ template <class T>
 void launch_jacobian(const Mesh& m, const CaseState& st, const vivParams& prm, double c0, T* vals,
                      cudaStream_t s);
 void launch_norm2(const double* v, int64_t n, double* partial, double* out, cudaStream_t s);
+void launch_step_time(const CaseState& st, double t_new, cudaStream_t s);
+void launch_mms_dirichlet(const Mesh& m, const CaseState& st, const vivParams& prm, cudaStream_t s);
 void launch_bdf_history(const Mesh& m, CaseState& st, double a_n, double a_nm1, bool shift, cudaStream_t s);
 void launch_extrapolate(const Mesh& m, CaseState& st, cudaStream_t s);
 void launch_update(const Mesh& m, CaseState& st, const double* dU, cudaStream_t s);

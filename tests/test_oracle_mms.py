@@ -67,3 +67,25 @@ def test_steady_mms_optimal_rates():
     assert abs(r["u_l2"] - 3) < 0.15 and abs(r["u_h1"] - 2) < 0.1
     assert abs(r["x_l2"] - 3) < 0.15 and abs(r["x_h1"] - 2) < 0.1
     assert r["p_l2"] > 1.8
+
+
+def test_unsteady_mms_bdf2_order_in_time():
+    """Section 5.1's time-dependent manufactured solution (u ~ t^3, p ~ t^2, mesh
+    moved by sin(pi t)): on a fixed 8 x 8 mesh the velocity error falls by 4
+    per halving of dt (BDF2), while the position - a quasi-static pseudo-solid
+    driven by exact boundary data - does not depend on dt at all."""
+    sol = mms.unsteady_mms()
+    errs, xs = [], []
+    for dt in (0.04, 0.02):
+        m = I.square_mesh(8)
+        m["tags"][0] |= I.P_FIX
+        c = OracleCase(m, rho=sol.rho, mu=sol.mu, k=0.0, dt=dt, u0=np.zeros((len(m["X"]), 2)), lame=1.0, src=sol)
+        sol.set_exact_state(c, 0.0)
+        for _ in range(int(round(0.2 / dt))):
+            c.step(dirichlet=sol.set_dirichlet)
+        assert abs(c.t - 0.2) < 1e-12
+        errs.append(mms.error_norms(c, sol, c.t))
+        xs.append(c.x.copy())
+    ratio = errs[0]["u_l2"] / errs[1]["u_l2"]
+    assert 3.6 < ratio < 4.4, ratio
+    assert np.abs(xs[0] - xs[1]).max() < 1e-12
