@@ -160,6 +160,16 @@ typedef struct {
    * U_inf, D and span_L default to 1 when 0.  k = 0 with Ustar = 0 is a problem
    * without a cylinder (no border unknowns). */
   double Re, Ustar, U_inf, D, span_L;
+  /* Adaptive time stepping (Section 6: a target Courant number as a simple
+   * convection error estimator).  cfl_target > 0: after every step the library
+   * computes CFL = dt max_e (max_a |u_a| / h_e) (largest nodal velocity of an
+   * element over its shortest corner-to-corner edge, current configuration)
+   * and sets the next step to dt cfl_target / CFL, kept within [dt / 2, 1.2 dt]
+   * (a step ratio below 1 + sqrt 2 keeps variable-step BDF2 zero-stable) and
+   * at most dt_max (when > 0).  BDF2 then uses the step ratio w = dt / dt_prev:
+   * rates [(1 + 2w)/(1 + w) v^{n+1} - (1 + w) v^n + w^2/(1 + w) v^{n-1}] / dt.
+   * cfl_target = 0 (default): constant dt. */
+  double cfl_target, dt_max;
 } vivParams;
 enum { VIV_PIVOT_THRESHOLD = 0, VIV_PIVOT_WINDOW = 1 };
 
@@ -172,6 +182,8 @@ typedef struct {
   double t;                /* time reached */
   double delta[2];         /* cylinder displacement x_c - X_c */
   double force[2];         /* F_fluid = -int_Gamma lambda */
+  double dt;               /* size of this step */
+  double cfl;              /* Courant number of the new state (0 unless cfl_target > 0) */
 } vivStepInfo;
 
 /* ---- mesh: numbering, sparsity, nested dissection, symbolic factorisation
@@ -214,8 +226,10 @@ vivStatus viv_case_params(const vivCase* c, vivParams* out);
  * next viv_step then computes exactly what the saved case would have
  * computed (same kernels, same inputs, deterministic reductions).  Saving
  * inside an open step (after viv_begin_step) returns VIV_ERR_STATE.  Factors
- * are not saved: the next step assembles and factors anew.  The format is
- * native-endian and tied to the mesh's node count. */
+ * are not saved: the next step assembles and factors anew.  A constant-step
+ * case (cfl_target = 0) must have the checkpoint's dt; an adaptive case
+ * resumes with the saved step sizes.  The format is native-endian and tied to
+ * the mesh's node count. */
 vivStatus viv_case_save(const vivCase* c, void* buf, size_t* bytes);
 vivStatus viv_case_load(vivCase* c, const void* buf, size_t bytes);
 

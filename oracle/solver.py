@@ -65,6 +65,7 @@ class OracleCase:
         self.faces = np.array([[self.conn[e, a] for a in EDGE_NODES[ed]] for e, ed in gf],
                               dtype=np.int64).reshape(-1, 3)
         self.rho, self.mu, self.k, self.dt = rho, mu, k, dt
+        self.dt_prev = dt     # size of the previous step (variable-step BDF2)
         self.src = src
         n = len(self.X)
         self.n = n
@@ -165,12 +166,39 @@ class OracleCase:
 
     # ---- time discretisation ------------------------------------------------
     def bdf_coefficients(self):
-        """(c0, hu, hx): nodal rates are c0*v + h (BDF1 first step, then BDF2)."""
+        """(c0, hu, hx): nodal rates are c0*v + h (BDF1 first step, then BDF2).
+
+        BDF2 with a step ratio w = dt / dt_prev is the derivative at t^{n+1} of the
+        quadratic through (t^{n-1}, v^{n-1}), (t^n, v^n), (t^{n+1}, v^{n+1}):
+        v' = [(1 + 2w)/(1 + w) v^{n+1} - (1 + w) v^n + w^2/(1 + w) v^{n-1}] / dt,
+        which is (3 v^{n+1} - 4 v^n + v^{n-1}) / (2 dt) for equal steps."""
         dt = self.dt
         if self.hist is None:
             return 1.0 / dt, -self.u_n / dt, -self.x_n / dt
         u_nm1, x_nm1 = self.hist
-        return 1.5 / dt, (-4.0 * self.u_n + u_nm1) / (2 * dt), (-4.0 * self.x_n + x_nm1) / (2 * dt)
+        w = dt / self.dt_prev
+        c0 = (1 + 2 * w) / ((1 + w) * dt)
+        a_n, a_nm1 = -(1 + w) / dt, w * w / ((1 + w) * dt)
+        return c0, a_n * self.u_n + a_nm1 * u_nm1, a_n * self.x_n + a_nm1 * x_nm1
+
+    def cfl(self):
+        """dt max_e (max_a |u_a| / h_e): velocity magnitude over the element's
+        nodes, h_e its shortest edge between corner nodes in the current
+        configuration (the convective Courant number of Section 6's adaptive
+        time stepping)."""
+        c = self.conn
+        corners = self.x[c[:, [0, 2, 8, 6]]]
+        h = np.min(np.linalg.norm(corners - np.roll(corners, -1, axis=1), axis=2), axis=1)
+        umax = np.max(np.linalg.norm(self.u[c], axis=2), axis=1)
+        return float(self.dt * np.max(umax / h))
+
+    def next_dt(self, cfl, cfl_target, dt_max=0.0):
+        """Step size after a step of size dt that ended at Courant number cfl:
+        dt (cfl_target / cfl), kept within [dt / 2, 1.2 dt] (a step ratio below
+        1 + sqrt 2 keeps variable-step BDF2 zero-stable) and below dt_max."""
+        r = cfl_target / cfl if cfl > 0 else 1.2
+        dt = self.dt * min(1.2, max(0.5, r))
+        return min(dt, dt_max) if dt_max > 0 else dt
 
     # ---- residual ----------------------------------------------------------
     def _element_inputs(self, u, p, x, hu, hx):
@@ -333,7 +361,18 @@ class OracleCase:
         self.hist = (self.u_n, self.x_n)
         self.t = t_new
         self.nstep += 1
+        self.dt_prev = self.dt
         return norms
+
+    def step_adaptive(self, cfl_target, dt_max=0.0, **kw):
+        """One step with the current dt, then the next dt from the Courant number
+        of the new state (Section 6: a target CFL of 1 as a simple convection
+        error estimator).  Returns (norms, dt used, cfl reached)."""
+        dt = self.dt
+        norms = self.step(**kw)
+        cfl = self.cfl()
+        self.dt = self.next_dt(cfl, cfl_target, dt_max)
+        return norms, dt, cfl
 
     def force(self):
         """F_fluid = -int_Gamma lambda on the current boundary."""

@@ -92,12 +92,12 @@ void run_graph(vivCase* c, vivCase::Graph& g, F&& body) {
     body();
     return;
   }
-  // kernel arguments are captured by value: the schedule version and the BDF
-  // coefficient (BDF1 on the first step, BDF2 after) key the graphs
-  if (c->graph_version != c->mesh->m.sched_version || c->graph_c0 != c->c0) {
+  // kernel arguments are captured by value: the schedule version keys the
+  // graphs (the step's time and BDF coefficient reach the kernels through
+  // device memory, so the same graphs serve every step size)
+  if (c->graph_version != c->mesh->m.sched_version) {
     drop_graphs(c);
     c->graph_version = c->mesh->m.sched_version;
-    c->graph_c0 = c->c0;
   }
   if (!g.exec) {
     cudaGraph_t graph = nullptr;
@@ -141,14 +141,17 @@ void begin_step(vivCase* c) {
   VIV_CUDA(cudaMemcpyAsync(s.x_n, s.x, n2, cudaMemcpyDeviceToDevice, c->stream));
   const double dt = c->prm.dt;
   if (bdf2) {
-    c->c0 = 1.5 / dt;
-    launch_bdf_history(m, s, -2.0 / dt, 0.5 / dt, false, c->stream);
-    if (c->prm.predictor == 1) launch_extrapolate(m, s, c->stream);
+    // BDF2 with step ratio w = dt / dt_prev: the derivative at t^{n+1} of the
+    // quadratic through the last three levels
+    const double w = dt / c->dt_prev;
+    c->c0 = (1 + 2 * w) / ((1 + w) * dt);
+    launch_bdf_history(m, s, -(1 + w) / dt, w * w / ((1 + w) * dt), false, c->stream);
+    if (c->prm.predictor == 1) launch_extrapolate(m, s, w, c->stream);
   } else {
     c->c0 = 1.0 / dt;
     launch_bdf_history(m, s, -1.0 / dt, 0.0, false, c->stream);
   }
-  launch_step_time(s, c->t + dt, c->stream);
+  launch_step_constants(s, c->t + dt, c->c0, c->stream);
   // time-dependent manufactured solution: the Dirichlet data of the new time
   // level (the history keeps the previous level's)
   if (c->prm.source == 2) launch_mms_dirichlet(m, s, c->prm, c->stream);
@@ -165,9 +168,9 @@ void jacobian(vivCase* c) {
   const Mesh& m = c->mesh->m;
   const int64_t nnz = m.row_ptr[m.n_dofs];
   if (mixed(c) && c->prm.jacobian_fp32) {
-    launch_jacobian_split(m, c->s, c->prm, c->c0, c->s.J32, c->s.J64, c->stream);
+    launch_jacobian_split(m, c->s, c->prm, c->s.J32, c->s.J64, c->stream);
   } else {
-    launch_jacobian<double>(m, c->s, c->prm, c->c0, c->s.J64, c->stream);
+    launch_jacobian<double>(m, c->s, c->prm, c->s.J64, c->stream);
     if (mixed(c)) launch_f64_to_f32(c->s.J32, c->s.J64, nnz, c->stream);
   }
 }
@@ -177,7 +180,7 @@ double assemble(vivCase* c, int what, bool want_norm) {
   VIV_CHECK(c->step_open, VIV_ERR_STATE, "viv_assemble before viv_begin_step");
   double nr = 0;
   if (what & VIV_RES) {
-    launch_residual(m, c->s, c->prm, c->c0, c->stream);
+    launch_residual(m, c->s, c->prm, c->stream);
     if (want_norm) nr = norm2(c, c->s.R, m.n_dofs);
   }
   if (what & VIV_JAC) {
@@ -439,6 +442,7 @@ static vivStatus case_create_impl(vivMesh* mesh, const vivParams* prm_in, const 
   VIV_CHECK(prm->jacobian_fp32 == 0 || prm->jacobian_fp32 == 1, VIV_ERR_ARG, "jacobian_fp32 must be 0 or 1");
   VIV_CHECK(prm->predictor == 0 || prm->predictor == 1, VIV_ERR_ARG, "predictor must be 0 or 1");
   VIV_CHECK(prm->source >= 0 && prm->source <= 2, VIV_ERR_ARG, "source must be 0, 1 or 2");
+  VIV_CHECK(prm->cfl_target >= 0 && prm->dt_max >= 0, VIV_ERR_ARG, "cfl_target and dt_max must not be negative");
   VIV_CHECK(mesh->m.on_device, VIV_ERR_STATE, "mesh was analysed on the host only");
   *out = nullptr;
   vivCase* c = new vivCase();
@@ -449,6 +453,7 @@ static vivStatus case_create_impl(vivMesh* mesh, const vivParams* prm_in, const 
     if (c->prm.newton_tol <= 0) c->prm.newton_tol = 1e-10;
     if (c->prm.max_newton <= 0) c->prm.max_newton = 25;
     c->stream = (cudaStream_t)stream;
+    c->dt_prev = c->prm.dt;
     c->arena.alloc = mesh->m.arena.alloc;
     c->arena.custom = mesh->m.arena.custom && !default_alloc;
     const Mesh& m = mesh->m;
@@ -496,7 +501,7 @@ static vivStatus case_create_impl(vivMesh* mesh, const vivParams* prm_in, const 
                    : nullptr;
     s.partial = A.make<double>(296);
     s.scal = A.make<double>(8);
-    s.t_src = A.make<double>(1);
+    s.step = A.make<double>(2);
     VIV_CUDA(cudaMallocHost(&c->h_pinned, 8 * sizeof(double)));
     cudaStream_t st = c->stream;
     VIV_CUDA(cudaMemcpyAsync(s.u, u0, 2 * n * sizeof(double), cudaMemcpyDefault, st));
@@ -794,7 +799,7 @@ static void step_impl(vivCase* c, vivStepInfo* info) {
   for (int it = 0;; ++it) {
     {
       auto res = [&] {
-        launch_residual(m, c->s, c->prm, c->c0, c->stream);
+        launch_residual(m, c->s, c->prm, c->stream);
         launch_norm2(c->s.R, m.n_dofs, c->s.partial, c->s.scal, c->stream);
       };
       if (it == 0)
@@ -846,10 +851,25 @@ static void step_impl(vivCase* c, vivStepInfo* info) {
     ++iters;
   }
   // the loop ends on a converged residual of the updated state
-  c->t += c->prm.dt;
+  const double dt_used = c->prm.dt;
+  c->t += dt_used;
   c->nstep += 1;
   c->step_open = false;
+  c->dt_prev = dt_used;
+  double cfl = 0;
+  if (c->prm.cfl_target > 0) {
+    // Section 6: the next step size from the Courant number of the new state
+    // (target CFL as a convection error estimator), within a factor 1/2 .. 1.2
+    // of the last (step ratio below 1 + sqrt 2: zero-stable BDF2) and dt_max
+    cfl = launch_cfl(m, c->s, dt_used, c->s.partial, c->s.scal + 5, c->h_pinned + 5, c->stream);
+    const double r = cfl > 0 ? c->prm.cfl_target / cfl : 1.2;
+    double next = dt_used * std::min(1.2, std::max(0.5, r));
+    if (c->prm.dt_max > 0) next = std::min(next, c->prm.dt_max);
+    c->prm.dt = next;
+  }
   if (info) {
+    info->dt = dt_used;
+    info->cfl = cfl;
     info->newton_iters = iters;
     info->refine_sweeps = sweeps;
     info->perturbed_pivots = st_acc[0];
@@ -886,14 +906,14 @@ vivStatus viv_case_params(const vivCase* c, vivParams* out) {
 }
 
 // Checkpoint layout (host bytes, native endianness):
-//   char magic[8] = "VIVCKPT1"; int64 n_nodes, n_dofs; int32 precision, bdf2_ready;
-//   double t, dt; int64 nstep;
+//   char magic[8] = "VIVCKPT2"; int64 n_nodes, n_dofs; int32 precision, bdf2_ready;
+//   double t, dt, dt_prev; int64 nstep;
 //   double u[2n], p[n], x[2n], lam[2n], delta[2], u_n[2n], x_n[2n]
 // u..delta is the current state (the last converged step), u_n and x_n the
 // previous time level, which the next BDF2 step needs.
 namespace {
-constexpr char CKPT_MAGIC[8] = {'V', 'I', 'V', 'C', 'K', 'P', 'T', '1'};
-constexpr size_t CKPT_HEADER = 8 + 2 * 8 + 2 * 4 + 2 * 8 + 8;
+constexpr char CKPT_MAGIC[8] = {'V', 'I', 'V', 'C', 'K', 'P', 'T', '2'};
+constexpr size_t CKPT_HEADER = 8 + 2 * 8 + 2 * 4 + 3 * 8 + 8;
 size_t ckpt_bytes(int64_t n) { return CKPT_HEADER + sizeof(double) * (size_t)(11 * n + 2); }
 }  // namespace
 
@@ -923,6 +943,7 @@ vivStatus viv_case_save(const vivCase* cc, void* buf, size_t* bytes) {
   put(&ready, 4);
   put(&c->t, 8);
   put(&c->prm.dt, 8);
+  put(&c->dt_prev, 8);
   put(&ns, 8);
   double* d = reinterpret_cast<double*>(b);   // copies go through unified addressing (any alignment)
   const CaseState& s = c->s;
@@ -950,17 +971,20 @@ vivStatus viv_case_load(vivCase* c, const void* buf, size_t bytes) {
   };
   int64_t n_s = 0, nd_s = 0, ns = 0;
   int32_t prec = 0, ready = 0;
-  double t = 0, dt = 0;
+  double t = 0, dt = 0, dt_prev = 0;
   get(&n_s, 8);
   get(&nd_s, 8);
   get(&prec, 4);
   get(&ready, 4);
   get(&t, 8);
   get(&dt, 8);
+  get(&dt_prev, 8);
   get(&ns, 8);
   VIV_CHECK(n_s == n && nd_s == c->mesh->m.n_dofs && bytes >= ckpt_bytes(n), VIV_ERR_ARG,
             "checkpoint was written for another mesh");
-  VIV_CHECK(dt == c->prm.dt, VIV_ERR_ARG, "checkpoint time step differs from the case's dt");
+  // a constant-step case must resume with its own dt; an adaptive one resumes
+  // with the saved step sizes
+  VIV_CHECK(c->prm.cfl_target > 0 || dt == c->prm.dt, VIV_ERR_ARG, "checkpoint time step differs from the case's dt");
   const double* d = reinterpret_cast<const double*>(b);
   CaseState& s = c->s;
   copy_in(c, s.u, d, 2 * n);
@@ -972,6 +996,8 @@ vivStatus viv_case_load(vivCase* c, const void* buf, size_t bytes) {
   copy_in(c, s.x_n, d + 9 * n + 2, 2 * n);
   VIV_CUDA(cudaStreamSynchronize(c->stream));
   c->t = t;
+  c->prm.dt = dt;
+  c->dt_prev = dt_prev;
   c->nstep = (int)ns;
   c->have_prev2 = ready != 0;
   c->step_open = false;

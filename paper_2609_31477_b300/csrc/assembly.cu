@@ -248,10 +248,12 @@ struct AsmArgs {
   const double *X, *x, *u, *p, *hu, *hx, *lame;
   const int32_t* node_dof;
   const int32_t* e2nz;
-  double c0, rho, mu;
+  double rho, mu;
   int source;        // 0 none, 1 the steady, 2 the time-dependent manufactured solution
   double source_amp;
-  const double* t_src;   // device: time of the step being solved (source 2)
+  // device: {time of the step being solved, BDF rate coefficient c0} - read by
+  // the kernels, so that captured CUDA graphs stay valid when either changes
+  const double* step;
 };
 
 // Threads are laid out by row kind so that a warp runs one kind of row:
@@ -268,13 +270,13 @@ __global__ void __launch_bounds__(ASM_THREADS, 2) element_kernel(AsmArgs A, doub
   if (tid < 14 * EPB) {
     const int le = tid / 14, gi = blockIdx.x * EPB + le;
     if (gi < A.n)
-      load_element<T>(A.conn, A.X, A.x, A.u, A.p, A.hu, A.hx, A.lame, A.c0, A.elems[gi], tid % 14, en[le]);
+      load_element<T>(A.conn, A.X, A.x, A.u, A.p, A.hu, A.hx, A.lame, A.step[1], A.elems[gi], tid % 14, en[le]);
   }
   __syncthreads();
   if (tid < 9 * EPB) {
     const int le = tid / 9, q = tid % 9;
     if (blockIdx.x * EPB + le < A.n)
-      qp_compute<T>(tb, en[le], q, (T)A.rho, (T)A.mu, A.source, A.source_amp, A.source == 2 ? *A.t_src : 0.0,
+      qp_compute<T>(tb, en[le], q, (T)A.rho, (T)A.mu, A.source, A.source_amp, A.source == 2 ? A.step[0] : 0.0,
                     qd[le][q]);
   }
   __syncthreads();
@@ -293,7 +295,7 @@ __global__ void __launch_bounds__(ASM_THREADS, 2) element_kernel(AsmArgs A, doub
   if (gi >= A.n) return;
   const int e = A.elems[gi];
   const int* cn = A.conn + e * 9;
-  const T c0 = (T)A.c0, rho = (T)A.rho, mu = (T)A.mu;
+  const T c0 = (T)A.step[1], rho = (T)A.rho, mu = (T)A.mu;
   if (t < 18) {  // momentum row (a, i)
     const int a = t >> 1, i = t & 1;
     const int row = A.node_dof[cn[a] * NSLOT + i];
@@ -439,13 +441,14 @@ struct FaceArgs {
   const double *x, *u, *lam, *hx;
   const int32_t* node_dof;
   const int32_t* f2nz;
-  double c0;
+  const double* step;   // device {time, c0} (see AsmArgs)
 };
 
 template <class T, bool JAC>
 __global__ void face_kernel(FaceArgs A, double* R, T* vals) {
   int gi = blockIdx.x * blockDim.x + threadIdx.x;
   if (gi >= A.n) return;
+  const double c0 = A.step[1];
   int f = A.list[gi];
   const int* fn = A.faces + 3 * f;
   double ds[3], N[3][3];
@@ -455,7 +458,7 @@ __global__ void face_kernel(FaceArgs A, double* R, T* vals) {
       xb[b][i] = A.x[2 * fn[b] + i];
       ub[b][i] = A.u[2 * fn[b] + i];
       lb[b][i] = A.lam[2 * fn[b] + i];
-      wb[b][i] = A.c0 * xb[b][i] + A.hx[2 * fn[b] + i];
+      wb[b][i] = c0 * xb[b][i] + A.hx[2 * fn[b] + i];
     }
   for (int q = 0; q < 3; ++q) {
     double L[3], dL[3];
@@ -502,7 +505,7 @@ __global__ void face_kernel(FaceArgs A, double* R, T* vals) {
         s = nz[fpairE(b, i, 2 * bp + i)];              // d R[lambda_b,i] / d u_bp,i
         if (s >= 0) vals[s] += (T)(-mass);
         s = nz[fpairE(b, i, 6 + 2 * bp + i)];          // d R[lambda_b,i] / d delta_i (w part)
-        if (s >= 0) vals[s] += (T)(A.c0 * mass);
+        if (s >= 0) vals[s] += (T)(c0 * mass);
       }
       if (b == 0)
         for (int i = 0; i < 2; ++i) {
@@ -621,7 +624,7 @@ void launch_element_areas(const Mesh& m, double* lame, double scale, double* scr
 
 // parts: 1 volume elements, 2 Gamma faces and border rows, 3 both
 template <class T, bool JAC>
-static void run_assembly(const Mesh& m, const CaseState& st, const vivParams& prm, double c0, double* R,
+static void run_assembly(const Mesh& m, const CaseState& st, const vivParams& prm, double* R,
                          T* vals, cudaStream_t s, int parts = 3) {
   AsmArgs A;
   A.conn = m.d_conn;
@@ -634,12 +637,11 @@ static void run_assembly(const Mesh& m, const CaseState& st, const vivParams& pr
   A.lame = st.lame;
   A.node_dof = m.d_node_dof;
   A.e2nz = m.d_e2nz;
-  A.c0 = c0;
   A.rho = prm.rho;
   A.mu = prm.mu;
   A.source = prm.source;
   A.source_amp = prm.source_amp;
-  A.t_src = st.t_src;
+  A.step = st.step;
   int ncol = (parts & 1) ? (int)m.color_off.size() - 1 : 0;
   for (int c = 0; c < ncol; ++c) {
     A.elems = m.d_color_elems + m.color_off[c];
@@ -656,7 +658,7 @@ static void run_assembly(const Mesh& m, const CaseState& st, const vivParams& pr
   Fa.hx = st.hx;
   Fa.node_dof = m.d_node_dof;
   Fa.f2nz = m.d_f2nz;
-  Fa.c0 = c0;
+  Fa.step = st.step;
   if (!(parts & 2)) {
     VIV_CUDA(cudaGetLastError());
     return;
@@ -677,40 +679,39 @@ static void run_assembly(const Mesh& m, const CaseState& st, const vivParams& pr
   VIV_CUDA(cudaGetLastError());
 }
 
-void launch_residual(const Mesh& m, const CaseState& st, const vivParams& prm, double c0, cudaStream_t s) {
+void launch_residual(const Mesh& m, const CaseState& st, const vivParams& prm, cudaStream_t s) {
   VIV_CUDA(cudaMemsetAsync(st.R, 0, sizeof(double) * m.n_dofs, s));
-  run_assembly<double, false>(m, st, prm, c0, st.R, (double*)nullptr, s);
+  run_assembly<double, false>(m, st, prm, st.R, (double*)nullptr, s);
 }
 
 template <class T>
-void launch_jacobian(const Mesh& m, const CaseState& st, const vivParams& prm, double c0, T* vals,
-                     cudaStream_t s) {
+void launch_jacobian(const Mesh& m, const CaseState& st, const vivParams& prm, T* vals, cudaStream_t s) {
   VIV_CUDA(cudaMemsetAsync(vals, 0, sizeof(T) * m.row_ptr[m.n_dofs], s));
-  run_assembly<T, true>(m, st, prm, c0, nullptr, vals, s);
+  run_assembly<T, true>(m, st, prm, nullptr, vals, s);
 }
-template void launch_jacobian<double>(const Mesh&, const CaseState&, const vivParams&, double, double*, cudaStream_t);
+template void launch_jacobian<double>(const Mesh&, const CaseState&, const vivParams&, double*, cudaStream_t);
 
 // Volume element Jacobians in FP32 arithmetic; the Gamma-face and border
 // (multiplier and cylinder position) entries in FP64.  Both arrays end up
 // holding the same values (J64 exact widenings of the FP32 volume entries).
-void launch_jacobian_split(const Mesh& m, const CaseState& st, const vivParams& prm, double c0, float* J32,
-                           double* J64, cudaStream_t s) {
+void launch_jacobian_split(const Mesh& m, const CaseState& st, const vivParams& prm, float* J32, double* J64,
+                           cudaStream_t s) {
   const int64_t nnz = m.row_ptr[m.n_dofs];
   VIV_CUDA(cudaMemsetAsync(J32, 0, sizeof(float) * nnz, s));
-  run_assembly<float, true>(m, st, prm, c0, nullptr, J32, s, 1);
+  run_assembly<float, true>(m, st, prm, nullptr, J32, s, 1);
   launch_f32_to_f64(J64, J32, nnz, s);
-  run_assembly<double, true>(m, st, prm, c0, nullptr, J64, s, 2);
+  run_assembly<double, true>(m, st, prm, nullptr, J64, s, 2);
   launch_f64_to_f32(J32, J64, nnz, s);
 }
-template void launch_jacobian<float>(const Mesh&, const CaseState&, const vivParams&, double, float*, cudaStream_t);
+template void launch_jacobian<float>(const Mesh&, const CaseState&, const vivParams&, float*, cudaStream_t);
 
 // Exact Dirichlet data of the time-dependent manufactured solution at the
 // step's time: prescribed velocity, position and pressure components
-__global__ void mms_dirichlet_kernel(int64_t n, const int32_t* tags, const double* X, const double* t_src, double amp,
+__global__ void mms_dirichlet_kernel(int64_t n, const int32_t* tags, const double* X, const double* step, double amp,
                                      double* u, double* x, double* p) {
   const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (a >= n) return;
-  const double pi = 3.14159265358979323846, t = *t_src;
+  const double pi = 3.14159265358979323846, t = step[0];
   const double Xa = X[2 * a], Ya = X[2 * a + 1];
   const double b = amp * sin(pi * t) * sin(pi * Xa) * sin(pi * Ya);
   const double xa = Xa + b, ya = Ya + b;
@@ -723,17 +724,21 @@ __global__ void mms_dirichlet_kernel(int64_t n, const int32_t* tags, const doubl
   if (tg & VIV_TAG_P_FIX) p[a] = t * t * cos(pi * xa) * cos(pi * ya);
 }
 
-__global__ void set_scalar_kernel(double* dst, double v) { *dst = v; }
+__global__ void set_pair_kernel(double* dst, double a, double b) {
+  dst[0] = a;
+  dst[1] = b;
+}
 
-void launch_step_time(const CaseState& st, double t_new, cudaStream_t s) {
+// the step's time and BDF rate coefficient, read by the assembly kernels
+void launch_step_constants(const CaseState& st, double t_new, double c0, cudaStream_t s) {
   Launched L(K_VEC, s);
-  set_scalar_kernel<<<1, 1, 0, s>>>(st.t_src, t_new);
+  set_pair_kernel<<<1, 1, 0, s>>>(st.step, t_new, c0);
   VIV_CUDA(cudaGetLastError());
 }
 
 void launch_mms_dirichlet(const Mesh& m, const CaseState& st, const vivParams& prm, cudaStream_t s) {
   Launched L(K_VEC, s);
-  mms_dirichlet_kernel<<<(unsigned)((m.n_nodes + 255) / 256), 256, 0, s>>>(m.n_nodes, m.d_tags, m.d_X, st.t_src,
+  mms_dirichlet_kernel<<<(unsigned)((m.n_nodes + 255) / 256), 256, 0, s>>>(m.n_nodes, m.d_tags, m.d_X, st.step,
                                                                            prm.source_amp, st.u, st.x, st.p);
   VIV_CUDA(cudaGetLastError());
 }

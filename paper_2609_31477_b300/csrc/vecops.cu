@@ -53,13 +53,57 @@ __global__ void bdf_kernel(int64_t n2, const double* u_n, const double* u_nm1, c
   hx[i] = sx;
 }
 
-// Newton starting point 2 U^n - U^{n-1} for u and x (all nodal entries)
+// Newton starting point U^n + w (U^n - U^{n-1}) for u and x (all nodal
+// entries): the linear extrapolation with step ratio w = dt / dt_prev
 __global__ void extrapolate_kernel(int64_t n2, const double* u_n, const double* u_nm1, const double* x_n,
-                                   const double* x_nm1, double* u, double* x) {
+                                   const double* x_nm1, double w, double* u, double* x) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n2) return;
-  u[i] = 2.0 * u_n[i] - u_nm1[i];
-  x[i] = 2.0 * x_n[i] - x_nm1[i];
+  u[i] = (1.0 + w) * u_n[i] - w * u_nm1[i];
+  x[i] = (1.0 + w) * x_n[i] - w * x_nm1[i];
+}
+
+// Courant number: per element the largest nodal |u| over the shortest edge
+// between corner nodes (current configuration); block maxima, then the max
+__global__ void __launch_bounds__(NORM_THREADS) cfl_partial_kernel(int64_t E, const int32_t* conn, const double* x,
+                                                                   const double* u, double* partial) {
+  __shared__ double red[NORM_THREADS];
+  double mx = 0;
+  for (int64_t e = blockIdx.x * (int64_t)NORM_THREADS + threadIdx.x; e < E; e += (int64_t)gridDim.x * NORM_THREADS) {
+    const int32_t* c = conn + 9 * e;
+    const int corner[4] = {0, 2, 8, 6};
+    double h2 = 1e300, um2 = 0;
+    for (int k = 0; k < 4; ++k) {
+      const int a = c[corner[k]], b = c[corner[(k + 1) & 3]];
+      const double dx = x[2 * a] - x[2 * b], dy = x[2 * a + 1] - x[2 * b + 1];
+      h2 = fmin(h2, dx * dx + dy * dy);
+    }
+    for (int k = 0; k < 9; ++k) {
+      const int a = c[k];
+      um2 = fmax(um2, u[2 * a] * u[2 * a] + u[2 * a + 1] * u[2 * a + 1]);
+    }
+    mx = fmax(mx, sqrt(um2) / sqrt(h2));
+  }
+  red[threadIdx.x] = mx;
+  __syncthreads();
+  for (int w = NORM_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void __launch_bounds__(NORM_THREADS) cfl_final_kernel(const double* partial, int n, double dt, double* out) {
+  __shared__ double red[NORM_THREADS];
+  double mx = 0;
+  for (int i = threadIdx.x; i < n; i += NORM_THREADS) mx = fmax(mx, partial[i]);
+  red[threadIdx.x] = mx;
+  __syncthreads();
+  for (int w = NORM_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = dt * red[0];
 }
 
 // delta read back from a Gamma node's position (x = X + delta on Gamma)
@@ -239,11 +283,11 @@ void launch_bdf_history(const Mesh& m, CaseState& st, double a_n, double a_nm1, 
   VIV_CUDA(cudaGetLastError());
 }
 
-void launch_extrapolate(const Mesh& m, CaseState& st, cudaStream_t s) {
+void launch_extrapolate(const Mesh& m, CaseState& st, double w, cudaStream_t s) {
   const int64_t n2 = 2 * m.n_nodes;
   {
     Launched L(K_VEC, s);
-    extrapolate_kernel<<<blocks_for(n2, 256), 256, 0, s>>>(n2, st.u_n, st.u_nm1, st.x_n, st.x_nm1, st.u, st.x);
+    extrapolate_kernel<<<blocks_for(n2, 256), 256, 0, s>>>(n2, st.u_n, st.u_nm1, st.x_n, st.x_nm1, w, st.u, st.x);
   }
   if (m.n_faces > 0) {
     Launched L(K_VEC, s);
@@ -330,6 +374,23 @@ void launch_border_solve(const Mesh& m, const double* J, const double* b, double
     border_back_kernel<<<blocks_for(m.n_front_dofs, 256), 256, 0, s>>>(m.n_front_dofs, Y, m.n_dofs, dtmp, x);
   }
   VIV_CUDA(cudaGetLastError());
+}
+
+// Courant number dt max_e (max_a |u_a| / h_e) of the current state, read back
+double launch_cfl(const Mesh& m, const CaseState& st, double dt, double* partial, double* out, double* host,
+                  cudaStream_t s) {
+  {
+    Launched L(K_VEC, s);
+    cfl_partial_kernel<<<NORM_BLOCKS, NORM_THREADS, 0, s>>>(m.n_elems, m.d_conn, st.x, st.u, partial);
+  }
+  {
+    Launched L(K_VEC, s);
+    cfl_final_kernel<<<1, NORM_THREADS, 0, s>>>(partial, NORM_BLOCKS, dt, out);
+  }
+  VIV_CUDA(cudaGetLastError());
+  VIV_CUDA(cudaMemcpyAsync(host, out, sizeof(double), cudaMemcpyDeviceToHost, s));
+  VIV_CUDA(cudaStreamSynchronize(s));
+  return *host;
 }
 
 }  // namespace viv

@@ -229,7 +229,7 @@ struct CaseState {
   void* yv2;                            // border: forward-solve vectors of the two columns (2 x n_dofs, T)
   double* partial;                      // norm partial sums
   double* scal;                         // host-visible scalars (device side)
-  double* t_src;                        // time of the step being solved (manufactured sources)
+  double* step;                         // {time of the step being solved, BDF rate coefficient c0}
 };
 
 }  // namespace viv
@@ -286,6 +286,7 @@ struct vivCase {
   bool have_prev2 = false;     // BDF2 available for the next step
   bool step_open = false;      // begin_step called
   double c0 = 0.0;             // rate coefficient of the current step
+  double dt_prev = 0.0;        // size of the previous step (variable-step BDF2)
   bool factored = false;
   bool have_dU = false;
   double* h_pinned = nullptr;  // pinned scalars
@@ -298,22 +299,22 @@ struct vivCase {
   };
   bool graphs = true;
   int graph_version = -1;
-  double graph_c0 = 0.0;   // BDF rate coefficient baked into the captured kernel arguments
   Graph g_res, g_upd_res, g_jac, g_fac, g_sinit, g_sweep;
 };
 
 // kernels (defined in .cu files), all launched on the case stream
 namespace viv {
 void launch_element_areas(const Mesh& m, double* lame, double scale, double* scratch, cudaStream_t s);
-void launch_residual(const Mesh& m, const CaseState& st, const vivParams& prm, double c0, cudaStream_t s);
+void launch_residual(const Mesh& m, const CaseState& st, const vivParams& prm, cudaStream_t s);
 template <class T>
-void launch_jacobian(const Mesh& m, const CaseState& st, const vivParams& prm, double c0, T* vals,
-                     cudaStream_t s);
+void launch_jacobian(const Mesh& m, const CaseState& st, const vivParams& prm, T* vals, cudaStream_t s);
 void launch_norm2(const double* v, int64_t n, double* partial, double* out, cudaStream_t s);
-void launch_step_time(const CaseState& st, double t_new, cudaStream_t s);
+void launch_step_constants(const CaseState& st, double t_new, double c0, cudaStream_t s);
 void launch_mms_dirichlet(const Mesh& m, const CaseState& st, const vivParams& prm, cudaStream_t s);
 void launch_bdf_history(const Mesh& m, CaseState& st, double a_n, double a_nm1, bool shift, cudaStream_t s);
-void launch_extrapolate(const Mesh& m, CaseState& st, cudaStream_t s);
+void launch_extrapolate(const Mesh& m, CaseState& st, double w, cudaStream_t s);
+double launch_cfl(const Mesh& m, const CaseState& st, double dt, double* partial, double* out, double* host,
+                  cudaStream_t s);
 void launch_update(const Mesh& m, CaseState& st, const double* dU, cudaStream_t s);
 void launch_spmv_residual(const Mesh& m, const double* J, const double* x, const double* b, double* r,
                           cudaStream_t s);
@@ -321,8 +322,8 @@ void launch_axpy(double* y, const double* x, double a, int64_t n, cudaStream_t s
 void launch_scale_copy(double* y, const double* x, double a, int64_t n, cudaStream_t s);
 void launch_f64_to_f32(float* y, const double* x, int64_t n, cudaStream_t s);
 void launch_f32_to_f64(double* y, const float* x, int64_t n, cudaStream_t s);
-void launch_jacobian_split(const Mesh& m, const CaseState& st, const vivParams& prm, double c0, float* J32,
-                           double* J64, cudaStream_t s);
+void launch_jacobian_split(const Mesh& m, const CaseState& st, const vivParams& prm, float* J32, double* J64,
+                           cudaStream_t s);
 // border of the Jacobian (the two delta unknowns, eliminated after the fronts)
 void launch_border_column(const Mesh& m, const double* J, int j, double* dst, cudaStream_t s);
 void launch_border_schur(const Mesh& m, const double* J, const double* Y, double* Sb, int32_t* flag,

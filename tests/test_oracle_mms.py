@@ -89,3 +89,47 @@ def test_unsteady_mms_bdf2_order_in_time():
     ratio = errs[0]["u_l2"] / errs[1]["u_l2"]
     assert 3.6 < ratio < 4.4, ratio
     assert np.abs(xs[0] - xs[1]).max() < 1e-12
+
+
+def test_variable_step_bdf2_exact_and_second_order():
+    """Variable-step BDF2 (the adaptive time stepping of Section 6): the nodal
+    trajectories of the translating box are quadratic in time, so any
+    sequence of step sizes must reproduce the exact solution to rounding; with
+    the cubic time factor the error must fall by 4 when every step of a
+    varying sequence is halved."""
+    sol = mms.translating_box()
+    seq = [0.05, 0.065, 0.04, 0.055, 0.03, 0.06]   # step ratios 1.3, 0.62, 1.38, 0.55, 2
+    c = _box_case(sol, 10, seq[0])
+    c.dt_prev = seq[0]   # the history level of _box_case lies one seq[0] back
+    for dt in seq:
+        c.dt = dt
+        c.step(dirichlet=sol.set_dirichlet)
+        t = c.t
+        assert np.abs(c.u - sol.velocity(c.X, t)).max() < 1e-11
+        assert np.abs(c.x - sol.position(c.X, t)).max() < 1e-12
+        assert np.abs(c.p - sol.pressure(c.X, t))[c.is_vertex].max() < 1e-8
+    sol3 = mms.translating_box(gamma=3.0)
+    errs = []
+    for scale in (1.0, 0.5, 0.25):
+        steps = [s * scale for s in (0.05, 0.07, 0.04, 0.06) for _ in range(int(round(1 / scale)))]
+        c = _box_case(sol3, 5, steps[0])
+        c.dt_prev = steps[0]
+        for dt in steps:
+            c.dt = dt
+            c.step(dirichlet=sol3.set_dirichlet)
+        errs.append(np.abs(c.u - sol3.velocity(c.X, c.t)).max())
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(rates > 1.85) and np.all(rates < 2.3), rates
+
+
+def test_courant_number_and_step_control():
+    """The Courant number of a uniform flow U on a uniform n x n mesh is
+    dt U n (shortest edge 1/n); the step control moves dt towards the target
+    within a factor 1/2 .. 1.2 per step and below dt_max."""
+    m = I.square_mesh(8)
+    c = OracleCase(m, rho=1.0, mu=0.01, k=0.0, dt=0.01, u0=np.tile([0.6, 0.8], (len(m["X"]), 1)), lame=1.0)
+    assert abs(c.cfl() - 0.01 * 1.0 * 8) < 1e-14
+    assert abs(c.next_dt(0.08, 1.0) - 0.012) < 1e-15        # growth capped at 1.2
+    assert abs(c.next_dt(0.08, 0.09) - 0.01 * 0.09 / 0.08) < 1e-15
+    assert abs(c.next_dt(0.08, 0.01) - 0.005) < 1e-15       # shrink capped at 1/2
+    assert abs(c.next_dt(0.08, 1.0, dt_max=0.011) - 0.011) < 1e-15
