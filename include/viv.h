@@ -336,6 +336,28 @@ vivStatus viv_step_host(vivCase* c, const double* state_in, double* state_out, v
 /* size in doubles of the packed host state used by viv_step_host */
 int64_t viv_state_size(const vivMesh* mesh);
 
+/* ---- force history analysis (host only, no device work) ------------------ */
+typedef struct {
+  double cd_mean, cd_amp;  /* drag coefficient C_D = F_x / (rho U^2 D / 2): time mean, half range */
+  double cl_mean, cl_amp;  /* lift coefficient C_L = F_y / (rho U^2 D / 2): time mean, half range */
+  double cl_rms;           /* root mean square of C_L - mean */
+  double frequency;        /* dominant frequency of the lift */
+  double strouhal;         /* St = frequency D / U */
+  int64_t samples;         /* samples analysed */
+} vivForceStats;
+/* Force coefficients and the vortex-shedding frequency of a force history
+ * (F = vivStepInfo.force, the fluid force -int_Gamma lambda of Section 5.3, at
+ * the step times t; n samples, increasing times; host arrays read during the
+ * call).  Only samples with t >= t_start are analysed (the start-up is
+ * excluded).  Means and the RMS are trapezoidal time averages (the times may
+ * be uneven, as with adaptive steps).  The frequency is the peak of the
+ * spectrum of the lift minus its mean, resampled linearly on as many uniform
+ * times, Hann-windowed and zero-padded eightfold, with the peak refined by a
+ * parabola through the log-magnitudes of its bin and the two neighbours.
+ * VIV_ERR_ARG with fewer than 8 samples after t_start. */
+vivStatus viv_force_analysis(const double* t, const double* Fx, const double* Fy, int64_t n, double rho, double U,
+                             double D, double t_start, vivForceStats* out);
+
 /* ---- launch batching and tuning ------------------------------------------ */
 /* Switch the per-case CUDA graphs on (default) or off.  With graphs on, the
  * residual, Jacobian, factorisation and each refinement sweep of viv_step are

@@ -71,6 +71,12 @@ class StepInfo(C.Structure):
                     delta=list(self.delta), force=list(self.force), dt=self.dt, cfl=self.cfl)
 
 
+class ForceStats(C.Structure):
+    _fields_ = [("cd_mean", C.c_double), ("cd_amp", C.c_double), ("cl_mean", C.c_double), ("cl_amp", C.c_double),
+                ("cl_rms", C.c_double), ("frequency", C.c_double), ("strouhal", C.c_double),
+                ("samples", C.c_int64)]
+
+
 class Request(C.Structure):
     _fields_ = [("mesh", C.c_void_p), ("params", Params), ("u0", C.c_void_p), ("n_steps", C.c_int32),
                 ("arrival_time", C.c_double)]
@@ -146,6 +152,8 @@ SIGNATURES = {
     "viv_server_stats": (C.c_int, [_P, C.POINTER(ServerStats)]),
     "viv_server_destroy": (C.c_int, [_P]),
     "viv_kernel_launches": (C.c_int64, []),
+    "viv_force_analysis": (C.c_int, [_P, _P, _P, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_double,
+                                     C.POINTER(ForceStats)]),
     "viv_profile": (C.c_int, [_P, C.c_int]),
     "viv_profile_read": (C.c_int, [_P, _P, _P]),
     "viv_profile_levels": (C.c_int, [_P, _P, C.c_int32, _P]),
@@ -512,6 +520,17 @@ def tc_schur_update(a, b, c, err, stream=None):
     ld = lambda t: t.stride(1) if t.shape[1] > 1 else max(1, t.shape[0])   # any ld >= rows for one column
     _check(load().viv_tc_schur_update(_dev_ptr(a), ld(a), _dev_ptr(b), ld(b), _dev_ptr(c), ld(c), M, N, K,
                                       _dev_ptr(err), C.c_void_p(st.cuda_stream)))
+
+
+def force_analysis(t, F, rho=1.0, U=1.0, D=1.0, t_start=0.0):
+    """Drag / lift coefficients and Strouhal number of a force history
+    (t: n times, F: n x 2 fluid forces) - viv_force_analysis."""
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    F = np.asarray(F, dtype=np.float64)
+    fx, fy = np.ascontiguousarray(F[:, 0]), np.ascontiguousarray(F[:, 1])
+    st = ForceStats()
+    _check(load().viv_force_analysis(_ptr(t), _ptr(fx), _ptr(fy), len(t), rho, U, D, t_start, C.byref(st)))
+    return {f: getattr(st, f) for f, _ in ForceStats._fields_}
 
 
 def kernel_launches():
