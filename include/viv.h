@@ -133,8 +133,15 @@ typedef struct {
                               time-dependent solution (u = t^3 (sin pi x cos pi y,
                               sin pi x sin pi y), p = t^2 cos pi x cos pi y) on a mesh moved by
                               X + source_amp sin(pi t) sin(pi X) sin(pi Y) (1, 1), whose
-                              Dirichlet data the library sets at each step's time; for
-                              verification on the unit square */
+                              Dirichlet data the library sets at each step's time; 3: the
+                              coupled quasi-manufactured solution of Section 5.2 on the
+                              unit square around a cylinder of radius 0.15 at (1/2, 1/2)
+                              (kernel radius 0.45, total displacement source_amp (0.8, 0.6),
+                              f(t) = sin 2 pi t, pressure -k f psi (e.d) / (0.15 pi)), for
+                              which viv_case_create sets the exact initial velocity and
+                              which needs no Dirichlet update (source_amp <= 0.05); sources
+                              of 1 .. 3 assume lambda_s = mu_s = 1 (lame_constant = 1);
+                              for verification */
   double source_amp;
   int32_t pivoting;        /* VIV_PIVOT_THRESHOLD (0): threshold partial pivoting over all
                               fully summed rows of a front; VIV_PIVOT_WINDOW (1): partial
@@ -170,6 +177,8 @@ typedef struct {
    * rates [(1 + 2w)/(1 + w) v^{n+1} - (1 + w) v^n + w^2/(1 + w) v^{n-1}] / dt.
    * cfl_target = 0 (default): constant dt. */
   double cfl_target, dt_max;
+  int32_t lame_constant;   /* 1: lambda_s = mu_s = lame_scale on every element (the
+                              manufactured solutions); 0 (default): lame_scale min|K_0|/|K_0| */
 } vivParams;
 enum { VIV_PIVOT_THRESHOLD = 0, VIV_PIVOT_WINDOW = 1 };
 

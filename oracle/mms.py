@@ -195,6 +195,158 @@ def unsteady_mms(rho=9.876, mu=1.234, amp=0.05):
     return _Manufactured((ux, uy), p, chi, rho, mu, 1.0, 1.0)
 
 
+QUASI_CENTER = (0.5, 0.5)
+QUASI_R0, QUASI_R1 = 0.15, 0.45
+QUASI_D_DIR = (0.8, 0.6)
+
+
+def _kernel_numpy(R0, R1):
+    """psi(r) = 1 - phi(s), s = (r - R0)/(R1 - R0) clamped to [0, 1], and its
+    first three r-derivatives (zero where s is clamped: phi'(0) = phi'(1) =
+    phi''(0) = phi''(1) = 0, so psi is C^2)."""
+    L = R1 - R0
+
+    def s_of(r):
+        return np.clip((np.asarray(r, dtype=np.float64) - R0) / L, 0.0, 1.0)
+
+    def inside(r):
+        r = np.asarray(r, dtype=np.float64)
+        return (r > R0) & (r < R1)
+
+    psi0 = lambda r: 1.0 - (6 * s_of(r) ** 5 - 15 * s_of(r) ** 4 + 10 * s_of(r) ** 3)
+    psi1 = lambda r: np.where(inside(r), -(30 * s_of(r) ** 4 - 60 * s_of(r) ** 3 + 30 * s_of(r) ** 2) / L, 0.0)
+    psi2 = lambda r: np.where(inside(r), -(120 * s_of(r) ** 3 - 180 * s_of(r) ** 2 + 60 * s_of(r)) / L ** 2, 0.0)
+    psi3 = lambda r: np.where(inside(r), -(360 * s_of(r) ** 2 - 360 * s_of(r) + 60) / L ** 3, 0.0)
+    return {"Psi": psi0, "Psi1": psi1, "Psi2": psi2, "Psi3": psi3}
+
+
+class Psi3(sy.Function):
+    pass
+
+
+class Psi2(sy.Function):
+    def fdiff(self, argindex=1):
+        return Psi3(self.args[0])
+
+
+class Psi1(sy.Function):
+    def fdiff(self, argindex=1):
+        return Psi2(self.args[0])
+
+
+class Psi(sy.Function):
+    """The bell-shaped kernel of Section 5.1; evaluated numerically (see
+    _kernel_numpy) so that the symbolic calculus stays small."""
+
+    def fdiff(self, argindex=1):
+        return Psi1(self.args[0])
+
+
+class QuasiMMS:
+    """Section 5.2's coupled quasi-manufactured solution on the unit square
+    around a rigid cylinder of radius R0 centred at X_c:
+      x = X + f(t) d psi(|X - X_c|),      u = f'(t) d psi(|x - x_c(t)|),
+      p = -k f(t) / (pi R0) (d . e) psi(|x - x_c(t)|),  e = (x - x_c)/|x - x_c|,
+    x_c(t) = X_c + f(t) d, f(t) = sin(2 pi t), psi(r) = 1 - phi((r - R0)/(R1 - R0))
+    with phi(s) = 6 s^5 - 15 s^4 + 10 s^3 (psi = 1 up to R0, 0 beyond R1).
+    The cylinder moves rigidly (delta = f d), u equals the mesh velocity on it
+    and the velocity gradient vanishes there, so the multiplier rows and the
+    coupling row k delta + int_Gamma lambda = 0 hold without source terms
+    (int_Gamma p e ds = -k f d); only the momentum, continuity and
+    pseudo-solid equations get sources, derived here with sympy:
+      f_u = rho (d_t u|_x + (u . grad) u) - div sigma(u, p),  g_p = div u,
+      f_x = -div_X sigma_s(x)  (lambda_s = mu_s = 1).
+    The total displacement d = amp (0.8, 0.6) with amp <= 0.05 keeps psi = 0
+    on the outer boundary, so the Dirichlet data there are u = 0, x = X (and a
+    pinned pressure 0)."""
+
+    def __init__(self, k=10.0, amp=0.05, rho=1.0, mu=0.1):
+        pi = sy.pi
+        cx, cy = QUASI_CENTER
+        R0 = QUASI_R0
+        self.rho, self.mu, self.k, self.lam_s, self.mu_s = rho, mu, k, 1.0, 1.0
+        self.hole = None
+        dx, dy = amp * QUASI_D_DIR[0], amp * QUASI_D_DIR[1]
+        f = sy.sin(2 * pi * t_)
+        fp = sy.diff(f, t_)
+        xcx, xcy = cx + f * dx, cy + f * dy
+        r = sy.sqrt((x_ - xcx) ** 2 + (y_ - xcy) ** 2)
+        ux, uy = fp * dx * Psi(r), fp * dy * Psi(r)
+        p = -k * f / (pi * R0) * (dx * (x_ - xcx) + dy * (y_ - xcy)) / r * Psi(r)
+        grad = sy.Matrix([[sy.diff(ux, x_), sy.diff(ux, y_)], [sy.diff(uy, x_), sy.diff(uy, y_)]])
+        sigma = -p * sy.eye(2) + mu * (grad + grad.T)
+        uvec = sy.Matrix([ux, uy])
+        divs = sy.Matrix([sy.diff(sigma[0, 0], x_) + sy.diff(sigma[0, 1], y_),
+                          sy.diff(sigma[1, 0], x_) + sy.diff(sigma[1, 1], y_)])
+        fu = rho * (sy.diff(uvec, t_) + grad * uvec) - divs
+        gp = grad[0, 0] + grad[1, 1]
+        RX = sy.sqrt((X_ - cx) ** 2 + (Y_ - cy) ** 2)
+        chx, chy = X_ + f * dx * Psi(RX), Y_ + f * dy * Psi(RX)
+        F = sy.Matrix([[sy.diff(chx, X_), sy.diff(chx, Y_)], [sy.diff(chy, X_), sy.diff(chy, Y_)]])
+        eps = (F + F.T) / 2 - sy.eye(2)
+        sig_s = (eps[0, 0] + eps[1, 1]) * sy.eye(2) + 2 * eps
+        fx = -sy.Matrix([sy.diff(sig_s[0, 0], X_) + sy.diff(sig_s[0, 1], Y_),
+                         sy.diff(sig_s[1, 0], X_) + sy.diff(sig_s[1, 1], Y_)])
+        mods = [_kernel_numpy(QUASI_R0, QUASI_R1), "numpy"]
+
+        def vec(exprs, args):
+            fn = sy.lambdify(args, exprs, modules=mods)
+
+            def call(*a):
+                shape = np.broadcast(*a).shape
+                return np.stack([np.broadcast_to(np.asarray(o, dtype=np.float64), shape) for o in fn(*a)], axis=-1)
+            return call
+
+        def scal(expr, args):
+            fn = sy.lambdify(args, expr, modules=mods)
+            return lambda *a: np.broadcast_to(np.asarray(fn(*a), dtype=np.float64), np.broadcast(*a).shape)
+
+        self._fu_x = vec([fu[0], fu[1]], (x_, y_, t_))
+        self._gp_x = scal(gp, (x_, y_, t_))
+        self._fx = vec([fx[0], fx[1]], (X_, Y_, t_))
+        self._u_phys = vec([ux, uy], (x_, y_, t_))
+        self._grad_u_phys = vec([grad[0, 0], grad[0, 1], grad[1, 0], grad[1, 1]], (x_, y_, t_))
+        self._p_phys = scal(p, (x_, y_, t_))
+        self._chi = vec([chx, chy], (X_, Y_, t_))
+        self._grad_chi = vec([F[0, 0], F[0, 1], F[1, 0], F[1, 1]], (X_, Y_, t_))
+        self.d = np.array([dx, dy], dtype=np.float64)
+        self.amp = amp
+
+    # ---- source interface used by oracle.fem --------------------------------
+    def volume(self, Xq, t):
+        xq = self._chi(Xq[..., 0], Xq[..., 1], t)
+        return (self._fu_x(xq[..., 0], xq[..., 1], t), self._gp_x(xq[..., 0], xq[..., 1], t),
+                self._fx(Xq[..., 0], Xq[..., 1], t))
+
+    def gamma(self, Xq, t):
+        return np.zeros(Xq.shape[:-1] + (2,))
+
+    def border(self, t):
+        return np.zeros(2)
+
+    # ---- exact values -------------------------------------------------------
+    def position(self, X, t):
+        return self._chi(X[..., 0], X[..., 1], t)
+
+    def velocity(self, X, t):
+        x = self.position(X, t)
+        return self._u_phys(x[..., 0], x[..., 1], t)
+
+    def pressure(self, X, t):
+        x = self.position(X, t)
+        return self._p_phys(x[..., 0], x[..., 1], t)
+
+    def delta(self, t):
+        return np.sin(2 * np.pi * t) * self.d
+
+    def force(self, t):
+        """F_fluid = -int_Gamma lambda = k delta (the spring balance)."""
+        return self.k * self.delta(t)
+
+    set_dirichlet = _Manufactured.set_dirichlet
+    set_exact_state = _Manufactured.set_exact_state
+
+
 def error_norms(case, sol, t):
     """Errors of the discrete state against the exact fields:
     u in L2 and H1-seminorm and p in L2 over Omega_t, x in L2 and H1-seminorm

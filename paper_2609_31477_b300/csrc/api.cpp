@@ -441,7 +441,7 @@ static vivStatus case_create_impl(vivMesh* mesh, const vivParams* prm_in, const 
             "unknown pivoting");
   VIV_CHECK(prm->jacobian_fp32 == 0 || prm->jacobian_fp32 == 1, VIV_ERR_ARG, "jacobian_fp32 must be 0 or 1");
   VIV_CHECK(prm->predictor == 0 || prm->predictor == 1, VIV_ERR_ARG, "predictor must be 0 or 1");
-  VIV_CHECK(prm->source >= 0 && prm->source <= 2, VIV_ERR_ARG, "source must be 0, 1 or 2");
+  VIV_CHECK(prm->source >= 0 && prm->source <= 3, VIV_ERR_ARG, "source must be 0 .. 3");
   VIV_CHECK(prm->cfl_target >= 0 && prm->dt_max >= 0, VIV_ERR_ARG, "cfl_target and dt_max must not be negative");
   VIV_CHECK(mesh->m.on_device, VIV_ERR_STATE, "mesh was analysed on the host only");
   *out = nullptr;
@@ -517,7 +517,8 @@ static vivStatus case_create_impl(vivMesh* mesh, const vivParams* prm_in, const 
     else
       prepare_kernels<double>();
     noalloc_prepare();   // the allocation-free solve's fixed array is committed here, not on its first call
-    launch_element_areas(m, s.lame, c->prm.lame_scale, s.scal + 1, st);
+    launch_element_areas(m, s.lame, c->prm.lame_scale, c->prm.lame_constant != 0, s.scal + 1, st);
+    if (c->prm.source == 3) launch_quasi_init(m, s, c->prm, st);   // the exact state at t = 0
     VIV_CUDA(cudaStreamSynchronize(st));
   } catch (...) {
     if (c->h_pinned) cudaFreeHost(c->h_pinned);

@@ -140,9 +140,70 @@ __device__ __noinline__ void mms_source_unsteady(double X, double Y, double t, d
   fx[1] = f;
 }
 
+// Coupled quasi-manufactured solution (Section 5.2) on the unit square around
+// a rigid cylinder of radius R0 at X_c = (1/2, 1/2): with f = sin 2 pi t,
+// d = amp (0.8, 0.6), x_c = X_c + f d, r = |x - x_c|, e = (x - x_c)/r and the
+// kernel psi(r) = 1 - phi((r - R0)/(R1 - R0)), phi(s) = 6 s^5 - 15 s^4 + 10 s^3:
+//   u = f' psi d,   p = A f psi (e.d) with A = -k/(pi R0),   x = X + f psi(|X - X_c|) d.
+// Derivatives (e.d written ed, psi' and psi'' by r):
+//   d_t u|_x      = f'' psi d - f'^2 psi' ed d          ((dr/dt = -f' ed)
+//   (u.grad) u    = f'^2 psi psi' ed d
+//   div u         = f' psi' ed,     lap u = f' (psi'' + psi'/r) d
+//   grad div u    = f' [psi'' ed e + psi' (d - ed e)/r]
+//   grad p        = A f [psi' ed e + psi (d - ed e)/r]
+//   f_u = rho (d_t u + (u.grad) u) + grad p - mu (lap u + grad div u),  g_p = div u
+//   f_x = -div_X sigma_s = -f [2 psi'' Ed E + 2 psi' (d - Ed E)/R + (psi'' + psi'/R) d]
+//         (lambda_s = mu_s = 1; R = |X - X_c|, E = (X - X_c)/R, Ed = E.d)
+constexpr double QUASI_CX = 0.5, QUASI_CY = 0.5, QUASI_R0 = 0.15, QUASI_R1 = 0.45;
+constexpr double QUASI_DX = 0.8, QUASI_DY = 0.6;
+
+__device__ __forceinline__ void quasi_kernel(double r, double& p0, double& p1, double& p2) {
+  const double L = QUASI_R1 - QUASI_R0;
+  const double s = fmin(1.0, fmax(0.0, (r - QUASI_R0) / L));
+  p0 = 1.0 - s * s * s * (10.0 + s * (-15.0 + 6.0 * s));
+  p1 = -30.0 * s * s * (s - 1.0) * (s - 1.0) / L;
+  p2 = -60.0 * s * (s - 1.0) * (2.0 * s - 1.0) / (L * L);
+}
+
+__device__ __noinline__ void mms_source_quasi(double X, double Y, double t, double amp, double k, double rho,
+                                              double mu, double* fu, double* gp, double* fx) {
+  const double pi = 3.14159265358979323846;
+  const double dx = amp * QUASI_DX, dy = amp * QUASI_DY;
+  const double f = sin(2 * pi * t), f1 = 2 * pi * cos(2 * pi * t), f2 = -4 * pi * pi * f;
+  // reference point: the mesh motion and the pseudo-solid source
+  double Ex = X - QUASI_CX, Ey = Y - QUASI_CY;
+  const double R = fmax(sqrt(Ex * Ex + Ey * Ey), 1e-12);
+  Ex /= R;
+  Ey /= R;
+  double q0, q1, q2;
+  quasi_kernel(R, q0, q1, q2);
+  const double Ed = Ex * dx + Ey * dy;
+  fx[0] = -f * (2 * q2 * Ed * Ex + 2 * q1 * (dx - Ed * Ex) / R + (q2 + q1 / R) * dx);
+  fx[1] = -f * (2 * q2 * Ed * Ey + 2 * q1 * (dy - Ed * Ey) / R + (q2 + q1 / R) * dy);
+  // physical point x = X + f psi(R) d and the fluid sources there
+  const double x = X + f * q0 * dx, y = Y + f * q0 * dy;
+  double ex = x - (QUASI_CX + f * dx), ey = y - (QUASI_CY + f * dy);
+  const double r = fmax(sqrt(ex * ex + ey * ey), 1e-12);
+  ex /= r;
+  ey /= r;
+  double p0, p1, p2;
+  quasi_kernel(r, p0, p1, p2);
+  const double ed = ex * dx + ey * dy;
+  const double A = -k / (pi * QUASI_R0);
+  const double dtu = f2 * p0, dtu_e = -f1 * f1 * p1 * ed;   // d_t u = (dtu + dtu_e) d
+  const double conv = f1 * f1 * p0 * p1 * ed;               // (u.grad) u = conv d
+  const double lap = f1 * (p2 + p1 / r);                   // lap u = lap d
+  const double gd_e = f1 * p2 * ed, gd_d = f1 * p1 / r;     // grad div u = gd_e e + gd_d (d - ed e)
+  const double gp_e = A * f * p1 * ed, gp_d = A * f * p0 / r;   // grad p = gp_e e + gp_d (d - ed e)
+  const double tdx = dx - ed * ex, tdy = dy - ed * ey;
+  fu[0] = rho * (dtu + dtu_e + conv) * dx + gp_e * ex + gp_d * tdx - mu * (lap * dx + gd_e * ex + gd_d * tdx);
+  fu[1] = rho * (dtu + dtu_e + conv) * dy + gp_e * ey + gp_d * tdy - mu * (lap * dy + gd_e * ey + gd_d * tdy);
+  *gp = f1 * p1 * ed;
+}
+
 template <class T>
 __device__ void qp_compute(const Tables<T>& tb, const ElemNodes<T>& en, int q, T rho, T mu, int source,
-                           double amp, double t_src, T* out) {
+                           double amp, double t_src, double k, T* out) {
   // current configuration
   T J00 = 0, J01 = 0, J10 = 0, J11 = 0;
   T K00 = 0, K01 = 0, K10 = 0, K11 = 0;   // reference
@@ -199,7 +260,7 @@ __device__ void qp_compute(const Tables<T>& tb, const ElemNodes<T>& en, int q, T
   out[Q_EPS] = e00; out[Q_EPS + 1] = e01; out[Q_EPS + 2] = e11;
   out[Q_TR] = e00 + e11;
   out[Q_FU] = out[Q_FU + 1] = out[Q_GP] = out[Q_FX] = out[Q_FX + 1] = T(0);
-  if (source == 1 || source == 2) {
+  if (source >= 1) {
     double Xq = 0, Yq = 0;
     for (int a = 0; a < 9; ++a) {
       Xq += (double)tb.N[q][a] * (double)en.X[a][0];
@@ -208,8 +269,10 @@ __device__ void qp_compute(const Tables<T>& tb, const ElemNodes<T>& en, int q, T
     double fu[2], gp, fx[2];
     if (source == 1)
       mms_source(Xq, Yq, amp, (double)rho, (double)mu, fu, &gp, fx);
-    else
+    else if (source == 2)
       mms_source_unsteady(Xq, Yq, t_src, amp, (double)rho, (double)mu, fu, &gp, fx);
+    else
+      mms_source_quasi(Xq, Yq, t_src, amp, k, (double)rho, (double)mu, fu, &gp, fx);
     out[Q_FU] = (T)fu[0];
     out[Q_FU + 1] = (T)fu[1];
     out[Q_GP] = (T)gp;
@@ -248,8 +311,8 @@ struct AsmArgs {
   const double *X, *x, *u, *p, *hu, *hx, *lame;
   const int32_t* node_dof;
   const int32_t* e2nz;
-  double rho, mu;
-  int source;        // 0 none, 1 the steady, 2 the time-dependent manufactured solution
+  double rho, mu, k;
+  int source;        // 0 none, 1 steady, 2 time-dependent, 3 coupled quasi-manufactured solution
   double source_amp;
   // device: {time of the step being solved, BDF rate coefficient c0} - read by
   // the kernels, so that captured CUDA graphs stay valid when either changes
@@ -276,8 +339,8 @@ __global__ void __launch_bounds__(ASM_THREADS, 2) element_kernel(AsmArgs A, doub
   if (tid < 9 * EPB) {
     const int le = tid / 9, q = tid % 9;
     if (blockIdx.x * EPB + le < A.n)
-      qp_compute<T>(tb, en[le], q, (T)A.rho, (T)A.mu, A.source, A.source_amp, A.source == 2 ? A.step[0] : 0.0,
-                    qd[le][q]);
+      qp_compute<T>(tb, en[le], q, (T)A.rho, (T)A.mu, A.source, A.source_amp, A.source >= 2 ? A.step[0] : 0.0,
+                    A.k, qd[le][q]);
   }
   __syncthreads();
   int le, t;
@@ -605,8 +668,20 @@ __global__ void lame_kernel(double* lame, int64_t E, const double* amin, double 
 
 }  // namespace
 
-void launch_element_areas(const Mesh& m, double* lame, double scale, double* scratch, cudaStream_t s) {
+__global__ void fill_kernel(double* v, int64_t n, double a) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) v[i] = a;
+}
+
+void launch_element_areas(const Mesh& m, double* lame, double scale, bool constant, double* scratch,
+                          cudaStream_t s) {
   int E = (int)m.n_elems;
+  if (constant) {   // lambda_s = mu_s = scale on every element
+    Launched L(K_VEC, s);
+    fill_kernel<<<(E + 255) / 256, 256, 0, s>>>(lame, E, scale);
+    VIV_CUDA(cudaGetLastError());
+    return;
+  }
   {
     Launched L(K_VEC, s);
     area_kernel<<<(E + 127) / 128, 128, 0, s>>>(m.d_conn, m.d_X, E, scale, lame);
@@ -639,6 +714,7 @@ static void run_assembly(const Mesh& m, const CaseState& st, const vivParams& pr
   A.e2nz = m.d_e2nz;
   A.rho = prm.rho;
   A.mu = prm.mu;
+  A.k = prm.k;
   A.source = prm.source;
   A.source_amp = prm.source_amp;
   A.step = st.step;
@@ -740,6 +816,24 @@ void launch_mms_dirichlet(const Mesh& m, const CaseState& st, const vivParams& p
   Launched L(K_VEC, s);
   mms_dirichlet_kernel<<<(unsigned)((m.n_nodes + 255) / 256), 256, 0, s>>>(m.n_nodes, m.d_tags, m.d_X, st.step,
                                                                            prm.source_amp, st.u, st.x, st.p);
+  VIV_CUDA(cudaGetLastError());
+}
+
+// initial velocity of the coupled quasi-manufactured solution: u(X, 0) = 2 pi psi(|X - X_c|) d
+__global__ void quasi_init_kernel(int64_t n, const double* X, double amp, double* u) {
+  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (a >= n) return;
+  const double pi = 3.14159265358979323846;
+  const double ex = X[2 * a] - QUASI_CX, ey = X[2 * a + 1] - QUASI_CY;
+  double q0, q1, q2;
+  quasi_kernel(sqrt(ex * ex + ey * ey), q0, q1, q2);
+  u[2 * a] = 2 * pi * q0 * amp * QUASI_DX;
+  u[2 * a + 1] = 2 * pi * q0 * amp * QUASI_DY;
+}
+
+void launch_quasi_init(const Mesh& m, const CaseState& st, const vivParams& prm, cudaStream_t s) {
+  Launched L(K_VEC, s);
+  quasi_init_kernel<<<(unsigned)((m.n_nodes + 255) / 256), 256, 0, s>>>(m.n_nodes, m.d_X, prm.source_amp, st.u);
   VIV_CUDA(cudaGetLastError());
 }
 

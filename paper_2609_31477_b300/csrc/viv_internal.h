@@ -304,7 +304,9 @@ struct vivCase {
 
 // kernels (defined in .cu files), all launched on the case stream
 namespace viv {
-void launch_element_areas(const Mesh& m, double* lame, double scale, double* scratch, cudaStream_t s);
+void launch_element_areas(const Mesh& m, double* lame, double scale, bool constant, double* scratch,
+                          cudaStream_t s);
+void launch_quasi_init(const Mesh& m, const CaseState& st, const vivParams& prm, cudaStream_t s);
 void launch_residual(const Mesh& m, const CaseState& st, const vivParams& prm, cudaStream_t s);
 template <class T>
 void launch_jacobian(const Mesh& m, const CaseState& st, const vivParams& prm, T* vals, cudaStream_t s);

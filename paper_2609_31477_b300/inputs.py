@@ -246,6 +246,75 @@ def square_mesh(n, hole=None, lo=0.0, hi=1.0):
                 name=f"square_n{n}" + ("_hole" if hole else ""))
 
 
+def hole_square_mesh(n, R0=0.15, center=(0.5, 0.5), lo=0.0, hi=1.0):
+    """Q2 O-grid of the square [lo,hi]^2 around a circular hole of radius R0:
+    4n cells around, n cells radially, blended linearly from the circle (nodes
+    on the circle, midpoints included) to the square boundary.  Outer nodes are
+    fully Dirichlet (u and x), hole nodes are the rigid body Gamma.  This is
+    the geometry of the coupled manufactured solution of Section 5.2 (a rigid
+    cylinder of radius R0 inside the unit square)."""
+    cx, cy = center
+    half = 0.5 * (hi - lo)
+    nodes = _NodeTable()
+    conn, gamma_faces = [], []
+    n_around = 8 * n
+    s_nodes = _q2_line(np.linspace(0.0, 1.0, n + 1))
+    perim = 8.0 * half
+
+    def square_point(t):
+        t = t % perim
+        h = half
+        if t < h:
+            return h, t
+        t -= h
+        if t < 2 * h:
+            return h - t, h
+        t -= 2 * h
+        if t < 2 * h:
+            return -h, h - t
+        t -= 2 * h
+        if t < 2 * h:
+            return -h + t, -h
+        t -= 2 * h
+        return h, -h + t
+
+    ring = np.empty((n_around, 2 * n + 1), dtype=np.int64)
+    for k in range(n_around):
+        th = 2.0 * math.pi * k / n_around
+        c = (cx + R0 * math.cos(th), cy + R0 * math.sin(th))
+        sq = square_point(perim * k / n_around)
+        s_pt = (cx + sq[0], cy + sq[1])
+        for r, sv in enumerate(s_nodes):
+            if r == 0:
+                px, py = c
+            elif r == 2 * n:
+                px, py = s_pt
+            else:
+                px = (1 - sv) * c[0] + sv * s_pt[0]
+                py = (1 - sv) * c[1] + sv * s_pt[1]
+            ring[k, r] = nodes.get(px, py)
+    for i in range(4 * n):
+        for j in range(n):
+            el = []
+            for b in range(3):
+                k = (2 * i + b) % n_around
+                for a in range(3):
+                    el.append(ring[k, 2 * j + a])
+            if j == 0:
+                gamma_faces.append((len(conn), 0))
+            conn.append(el)
+    X = np.array(nodes.coords, dtype=np.float64)
+    tags = np.zeros(len(X), dtype=np.int32)
+    tol = 1e-9
+    outer = ((np.abs(X[:, 0] - lo) < tol) | (np.abs(X[:, 0] - hi) < tol)
+             | (np.abs(X[:, 1] - lo) < tol) | (np.abs(X[:, 1] - hi) < tol))
+    tags[outer] |= ALL_DIRICHLET_TAG
+    tags[np.abs(np.hypot(X[:, 0] - cx, X[:, 1] - cy) - R0) < 1e-9] |= CYL
+    return dict(X=X, conn=np.array(conn, dtype=np.int64), tags=tags,
+                gamma_faces=np.array(gamma_faces, dtype=np.int64).reshape(-1, 2),
+                Xc=np.array([cx, cy], dtype=np.float64), D=2.0 * R0, name=f"hole_square_n{n}")
+
+
 # --- seeded normal samples: splitmix64 + Box-Muller ----------------------------
 _M64 = (1 << 64) - 1
 

@@ -55,7 +55,8 @@ class Params(C.Structure):
                 ("pivot_threshold", C.c_double), ("source", C.c_int32), ("source_amp", C.c_double),
                 ("pivoting", C.c_int32), ("jacobian_fp32", C.c_int32), ("predictor", C.c_int32),
                 ("Re", C.c_double), ("Ustar", C.c_double), ("U_inf", C.c_double), ("D", C.c_double),
-                ("span_L", C.c_double), ("cfl_target", C.c_double), ("dt_max", C.c_double)]
+                ("span_L", C.c_double), ("cfl_target", C.c_double), ("dt_max", C.c_double),
+                ("lame_constant", C.c_int32)]
 
 
 class StepInfo(C.Structure):
@@ -297,12 +298,12 @@ class Case:
     def __init__(self, mesh: Mesh, u0, rho, mu, k, dt, precision=VIV_FP64, lame_scale=1.0,
                  newton_tol=1e-10, max_newton=25, refine_tol=0.0, refine_max=0, pivot_threshold=0.01,
                  stream=None, source=0, source_amp=0.0, pivoting=0, jacobian_fp32=0, predictor=0,
-                 Re=0.0, Ustar=0.0, U_inf=0.0, D=0.0, span_L=0.0, cfl_target=0.0, dt_max=0.0):
+                 Re=0.0, Ustar=0.0, U_inf=0.0, D=0.0, span_L=0.0, cfl_target=0.0, dt_max=0.0, lame_constant=0):
         lib = load()
         self.mesh = mesh
         self.params = Params(rho, mu, k, dt, lame_scale, newton_tol, max_newton, precision, refine_tol,
                              refine_max, pivot_threshold, source, source_amp, pivoting, jacobian_fp32,
-                             predictor, Re, Ustar, U_inf, D, span_L, cfl_target, dt_max)
+                             predictor, Re, Ustar, U_inf, D, span_L, cfl_target, dt_max, lame_constant)
         u0 = np.ascontiguousarray(u0, dtype=np.float64)
         import torch
         # each case owns a non-default stream (graphs cannot capture the legacy stream)
@@ -467,7 +468,7 @@ class Server:
                jacobian_fp32=0, predictor=0):
         # mu and k are derived from Re and U* by the library (vivParams)
         prm = Params(rho, 0.0, 0.0, dt, 1.0, newton_tol, max_newton, precision, 0.0, 0,
-                     0.01, 0, 0.0, pivoting, jacobian_fp32, predictor, Re, Ustar, U_inf, D, 0.0, 0.0, 0.0)
+                     0.01, 0, 0.0, pivoting, jacobian_fp32, predictor, Re, Ustar, U_inf, D, 0.0, 0.0, 0.0, 0)
         u0 = np.ascontiguousarray(u0, dtype=np.float64)
         req = Request(mesh.h.value, prm, u0.ctypes.data, int(n_steps), float(arrival_time))
         rid = C.c_int64()

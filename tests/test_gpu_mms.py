@@ -43,7 +43,7 @@ def test_steady_mms_matches_oracle_and_converges(precision):
         p0 = np.zeros(len(m["X"]))
         p0[0] = sol.pressure(m["X"][:1], 0.0)[0]
         M = viv.Mesh(m)
-        case = viv.Case(M, u0, sol.rho, sol.mu, 0.0, 1e8, precision=prec, lame_scale=1.0, source=1, source_amp=AMP)
+        case = viv.Case(M, u0, sol.rho, sol.mu, 0.0, 1e8, precision=prec, lame_scale=1.0, lame_constant=1, source=1, source_amp=AMP)
         case.set_state(p=p0)
         info = case.step()
         assert info["res_norm"] <= 1e-10
@@ -67,7 +67,7 @@ def _unsteady_gpu(viv, sol, n, dt, prec, T=0.2, pivoting=0):
     m = I.square_mesh(n)
     m["tags"][0] |= I.P_FIX
     M = viv.Mesh(m)
-    case = viv.Case(M, np.zeros((len(m["X"]), 2)), sol.rho, sol.mu, 0.0, dt, precision=prec, lame_scale=1.0,
+    case = viv.Case(M, np.zeros((len(m["X"]), 2)), sol.rho, sol.mu, 0.0, dt, precision=prec, lame_scale=1.0, lame_constant=1,
                     source=2, source_amp=AMP, pivoting=pivoting)
     for _ in range(int(round(T / dt))):
         info = case.step()

@@ -30,7 +30,9 @@ def test_fixed_cylinder_re200_shedding():
         assert info["res_norm"] <= 1e-10
         ts.append(info["t"])
         F.append(info["force"])
-        assert abs(info["delta"][0]) < 1e-5 and abs(info["delta"][1]) < 1e-5   # held by the stiff spring
+        # held by the stiff spring: delta = F / k (the start-up force reaches ~18)
+        assert np.allclose(np.array(info["delta"]) * 1e6, info["force"], rtol=1e-6, atol=1e-9)
+        assert max(abs(info["delta"][0]), abs(info["delta"][1])) < 1e-4
     case.close()
     M.close()
     r = viv.force_analysis(np.array(ts), np.array(F), rho=1.0, U=1.0, D=1.0, t_start=60.0)

@@ -133,3 +133,51 @@ def test_courant_number_and_step_control():
     assert abs(c.next_dt(0.08, 0.09) - 0.01 * 0.09 / 0.08) < 1e-15
     assert abs(c.next_dt(0.08, 0.01) - 0.005) < 1e-15       # shrink capped at 1/2
     assert abs(c.next_dt(0.08, 1.0, dt_max=0.011) - 0.011) < 1e-15
+
+
+def _quasi_case(sol, n, dt):
+    m = I.hole_square_mesh(n)
+    m["tags"][np.argmin(m["X"][:, 0] + m["X"][:, 1])] |= I.P_FIX   # a corner vertex, where p = 0
+    c = OracleCase(m, rho=sol.rho, mu=sol.mu, k=sol.k, dt=dt, u0=np.zeros((len(m["X"]), 2)), lame=1.0, src=sol)
+    sol.set_exact_state(c, 0.0)
+    return c
+
+
+def test_quasi_mms_pressure_carries_the_spring_force():
+    """Section 5.2: on the rigid cylinder the manufactured velocity gradient
+    vanishes, so the multiplier is the pressure times the normal and
+    int_Gamma lambda = int_Gamma p e ds; with p = -k f (d.e) psi / (pi R0) this
+    is -k f d, which is what the coupling row k delta + int_Gamma lambda = 0
+    needs with delta = f d.  Quadrature on the exact moved circle."""
+    sol = mms.QuasiMMS()
+    th = np.linspace(0.0, 2 * np.pi, 2001)[:-1]
+    e = np.stack([np.cos(th), np.sin(th)], 1)
+    for t in (0.05, 0.1, 0.2):
+        xc = np.array(mms.QUASI_CENTER) + np.sin(2 * np.pi * t) * sol.d
+        x = xc + mms.QUASI_R0 * e
+        pl = sol._p_phys(x[:, 0], x[:, 1], t)
+        grad = sol._grad_u_phys(x[:, 0], x[:, 1], t)
+        assert np.abs(grad).max() < 1e-12
+        integral = (pl[:, None] * e).sum(0) * mms.QUASI_R0 * (2 * np.pi / len(th))
+        assert np.allclose(sol.k * sol.delta(t) + integral, 0.0, atol=1e-12)
+        # the cylinder moves rigidly with the manufactured velocity
+        X = np.array(mms.QUASI_CENTER) + mms.QUASI_R0 * e
+        assert np.allclose(sol.position(X, t) - X, sol.delta(t), atol=1e-14)
+
+
+def test_quasi_mms_converges_under_joint_refinement():
+    """Mesh and step halved together (4 -> 8 cells radially, dt 0.02 -> 0.01,
+    to t = 0.1): the cylinder displacement (and so the fluid force k delta) and
+    the velocity converge at least at second order."""
+    sol = mms.QuasiMMS()
+    errs = []
+    for n, dt in ((4, 0.02), (8, 0.01)):
+        c = _quasi_case(sol, n, dt)
+        for _ in range(int(round(0.1 / dt))):
+            c.step(dirichlet=sol.set_dirichlet)
+        e = mms.error_norms(c, sol, c.t)
+        e["delta"] = np.abs(c.delta - sol.delta(c.t)).max()
+        assert np.allclose(c.force(), sol.k * c.delta, atol=1e-10)
+        errs.append(e)
+    assert errs[0]["delta"] / errs[1]["delta"] > 3.5, errs
+    assert errs[0]["u_l2"] / errs[1]["u_l2"] > 3.5, errs
