@@ -591,6 +591,445 @@ __global__ void __launch_bounds__(WINDOW_THREADS) window_kernel(FT ft, const int
   }
 }
 
+// ---- 128-column blocks of large fronts, windowed pivoting (FP32) -----------------
+// One CTA factors the block's nb x nb diagonal part (nb = min(128, p - k2)) in
+// shared memory, one 32-column window at a time:
+//   window  one warp: LU with partial pivoting inside the 32 x 32 window, the
+//           rows in registers (no interchanges: rows stay in place, a done
+//           mask marks the pivotal ones; a row shifts left by one column per
+//           step so that the current column is always register 0, and the
+//           pivot row is broadcast by shuffles).
+//   perm    the window rows put in pivot order on every block column.
+//   inv     U11^{-1} and L11^{-1} of the window (one warp each, by
+//           substitution): the diagonal blocks of the block's inverses.
+//   panel   L21 = A21 U11^{-1} for the block rows below the window and
+//           U12 = L11^{-1} P A12 for the block columns right of it, 4 x 4
+//           register tiles.
+//   rank    A22 -= L21 U12 for the rest of the block, 4 x 4 register tiles.
+// It then completes U^{-1} and L^{-1} of the whole block (off-diagonal 32 x 32
+// blocks by distance from the diagonal) and writes (I - U^{-1}) and
+// (I - L^{-1}) as hi/lo TF32 operand images, so that the tensor-core pipeline
+// (C -= A B) turns the block's rows below into L21 = A21 - A21 (I - U^{-1}) and
+// its columns to the right into U12 = P A12 - (I - L^{-1}) P A12.
+// Item: {f, k2, a_blk, b_blk, nchunks} (image blocks of (I - L^{-1}) and
+// (I - U^{-1}); -1 when the front has no rows below the block).  A launch runs
+// 4 nn_max threads per CTA (nn = 32 nchunks) with three nn_max x (nn_max + 1)
+// matrices in shared memory, so blocks of small fronts share an SM.
+constexpr int BLK_MAX_THREADS = 4 * OUTER_NB;
+
+__host__ __device__ constexpr size_t blk_smem_bytes(int nn_max) {
+  return 3 * sizeof(float) * (size_t)nn_max * (nn_max + 1);
+}
+
+// operand image of a 128 x 128 matrix given by val(r, k) (r: M or N index,
+// k: K index), chunks blk .. blk + nch - 1 (layout of tc_split_kernel)
+template <class Val>
+__device__ void write_operand_image(unsigned char* img, int blk, int nch, Val val) {
+  for (int e = threadIdx.x; e < nch * OUTER_NB * (tcp::KC / 4); e += blockDim.x) {
+    const int ch = e / (OUTER_NB * (tcp::KC / 4)), rem = e % (OUTER_NB * (tcp::KC / 4));
+    const int r = rem % OUTER_NB, g = rem / OUTER_NB;
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float v = val(r, ch * tcp::KC + 4 * g + j);
+      h[j] = tc::to_tf32(v);
+      l[j] = tc::to_tf32(v - __uint_as_float(h[j]));
+    }
+    unsigned char* out = img + (int64_t)(blk + ch) * tcp::CHUNK_BYTES;
+    const int o = g * tcp::KCORE_STRIDE + (r >> 3) * tcp::CORE_BYTES + (r & 7) * 16;
+    *reinterpret_cast<uint4*>(out + o) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(out + tcp::OPERAND_BYTES + o) = make_uint4(l[0], l[1], l[2], l[3]);
+  }
+}
+
+// 4 x 4 register tile of sum_{t < K} A(ia[a], ka + t) B(kb + t, jb[b]) over
+// row-major shared matrices with leading dimension ld
+__device__ __forceinline__ void blk_tile(const float* __restrict__ A, const float* __restrict__ B, int ld,
+                                         const int (&ia)[4], int ka, int kb, const int (&jb)[4], int K,
+                                         float (&acc)[4][4]) {
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+#pragma unroll 4
+  for (int t = 0; t < K; ++t) {
+    float x[4], y[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) x[a] = A[ia[a] * ld + ka + t];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) y[b] = B[(kb + t) * ld + jb[b]];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] += x[a] * y[b];
+  }
+}
+
+// hardware reciprocal (about 1 ulp); the multipliers of the FP32 window LU,
+// whose rounding the FP64 refinement absorbs
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// One warp: LU with partial pivoting inside the w x w window P (row-major,
+// leading dimension ld).  Lane r keeps row r in registers, shifted left by
+// one column per step so that x[0] is always the current column.  At step jj
+// the candidates are the rows not pivotal yet; the pivot row stores its
+// registers (U(jj, jj + c) = x[c]) into Ub[jj], every lane reads them back as
+// a broadcast, and the other candidates are eliminated (multiplier into
+// Lb[row][jj]).  Rows stay in place; the caller writes the window in pivot
+// order: row s = original row s_order[s], its multipliers left of column s and
+// its U part from column s on.
+__device__ void window_lu(float* P, int ld, int w, float (*Ub)[PANEL_NB + 4], float (*Lb)[PANEL_NB + 1],
+                          int* s_order, int32_t* stats) {
+  const int lane = threadIdx.x & 31;
+  float x[PANEL_NB];
+#pragma unroll
+  for (int c = 0; c < PANEL_NB; ++c) x[c] = (lane < w && c < w) ? P[lane * ld + c] : 0.f;
+  float bmax = 0.f;   // largest entry of the window, the perturbation scale
+#pragma unroll
+  for (int c = 0; c < PANEL_NB; ++c) bmax = fmaxf(bmax, fabsf(x[c]));
+  for (int o = 16; o > 0; o >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+  uint32_t done = 0;
+  int perturbed = 0;
+  for (int jj = 0; jj < w; ++jj) {
+    const bool cand = lane < w && !((done >> lane) & 1u);
+    const uint32_t key = cand ? ((mag_bits(x[0]) & ~31u) | (31u - lane)) : 0u;
+    const uint32_t best = __reduce_max_sync(0xffffffffu, key);
+    const bool empty = (best & ~31u) == 0u;   // no nonzero candidate: perturbed pivot
+    const int pr = empty ? __ffs(~done) - 1 : (int)(31u - (best & 31u));
+    perturbed += empty;
+    if (lane == pr) {
+      if (empty) x[0] = sqrtf(FLT_EPSILON) * (bmax > 0.f ? bmax : 1.f);
+      float4* dst = reinterpret_cast<float4*>(Ub[jj]);
+#pragma unroll
+      for (int q = 0; q < PANEL_NB / 4; ++q) dst[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+    }
+    s_order[jj] = pr;   // (every lane, the same value)
+    __syncwarp();
+    float u[PANEL_NB];
+    const float4* src = reinterpret_cast<const float4*>(Ub[jj]);
+#pragma unroll
+    for (int q = 0; q < PANEL_NB / 4; ++q) {
+      const float4 t = src[q];
+      u[4 * q] = t.x;
+      u[4 * q + 1] = t.y;
+      u[4 * q + 2] = t.z;
+      u[4 * q + 3] = t.w;
+    }
+    const bool elim = cand && lane != pr;
+    // (rows that are pivotal shift too: their U part is in Ub already)
+    const float l = elim ? x[0] * rcp_approx(u[0]) : 0.f;
+    Lb[lane][jj] = l;   // (0 for the other rows: never read)
+#pragma unroll
+    for (int c = 1; c < PANEL_NB; ++c) x[c - 1] = x[c] - l * u[c];
+    x[PANEL_NB - 1] = 0.f;   // (beyond the window)
+    done |= 1u << pr;
+  }
+  if (perturbed && lane == 0) atomicAdd(&stats[0], perturbed);
+}
+
+// U^{-1} into V and L^{-1} into W for the 32 x 32 diagonal block at o: the
+// 8 x 8 diagonal blocks by substitution (one thread per column, registers),
+// then the off-diagonal 8 x 8 blocks by distance from the diagonal (as for the
+// 32 x 32 blocks below); the other triangles are zeroed (the products read
+// whole blocks).  Every thread of the CTA takes part (blockDim >= 128).
+__device__ void diag_inverse(const float* __restrict__ D, float* __restrict__ V, float* __restrict__ W, int ld,
+                             int o) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  for (int e = tid; e < PANEL_NB * PANEL_NB; e += nthr) {
+    const int i = e & 31, j = e >> 5;
+    if (i > j) V[(o + i) * ld + o + j] = 0.f;
+    if (i < j) W[(o + i) * ld + o + j] = 0.f;
+  }
+  if (tid < 64) {
+    const int task = tid >> 3, j = tid & 7, ob = o + 8 * (task & 3);
+    float y[8];
+    if (task < 4) {   // column j of U_bb^{-1}
+#pragma unroll
+      for (int i = 7; i >= 0; --i) {
+        float s0 = i == j ? 1.f : 0.f;
+#pragma unroll
+        for (int t = i + 1; t < 8; ++t) s0 -= D[(ob + i) * ld + ob + t] * y[t];
+        y[i] = i <= j ? s0 * rcp_approx(D[(ob + i) * ld + ob + i]) : 0.f;
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (i <= j) V[(ob + i) * ld + ob + j] = y[i];
+    } else {          // column j of L_bb^{-1}
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        float s0 = i == j ? 1.f : 0.f;
+#pragma unroll
+        for (int t = 0; t < i; ++t) s0 -= D[(ob + i) * ld + ob + t] * y[t];
+        y[i] = i >= j ? s0 : 0.f;
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (i >= j) W[(ob + i) * ld + ob + j] = y[i];
+    }
+  }
+  __syncthreads();
+  for (int d = 1; d < 4; ++d) {
+    const int nblk = 4 - d, nt = 2 * nblk * 64;   // outputs of this distance (<= 384)
+    float r[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {   // sums, straight into the target blocks
+      const int e = tid + q * nthr;
+      if (e < nt) {
+        const int task = e >> 6, i = e & 7, j = (e >> 3) & 7;
+        const bool up = task < nblk;
+        const int I = up ? task : task - nblk, J = I + d;
+        float s0 = 0.f;
+        if (up) {
+          for (int t = 8 * (I + 1); t < 8 * (J + 1); ++t) s0 += D[(o + 8 * I + i) * ld + o + t] * V[(o + t) * ld + o + 8 * J + j];
+          V[(o + 8 * I + i) * ld + o + 8 * J + j] = s0;
+        } else {
+          for (int t = 8 * I; t < 8 * J; ++t) s0 += D[(o + 8 * J + i) * ld + o + t] * W[(o + t) * ld + o + 8 * I + j];
+          W[(o + 8 * J + i) * ld + o + 8 * I + j] = s0;
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {   // products with the diagonal inverses
+      const int e = tid + q * nthr;
+      if (e < nt) {
+        const int task = e >> 6, i = e & 7, j = (e >> 3) & 7;
+        const bool up = task < nblk;
+        const int I = up ? task : task - nblk, J = I + d;
+        float s0 = 0.f;
+        if (up) {
+#pragma unroll
+          for (int t = 0; t < 8; ++t) s0 += V[(o + 8 * I + i) * ld + o + 8 * I + t] * V[(o + 8 * I + t) * ld + o + 8 * J + j];
+        } else {
+#pragma unroll
+          for (int t = 0; t < 8; ++t) s0 += W[(o + 8 * J + i) * ld + o + 8 * J + t] * W[(o + 8 * J + t) * ld + o + 8 * I + j];
+        }
+        r[q] = -s0;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int e = tid + q * nthr;
+      if (e < nt) {
+        const int task = e >> 6, i = e & 7, j = (e >> 3) & 7;
+        const bool up = task < nblk;
+        const int I = up ? task : task - nblk, J = I + d;
+        if (up) V[(o + 8 * I + i) * ld + o + 8 * J + j] = r[q];
+        else W[(o + 8 * J + i) * ld + o + 8 * I + j] = r[q];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// off-diagonal 32 x 32 blocks of V = U^{-1} and W = L^{-1} (diagonal blocks
+// in place), by distance d = J - I from the diagonal, all of one distance at
+// once (they need only blocks nearer the diagonal):
+//   U^{-1}_IJ = -U_II^{-1} sum_{K=I+1..J} U_IK U^{-1}_KJ
+//   L^{-1}_JI = -L_JJ^{-1} sum_{K=I..J-1} L_JK L^{-1}_KI
+// The sums go straight into the target block (no task of this distance reads
+// it); the products with the diagonal inverses are held in registers until
+// every tile has read its sums.  64 tiles of 4 x 4 per block, at most
+// 2 (nbk - 1) blocks: one tile per thread.
+__device__ void offdiag_inverses(const float* __restrict__ D, float* __restrict__ V, float* __restrict__ W, int ld,
+                                 int nbk) {
+  for (int d = 1; d < nbk; ++d) {
+    const int nt = 2 * (nbk - d) * 64;
+    const int tile = threadIdx.x;
+    const bool act = tile < nt;
+    const int task = tile >> 6, ti = tile & 7, tj = (tile >> 3) & 7;
+    const bool up = task < nbk - d;
+    const int I = up ? task : task - (nbk - d), J = I + d;
+    float* X = up ? V : W;
+    int ia[4], jb[4];
+    float acc[4][4];
+    if (act) {
+      const int r0 = up ? 32 * I : 32 * J, c0 = up ? 32 * J : 32 * I;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        ia[a] = r0 + ti + 8 * a;
+        jb[a] = c0 + tj + 8 * a;
+      }
+      if (up) blk_tile(D, V, ld, ia, 32 * (I + 1), 32 * (I + 1), jb, 32 * d, acc);
+      else blk_tile(D, W, ld, ia, 32 * I, 32 * I, jb, 32 * d, acc);
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) X[ia[a] * ld + jb[b]] = acc[a][b];
+    }
+    __syncthreads();
+    if (act) {
+      const int dg = up ? 32 * I : 32 * J;   // -U_II^{-1} sums(I, J) / -L_JJ^{-1} sums(J, I)
+      blk_tile(X, X, ld, ia, dg, dg, jb, 32, acc);
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) X[ia[a] * ld + jb[b]] = -acc[a][b];
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(BLK_MAX_THREADS, 1) block_lu_kernel(FT ft, const int32_t* work, float* pool,
+                                                                      int32_t* perm, int32_t* stats, float thresh,
+                                                                      unsigned char* img, int nn_max) {
+  extern __shared__ __align__(16) float blk_sm[];
+  const int ld = nn_max + 1;
+  float* __restrict__ D = blk_sm;
+  float* __restrict__ V = blk_sm + nn_max * ld;
+  float* __restrict__ W = V + nn_max * ld;
+  __shared__ int s_order[PANEL_NB];
+  __shared__ __align__(16) float s_ub[PANEL_NB][PANEL_NB + 4];   // window pivot rows (16-byte rows)
+  __shared__ float s_lb[PANEL_NB][PANEL_NB + 1];                 // window multipliers by original row
+  const int32_t* it = work + WORK_STRIDE * blockIdx.x;
+  const int f = it[0], k2 = it[1], a_blk = it[2], b_blk = it[3], nch = it[4];
+  const int m = ft.m[f], p = ft.p[f];
+  const int nb = min(OUTER_NB, p - k2), nn = 32 * nch;   // nb <= nn <= nn_max
+  float* F = pool + ft.off[f] + (int64_t)k2 * m + k2;
+  const int tid = threadIdx.x, warp = tid >> 5, nthr = blockDim.x;
+  // the nn x nn block, identity outside nb x nb; column j of the front is
+  // contiguous, so consecutive threads take consecutive rows (8 loads in flight)
+  const int jstep = nthr / nn, li = tid % nn;   // threads at or beyond jstep nn take no part
+  for (int jb = tid < jstep * nn ? tid / nn : nn; jb < nn; jb += 8 * jstep) {
+    float v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int j = jb + q * jstep;
+      v[q] = (li < nb && j < nb) ? F[(int64_t)j * m + li] : (li == j ? 1.f : 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int j = jb + q * jstep;
+      if (j < nn) D[li * ld + j] = v[q];
+    }
+  }
+  __syncthreads();
+  const int pc = tid & 127, pr0 = tid >> 7, prs = nthr >> 7;   // (row, column) pattern of the row moves
+  bool big = false;
+  for (int j0 = 0; j0 < nb; j0 += PANEL_NB) {
+    const int w = min(PANEL_NB, nb - j0), r0 = j0 + w, cr = nb - r0;
+    if (warp == 0) window_lu(D + j0 * ld + j0, ld, w, s_ub, s_lb, s_order, stats);
+    __syncthreads();
+    for (int e = tid; e < w * PANEL_NB; e += nthr) {   // the window in pivot order
+      const int s = e >> 5, c = e & 31;
+      if (c < w) D[(j0 + s) * ld + j0 + c] = c < s ? s_lb[s_order[s]][c] : s_ub[s][c - s];
+    }
+    if (nb == w) __syncthreads();   // (uniform; otherwise the row moves below end with one)
+    // the composed permutation (new row s of the window holds old row
+    // s_order[s]; windowed pivoting keeps no interchange sequence), and the
+    // window rows in pivot order on the other block columns (rows j0.. of V
+    // hold them meanwhile: V's diagonal block there is written only afterwards)
+    if (tid < w) perm[ft.piv_off[f] + k2 + j0 + tid] = k2 + j0 + s_order[tid];
+    if (nb > w) {   // (uniform)
+      const bool col = pc < nb && (pc < j0 || pc >= j0 + w);
+      if (col)
+        for (int s = pr0; s < w; s += prs) V[(j0 + s) * ld + pc] = D[(j0 + s_order[s]) * ld + pc];
+      __syncthreads();
+      if (col)
+        for (int s = pr0; s < w; s += prs) D[(j0 + s) * ld + pc] = V[(j0 + s) * ld + pc];
+      __syncthreads();
+    }
+    diag_inverse(D, V, W, ld, j0);
+    __syncthreads();
+    if (cr > 0) {
+      // L21 = A21 U11^{-1} (rows r0.., window columns) and U12 = L11^{-1} P A12
+      // (window rows, columns r0..): one 4 x 4 tile per thread, written after
+      // every tile has read its operands
+      const int RT = (cr + 3) >> 2, nl = RT * 8;
+      const int t = tid;
+      const bool act = t < 2 * nl;
+      const bool lower = t < nl;
+      int ia[4], jb[4];
+      float acc[4][4];
+      if (act) {
+        const int u = lower ? t : t - nl, ta = lower ? u % RT : u & 7, tb = lower ? u / RT : u >> 3;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          ia[a] = lower ? r0 + min(ta + RT * a, cr - 1) : j0 + ta + 8 * a;
+          jb[a] = lower ? j0 + tb + 8 * a : r0 + min(tb + RT * a, cr - 1);
+        }
+        if (lower) blk_tile(D, V, ld, ia, j0, j0, jb, w, acc);
+        else blk_tile(W, D, ld, ia, j0, j0, jb, w, acc);
+      }
+      __syncthreads();
+      if (act) {
+        const int u = lower ? t : t - nl, ta = lower ? u % RT : u & 7, tb = lower ? u / RT : u >> 3;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const bool ok = lower ? (ta + RT * a < cr && tb + 8 * b < w) : (ta + 8 * a < w && tb + RT * b < cr);
+            if (ok) {
+              D[ia[a] * ld + jb[b]] = acc[a][b];
+              // a multiplier above 1/threshold: the window pivot missed the
+              // threshold test that pivoting over all fully summed rows would apply
+              big = big || (lower && fabsf(acc[a][b]) * thresh > 1.f);
+            }
+          }
+      }
+      __syncthreads();
+      // rank-w update of the rest of the block: rows and columns r0 .. nb - 1
+      for (int q = tid; q < RT * RT; q += nthr) {
+        const int ti = q % RT, tj = q / RT;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          ia[a] = r0 + min(ti + RT * a, cr - 1);
+          jb[a] = r0 + min(tj + RT * a, cr - 1);
+        }
+        blk_tile(D, D, ld, ia, j0, j0, jb, w, acc);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b)
+            if (ti + RT * a < cr && tj + RT * b < cr) D[ia[a] * ld + jb[b]] -= acc[a][b];
+      }
+      __syncthreads();
+    }
+  }
+  if (__syncthreads_or(big) && tid == 0) atomicAdd(&stats[1], 1);
+  if (li < nb && tid < jstep * nn)
+    for (int j = tid / nn; j < nb; j += jstep) F[(int64_t)j * m + li] = D[li * ld + j];
+  if (a_blk < 0) return;   // (uniform) no rows below the block: no inverses needed
+  offdiag_inverses(D, V, W, ld, nch);
+  // B operand (K x N: row k, column n of I - U^{-1}), A operand (M x K: row i,
+  // column k of I - L^{-1}); zero outside nn x nn and outside the triangles
+  write_operand_image(img, b_blk, nch, [&](int n, int k) {
+    return (n < nn && k <= n) ? (k == n ? 1.f : 0.f) - V[k * ld + n] : 0.f;
+  });
+  write_operand_image(img, a_blk, nch, [&](int i, int k) { return (i < nn && i > k) ? -W[i * ld + k] : 0.f; });
+}
+
+// the blocks' row permutations (one per 32-row window) on the front columns
+// outside the block; item {f, k2, c0}: columns c0 .. c0 + 255
+__global__ void __launch_bounds__(256) block_perm_kernel(FT ft, const int32_t* work, float* pool,
+                                                         const int32_t* perm) {
+  __shared__ int s_src[OUTER_NB];
+  const int32_t* it = work + WORK_STRIDE * blockIdx.x;
+  const int f = it[0], k2 = it[1], c = it[2] + threadIdx.x;
+  const int m = ft.m[f], p = ft.p[f];
+  const int nb = min(OUTER_NB, p - k2);
+  if (threadIdx.x < nb) s_src[threadIdx.x] = perm[ft.piv_off[f] + k2 + threadIdx.x] - k2;
+  __syncthreads();
+  if (c >= m || (c >= k2 && c < k2 + nb)) return;
+  float* col = pool + ft.off[f] + (int64_t)c * m + k2;
+  for (int j0 = 0; j0 < nb; j0 += PANEL_NB) {   // the permutations stay inside their windows
+    float x[PANEL_NB];
+#pragma unroll
+    for (int i = 0; i < PANEL_NB; ++i) x[i] = j0 + i < nb ? col[s_src[j0 + i]] : 0.f;
+#pragma unroll
+    for (int i = 0; i < PANEL_NB; ++i)
+      if (j0 + i < nb) col[j0 + i] = x[i];
+  }
+}
+
 // row interchanges of a cluster panel applied to the columns outside it
 template <class T>
 __global__ void laswp_kernel(FT ft, const int32_t* work, int k, T* pool, const int32_t* piv) {
@@ -1039,7 +1478,11 @@ __global__ void __launch_bounds__(solve_threads_max<T>(), 1) bwd_tri_kernel(FT f
 // kernel attributes (dynamic shared memory limits) of one precision
 template <class T>
 static void set_kernel_attributes() {
-  if constexpr (std::is_same<T, float>::value) tcp::prepare();
+  if constexpr (std::is_same<T, float>::value) {
+    tcp::prepare();
+    VIV_CUDA(cudaFuncSetAttribute(block_lu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)blk_smem_bytes(OUTER_NB)));
+  }
   VIV_CUDA(cudaFuncSetAttribute(panel_smem_kernel<T, 1, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 PANEL_SMEM_BYTES));
   VIV_CUDA(cudaFuncSetAttribute(panel_smem_kernel<T, PANEL_CLUSTER, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1077,8 +1520,8 @@ void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* front
     prof_level(L.level);
     const int32_t* w = work + (int64_t)WORK_STRIDE * L.item0;
     const unsigned grid = (unsigned)L.count;
-    static const int kk[11] = {K_FRONT_ASM, K_PANEL,  K_TRSM,   K_GEMM,  K_PANEL,  K_TRSM,
-                               K_PANEL,     K_TCGEMM, K_PANEL, K_TRSM, K_TCSPLIT};
+    static const int kk[13] = {K_FRONT_ASM, K_PANEL,  K_TRSM,   K_GEMM,    K_PANEL, K_TRSM, K_PANEL,
+                               K_TCGEMM,    K_PANEL, K_TRSM, K_TCSPLIT, K_PANEL, K_TRSM};
     Launched LL(kk[L.kind], s);
     switch (L.kind) {
       case L_ASSEMBLE:
@@ -1096,8 +1539,16 @@ void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* front
       case L_GEMM:
         gemm_kernel<T><<<grid, 256, 0, s>>>(ft, w, fronts, piv, perm, stats);
         break;
+      case L_BLOCK_LU:   // aux: the launch's largest block width nn (a multiple of 32)
+        if constexpr (std::is_same<T, float>::value)
+          block_lu_kernel<<<grid, 4 * L.aux, blk_smem_bytes(L.aux), s>>>(ft, w, fronts, perm, stats,
+                                                                        (float)threshold, tc_img, L.aux);
+        break;
+      case L_BLOCK_PERM:
+        if constexpr (std::is_same<T, float>::value) block_perm_kernel<<<grid, 256, 0, s>>>(ft, w, fronts, perm);
+        break;
       case L_TC_SPLIT:
-        if constexpr (std::is_same<T, float>::value) tcp::split_launch(w, (int)L.count, fronts, ft.off, ft.m, tc_img, s);
+        if constexpr (std::is_same<T, float>::value) tcp::split_launch(w, (int)L.count, fronts, ft.off, ft.m, tc_img, stats, (float)threshold, s);
         break;
       case L_TC_GEMM:
         if constexpr (std::is_same<T, float>::value)

@@ -660,7 +660,8 @@ void build_mesh(Mesh& m, const vivMeshDesc* d) {
           const int f = m.level_fronts[q];
           const int be = std::min(k2 + OUTER_NB, m.f_p[f]);
           if (m.f_p[f] <= k2 || be >= m.f_m[f]) continue;
-          const int64_t need = 2 * (int64_t)((m.f_m[f] - be + 127) / 128) * ((be - k2 + 31) / 32);
+          // (+ 2 chunks of each K slice for the inverse triangles of the block path)
+          const int64_t need = 2 * (int64_t)((m.f_m[f] - be + 127) / 128 + 1) * ((be - k2 + 31) / 32);
           sum += need;
           single = std::max(single, need);
         }
@@ -670,6 +671,130 @@ void build_mesh(Mesh& m, const vivMeshDesc* d) {
     m.tc_img_chunks = std::min(bound, std::max(TC_IMG_MAX_CHUNKS, single));
   }
   build_schedule(m, BIG_FRONT);
+}
+
+// The 128-column block at pivot k2 of every large FP32 front of level l with
+// windowed pivoting: block LU (one CTA per front: the diagonal block, its row
+// permutations and the inverse triangles as operand images), the block rows'
+// permutation on the other columns, then on the tensor cores L21 = A21 U11^-1
+// and U12 = L11^-1 P A12, and the Schur update A22 -= L21 U12.  Fronts are
+// grouped so that a group's operand images fit the case's image buffer:
+// per front [A21 row blocks][P A12 column blocks][(I - L^-1)][(I - U^-1)],
+// the L21 / U12 split reusing the first two.
+// fronts of the block path: large, with more than one pivot window (a single
+// window is factored faster by the per-panel kernels)
+static bool block_front(const Mesh& m, int f, int big_front) {
+  return m.f_m[f] >= big_front && m.f_p[f] > PANEL_NB;
+}
+
+template <class Push, class Open, class Close, class Items>
+static void emit_blocks(Mesh& m, int l, int k2, int big_front, Push& push, Open& open, Close& close, Items& items) {
+  std::vector<int> fr;
+  for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
+    const int f = m.level_fronts[q];
+    if (block_front(m, f, big_front) && m.f_p[f] > k2) fr.push_back(f);
+  }
+  auto geom = [&](int f, int& be, int& nb, int& nch, int& nbk) {
+    be = std::min(k2 + OUTER_NB, m.f_p[f]);
+    nb = be - k2;
+    nch = (nb + 31) / 32;
+    nbk = (m.f_m[f] - be + 127) / 128;
+  };
+  size_t g0 = 0;
+  while (g0 < fr.size()) {
+    // a group within the image capacity
+    size_t g1 = g0;
+    int64_t chunks = 0;
+    while (g1 < fr.size()) {
+      int be, nb, nch, nbk;
+      geom(fr[g1], be, nb, nch, nbk);
+      const int64_t need = nbk > 0 ? 2 * (int64_t)(nbk + 1) * nch : 0;
+      if (g1 > g0 && chunks + need > m.tc_img_chunks) break;
+      chunks += need;
+      ++g1;
+    }
+    VIV_CHECK(chunks <= m.tc_img_chunks, VIV_ERR_ARG, "tensor-core operand images exceed the case buffer");
+    std::vector<int64_t> a21(g1 - g0), pa12(g1 - g0), ainv(g1 - g0), binv(g1 - g0);
+    int64_t blk = 0;
+    for (size_t g = g0; g < g1; ++g) {
+      int be, nb, nch, nbk;
+      geom(fr[g], be, nb, nch, nbk);
+      if (nbk == 0) {
+        a21[g - g0] = pa12[g - g0] = ainv[g - g0] = binv[g - g0] = -1;
+        continue;
+      }
+      a21[g - g0] = blk;
+      blk += (int64_t)nbk * nch;
+      pa12[g - g0] = blk;
+      blk += (int64_t)nbk * nch;
+      ainv[g - g0] = blk;
+      blk += nch;
+      binv[g - g0] = blk;
+      blk += nch;
+    }
+    auto L1 = open(L_BLOCK_LU, l, k2);
+    for (size_t g = g0; g < g1; ++g) {
+      int be, nb, nch, nbk;
+      geom(fr[g], be, nb, nch, nbk);
+      push({fr[g], k2, (int)ainv[g - g0], (int)binv[g - g0], nch});
+      L1.aux = std::max(L1.aux, 32 * nch);   // CTA size and shared memory of the launch
+    }
+    close(L1);
+    auto L2 = open(L_BLOCK_PERM, l, k2);
+    for (size_t g = g0; g < g1; ++g) {
+      const int f = fr[g];
+      int be, nb, nch, nbk;
+      geom(f, be, nb, nch, nbk);
+      if (m.f_m[f] > nb)
+        for (int c0 = 0; c0 < m.f_m[f]; c0 += 256) push({f, k2, c0});
+    }
+    close(L2);
+    // splits of A21 / P A12 (first) and of L21 / U12 (after the first update)
+    auto split = [&](int check) {
+      auto S = open(L_TC_SPLIT, l, k2);
+      for (size_t g = g0; g < g1; ++g) {
+        const int f = fr[g], mm = m.f_m[f];
+        int be, nb, nch, nbk;
+        geom(f, be, nb, nch, nbk);
+        for (int i = 0; i < nbk; ++i)
+          for (int ch = 0; ch < nch; ++ch)
+            push({f, be + 128 * i, 0, k2 + 32 * ch, std::min(32, nb - 32 * ch), (int)(a21[g - g0] + i * nch + ch), mm,
+                  check});
+        for (int j = 0; j < nbk; ++j)
+          for (int ch = 0; ch < nch; ++ch)
+            push({f, be + 128 * j, 1, k2 + 32 * ch, std::min(32, nb - 32 * ch), (int)(pa12[g - g0] + j * nch + ch), mm});
+      }
+      close(S);
+    };
+    split(0);
+    auto T1 = open(L_TC_GEMM, l, k2);   // L21 = A21 - A21 (I - U^-1), U12 = P A12 - (I - L^-1) P A12
+    for (size_t g = g0; g < g1; ++g) {
+      const int f = fr[g], mm = m.f_m[f];
+      int be, nb, nch, nbk;
+      geom(f, be, nb, nch, nbk);
+      for (int i = 0; i < nbk; ++i)
+        push({f, be + 128 * i, k2, mm, be, (int)(a21[g - g0] + i * nch), (int)binv[g - g0], nch});
+      for (int j = 0; j < nbk; ++j)
+        push({f, k2, be + 128 * j, be, mm, (int)ainv[g - g0], (int)(pa12[g - g0] + j * nch), nch});
+    }
+    close(T1);
+    split(1);   // (and the threshold test of the multipliers L21)
+    auto T2 = open(L_TC_GEMM, l, k2);   // A22 -= L21 U12
+    for (size_t g = g0; g < g1; ++g) {
+      const int f = fr[g], mm = m.f_m[f];
+      int be, nb, nch, nbk;
+      geom(f, be, nb, nch, nbk);
+      for (int i = 0; i < nbk; ++i)
+        for (int j = 0; j < nbk; ++j)
+          push({f, be + 128 * i, be + 128 * j, mm, mm, (int)(a21[g - g0] + i * nch), (int)(pa12[g - g0] + j * nch),
+                nch});
+      const double rest = (double)(mm - be);
+      m.window_tc_flops += 4.0 * nb * nb * rest + 2.0 * rest * rest * nb;
+    }
+    close(T2);
+    (void)items;
+    g0 = g1;
+  }
 }
 
 // Launch schedules of the numeric factorisation for a large-front threshold
@@ -684,6 +809,7 @@ void build_schedule(Mesh& m, int big_front) {
   m.work.clear();
   m.gemm_flops = m.trsm_flops = m.panel_flops = m.outer_flops = 0;
   m.tc_split_chunks = m.tc_tiles = 0;
+  m.window_tc_flops = 0;
   auto push = [&](std::initializer_list<int> v) {
     int n = 0;
     for (int x : v) {
@@ -719,6 +845,11 @@ void build_schedule(Mesh& m, int big_front) {
     auto diag_fused = [&](int f, int k) {
       return window && k > 0 && k < m.f_p[f] && (m.f_m[f] < big_front || k % OUTER_NB != 0);
     };
+    // FP32 fronts with windowed pivoting and 128-column blocks: each block is
+    // factored by one CTA (block_lu_kernel) and its L21 / U12 and the Schur
+    // update run on the tensor cores; these fronts take no per-panel launches
+    const bool blockpath = window && prec == 0 && m.block_lu;
+    auto newblk = [&](int f) { return blockpath && block_front(m, f, big_front); };
     for (int l = 0; l < m.n_levels; ++l) {
       Launch L = open(L_ASSEMBLE, l, 0);
       L.aux = m.level_maxm[l] >= 1024 ? 512 : 256;   // assembly threads per item
@@ -733,6 +864,7 @@ void build_schedule(Mesh& m, int big_front) {
         const int k2 = (k / OUTER_NB) * OUTER_NB;
         auto big = [&](int f) { return m.f_m[f] >= big_front; };
         auto block_end = [&](int f) { return std::min(k2 + OUTER_NB, m.f_p[f]); };
+        if (blockpath && k == k2) emit_blocks(m, l, k2, big_front, push, open, close, items);
         // panel kind of a front: 0 one CTA, 1 cluster, 2 global-memory fallback
         auto kind = [&](int f) {
           const int rows = m.f_m[f] - k;
@@ -747,13 +879,13 @@ void build_schedule(Mesh& m, int big_front) {
           Launch D = open(L_DIAG, l, k);
           for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
             int f = m.level_fronts[q];
-            if (m.f_p[f] > k && !diag_fused(f, k)) push({f});
+            if (m.f_p[f] > k && !diag_fused(f, k) && !newblk(f)) push({f});
           }
           close(D);
           Launch W = open(L_WINDOW, l, k);
           for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
             int f = m.level_fronts[q];
-            if (m.f_p[f] <= k) continue;
+            if (m.f_p[f] <= k || newblk(f)) continue;
             const int nbe = std::min(PANEL_NB, m.f_p[f] - k);
             // U12 for every column right of the panel, the outer columns of a
             // large front included (their in-block rows are updated below)
@@ -812,7 +944,7 @@ void build_schedule(Mesh& m, int big_front) {
         Launch G = open(L_GEMM, l, k);
         for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
           int f = m.level_fronts[q];
-          if (m.f_p[f] <= k) continue;
+          if (m.f_p[f] <= k || newblk(f)) continue;
           const int nbe = std::min(PANEL_NB, m.f_p[f] - k);
           const int r0 = k + nbe;
           const int c_end = big(f) ? block_end(f) : m.f_m[f];
@@ -825,7 +957,7 @@ void build_schedule(Mesh& m, int big_front) {
         std::vector<int> done;
         for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
           int f = m.level_fronts[q];
-          if (m.f_p[f] <= k || !big(f)) continue;
+          if (m.f_p[f] <= k || !big(f) || newblk(f)) continue;
           const int nbe = std::min(PANEL_NB, m.f_p[f] - k);
           if (k + nbe == block_end(f) && block_end(f) < m.f_m[f]) done.push_back(f);
         }
@@ -902,6 +1034,7 @@ void build_schedule(Mesh& m, int big_front) {
               m.gemm_flops += 2.0 * rest * rest * (be - k2);
               m.outer_flops += 2.0 * rest * rest * (be - k2);
             }
+            if (window) m.window_tc_flops += 2.0 * rest * rest * (be - k2);
           }
           flush();
         } else {

@@ -19,9 +19,11 @@ __global__ void __launch_bounds__(SPLIT_THREADS) tc_split_kernel(const int32_t* 
                                                                  const float* __restrict__ pool,
                                                                  const int64_t* __restrict__ off,
                                                                  const int32_t* __restrict__ ld,
-                                                                 unsigned char* __restrict__ img) {
+                                                                 unsigned char* __restrict__ img,
+                                                                 int* __restrict__ stats, float thresh) {
   const int32_t* it = items + (int64_t)ITEM * blockIdx.x;
   const int f = it[0], start = it[1], kind = it[2], k0 = it[3], klen = it[4], blk = it[5], limit = it[6];
+  const int check = it[7];
   const float* base = pool + off[f];
   const int64_t L = ld[f];
   unsigned char* out = img + (int64_t)blk * CHUNK_BYTES;
@@ -44,6 +46,14 @@ __global__ void __launch_bounds__(SPLIT_THREADS) tc_split_kernel(const int32_t* 
       const int64_t e = kind == 0 ? (int64_t)(k0 + k) * L + start + r : (int64_t)(start + r) * L + k0 + k;
       v[t][j] = ok ? __ldg(base + e) : 0.f;
     }
+  }
+  if (check) {   // (uniform per CTA)
+    bool big = false;
+#pragma unroll
+    for (int t = 0; t < PER; ++t)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) big = big || fabsf(v[t][j]) * thresh > 1.f;
+    if (__syncthreads_or(big) && threadIdx.x == 0) atomicAdd(&stats[1], 1);
   }
 #pragma unroll
   for (int t = 0; t < PER; ++t) {
@@ -295,8 +305,9 @@ void prepare() {
 }
 
 void split_launch(const int32_t* items, int n_items, const float* pool, const int64_t* off, const int32_t* ld,
-                  unsigned char* img, cudaStream_t s) {
-  if (n_items > 0) tc_split_kernel<<<(unsigned)n_items, SPLIT_THREADS, 0, s>>>(items, pool, off, ld, img);
+                  unsigned char* img, int* stats, float thresh, cudaStream_t s) {
+  if (n_items > 0)
+    tc_split_kernel<<<(unsigned)n_items, SPLIT_THREADS, 0, s>>>(items, pool, off, ld, img, stats, thresh);
 }
 
 // persistent: one CTA per SM at most (the ring and the two accumulators fill
@@ -373,7 +384,7 @@ void tc_gemm_update(const float* A, int lda, const float* B, int ldb, float* C, 
   VIV_CUDA(cudaMemcpyAsync(d_ld, lds, sizeof(lds), cudaMemcpyHostToDevice, s));
   {
     Launched L(K_TCSPLIT, s);
-    tcp::split_launch(d_split, blk, C, d_off, d_ld, img, s);
+    tcp::split_launch(d_split, blk, C, d_off, d_ld, img, nullptr, 0.f, s);
   }
   {
     Launched L(K_TCGEMM, s);

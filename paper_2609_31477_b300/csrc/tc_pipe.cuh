@@ -56,10 +56,12 @@ constexpr int ITEM = 8;                          // ints per work item
 constexpr long long WAIT_LIMIT = 1LL << 26;      // polls before a wait gives up
 
 // work items
-//   split: {f, start, kind (0: rows of A, 1: columns of B), k0, klen, block, limit, 0}
+//   split: {f, start, kind (0: rows of A, 1: columns of B), k0, klen, block, limit, check}
 //          operand element (r, k) of kind 0 is base[(k0 + k) ld + start + r],
 //          of kind 1 base[(start + r) ld + k0 + k]; base = pool + off[f], ld = ld[f];
-//          rows (columns) at or beyond `limit` and k >= klen are written as 0
+//          rows (columns) at or beyond `limit` and k >= klen are written as 0;
+//          with check != 0 an element above 1 / thresh in magnitude (a
+//          multiplier that fails the threshold test) adds 1 to stats[1]
 //   pipe:  {f, rb, cb, r_end, c_end, a_block, b_block, nchunks}: one tile; C =
 //          pool + off[f] with leading dimension ld[f]; rows < r_end and
 //          columns < c_end of the tile are updated; chunk ch of A (B) is image
@@ -132,7 +134,7 @@ __device__ __forceinline__ void bulk_copy(void* dst_smem, const void* src_gmem, 
 
 // host launchers (tc_pipe.cu); both enqueue on stream s
 void split_launch(const int32_t* items, int n_items, const float* pool, const int64_t* off, const int32_t* ld,
-                  unsigned char* img, cudaStream_t s);
+                  unsigned char* img, int* stats, float thresh, cudaStream_t s);
 void pipe_launch(const int32_t* items, int n_items, const unsigned char* img, float* pool, const int64_t* off,
                  const int32_t* ld, int* err, cudaStream_t s);
 void prepare();   // kernel attributes of the current device (once per device)

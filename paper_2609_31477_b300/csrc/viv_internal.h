@@ -61,7 +61,9 @@ enum LaunchKind {
   L_ASSEMBLE = 0, L_PANEL = 1, L_TRSM = 2, L_GEMM = 3, L_PANEL_CL = 4, L_LASWP = 5, L_PANEL_1 = 6, L_TC_GEMM = 7,
   L_DIAG = 8,      // windowed pivoting: one warp factors the 32 x 32 diagonal block
   L_WINDOW = 9,    // windowed pivoting: L21 rows and permuted / solved columns
-  L_TC_SPLIT = 10  // tensor-core operands: hi/lo TF32 images of the outer block's L21 and U12 chunks
+  L_TC_SPLIT = 10, // tensor-core operands: hi/lo TF32 images of the outer block's L21 and U12 chunks
+  L_BLOCK_LU = 11, // windowed FP32: one CTA factors a large front's 128-column block, writes its inverse images
+  L_BLOCK_PERM = 12  // windowed FP32: the block rows' permutation on the front's other columns
 };
 constexpr int WORK_STRIDE = 8;   // ints per work item
 // work items:  ASSEMBLE (f, c0)           PANEL* (f)              LASWP (f, c0)
@@ -69,6 +71,7 @@ constexpr int WORK_STRIDE = 8;   // ints per work item
 //              TC_SPLIT (f, start, kind, k0, klen, block, limit)  [one 128 x 32 operand chunk]
 //              TC_GEMM (f, rb, cb, r_end, c_end, a_block, b_block, nchunks)  [128 x 128 tiles, tensor cores]
 //              DIAG (f)   WINDOW (0, f, r0) rows of L21 | (1, f, c0, c_end) permuted / solved columns
+//              BLOCK_LU (f, k2, a_inv_block, b_inv_block, nchunks)   BLOCK_PERM (f, k2, c0)
 constexpr int WINDOW_THREADS = 256;   // rows or columns per WINDOW item
 // solves: the bandwidth-bound products with the off-diagonal factor blocks run
 // as items of SOLVE_ROWS rows x SOLVE_SLICE columns (one partial sum per slice)
@@ -176,6 +179,8 @@ struct Mesh {
   double outer_flops = 0;   // part of gemm_flops done by the K = 128 outer updates (tensor cores)
   int64_t tc_img_chunks = 0;   // image chunks a mixed case holds: the largest group of any schedule
   int64_t tc_split_chunks = 0, tc_tiles = 0;   // per numeric factorisation: chunks split, tiles updated
+  bool block_lu = true;        // FP32 windowed schedule: 128-column blocks of large fronts by block_lu_kernel
+  double window_tc_flops = 0;  // tensor-core flops of one factorisation of that schedule
   // device copies
   cudaStream_t stream = nullptr;
   bool on_device = false;
