@@ -35,9 +35,9 @@ WORKLOADS = {
     "viv_re100_m24": dict(m=24, Re=100.0, Ustar=8.0, dt=0.05),
 }
 FP32_SIMT_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12      # 148 SMs x 128 FP32 lanes x FMA x 2.032 GHz
-# DRAM bytes (read + write) per 128 x 128 tile of the tensor-core Schur update, from one ncu capture of that
-# kernel on the 6,208-quad member of the mesh family; scaled by the tiles of an average launch
-TC_DRAM_BYTES_PER_TILE = 73.4e3
+# DRAM bytes (read + write) per 128 x 128 tile of the tensor-core Schur update (tc_pipe_kernel), from one
+# ncu capture of that kernel; None until a capture of the current kernel exists (the line's traffic is null)
+TC_DRAM_BYTES_PER_TILE = None
 
 
 def parse():
@@ -352,6 +352,8 @@ def run_ours(args, wl, rank, world, local):
     bf16_key = "bf16_tflops_sustained" if "bf16_tflops_sustained" in peaks else "bf16_tflops"
     tc_peak = peaks[bf16_key] / 2.0 / 3.0
     fbytes = 4 * info["front_entries"]
+    window = args.pivoting == "window"
+    tc_flops = info["window_tc_flops"] if window else info["outer_flops"]
 
     def roofline_of(kind):
         k_ms, k_n = kern[kind]
@@ -361,12 +363,17 @@ def run_ours(args, wl, rank, world, local):
         if kind == "tc_schur_gemm":
             # kind::tf32 with three products per FP32 multiply-add (3xTF32): algorithmic
             # FP32 flops / time against TF32 dense (BF16 measured / 2, nominal) / 3
-            a = info["outer_flops"] * n_fact / sec / 1e12
+            a = tc_flops * n_fact / sec / 1e12
             return {"bound": "tensor", "achieved": a, "peak": tc_peak, "unit": "TFLOP/s", "frac": a / tc_peak,
                     "peak_source": f"{src} {bf16_key} / 2 (TF32:BF16 nominal) / 3 (3xTF32 products)"}
         if kind in ("schur_gemm", "panel_lu", "trsm"):
-            fl = {"schur_gemm": info["gemm_flops"] - info["outer_flops"],
-                  "panel_lu": info["panel_flops"], "trsm": info["trsm_flops"]}[kind]
+            if window:
+                fl = {"schur_gemm": info["window_gemm_flops"], "panel_lu": info["window_lu_flops"]}.get(kind)
+                if fl is None:   # (windowed: row moves and window solves, no flop count)
+                    return None
+            else:
+                fl = {"schur_gemm": info["gemm_flops"] - info["outer_flops"],
+                      "panel_lu": info["panel_flops"], "trsm": info["trsm_flops"]}[kind]
             a = fl * n_fact / sec / 1e12
             return {"bound": "alu", "achieved": a, "peak": FP32_SIMT_TFLOPS, "unit": "TFLOP/s",
                     "frac": a / FP32_SIMT_TFLOPS,
@@ -388,12 +395,12 @@ def run_ours(args, wl, rank, world, local):
     dom = max((k for k in kern if roofline_of(k) is not None), key=lambda k: kern[k][0])
     roof = roofline_of(dom)
     traffic = None
-    if dom == "tc_schur_gemm" and kern[dom][1]:
-        # tiles per launch from the outer-update flops (K = 128 per outer block)
-        tiles = info["outer_flops"] * n_fact / (2.0 * 128 * 128 * 128) / kern[dom][1]
+    if dom == "tc_schur_gemm" and kern[dom][1] and TC_DRAM_BYTES_PER_TILE:
+        # tiles per launch from the tensor-core flops (K = 128 per tile)
+        tiles = tc_flops * n_fact / (2.0 * 128 * 128 * 128) / kern[dom][1]
         traffic = TC_DRAM_BYTES_PER_TILE * tiles
-        roof["traffic_note"] = (f"ncu DRAM bytes per tile (6,208-quad capture) x {tiles:.0f} tiles per launch; "
-                                "algorithmic operand + C bytes per tile without reuse: 262144")
+        roof["traffic_note"] = (f"ncu DRAM bytes per tile x {tiles:.0f} tiles per launch; algorithmic "
+                                "operand + C bytes per tile without reuse: 393216")
     roof.update({"traffic": traffic, "kernel": dom, "launches": kern[dom][1], "ms_total": kern[dom][0]})
 
     out = {"metric": METRIC, "value": value, "unit": "time steps/s", "n_gpus": world, "steps": args.steps,

@@ -107,6 +107,11 @@ typedef struct {
                               TF32 images (16 KB read, 32 KB written each) */
   int64_t tc_tiles;        /* mixed path, per factorisation: 128 x 128 tiles of the outer updates */
   size_t tc_image_bytes;   /* the operand-image buffer a mixed case holds (in device_bytes_mixed) */
+  /* mixed path with windowed pivoting, per factorisation (the counters above
+   * describe the threshold-pivoting schedule): */
+  double window_tc_flops;  /* tensor-core flops: L21, U12 and Schur updates of the 128-column blocks */
+  double window_lu_flops;  /* LU flops of the pivot blocks (windows and block LU incl. the block inverses) */
+  double window_gemm_flops;/* SIMT Schur-update flops (fronts below the large-front order) */
 } vivMeshInfo;
 
 /* Physical and solver parameters.  rho, mu: fluid density and viscosity;

@@ -25,6 +25,11 @@ void upload_work(Mesh& m, cudaStream_t s);
 
 static thread_local std::string g_err;
 void set_error(const std::string& msg) { g_err = msg; }
+// the factors come from the block LU (mixed precision, windowed pivoting)
+bool block_factors(const vivCase* c) {
+  return c->prm.precision == VIV_MIXED && c->prm.pivoting == VIV_PIVOT_WINDOW && c->mesh->m.block_lu;
+}
+
 }  // namespace viv
 
 using namespace viv;
@@ -192,15 +197,16 @@ double assemble(vivCase* c, int what, bool want_norm) {
 
 bool has_border(const Mesh& m) { return m.n_front_dofs < m.n_dofs; }
 
+
 // x[0 : n_front_dofs] = A^{-1} b[0 : n_front_dofs] with the fronts' factors
 void front_solve(vivCase* c, const double* b, double* x) {
   const Mesh& m = c->mesh->m;
   if (mixed(c))
     solve_fronts<float>(m, (const float*)c->s.fronts, c->s.perm, b, x, (float*)c->s.vec, (float*)c->s.yv,
-                        c->stream);
+                        block_factors(c), c->stream);
   else
     solve_fronts<double>(m, (const double*)c->s.fronts, c->s.perm, b, x, (double*)c->s.vec,
-                         (double*)c->s.yv, c->stream);
+                         (double*)c->s.yv, false, c->stream);
 }
 
 // Numeric factorisation of A (the Jacobian without the delta rows and
@@ -222,10 +228,10 @@ void factor(vivCase* c) {
     for (int j = 0; j < 2; ++j) launch_border_column(m, c->s.J64, j, c->s.Bcol + (int64_t)j * m.n_dofs, c->stream);
     if (mixed(c))
       solve_fronts2<float>(m, (const float*)c->s.fronts, c->s.perm, c->s.Bcol, c->s.Y, (float*)c->s.vec2,
-                           (float*)c->s.yv2, c->stream);
+                           (float*)c->s.yv2, block_factors(c), c->stream);
     else
       solve_fronts2<double>(m, (const double*)c->s.fronts, c->s.perm, c->s.Bcol, c->s.Y, (double*)c->s.vec2,
-                            (double*)c->s.yv2, c->stream);
+                            (double*)c->s.yv2, false, c->stream);
     launch_border_schur(m, c->s.J64, c->s.Y, c->s.Sb, c->s.stats + 3, c->stream);
   }
   c->factored = true;
@@ -361,6 +367,9 @@ vivStatus viv_mesh_info(const vivMesh* mesh, vivMeshInfo* info) {
   info->outer_flops = m.outer_flops;
   info->tc_split_chunks = m.tc_split_chunks;
   info->tc_tiles = m.tc_tiles;
+  info->window_tc_flops = m.window_tc_flops;
+  info->window_lu_flops = m.window_lu_flops;
+  info->window_gemm_flops = m.window_gemm_flops;
   info->tc_image_bytes = (size_t)m.tc_img_chunks * TC_IMG_CHUNK_BYTES;
   API_END
 }

@@ -74,12 +74,13 @@ struct FT {   // front tables passed by value
   const int32_t* piv_off;
   const int32_t* col_nz;
   const int64_t* col_nz_off;
+  const uint8_t* blk;   // solves: fronts whose 128-row diagonal blocks are stored inverted (or null)
 };
 
-FT make_ft(const Mesh& m) {
+FT make_ft(const Mesh& m, bool blk = false) {
   const FrontTables& t = m.ft;
   return FT{t.off, t.m, t.p, t.first, t.idx_off, t.idx, t.nz_off, t.nz_csr, t.nz_pos, t.child_off,
-            t.child, t.ea_off, t.ea, t.vec_off, t.piv_off, t.col_nz, t.col_nz_off};
+            t.child, t.ea_off, t.ea, t.vec_off, t.piv_off, t.col_nz, t.col_nz_off, blk ? m.d_blk_front : nullptr};
 }
 
 __device__ __forceinline__ int lower_bound_i(const int32_t* a, int n, int v) {
@@ -607,8 +608,10 @@ __global__ void __launch_bounds__(WINDOW_THREADS) window_kernel(FT ft, const int
 //           register tiles.
 //   rank    A22 -= L21 U12 for the rest of the block, 4 x 4 register tiles.
 // It then completes U^{-1} and L^{-1} of the whole block (off-diagonal 32 x 32
-// blocks by distance from the diagonal) and writes (I - U^{-1}) and
-// (I - L^{-1}) as hi/lo TF32 operand images, so that the tensor-core pipeline
+// blocks by distance from the diagonal), stores them in place of the block's
+// diagonal part (the solves of these fronts step over whole blocks), and
+// writes (I - U^{-1}) and (I - L^{-1}) as hi/lo TF32 operand images, so that
+// the tensor-core pipeline
 // (C -= A B) turns the block's rows below into L21 = A21 - A21 (I - U^{-1}) and
 // its columns to the right into U12 = P A12 - (I - L^{-1}) P A12.
 // Item: {f, k2, a_blk, b_blk, nchunks} (image blocks of (I - L^{-1}) and
@@ -995,10 +998,13 @@ __global__ void __launch_bounds__(BLK_MAX_THREADS, 1) block_lu_kernel(FT ft, con
     }
   }
   if (__syncthreads_or(big) && tid == 0) atomicAdd(&stats[1], 1);
-  if (li < nb && tid < jstep * nn)
-    for (int j = tid / nn; j < nb; j += jstep) F[(int64_t)j * m + li] = D[li * ld + j];
-  if (a_blk < 0) return;   // (uniform) no rows below the block: no inverses needed
   offdiag_inverses(D, V, W, ld, nch);
+  // the block's diagonal part is kept inverted (the solves step over whole
+  // blocks): L^{-1} below the diagonal (unit diagonal implied), U^{-1} on and
+  // above it
+  if (li < nb && tid < jstep * nn)
+    for (int j = tid / nn; j < nb; j += jstep) F[(int64_t)j * m + li] = li > j ? W[li * ld + j] : V[li * ld + j];
+  if (a_blk < 0) return;   // (uniform) no rows below the block: no operand images
   // B operand (K x N: row k, column n of I - U^{-1}), A operand (M x K: row i,
   // column k of I - L^{-1}); zero outside nn x nn and outside the triangles
   write_operand_image(img, b_blk, nch, [&](int n, int k) {
@@ -1310,6 +1316,76 @@ __global__ void __launch_bounds__(GEMV_THREADS) solve_gemv_kernel(FT ft, const i
   }
 }
 
+// One 128-row step of a chain over a front whose 128 x 128 diagonal blocks
+// are stored inverted (block-LU fronts).  FWD: x_b = L_bb^{-1} w_b (unit lower
+// part of the stored inverse; x_b -> yv), then w_i -= L(i, b) x_b for the pivot
+// rows below the block.  !FWD: x_b = U_bb^{-1} v_b (upper part with the
+// diagonal; x_b -> xo, FP64), then v_i -= U(i, b) x_b for the pivot rows above
+// it.  The block product is split over all threads (row of the block x 16-column
+// group, partial sums in red = NR x 1024 shared entries), the row updates take
+// one row per thread with 32 loads in flight.
+template <class T, int NR, bool FWD>
+__device__ void chain_block128(const T* __restrict__ F, int m, int p, int jb, T* const (&w)[NR], T* red,
+                               T* yo, int64_t ldv, double* xo = nullptr) {
+  __shared__ T xb[NR][OUTER_NB];
+  const int nb = min(OUTER_NB, p - jb), nthr = blockDim.x;
+  __syncthreads();   // w of the block final (row updates of the previous step)
+  for (int e = threadIdx.x; e < OUTER_NB * 8; e += nthr) {
+    const int rr = e & (OUTER_NB - 1), g = e >> 7;   // row of the block, 16-column group
+    T a[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) a[r] = T(0);
+    if (rr < nb) {
+      const T* Dc = F + (int64_t)(jb + 16 * g) * m + jb + rr;
+      T d[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int c = 16 * g + j;
+        d[j] = (c < nb && (FWD ? c < rr : c >= rr)) ? Dc[(int64_t)j * m] : T(0);
+      }
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int c = min(16 * g + j, nb - 1);
+          a[r] += d[j] * w[r][jb + c];
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) red[r * 1024 + g * OUTER_NB + rr] = a[r];
+  }
+  __syncthreads();
+  for (int rr = threadIdx.x; rr < nb; rr += nthr)
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      T s = FWD ? w[r][jb + rr] : T(0);   // (unit diagonal of L^{-1})
+#pragma unroll
+      for (int g = 0; g < 8; ++g) s += red[r * 1024 + g * OUTER_NB + rr];
+      xb[r][rr] = s;
+      if (FWD) yo[r * ldv + jb + rr] = s;
+      else xo[r * ldv + jb + rr] = (double)s;
+    }
+  __syncthreads();
+  const int i0 = FWD ? jb + OUTER_NB : 0, i1 = FWD ? p : jb;
+  for (int i = i0 + threadIdx.x; i < i1; i += nthr) {
+    const T* col = F + (int64_t)jb * m + i;
+    T a[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) a[r] = T(0);
+    for (int c0 = 0; c0 < nb; c0 += 32) {
+      T v[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) v[j] = c0 + j < nb ? col[(int64_t)(c0 + j) * m] : T(0);
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+#pragma unroll
+        for (int j = 0; j < 32; ++j) a[r] += v[j] * xb[r][min(c0 + j, nb - 1)];
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) w[r][i] -= a[r];
+  }
+}
+
 // forward chain of one front: gather, permute, L11^{-1} blocks and the pivot
 // rows below them; the non-pivot rows keep the gathered values for the slices
 template <class T, int NR>
@@ -1361,7 +1437,12 @@ __global__ void __launch_bounds__(solve_threads_max<T>(), 1) fwd_tri_kernel(FT f
 #pragma unroll
     for (int r = 0; r < NR; ++r) w[r][i] = tmp[r][i];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int jb = 0; jb < p; jb += 32) {
+  const bool b128 = ft.blk && ft.blk[f];   // (block-LU fronts: 128-row blocks stored inverted)
+  for (int jb = 0; jb < p; jb += b128 ? OUTER_NB : 32) {
+    if (b128) {
+      chain_block128<T, NR, true>(F, m, p, jb, w, xw[0][0], yv + first, ldv);
+      continue;
+    }
     const int nb = min(32, p - jb);
     // row `lane` of L11^{-1} (strictly lower part), loaded before the barrier
     T d[32];
@@ -1433,6 +1514,11 @@ __global__ void __launch_bounds__(solve_threads_max<T>(), 1) bwd_tri_kernel(FT f
       v[r][i] = a;
     }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (ft.blk && ft.blk[f]) {   // (block-LU fronts: 128-row blocks stored inverted)
+    for (int jb = ((p - 1) / OUTER_NB) * OUTER_NB; jb >= 0 && p > 0; jb -= OUTER_NB)
+      chain_block128<T, NR, false>(F, m, p, jb, v, xw[0][0], nullptr, ldv, x + first);
+    return;
+  }
   for (int jb = ((p - 1) / 32) * 32; jb >= 0 && p > 0; jb -= 32) {
     const int nb = min(32, p - jb);
     // row `lane` of U11^{-1} (upper part, diagonal included)
@@ -1595,10 +1681,14 @@ void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* front
     Launched LL(K_TRSM, s);
     perm_kernel<<<m.n_fronts, 128, 2 * (size_t)std::max(1, m.max_p) * sizeof(int32_t), s>>>(ft, piv, perm);
   }
-  if (!m.inv_items.empty()) {
+  // (the block LU stored its blocks' diagonal parts inverted already)
+  const bool blk = std::is_same<T, float>::value && window && m.block_lu;
+  const std::vector<int32_t>& inv = blk ? m.inv_items_blk : m.inv_items;
+  if (!inv.empty()) {
     Launched LL(K_TRSM, s);
-    const int n = (int)(m.inv_items.size() / 2);
-    diag_inv_kernel<T><<<(n + INV_WARPS - 1) / INV_WARPS, INV_WARPS * 32, 0, s>>>(ft, m.d_inv_items, n, fronts);
+    const int n = (int)(inv.size() / 2);
+    diag_inv_kernel<T><<<(n + INV_WARPS - 1) / INV_WARPS, INV_WARPS * 32, 0, s>>>(
+        ft, blk ? m.d_inv_items_blk : m.d_inv_items, n, fronts);
   }
   VIV_CUDA(cudaGetLastError());
 }
@@ -1607,10 +1697,11 @@ void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* front
 // r * ldv (T), of the workspace vec at r * vstride (T)
 template <class T, int NR>
 void solve_fronts_nr(const Mesh& m, const T* fronts, const int32_t* perm, const double* b, double* x, T* vec, T* yv,
-                     int64_t ldv, int64_t vstride, cudaStream_t s) {
-  FT ft = make_ft(m);
+                     int64_t ldv, int64_t vstride, bool blk, cudaStream_t s) {
+  FT ft = make_ft(m, blk);
   prepare_kernels<T>();
   for (int l = 0; l < m.n_levels; ++l) {
+    prof_level(l);
     const int n = m.level_off[l + 1] - m.level_off[l];
     const size_t need = (size_t)NR * (m.level_maxm[l] + m.level_maxp[l]) * sizeof(T);
     const bool sm = need <= (size_t)SOLVE_SMEM_MAX;
@@ -1627,6 +1718,7 @@ void solve_fronts_nr(const Mesh& m, const T* fronts, const int32_t* perm, const 
     }
   }
   for (int l = m.n_levels - 1; l >= 0; --l) {
+    prof_level(l);
     const int ng = m.bg_off[l + 1] - m.bg_off[l];
     if (ng) {
       Launched L(K_BWD, s);
@@ -1640,21 +1732,22 @@ void solve_fronts_nr(const Mesh& m, const T* fronts, const int32_t* perm, const 
     bwd_tri_kernel<T, NR><<<n, std::min(m.level_threads[l], solve_threads_max<T>()), sm ? need : 0, s>>>(
         ft, m.d_level_fronts + m.level_off[l], fronts, yv, vec, x, sm, ldv, vstride);
   }
+  prof_level(-1);
   VIV_CUDA(cudaGetLastError());
 }
 
 template <class T>
 void solve_fronts(const Mesh& m, const T* fronts, const int32_t* perm, const double* b, double* x, T* vec, T* yv,
-                  cudaStream_t s) {
-  solve_fronts_nr<T, 1>(m, fronts, perm, b, x, vec, yv, m.n_dofs, m.vec_entries, s);
+                  bool blk, cudaStream_t s) {
+  solve_fronts_nr<T, 1>(m, fronts, perm, b, x, vec, yv, m.n_dofs, m.vec_entries, blk, s);
 }
 
 // two right-hand sides in one pass (the border columns): b, x, yv hold two
 // vectors of m.n_dofs, vec two workspaces of m.vec_entries
 template <class T>
 void solve_fronts2(const Mesh& m, const T* fronts, const int32_t* perm, const double* b, double* x, T* vec, T* yv,
-                   cudaStream_t s) {
-  solve_fronts_nr<T, 2>(m, fronts, perm, b, x, vec, yv, m.n_dofs, m.vec_entries, s);
+                   bool blk, cudaStream_t s) {
+  solve_fronts_nr<T, 2>(m, fronts, perm, b, x, vec, yv, m.n_dofs, m.vec_entries, blk, s);
 }
 
 template void factor_numeric<double>(const Mesh&, const double*, const float*, double*, int32_t*, int32_t*,
@@ -1662,12 +1755,12 @@ template void factor_numeric<double>(const Mesh&, const double*, const float*, d
 template void factor_numeric<float>(const Mesh&, const double*, const float*, float*, int32_t*, int32_t*, int32_t*,
                                     double, bool, unsigned char*, cudaStream_t);
 template void solve_fronts<double>(const Mesh&, const double*, const int32_t*, const double*, double*, double*,
-                                   double*, cudaStream_t);
+                                   double*, bool, cudaStream_t);
 template void solve_fronts<float>(const Mesh&, const float*, const int32_t*, const double*, double*, float*,
-                                  float*, cudaStream_t);
+                                  float*, bool, cudaStream_t);
 template void solve_fronts2<double>(const Mesh&, const double*, const int32_t*, const double*, double*, double*,
-                                    double*, cudaStream_t);
+                                    double*, bool, cudaStream_t);
 template void solve_fronts2<float>(const Mesh&, const float*, const int32_t*, const double*, double*, float*,
-                                   float*, cudaStream_t);
+                                   float*, bool, cudaStream_t);
 
 }  // namespace viv

@@ -790,6 +790,10 @@ static void emit_blocks(Mesh& m, int l, int k2, int big_front, Push& push, Open&
                 nch});
       const double rest = (double)(mm - be);
       m.window_tc_flops += 4.0 * nb * nb * rest + 2.0 * rest * rest * nb;
+      // LU of the nb x nb block, and with rows below it the two triangle inverses
+      double lu = 0;
+      for (int j = 0; j < nb; ++j) lu += (double)(nb - j - 1) + 2.0 * (nb - j - 1) * (nb - j - 1);
+      m.window_lu_flops += lu + (nbk > 0 ? 2.0 * nb * (double)nb * nb / 3.0 : 0.0);
     }
     close(T2);
     (void)items;
@@ -809,7 +813,15 @@ void build_schedule(Mesh& m, int big_front) {
   m.work.clear();
   m.gemm_flops = m.trsm_flops = m.panel_flops = m.outer_flops = 0;
   m.tc_split_chunks = m.tc_tiles = 0;
-  m.window_tc_flops = 0;
+  m.window_tc_flops = m.window_lu_flops = m.window_gemm_flops = 0;
+  m.blk_front.assign(m.n_fronts, 0);
+  for (int f = 0; f < m.n_fronts; ++f) m.blk_front[f] = m.block_lu && block_front(m, f, big_front) ? 1 : 0;
+  m.inv_items_blk.clear();
+  for (size_t q = 0; q + 1 < m.inv_items.size(); q += 2)
+    if (!m.blk_front[m.inv_items[q]]) {
+      m.inv_items_blk.push_back(m.inv_items[q]);
+      m.inv_items_blk.push_back(m.inv_items[q + 1]);
+    }
   auto push = [&](std::initializer_list<int> v) {
     int n = 0;
     for (int x : v) {
@@ -837,7 +849,9 @@ void build_schedule(Mesh& m, int big_front) {
       for (int rb = r0; rb < r_end; rb += GEMM_TILE)
         for (int cb = c0; cb < c_end; cb += GEMM_TILE)
           push({f, rb, cb, r_end, c_end, kb, kl, (diag_tile && rb == r0 && cb == c0) ? 1 : 0});
-      if (count) m.gemm_flops += 2.0 * std::max(0, r_end - r0) * std::max(0, c_end - c0) * kl;
+      const double fl = 2.0 * std::max(0, r_end - r0) * std::max(0, c_end - c0) * kl;
+      if (count) m.gemm_flops += fl;
+      if (window && prec == 0) m.window_gemm_flops += fl;
     };
     // windowed pivoting: the diagonal block of panel k of front f is factored by
     // the Schur update of panel k - 32 when that update covers it (every panel
@@ -932,13 +946,16 @@ void build_schedule(Mesh& m, int big_front) {
           const int c_end = big(f) ? block_end(f) : m.f_m[f];
           if (!window)
             for (int c0 = k + nbe; c0 < c_end; c0 += TRSM_COLS) push({f, c0, c_end, k});
+          double pf = 0;   // the panel's LU flops (its rows below included)
+          for (int j = k; j < k + nbe; ++j) {
+            const double below = (double)(m.f_m[f] - j - 1);
+            pf += below + 2.0 * below * (k + nbe - j - 1);
+          }
           if (count) {
             m.trsm_flops += (double)nbe * (nbe - 1) * std::max(0, c_end - k - nbe);
-            for (int j = k; j < k + nbe; ++j) {
-              double below = (double)(m.f_m[f] - j - 1);
-              m.panel_flops += below + 2.0 * below * (k + nbe - j - 1);
-            }
+            m.panel_flops += pf;
           }
+          if (window && prec == 0 && !newblk(f)) m.window_lu_flops += pf;
         }
         close(T);
         Launch G = open(L_GEMM, l, k);
@@ -1060,6 +1077,15 @@ void upload_work(Mesh& m, cudaStream_t s) {
   }
   if (!m.work.empty())
     VIV_CUDA(cudaMemcpyAsync(m.ft.work, m.work.data(), m.work.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  if (!m.d_blk_front) {
+    m.d_blk_front = m.arena.make<uint8_t>(std::max<size_t>(1, m.blk_front.size()));
+    m.d_inv_items_blk = m.arena.make<int32_t>(std::max<size_t>(1, m.inv_items.size()));
+  }
+  if (!m.blk_front.empty())
+    VIV_CUDA(cudaMemcpyAsync(m.d_blk_front, m.blk_front.data(), m.blk_front.size(), cudaMemcpyHostToDevice, s));
+  if (!m.inv_items_blk.empty())
+    VIV_CUDA(cudaMemcpyAsync(m.d_inv_items_blk, m.inv_items_blk.data(), m.inv_items_blk.size() * sizeof(int32_t),
+                             cudaMemcpyHostToDevice, s));
   VIV_CUDA(cudaStreamSynchronize(s));
   m.sched_version += 1;
 }

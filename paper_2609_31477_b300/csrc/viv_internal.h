@@ -168,6 +168,11 @@ struct Mesh {
   std::vector<int32_t> level_maxp;     // largest pivot count per level
   int max_p = 0;                       // largest pivot count of any front
   std::vector<int32_t> inv_items;      // (front, first row) of every 32 x 32 diagonal block
+  // windowed FP32 schedule: fronts whose 128-column blocks the block LU
+  // factors (it stores each block's diagonal part inverted: the solves step
+  // 128 rows at a time there), and the 32 x 32 inversions left for the others
+  std::vector<uint8_t> blk_front;
+  std::vector<int32_t> inv_items_blk;
   std::vector<int32_t> fg_items, fg_off;   // forward slice items (f, r0, slice, 0) by level
   std::vector<int32_t> bg_items, bg_off;   // backward slice items by level
   int64_t front_entries = 0, vec_entries = 0, piv_entries = 0;
@@ -180,7 +185,9 @@ struct Mesh {
   int64_t tc_img_chunks = 0;   // image chunks a mixed case holds: the largest group of any schedule
   int64_t tc_split_chunks = 0, tc_tiles = 0;   // per numeric factorisation: chunks split, tiles updated
   bool block_lu = true;        // FP32 windowed schedule: 128-column blocks of large fronts by block_lu_kernel
-  double window_tc_flops = 0;  // tensor-core flops of one factorisation of that schedule
+  double window_tc_flops = 0;  // per factorisation of that schedule: tensor-core flops,
+  double window_lu_flops = 0;  //   pivot-block LU flops (block inverses included),
+  double window_gemm_flops = 0;//   SIMT Schur-update flops
   // device copies
   cudaStream_t stream = nullptr;
   bool on_device = false;
@@ -199,6 +206,8 @@ struct Mesh {
   int32_t* d_fcolor_faces = nullptr;
   int32_t* d_level_fronts = nullptr;
   int32_t* d_inv_items = nullptr;
+  uint8_t* d_blk_front = nullptr;      // (device copies, sized once: n_fronts / inv_items)
+  int32_t* d_inv_items_blk = nullptr;
   int32_t* d_fg_items = nullptr;
   int32_t* d_bg_items = nullptr;
   int32_t *d_bc_col = nullptr, *d_bc_q = nullptr, *d_bb_row = nullptr, *d_bb_q = nullptr;
@@ -342,12 +351,16 @@ void prepare_kernels();
 template <class T>
 void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* fronts, int32_t* piv, int32_t* perm,
                     int32_t* stats, double threshold, bool window, unsigned char* tc_img, cudaStream_t s);
+// the case's factors come from the block LU (mixed precision, windowed pivoting)
+bool block_factors(const vivCase* c);
+// blk: the factors come from the block LU of the windowed FP32 schedule
+// (diagonal 128-blocks of the flagged fronts stored inverted)
 template <class T>
 void solve_fronts(const Mesh& m, const T* fronts, const int32_t* perm, const double* b, double* x,
-                  T* vec, T* yv, cudaStream_t s);
+                  T* vec, T* yv, bool blk, cudaStream_t s);
 template <class T>
 void solve_fronts2(const Mesh& m, const T* fronts, const int32_t* perm, const double* b, double* x, T* vec, T* yv,
-                   cudaStream_t s);
+                   bool blk, cudaStream_t s);
 }  // namespace viv
 
 // ----- canonical order of the element matrix pairs scattered through e2nz ----

@@ -45,7 +45,8 @@ class MeshInfo(C.Structure):
                 ("device_bytes_mixed", C.c_size_t), ("n_colors", C.c_int32),
                 ("gemm_flops", C.c_double), ("panel_flops", C.c_double), ("trsm_flops", C.c_double),
                 ("outer_flops", C.c_double), ("tc_split_chunks", C.c_int64), ("tc_tiles", C.c_int64),
-                ("tc_image_bytes", C.c_size_t)]
+                ("tc_image_bytes", C.c_size_t), ("window_tc_flops", C.c_double),
+                ("window_lu_flops", C.c_double), ("window_gemm_flops", C.c_double)]
 
 
 class Params(C.Structure):

@@ -219,7 +219,7 @@ def test_large_front_threshold_and_level_profile(viv):
     """The same refined solution whatever the large-front threshold (outer
     blocks on the tensor cores for every front of order >= 96, for fronts of
     order >= 256, or for none), and a per-level profile that splits the
-    factorisation time by tree level and kind."""
+    factorisation and solve times by tree level and kind."""
     mesh, oc, M, case = _pair(viv, 12, viv.VIV_MIXED, pivoting=viv.VIV_PIVOT_WINDOW)
     _mid_step_state(viv, oc, case, 31)
     case.assemble(viv.VIV_RES | viv.VIV_JAC)
@@ -236,9 +236,10 @@ def test_large_front_threshold_and_level_profile(viv):
         lv = case.profile_levels()
         case.profile(False)
         assert len(lv) == levels
-        per_level = sum(sum(d.values()) for d in lv)
-        per_kind = sum(kinds[k][0] for k in fact_kinds)
-        assert 0 < per_level <= per_kind * (1 + 1e-9) + 1e-9
+        for group in (fact_kinds, ("fwd_solve", "bwd_solve")):
+            per_level = sum(v for d in lv for k, v in d.items() if k in group)
+            per_kind = sum(kinds[k][0] for k in group if k in kinds)
+            assert 0 < per_level <= per_kind * (1 + 1e-9) + 1e-9, group
         uses_tc = any("tc_schur_gemm" in d for d in lv)
         assert uses_tc == (bf != 1 << 30)
         assert uses_tc == any("tc_split" in d for d in lv)   # every tensor-core update splits its operands
