@@ -203,10 +203,10 @@ void front_solve(vivCase* c, const double* b, double* x) {
   const Mesh& m = c->mesh->m;
   if (mixed(c))
     solve_fronts<float>(m, (const float*)c->s.fronts, c->s.perm, b, x, (float*)c->s.vec, (float*)c->s.yv,
-                        block_factors(c), c->stream);
+                        block_factors(c), c->s.chain, c->s.stats + 2, c->stream);
   else
     solve_fronts<double>(m, (const double*)c->s.fronts, c->s.perm, b, x, (double*)c->s.vec,
-                         (double*)c->s.yv, false, c->stream);
+                         (double*)c->s.yv, false, nullptr, nullptr, c->stream);
 }
 
 // Numeric factorisation of A (the Jacobian without the delta rows and
@@ -228,10 +228,10 @@ void factor(vivCase* c) {
     for (int j = 0; j < 2; ++j) launch_border_column(m, c->s.J64, j, c->s.Bcol + (int64_t)j * m.n_dofs, c->stream);
     if (mixed(c))
       solve_fronts2<float>(m, (const float*)c->s.fronts, c->s.perm, c->s.Bcol, c->s.Y, (float*)c->s.vec2,
-                           (float*)c->s.yv2, block_factors(c), c->stream);
+                           (float*)c->s.yv2, block_factors(c), c->s.chain, c->s.stats + 2, c->stream);
     else
       solve_fronts2<double>(m, (const double*)c->s.fronts, c->s.perm, c->s.Bcol, c->s.Y, (double*)c->s.vec2,
-                            (double*)c->s.yv2, false, c->stream);
+                            (double*)c->s.yv2, false, nullptr, nullptr, c->stream);
     launch_border_schur(m, c->s.J64, c->s.Y, c->s.Sb, c->s.stats + 3, c->stream);
   }
   c->factored = true;
@@ -354,7 +354,8 @@ vivStatus viv_mesh_info(const vivMesh* mesh, vivMeshInfo* info) {
   info->factor_flops = m.factor_flops;
   info->front_entries = (size_t)m.front_entries;
   size_t nodes = (size_t)m.n_nodes, nnz = (size_t)info->nnz, nd = (size_t)m.n_dofs;
-  size_t state = 8 * (17 * nodes + (size_t)m.n_elems + 3 * nd + 2 * 296 + 64) + 8 * (size_t)m.piv_entries;
+  size_t state = 8 * (17 * nodes + (size_t)m.n_elems + 3 * nd + 2 * 296 + 64) + 8 * (size_t)m.piv_entries +
+                 4 * (1 + (size_t)std::max(1, m.chain_flag_bound));   // (+ the solve chains' flags)
   if (m.n_front_dofs < m.n_dofs) state += 8 * 4 * nd;   // border: Y and the columns of B
   const size_t nv = m.n_front_dofs < m.n_dofs ? 3 : 1;   // solve workspaces: one, plus two for the border columns
   info->device_bytes_fp64 = state + 8 * (nnz + (size_t)m.front_entries + nv * ((size_t)m.vec_entries + nd));
@@ -496,6 +497,7 @@ static vivStatus case_create_impl(vivMesh* mesh, const vivParams* prm_in, const 
     s.piv = A.make<int32_t>(m.piv_entries);
     s.perm = A.make<int32_t>(m.piv_entries);
     s.stats = A.make<int32_t>(4);
+    s.chain = A.make<int32_t>(1 + (size_t)std::max(1, m.chain_flag_bound));
     if (has_border(m)) {
       s.Y = A.make<double>(2 * (size_t)nd);
       s.Bcol = A.make<double>(2 * (size_t)nd);

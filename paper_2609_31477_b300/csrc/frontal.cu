@@ -1436,6 +1436,15 @@ __global__ void __launch_bounds__(solve_threads_max<T>(), 1) fwd_tri_kernel(FT f
   for (int i = threadIdx.x; i < p; i += blockDim.x)
 #pragma unroll
     for (int r = 0; r < NR; ++r) w[r][i] = tmp[r][i];
+  if (ft.blk && ft.blk[f] == 2) {   // the chain runs on many CTAs (chain_multi_kernel): w's pivot part -> yv
+    for (int i = threadIdx.x; i < m; i += blockDim.x)
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        if (i < p) yv[r * ldv + first + i] = w[r][i];
+        else if (in_smem) vec[r * vstride + ft.vec_off[f] + i] = w[r][i];
+      }
+    return;
+  }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const bool b128 = ft.blk && ft.blk[f];   // (block-LU fronts: 128-row blocks stored inverted)
   for (int jb = 0; jb < p; jb += b128 ? OUTER_NB : 32) {
@@ -1513,6 +1522,13 @@ __global__ void __launch_bounds__(solve_threads_max<T>(), 1) bwd_tri_kernel(FT f
       for (int s2 = 0; s2 < ns; ++s2) a -= part[(int64_t)s2 * p + i];
       v[r][i] = a;
     }
+  if (ft.blk && ft.blk[f] == 2) {   // the chain runs on many CTAs (chain_multi_kernel): v -> yv
+    if (in_smem)
+      for (int i = threadIdx.x; i < p; i += blockDim.x)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) yv[r * ldv + first + i] = v[r][i];
+    return;
+  }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (ft.blk && ft.blk[f]) {   // (block-LU fronts: 128-row blocks stored inverted)
     for (int jb = ((p - 1) / OUTER_NB) * OUTER_NB; jb >= 0 && p > 0; jb -= OUTER_NB)
@@ -1556,6 +1572,127 @@ __global__ void __launch_bounds__(solve_threads_max<T>(), 1) bwd_tri_kernel(FT f
         v[r][i] -= (a0 + a1) + (a2 + a3);
       }
     }
+  }
+}
+
+// Multi-CTA chains of the large block-LU fronts of one level.  A persistent
+// grid takes tasks (front f, block b of 128 pivot rows) from a counter in
+// dependency order: forward, the blocks of every front top down; backward,
+// bottom up.  A task applies the finished blocks of its front to its rows as
+// their flags appear (w_b -= L(b, k) x_k; backward with U), then forms its
+// own x_b with the stored inverse of its diagonal block (forward: unit lower
+// part of L^{-1}; backward: U^{-1}), writes it (yv; backward also x in FP64)
+// and releases its flag.  A task waits only on tasks taken before it, which
+// are running or done, so the grid needs no co-residency.  Every wait is
+// bounded: on expiry the task sets *err and goes on (the solve is then
+// reported, not trusted).  chain[0] is the task counter, chain[1 + i] the
+// flags; both are zeroed before the launch.
+constexpr int MC_THREADS = 512;                  // 128 rows x 4 column quarters
+constexpr long long MC_WAIT_LIMIT = 1LL << 24;   // polls (64 ns apart) before a wait gives up
+
+__device__ __forceinline__ int ld_acquire_gpu(const int32_t* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(int32_t* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <class T, int NR, bool FWD>
+__global__ void __launch_bounds__(MC_THREADS) chain_multi_kernel(FT ft, const int32_t* __restrict__ tasks,
+                                                                 int n_tasks, const T* __restrict__ pool, T* yv,
+                                                                 double* x, int32_t* chain, int32_t* err,
+                                                                 int64_t ldv) {
+  __shared__ T wr[NR][OUTER_NB];       // the task's rows
+  __shared__ T xs[NR][OUTER_NB];       // x of the block being applied
+  __shared__ T red[NR][4][OUTER_NB];   // partial sums of the four column quarters
+  __shared__ int s_task;
+  int32_t* flags = chain + 1;
+  const int tid = threadIdx.x, rr = tid & (OUTER_NB - 1), q = tid >> 7;
+  for (;;) {
+    if (tid == 0) s_task = atomicAdd(&chain[0], 1);
+    __syncthreads();
+    const int t = s_task;
+    if (t >= n_tasks) break;   // (uniform)
+    const int f = tasks[3 * t], b = tasks[3 * t + 1], fb = tasks[3 * t + 2];
+    const int m = ft.m[f], p = ft.p[f], first = ft.first[f];
+    const int nblk = (p + OUTER_NB - 1) / OUTER_NB, r0 = OUTER_NB * b, nr = min(OUTER_NB, p - r0);
+    const T* F = pool + ft.off[f];
+    if (tid < OUTER_NB)
+#pragma unroll
+      for (int r = 0; r < NR; ++r) wr[r][tid] = tid < nr ? yv[r * ldv + first + r0 + tid] : T(0);
+    __syncthreads();
+    const int n_apply = FWD ? b : nblk - 1 - b;
+    for (int k = 0; k < n_apply; ++k) {
+      const int kb = FWD ? k : nblk - 1 - k, c0 = OUTER_NB * kb, nc = min(OUTER_NB, p - c0);
+      if (tid == 0) {   // bounded wait for block kb
+        long long it = 0;
+        while (!ld_acquire_gpu(&flags[fb + kb])) {
+          if (++it >= MC_WAIT_LIMIT) {
+            atomicExch(err, 1);
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+      __syncthreads();
+      if (tid < OUTER_NB)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) xs[r][tid] = tid < nc ? __ldcg(&yv[r * ldv + first + c0 + tid]) : T(0);
+      __syncthreads();
+      T a[NR];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) a[r] = T(0);
+      if (rr < nr) {
+        const T* col = F + (int64_t)(c0 + 32 * q) * m + r0 + rr;
+        T v[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = 32 * q + j < nc ? col[(int64_t)j * m] : T(0);
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+#pragma unroll
+          for (int j = 0; j < 32; ++j) a[r] += v[j] * xs[r][min(32 * q + j, nc - 1)];
+      }
+#pragma unroll
+      for (int r = 0; r < NR; ++r) red[r][q][rr] = a[r];
+      __syncthreads();
+      if (tid < OUTER_NB)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) wr[r][tid] -= (red[r][0][tid] + red[r][1][tid]) + (red[r][2][tid] + red[r][3][tid]);
+      __syncthreads();
+    }
+    // x_b = L_bb^{-1} w_b (forward) / U_bb^{-1} v_b (backward) with the stored inverse
+    T a[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) a[r] = T(0);
+    if (rr < nr) {
+      const T* col = F + (int64_t)(r0 + 32 * q) * m + r0 + rr;
+      T v[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int c = 32 * q + j;
+        v[j] = (c < nr && (FWD ? c < rr : c >= rr)) ? col[(int64_t)j * m] : T(0);
+      }
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+#pragma unroll
+        for (int j = 0; j < 32; ++j) a[r] += v[j] * wr[r][min(32 * q + j, nr - 1)];
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) red[r][q][rr] = a[r];
+    __syncthreads();
+    if (tid < nr) {
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        const T s = (FWD ? wr[r][tid] : T(0)) + (red[r][0][tid] + red[r][1][tid]) + (red[r][2][tid] + red[r][3][tid]);
+        yv[r * ldv + first + r0 + tid] = s;
+        if (!FWD) x[r * ldv + first + r0 + tid] = (double)s;
+      }
+      __threadfence();
+    }
+    __syncthreads();
+    if (tid == 0) st_release_gpu(&flags[fb + b], 1);
   }
 }
 
@@ -1697,8 +1834,24 @@ void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* front
 // r * ldv (T), of the workspace vec at r * vstride (T)
 template <class T, int NR>
 void solve_fronts_nr(const Mesh& m, const T* fronts, const int32_t* perm, const double* b, double* x, T* vec, T* yv,
-                     int64_t ldv, int64_t vstride, bool blk, cudaStream_t s) {
+                     int64_t ldv, int64_t vstride, bool blk, int32_t* chain, int32_t* err, cudaStream_t s) {
   FT ft = make_ft(m, blk);
+  VIV_CHECK(!blk || (chain && err), VIV_ERR_ARG, "block-LU solves need the case's chain flags");
+  // the level's multi-CTA chains (block-LU fronts of order >= MULTI_CHAIN_P)
+  auto multi = [&](int l, bool fwd) {
+    if constexpr (std::is_same<T, float>::value) {
+      const int n = blk ? m.mc_off[l + 1] - m.mc_off[l] : 0;
+      if (!n) return;
+      VIV_CUDA(cudaMemsetAsync(chain, 0, (1 + (size_t)m.mc_flags) * sizeof(int32_t), s));
+      Launched L(fwd ? K_FWD : K_BWD, s);
+      const int grid = std::min(n, device_sm_count());
+      const int32_t* tasks = (fwd ? m.d_mc_fwd : m.d_mc_bwd) + 3 * (int64_t)m.mc_off[l];
+      if (fwd)
+        chain_multi_kernel<T, NR, true><<<grid, MC_THREADS, 0, s>>>(ft, tasks, n, fronts, yv, x, chain, err, ldv);
+      else
+        chain_multi_kernel<T, NR, false><<<grid, MC_THREADS, 0, s>>>(ft, tasks, n, fronts, yv, x, chain, err, ldv);
+    }
+  };
   prepare_kernels<T>();
   for (int l = 0; l < m.n_levels; ++l) {
     prof_level(l);
@@ -1710,6 +1863,7 @@ void solve_fronts_nr(const Mesh& m, const T* fronts, const int32_t* perm, const 
       fwd_tri_kernel<T, NR><<<n, std::min(m.level_threads[l], solve_threads_max<T>()), sm ? need : 0, s>>>(
           ft, m.d_level_fronts + m.level_off[l], fronts, perm, b, vec, yv, sm, ldv, vstride);
     }
+    multi(l, true);
     const int ng = m.fg_off[l + 1] - m.fg_off[l];
     if (ng) {
       Launched L(K_FWD, s);
@@ -1728,9 +1882,12 @@ void solve_fronts_nr(const Mesh& m, const T* fronts, const int32_t* perm, const 
     const int n = m.level_off[l + 1] - m.level_off[l];
     const size_t need = (size_t)NR * m.level_maxp[l] * sizeof(T);
     const bool sm = need <= (size_t)SOLVE_SMEM_MAX;
-    Launched L(K_BWD, s);
-    bwd_tri_kernel<T, NR><<<n, std::min(m.level_threads[l], solve_threads_max<T>()), sm ? need : 0, s>>>(
-        ft, m.d_level_fronts + m.level_off[l], fronts, yv, vec, x, sm, ldv, vstride);
+    {
+      Launched L(K_BWD, s);
+      bwd_tri_kernel<T, NR><<<n, std::min(m.level_threads[l], solve_threads_max<T>()), sm ? need : 0, s>>>(
+          ft, m.d_level_fronts + m.level_off[l], fronts, yv, vec, x, sm, ldv, vstride);
+    }
+    multi(l, false);
   }
   prof_level(-1);
   VIV_CUDA(cudaGetLastError());
@@ -1738,16 +1895,16 @@ void solve_fronts_nr(const Mesh& m, const T* fronts, const int32_t* perm, const 
 
 template <class T>
 void solve_fronts(const Mesh& m, const T* fronts, const int32_t* perm, const double* b, double* x, T* vec, T* yv,
-                  bool blk, cudaStream_t s) {
-  solve_fronts_nr<T, 1>(m, fronts, perm, b, x, vec, yv, m.n_dofs, m.vec_entries, blk, s);
+                  bool blk, int32_t* chain, int32_t* err, cudaStream_t s) {
+  solve_fronts_nr<T, 1>(m, fronts, perm, b, x, vec, yv, m.n_dofs, m.vec_entries, blk, chain, err, s);
 }
 
 // two right-hand sides in one pass (the border columns): b, x, yv hold two
 // vectors of m.n_dofs, vec two workspaces of m.vec_entries
 template <class T>
 void solve_fronts2(const Mesh& m, const T* fronts, const int32_t* perm, const double* b, double* x, T* vec, T* yv,
-                   bool blk, cudaStream_t s) {
-  solve_fronts_nr<T, 2>(m, fronts, perm, b, x, vec, yv, m.n_dofs, m.vec_entries, blk, s);
+                   bool blk, int32_t* chain, int32_t* err, cudaStream_t s) {
+  solve_fronts_nr<T, 2>(m, fronts, perm, b, x, vec, yv, m.n_dofs, m.vec_entries, blk, chain, err, s);
 }
 
 template void factor_numeric<double>(const Mesh&, const double*, const float*, double*, int32_t*, int32_t*,
@@ -1755,12 +1912,12 @@ template void factor_numeric<double>(const Mesh&, const double*, const float*, d
 template void factor_numeric<float>(const Mesh&, const double*, const float*, float*, int32_t*, int32_t*, int32_t*,
                                     double, bool, unsigned char*, cudaStream_t);
 template void solve_fronts<double>(const Mesh&, const double*, const int32_t*, const double*, double*, double*,
-                                   double*, bool, cudaStream_t);
+                                   double*, bool, int32_t*, int32_t*, cudaStream_t);
 template void solve_fronts<float>(const Mesh&, const float*, const int32_t*, const double*, double*, float*,
-                                  float*, bool, cudaStream_t);
+                                  float*, bool, int32_t*, int32_t*, cudaStream_t);
 template void solve_fronts2<double>(const Mesh&, const double*, const int32_t*, const double*, double*, double*,
-                                    double*, bool, cudaStream_t);
+                                    double*, bool, int32_t*, int32_t*, cudaStream_t);
 template void solve_fronts2<float>(const Mesh&, const float*, const int32_t*, const double*, double*, float*,
-                                   float*, bool, cudaStream_t);
+                                   float*, bool, int32_t*, int32_t*, cudaStream_t);
 
 }  // namespace viv

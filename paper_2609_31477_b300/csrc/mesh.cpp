@@ -12,6 +12,7 @@
 //     index lists, assembly and extend-add maps, and the launch schedule of
 //     the blocked numeric factorisation
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -816,6 +817,35 @@ void build_schedule(Mesh& m, int big_front) {
   m.window_tc_flops = m.window_lu_flops = m.window_gemm_flops = 0;
   m.blk_front.assign(m.n_fronts, 0);
   for (int f = 0; f < m.n_fronts; ++f) m.blk_front[f] = m.block_lu && block_front(m, f, big_front) ? 1 : 0;
+  // multi-CTA chains: tasks per level, flags per block
+  m.mc_fwd.clear();
+  m.mc_bwd.clear();
+  m.mc_off.assign(m.n_levels + 1, 0);
+  m.mc_flags = 0;
+  m.chain_flag_bound = 0;
+  for (int f = 0; f < m.n_fronts; ++f)
+    if (m.f_p[f] >= MULTI_CHAIN_P) m.chain_flag_bound += (m.f_p[f] + OUTER_NB - 1) / OUTER_NB;
+  for (int l = 0; l < m.n_levels; ++l) {
+    std::vector<std::array<int, 3>> fr;   // (front, blocks, first flag)
+    for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
+      const int f = m.level_fronts[q];
+      if (m.blk_front[f] && m.f_p[f] >= MULTI_CHAIN_P) {
+        m.blk_front[f] = 2;
+        const int nblk = (m.f_p[f] + OUTER_NB - 1) / OUTER_NB;
+        fr.push_back({f, nblk, m.mc_flags});
+        m.mc_flags += nblk;
+      }
+    }
+    int maxb = 0;
+    for (auto& e : fr) maxb = std::max(maxb, e[1]);
+    for (int d = 0; d < maxb; ++d)
+      for (auto& e : fr)
+        if (d < e[1]) {
+          m.mc_fwd.insert(m.mc_fwd.end(), {e[0], d, e[2]});
+          m.mc_bwd.insert(m.mc_bwd.end(), {e[0], e[1] - 1 - d, e[2]});
+        }
+    m.mc_off[l + 1] = (int)(m.mc_fwd.size() / 3);
+  }
   m.inv_items_blk.clear();
   for (size_t q = 0; q + 1 < m.inv_items.size(); q += 2)
     if (!m.blk_front[m.inv_items[q]]) {
@@ -1086,6 +1116,15 @@ void upload_work(Mesh& m, cudaStream_t s) {
   if (!m.inv_items_blk.empty())
     VIV_CUDA(cudaMemcpyAsync(m.d_inv_items_blk, m.inv_items_blk.data(), m.inv_items_blk.size() * sizeof(int32_t),
                              cudaMemcpyHostToDevice, s));
+  if (m.mc_cap < std::max<size_t>(1, m.mc_fwd.size())) {
+    m.mc_cap = std::max<size_t>(1, m.mc_fwd.size());
+    m.d_mc_fwd = m.arena.make<int32_t>(m.mc_cap);
+    m.d_mc_bwd = m.arena.make<int32_t>(m.mc_cap);
+  }
+  if (!m.mc_fwd.empty()) {
+    VIV_CUDA(cudaMemcpyAsync(m.d_mc_fwd, m.mc_fwd.data(), m.mc_fwd.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    VIV_CUDA(cudaMemcpyAsync(m.d_mc_bwd, m.mc_bwd.data(), m.mc_bwd.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  }
   VIV_CUDA(cudaStreamSynchronize(s));
   m.sched_version += 1;
 }

@@ -72,10 +72,10 @@ void lu_solve_noalloc(vivCase* c, const double* b, double* x) {
   unsigned char* base = static_cast<unsigned char*>(scratch_address());
   if (f32)
     solve_fronts<float>(m, (const float*)c->s.fronts, c->s.perm, b, x, (float*)base, (float*)(base + vec_bytes),
-                        block_factors(c), c->stream);
+                        block_factors(c), c->s.chain, c->s.stats + 2, c->stream);
   else
     solve_fronts<double>(m, (const double*)c->s.fronts, c->s.perm, b, x, (double*)base,
-                         (double*)(base + vec_bytes), false, c->stream);
+                         (double*)(base + vec_bytes), false, nullptr, nullptr, c->stream);
   // the cylinder position through the FP64 border Schur block formed at factorisation
   if (border)
     launch_border_solve(m, c->s.J64, b, x, c->s.Y, c->s.Sb, (double*)(base + vec_bytes + yv_bytes), c->stream);

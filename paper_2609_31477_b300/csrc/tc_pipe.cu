@@ -11,7 +11,6 @@
 #include "viv_internal.h"
 
 namespace viv {
-int device_sm_count();
 namespace tcp {
 
 // ---- split ---------------------------------------------------------------------

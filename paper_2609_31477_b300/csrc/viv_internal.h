@@ -80,6 +80,7 @@ constexpr int SOLVE_SLICE = 256;
 constexpr int PERM_SMEM_MAX = 200 * 1024;   // composed permutation of one front (2 ints per pivot)
 constexpr int BIG_FRONT = 96;    // default: fronts at least this large use 128-column outer blocks
 constexpr int OUTER_NB = 128;    // outer block width (K of the outer Schur update)
+constexpr int MULTI_CHAIN_P = 512;   // block-LU fronts with this many pivots solve their chains on many CTAs
 // operand images of the tensor-core updates: 32 KB per 128 x 32 chunk (hi + lo);
 // the launches of one outer-block step are cut into groups of at most this
 // many chunks, which bounds each mixed case's image buffer (256 MB)
@@ -171,8 +172,14 @@ struct Mesh {
   // windowed FP32 schedule: fronts whose 128-column blocks the block LU
   // factors (it stores each block's diagonal part inverted: the solves step
   // 128 rows at a time there), and the 32 x 32 inversions left for the others
-  std::vector<uint8_t> blk_front;
+  std::vector<uint8_t> blk_front;      // 1: block-LU front, 2: and its solve chains span many CTAs
   std::vector<int32_t> inv_items_blk;
+  // multi-CTA solve chains (block-LU fronts of order >= MULTI_CHAIN_P): per
+  // level, tasks (front, block, first flag) in dependency order (forward:
+  // blocks top down, backward: bottom up; fronts interleaved), and one flag
+  // per block (per case: chain_flag_bound covers any large-front threshold)
+  std::vector<int32_t> mc_fwd, mc_bwd, mc_off;
+  int32_t mc_flags = 0, chain_flag_bound = 0;
   std::vector<int32_t> fg_items, fg_off;   // forward slice items (f, r0, slice, 0) by level
   std::vector<int32_t> bg_items, bg_off;   // backward slice items by level
   int64_t front_entries = 0, vec_entries = 0, piv_entries = 0;
@@ -208,6 +215,9 @@ struct Mesh {
   int32_t* d_inv_items = nullptr;
   uint8_t* d_blk_front = nullptr;      // (device copies, sized once: n_fronts / inv_items)
   int32_t* d_inv_items_blk = nullptr;
+  int32_t* d_mc_fwd = nullptr;         // (device copies, sized for the largest task list)
+  int32_t* d_mc_bwd = nullptr;
+  size_t mc_cap = 0;
   int32_t* d_fg_items = nullptr;
   int32_t* d_bg_items = nullptr;
   int32_t *d_bc_col = nullptr, *d_bc_q = nullptr, *d_bb_row = nullptr, *d_bb_q = nullptr;
@@ -233,7 +243,8 @@ struct CaseState {
   void* yv;                             // forward-solve vector (n_dofs)
   int32_t* piv;                         // row pivots of all fronts
   int32_t* perm;                        // composed row permutation of each front (solves)
-  int32_t* stats;                       // [0] perturbed, [1] threshold misses, [2] tensor-core wait expired
+  int32_t* stats;                       // [0] perturbed, [1] threshold misses, [2] a bounded device wait expired
+  int32_t* chain;                       // multi-CTA solve chains: task counter + one flag per block
   unsigned char* tc_img;                // operand images of the tensor-core updates (mixed path)
   double* Y;                            // border: A^{-1} B (2 columns of n_dofs; rows < n_front_dofs used)
   double* Sb;                           // border: S_b = D - C Y (4) and its inverse (4), FP64
@@ -353,14 +364,17 @@ void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* front
                     int32_t* stats, double threshold, bool window, unsigned char* tc_img, cudaStream_t s);
 // the case's factors come from the block LU (mixed precision, windowed pivoting)
 bool block_factors(const vivCase* c);
+int device_sm_count();   // streaming multiprocessors of the current device
 // blk: the factors come from the block LU of the windowed FP32 schedule
 // (diagonal 128-blocks of the flagged fronts stored inverted)
+// (chain: the case's multi-CTA chain flags, err: its expired-wait flag;
+// both used with blk)
 template <class T>
 void solve_fronts(const Mesh& m, const T* fronts, const int32_t* perm, const double* b, double* x,
-                  T* vec, T* yv, bool blk, cudaStream_t s);
+                  T* vec, T* yv, bool blk, int32_t* chain, int32_t* err, cudaStream_t s);
 template <class T>
 void solve_fronts2(const Mesh& m, const T* fronts, const int32_t* perm, const double* b, double* x, T* vec, T* yv,
-                   bool blk, cudaStream_t s);
+                   bool blk, int32_t* chain, int32_t* err, cudaStream_t s);
 }  // namespace viv
 
 // ----- canonical order of the element matrix pairs scattered through e2nz ----
