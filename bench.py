@@ -33,6 +33,7 @@ WORKLOADS = {
     "viv_re200_m60": dict(m=60, Re=200.0, Ustar=10.0, dt=0.02),
     "viv_re100_m12": dict(m=12, Re=100.0, Ustar=8.0, dt=0.1),
     "viv_re100_m24": dict(m=24, Re=100.0, Ustar=8.0, dt=0.05),
+    "viv_re200_m40": dict(m=40, Re=200.0, Ustar=10.0, dt=0.02),   # (profiling: top fronts of ~2,500)
 }
 FP32_SIMT_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12      # 148 SMs x 128 FP32 lanes x FMA x 2.032 GHz
 # DRAM bytes (read + write) per 128 x 128 tile of the tensor-core Schur update (tc_pipe_kernel), from one

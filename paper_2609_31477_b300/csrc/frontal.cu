@@ -1013,26 +1013,36 @@ __global__ void __launch_bounds__(BLK_MAX_THREADS, 1) block_lu_kernel(FT ft, con
   write_operand_image(img, a_blk, nch, [&](int i, int k) { return (i < nn && i > k) ? -W[i * ld + k] : 0.f; });
 }
 
-// the blocks' row permutations (one per 32-row window) on the front columns
-// outside the block; item {f, k2, c0}: columns c0 .. c0 + 255
-__global__ void __launch_bounds__(256) block_perm_kernel(FT ft, const int32_t* work, float* pool,
-                                                         const int32_t* perm) {
-  __shared__ int s_src[OUTER_NB];
+// the block's row permutation (new row i of the block holds old row s_src[i],
+// which stays inside its 32-row window) on the front's columns outside the
+// block; item {f, k2, c0}: columns c0 .. c0 + 255.  Threads are rows of the
+// block (coalesced within a column), two column groups per CTA, eight columns
+// per thread in flight: all reads of a batch before its writes.
+constexpr int PERM_THREADS = 2 * OUTER_NB;
+__global__ void __launch_bounds__(PERM_THREADS) block_perm_kernel(FT ft, const int32_t* work, float* pool,
+                                                                  const int32_t* perm) {
   const int32_t* it = work + WORK_STRIDE * blockIdx.x;
-  const int f = it[0], k2 = it[1], c = it[2] + threadIdx.x;
+  const int f = it[0], k2 = it[1], c0 = it[2];
   const int m = ft.m[f], p = ft.p[f];
   const int nb = min(OUTER_NB, p - k2);
-  if (threadIdx.x < nb) s_src[threadIdx.x] = perm[ft.piv_off[f] + k2 + threadIdx.x] - k2;
-  __syncthreads();
-  if (c >= m || (c >= k2 && c < k2 + nb)) return;
-  float* col = pool + ft.off[f] + (int64_t)c * m + k2;
-  for (int j0 = 0; j0 < nb; j0 += PANEL_NB) {   // the permutations stay inside their windows
-    float x[PANEL_NB];
+  const int i = threadIdx.x & (OUTER_NB - 1), g = threadIdx.x >> 7;
+  const int src = i < nb ? perm[ft.piv_off[f] + k2 + i] : 0;   // absolute row
+  float* F = pool + ft.off[f];
+  const int c_end = min(c0 + 256, m);
+  for (int cb = c0; cb < c_end; cb += 16) {
+    float v[8];
 #pragma unroll
-    for (int i = 0; i < PANEL_NB; ++i) x[i] = j0 + i < nb ? col[s_src[j0 + i]] : 0.f;
+    for (int u = 0; u < 8; ++u) {
+      const int c = cb + 2 * u + g;
+      const bool ok = i < nb && c < c_end && (c < k2 || c >= k2 + nb);
+      v[u] = ok ? F[(int64_t)c * m + src] : 0.f;
+    }
+    __syncthreads();
 #pragma unroll
-    for (int i = 0; i < PANEL_NB; ++i)
-      if (j0 + i < nb) col[j0 + i] = x[i];
+    for (int u = 0; u < 8; ++u) {
+      const int c = cb + 2 * u + g;
+      if (i < nb && c < c_end && (c < k2 || c >= k2 + nb)) F[(int64_t)c * m + k2 + i] = v[u];
+    }
   }
 }
 
@@ -1768,7 +1778,8 @@ void factor_numeric(const Mesh& m, const double* J64, const float* J32, T* front
                                                                         (float)threshold, tc_img, L.aux);
         break;
       case L_BLOCK_PERM:
-        if constexpr (std::is_same<T, float>::value) block_perm_kernel<<<grid, 256, 0, s>>>(ft, w, fronts, perm);
+        if constexpr (std::is_same<T, float>::value)
+          block_perm_kernel<<<grid, PERM_THREADS, 0, s>>>(ft, w, fronts, perm);
         break;
       case L_TC_SPLIT:
         if constexpr (std::is_same<T, float>::value) tcp::split_launch(w, (int)L.count, fronts, ft.off, ft.m, tc_img, stats, (float)threshold, s);
