@@ -263,7 +263,8 @@ def run_sweep(viv, I, n_cases, n_steps, pivoting, jacobian_fp32, predictor, seed
             "cases_per_hour_at_200_steps": 3600.0 * ok / last * n_steps / 200.0 if last else None,
             "peak_active": st["peak_active"], "peak_gb": st["peak_bytes"] / 1e9,
             "quads": sorted({int(1552 * (m / 12) ** 2) for m, _, _ in cases}),
-            "sample": f"{n_cases} of 64 cases, {n_steps} of 200 steps each; cases/hour extrapolated"}
+            "sample": ("the full sweep: 64 cases x 200 steps" if (n_cases, n_steps) == (64, 200) else
+                       f"{n_cases} of 64 cases, {n_steps} of 200 steps each; cases/hour extrapolated")}
 
 
 def run_reference(args, wl, rank):
