@@ -75,12 +75,14 @@ struct FT {   // front tables passed by value
   const int32_t* col_nz;
   const int64_t* col_nz_off;
   const uint8_t* blk;   // solves: fronts whose 128-row diagonal blocks are stored inverted (or null)
+  const uint8_t* fused; // solves: slice products formed in the chain CTA (1 forward, 2 backward)
 };
 
 FT make_ft(const Mesh& m, bool blk = false) {
   const FrontTables& t = m.ft;
   return FT{t.off, t.m, t.p, t.first, t.idx_off, t.idx, t.nz_off, t.nz_csr, t.nz_pos, t.child_off,
-            t.child, t.ea_off, t.ea, t.vec_off, t.piv_off, t.col_nz, t.col_nz_off, blk ? m.d_blk_front : nullptr};
+            t.child, t.ea_off, t.ea, t.vec_off, t.piv_off, t.col_nz, t.col_nz_off, blk ? m.d_blk_front : nullptr,
+            m.d_solve_fused};
 }
 
 __device__ __forceinline__ int lower_bound_i(const int32_t* a, int n, int v) {
@@ -1502,6 +1504,29 @@ __global__ void __launch_bounds__(solve_threads_max<T>(), 1) fwd_tri_kernel(FT f
     }
     // (a short last block has no pivot rows below it)
   }
+  if ((ft.fused[f] & 1) && m > p) {   // (uniform) L21 x of the non-pivot rows: slice 0 of the partial sums
+    __syncthreads();   // the chain's x (yv) written
+    if (in_smem) {     // x into the shared tmp (otherwise tmp is yv itself)
+      for (int c = threadIdx.x; c < p; c += blockDim.x)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) tmp[r][c] = yv[r * ldv + first + c];
+      __syncthreads();
+    }
+    for (int i = p + threadIdx.x; i < m; i += blockDim.x) {
+      const T* row = F + i;
+      T a[NR];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) a[r] = T(0);
+#pragma unroll 8
+      for (int c = 0; c < p; ++c) {
+        const T l = row[(int64_t)c * m];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) a[r] += l * tmp[r][c];
+      }
+#pragma unroll
+      for (int r = 0; r < NR; ++r) vec[r * vstride + ft.vec_off[f] + m + (i - p)] = a[r];
+    }
+  }
   if (in_smem)
     for (int i = p + threadIdx.x; i < m; i += blockDim.x)
 #pragma unroll
@@ -1524,14 +1549,37 @@ __global__ void __launch_bounds__(solve_threads_max<T>(), 1) bwd_tri_kernel(FT f
   for (int r = 0; r < NR; ++r) v[r] = in_smem ? vsm + (int64_t)r * p : yv + r * ldv + first;
   const T* F = pool + ft.off[f];
   const int ns = (m - p + SOLVE_SLICE - 1) / SOLVE_SLICE;
-  for (int i = threadIdx.x; i < p; i += blockDim.x)
+  if ((ft.fused[f] & 2) && m > p) {   // (uniform) U12 x2 formed here: x2 of the non-pivot columns first
+    __shared__ T x2s[NR][SOLVE_SLICE];
+    const int32_t* idx = ft.idx + ft.idx_off[f];
+    for (int c = threadIdx.x; c < m - p; c += blockDim.x)
 #pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      const T* part = vec + r * vstride + ft.vec_off[f] + m;
-      T a = yv[r * ldv + first + i];
-      for (int s2 = 0; s2 < ns; ++s2) a -= part[(int64_t)s2 * p + i];
-      v[r][i] = a;
+      for (int r = 0; r < NR; ++r) x2s[r][c] = (T)x[r * ldv + idx[p + c]];
+    __syncthreads();
+    for (int i = threadIdx.x; i < p; i += blockDim.x) {
+      const T* row = F + (int64_t)p * m + i;
+      T a[NR];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) a[r] = T(0);
+#pragma unroll 8
+      for (int c = 0; c < m - p; ++c) {
+        const T u = row[(int64_t)c * m];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) a[r] += u * x2s[r][c];
+      }
+#pragma unroll
+      for (int r = 0; r < NR; ++r) v[r][i] = yv[r * ldv + first + i] - a[r];
     }
+  } else {
+    for (int i = threadIdx.x; i < p; i += blockDim.x)
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        const T* part = vec + r * vstride + ft.vec_off[f] + m;
+        T a = yv[r * ldv + first + i];
+        for (int s2 = 0; s2 < ns; ++s2) a -= part[(int64_t)s2 * p + i];
+        v[r][i] = a;
+      }
+  }
   if (ft.blk && ft.blk[f] == 2) {   // the chain runs on many CTAs (chain_multi_kernel): v -> yv
     if (in_smem)
       for (int i = threadIdx.x; i < p; i += blockDim.x)

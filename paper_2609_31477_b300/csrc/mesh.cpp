@@ -634,14 +634,25 @@ void build_mesh(Mesh& m, const vivMeshDesc* d) {
   m.bg_items.clear();
   m.fg_off.assign(m.n_levels + 1, 0);
   m.bg_off.assign(m.n_levels + 1, 0);
+  m.solve_fused.assign(NF, 0);
   for (int l = 0; l < m.n_levels; ++l) {
+    bool fuse_f = true, fuse_b = true;
     for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
       const int f = m.level_fronts[q];
       const int pp = m.f_p[f], nn = m.f_m[f] - pp;
-      for (int s0 = 0; s0 * SOLVE_SLICE < pp; ++s0)
-        for (int r0 = 0; r0 < nn; r0 += SOLVE_ROWS) m.fg_items.insert(m.fg_items.end(), {f, r0, s0, 0});
-      for (int s0 = 0; s0 * SOLVE_SLICE < nn; ++s0)
-        for (int r0 = 0; r0 < pp; r0 += SOLVE_ROWS) m.bg_items.insert(m.bg_items.end(), {f, r0, s0, 0});
+      fuse_f = fuse_f && pp <= SOLVE_FUSE_F && nn <= 2 * SOLVE_SLICE;
+      fuse_b = fuse_b && nn <= SOLVE_FUSE_B && pp <= SOLVE_SLICE;
+    }
+    for (int q = m.level_off[l]; q < m.level_off[l + 1]; ++q) {
+      const int f = m.level_fronts[q];
+      const int pp = m.f_p[f], nn = m.f_m[f] - pp;
+      m.solve_fused[f] = (fuse_f ? 1 : 0) | (fuse_b ? 2 : 0);
+      if (!(m.solve_fused[f] & 1))
+        for (int s0 = 0; s0 * SOLVE_SLICE < pp; ++s0)
+          for (int r0 = 0; r0 < nn; r0 += SOLVE_ROWS) m.fg_items.insert(m.fg_items.end(), {f, r0, s0, 0});
+      if (!(m.solve_fused[f] & 2))
+        for (int s0 = 0; s0 * SOLVE_SLICE < nn; ++s0)
+          for (int r0 = 0; r0 < pp; r0 += SOLVE_ROWS) m.bg_items.insert(m.bg_items.end(), {f, r0, s0, 0});
     }
     m.fg_off[l + 1] = (int32_t)(m.fg_items.size() / 4);
     m.bg_off[l + 1] = (int32_t)(m.bg_items.size() / 4);
@@ -1145,6 +1156,7 @@ void upload_mesh(Mesh& m, cudaStream_t s) {
   m.d_fcolor_faces = A.upload(m.fcolor_faces, s);
   m.d_level_fronts = A.upload(m.level_fronts, s);
   m.d_inv_items = A.upload(m.inv_items, s);
+  m.d_solve_fused = A.upload(m.solve_fused, s);
   m.d_fg_items = A.upload(m.fg_items, s);
   m.d_bg_items = A.upload(m.bg_items, s);
   m.d_bc_col = A.upload(m.bc_col, s);

@@ -77,6 +77,14 @@ constexpr int WINDOW_THREADS = 256;   // rows or columns per WINDOW item
 // as items of SOLVE_ROWS rows x SOLVE_SLICE columns (one partial sum per slice)
 constexpr int SOLVE_ROWS = 256;
 constexpr int SOLVE_SLICE = 256;
+// levels of small fronts form those products inside their chain CTAs instead
+// (one thread per row, a loop over the columns), decided per tree level so a
+// level runs one launch: forward when every front has at most SOLVE_FUSE_F
+// pivots and 2 SOLVE_SLICE non-pivot rows, backward when every front has at
+// most SOLVE_FUSE_B non-pivot columns and SOLVE_SLICE pivots (measured at
+// 38,800 quads: longer loops lose to the multi-CTA slice products)
+constexpr int SOLVE_FUSE_F = 64;
+constexpr int SOLVE_FUSE_B = 200;
 constexpr int PERM_SMEM_MAX = 200 * 1024;   // composed permutation of one front (2 ints per pivot)
 constexpr int BIG_FRONT = 96;    // default: fronts at least this large use 128-column outer blocks
 constexpr int OUTER_NB = 128;    // outer block width (K of the outer Schur update)
@@ -169,6 +177,7 @@ struct Mesh {
   std::vector<int32_t> level_maxp;     // largest pivot count per level
   int max_p = 0;                       // largest pivot count of any front
   std::vector<int32_t> inv_items;      // (front, first row) of every 32 x 32 diagonal block
+  std::vector<uint8_t> solve_fused;    // per front: 1 forward, 2 backward slice products in the chain CTA
   // windowed FP32 schedule: fronts whose 128-column blocks the block LU
   // factors (it stores each block's diagonal part inverted: the solves step
   // 128 rows at a time there), and the 32 x 32 inversions left for the others
@@ -213,6 +222,7 @@ struct Mesh {
   int32_t* d_fcolor_faces = nullptr;
   int32_t* d_level_fronts = nullptr;
   int32_t* d_inv_items = nullptr;
+  uint8_t* d_solve_fused = nullptr;
   uint8_t* d_blk_front = nullptr;      // (device copies, sized once: n_fronts / inv_items)
   int32_t* d_inv_items_blk = nullptr;
   int32_t* d_mc_fwd = nullptr;         // (device copies, sized for the largest task list)
