@@ -41,7 +41,8 @@ typedef enum {
   VIV_ERR_PIVOT = 4,           /* a front met an exactly zero pivot column */
   VIV_ERR_NEWTON = 5,          /* Newton did not reach the tolerance in max_newton */
   VIV_ERR_NONFINITE = 6,       /* a residual or correction norm is NaN/Inf */
-  VIV_ERR_TIMEOUT = 7,         /* a bounded device wait expired (tensor-core mbarrier) */
+  VIV_ERR_TIMEOUT = 7,         /* a bounded device wait expired (tensor-core mbarrier, or a
+                                  multi-CTA solve chain's release flag) */
   VIV_ERR_ADMISSION = 8,       /* server: request exceeds the memory budget */
   VIV_ERR_STATE = 9            /* call out of order (e.g. solve before factor) */
 } vivStatus;
@@ -282,7 +283,10 @@ vivStatus viv_get_jacobian(const vivCase* c, double* vals);
  * the factors), S_b = D - C Y, and S_b^{-1}, all in FP64; every solve then
  * takes delta = S_b^{-1} (b_delta - C A^{-1} b_A).  A singular S_b returns
  * VIV_ERR_PIVOT from viv_step.  The factors keep each 32 x 32 diagonal block's
- * L and U inverted (for the solves) and are read only by this library's
+ * L and U inverted (for the solves); on the mixed path with windowed pivoting
+ * the fronts of order >= the large-front threshold with more than 32 pivots
+ * are factored in 128-column blocks and keep each 128 x 128 diagonal block's
+ * L and U inverted instead.  The factors are read only by this library's
  * solves. */
 vivStatus viv_factor(vivCase* c);
 /* The FP64 border Schur block S_b = D - C A^{-1} B of the last factorisation,

@@ -856,7 +856,7 @@ static void step_impl(vivCase* c, vivStepInfo* info) {
     int32_t stv[4];
     VIV_CUDA(cudaMemcpyAsync(stv, c->s.stats, sizeof(stv), cudaMemcpyDeviceToHost, c->stream));
     VIV_CUDA(cudaStreamSynchronize(c->stream));
-    VIV_CHECK(stv[2] == 0, VIV_ERR_TIMEOUT, "a tensor-core wait expired during the factorisation");
+    VIV_CHECK(stv[2] == 0, VIV_ERR_TIMEOUT, "a bounded device wait expired (tensor-core pipeline or solve chain)");
     VIV_CHECK(stv[3] == 0, VIV_ERR_PIVOT, "the border Schur block of the cylinder position is singular");
     st_acc[0] += stv[0];
     st_acc[1] += stv[1];
