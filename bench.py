@@ -54,7 +54,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="skip viv_autotune (large-front threshold and per-level block LU choice) before "
+                         "the warm-up steps")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--sweep-cases", type=int, default=16)
     ap.add_argument("--sweep-steps", type=int, default=10)
@@ -309,6 +311,7 @@ def run_ours(args, wl, rank, world, local):
     stream = case.stream           # every kernel of the case runs on its own stream
     if args.autotune:
         tuned = case.autotune()
+        info = M.refresh_info()
     for _ in range(args.warmup):
         case.step()
 
@@ -320,6 +323,9 @@ def run_ours(args, wl, rank, world, local):
     gpu_id = vis.split(",")[local] if vis else str(local)
     clocks = ClockSampler(gpu_id)
     l0 = viv.kernel_launches()
+    # (for an ncu launch list of the timed steps: this library's launches before them,
+    # to pass as ncu --kernel-name-base mangled -k regex:_ZN3viv -s <count>)
+    print(f"# library kernel launches before the timed steps: {l0}", file=sys.stderr, flush=True)
     barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -426,7 +432,8 @@ def run_ours(args, wl, rank, world, local):
            "roofline": roof, "rooflines_by_kind": rooflines, "gpu_launches": launches, "clocks": clk,
            "graphs": "residual, Jacobian, factorisation and refinement sweeps replayed as CUDA graphs"}
     if args.autotune:
-        out["autotune"] = {"big_front": tuned[0], "factor_ms": tuned[1]}
+        out["autotune"] = {"big_front": tuned[0], "factor_ms": tuned[1],
+                           "block_lu_levels": [l for l in range(info["n_levels"]) if info["block_level_mask"] >> l & 1]}
 
     if not args.no_fp64 and rank == 0:
         c64 = viv.viv_case(M, wl["Re"], wl["Ustar"], wl["dt"], u0, precision=viv.VIV_FP64, pivoting=piv,

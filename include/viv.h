@@ -113,6 +113,7 @@ typedef struct {
   double window_tc_flops;  /* tensor-core flops: L21, U12 and Schur updates of the 128-column blocks */
   double window_lu_flops;  /* LU flops of the pivot blocks (windows and block LU incl. the block inverses) */
   double window_gemm_flops;/* SIMT Schur-update flops (fronts below the large-front order) */
+  int64_t block_level_mask;/* tree levels (bit l) whose large fronts may use the block LU */
 } vivMeshInfo;
 
 /* Physical and solver parameters.  rho, mu: fluid density and viscosity;
@@ -386,7 +387,11 @@ vivStatus viv_case_graphs(vivCase* c, int on);
 /* Project autotuner: times the numeric factorisation of the case's current
  * Jacobian for several large-front thresholds (fronts at least this large use
  * 128-column outer blocks whose Schur updates run on the tensor cores) and
- * keeps the fastest schedule for the mesh.  Affects every case of the mesh;
+ * keeps the fastest.  On the mixed path with windowed pivoting it then chooses
+ * per tree level (a front-size bucket) between the block LU and the per-panel
+ * kernels for the level's large fronts, by the level's factorisation and solve
+ * time (vivMeshInfo.block_level_mask reports the choice).  The choice belongs
+ * to the mesh, never to a mix of cases: it affects every case of the mesh, so
  * call it while no other case of the mesh is running. */
 vivStatus viv_autotune(vivCase* c, int32_t* best_big_front, double* best_ms);
 /* Set the large-front threshold by hand (a front of order >= big_front uses

@@ -371,6 +371,9 @@ vivStatus viv_mesh_info(const vivMesh* mesh, vivMeshInfo* info) {
   info->window_tc_flops = m.window_tc_flops;
   info->window_lu_flops = m.window_lu_flops;
   info->window_gemm_flops = m.window_gemm_flops;
+  info->block_level_mask = 0;
+  for (int l = 0; l < m.n_levels && l < 64; ++l)
+    if (m.level_block.empty() || m.level_block[l]) info->block_level_mask |= (int64_t)1 << l;
   info->tc_image_bytes = (size_t)m.tc_img_chunks * TC_IMG_CHUNK_BYTES;
   API_END
 }
@@ -707,6 +710,37 @@ vivStatus viv_autotune(vivCase* c, int32_t* best_big_front, double* best_ms) {
       best_t = ms / 2;
       best = bf;
     }
+  }
+  // per tree level (a front-size bucket) on the windowed FP32 schedule: the
+  // block LU or the per-panel kernels for the level's large fronts, whichever
+  // factors the level and runs its part of one solve faster (per-level CUDA
+  // event timing; levels run one after the other, so their times add up)
+  if (mixed(c) && c->prm.pivoting == VIV_PIVOT_WINDOW) {
+    const bool prof_was_on = c->prof.on;
+    auto level_times = [&](std::vector<double>& t) {
+      build_schedule(m, best);
+      upload_work(m, c->stream);
+      factor(c);   // warm-up
+      lu_solve(c, c->s.R, c->s.d);
+      c->prof.used = 0;
+      c->prof.on = true;
+      factor(c);
+      lu_solve(c, c->s.R, c->s.d);
+      double ms[K_NKINDS];
+      int64_t cnt[K_NKINDS];
+      c->prof.read(ms, cnt);
+      c->prof.on = false;
+      t.assign(m.n_levels, 0.0);
+      for (int l = 0; l < m.n_levels && (size_t)(l + 1) * K_NKINDS <= c->prof.level_ms.size(); ++l)
+        for (int k = 0; k < K_NKINDS; ++k) t[l] += c->prof.level_ms[(size_t)l * K_NKINDS + k];
+    };
+    std::vector<double> t_on, t_off;
+    m.level_block.assign(m.n_levels, 1);
+    level_times(t_on);
+    m.level_block.assign(m.n_levels, 0);
+    level_times(t_off);
+    for (int l = 0; l < m.n_levels; ++l) m.level_block[l] = t_on[l] <= t_off[l] ? 1 : 0;
+    c->prof.on = prof_was_on;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

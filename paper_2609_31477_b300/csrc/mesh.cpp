@@ -696,7 +696,7 @@ void build_mesh(Mesh& m, const vivMeshDesc* d) {
 // fronts of the block path: large, with more than one pivot window (a single
 // window is factored faster by the per-panel kernels)
 static bool block_front(const Mesh& m, int f, int big_front) {
-  return m.f_m[f] >= big_front && m.f_p[f] > PANEL_NB;
+  return m.f_m[f] >= big_front && m.f_p[f] > PANEL_NB && (m.level_block.empty() || m.level_block[m.f_level[f]]);
 }
 
 template <class Push, class Open, class Close, class Items>

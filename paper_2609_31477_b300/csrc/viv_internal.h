@@ -182,6 +182,7 @@ struct Mesh {
   // factors (it stores each block's diagonal part inverted: the solves step
   // 128 rows at a time there), and the 32 x 32 inversions left for the others
   std::vector<uint8_t> blk_front;      // 1: block-LU front, 2: and its solve chains span many CTAs
+  std::vector<int8_t> level_block;     // per tree level: the block LU allowed (empty: every level; autotuner)
   std::vector<int32_t> inv_items_blk;
   // multi-CTA solve chains (block-LU fronts of order >= MULTI_CHAIN_P): per
   // level, tasks (front, block, first flag) in dependency order (forward:

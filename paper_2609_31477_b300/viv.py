@@ -46,7 +46,8 @@ class MeshInfo(C.Structure):
                 ("gemm_flops", C.c_double), ("panel_flops", C.c_double), ("trsm_flops", C.c_double),
                 ("outer_flops", C.c_double), ("tc_split_chunks", C.c_int64), ("tc_tiles", C.c_int64),
                 ("tc_image_bytes", C.c_size_t), ("window_tc_flops", C.c_double),
-                ("window_lu_flops", C.c_double), ("window_gemm_flops", C.c_double)]
+                ("window_lu_flops", C.c_double), ("window_gemm_flops", C.c_double),
+                ("block_level_mask", C.c_int64)]
 
 
 class Params(C.Structure):
@@ -253,10 +254,8 @@ class Mesh:
             self.stream = None
             _check(lib.viv_mesh_analyze(C.byref(d), C.byref(h)))
         self.h = h
-        info = MeshInfo()
-        _check(lib.viv_mesh_info(h, C.byref(info)))
-        self.info = {f: getattr(info, f) for f, _ in MeshInfo._fields_}
-        self.n_dofs = info.n_dofs
+        self.refresh_info()
+        self.n_dofs = self.info["n_dofs"]
         self.n_nodes = len(mesh["X"])
 
     def dof_labels(self):
@@ -271,6 +270,14 @@ class Mesh:
         col = np.empty(rp[-1], np.int32)
         _check(_lib.viv_mesh_pattern(self.h, _ptr(rp), _ptr(col)))
         return rp, col
+
+    def refresh_info(self):
+        """Re-read viv_mesh_info (the schedule counters change with the large-front
+        threshold and the autotuner's per-level choice)."""
+        info = MeshInfo()
+        _check(_lib.viv_mesh_info(self.h, C.byref(info)))
+        self.info = {f: getattr(info, f) for f, _ in MeshInfo._fields_}
+        return self.info
 
     def fronts(self):
         n = int(self.info["n_fronts"])

@@ -245,3 +245,24 @@ def test_large_front_threshold_and_level_profile(viv):
         assert uses_tc == any("tc_split" in d for d in lv)   # every tensor-core update splits its operands
     for bf in (1 << 30, 256):
         assert rel_l2(ys[bf], ys[96]) <= 1e-10, (bf, rel_l2(ys[bf], ys[96]))
+
+
+def test_autotune_per_level_keeps_the_solution(viv):
+    """The autotuner's choices (large-front threshold, then per tree level the
+    block LU or the per-panel kernels for the level's large fronts, windowed
+    FP32 schedule) change the factorisation's path, not the refined solution:
+    the same right-hand side solves to 1e-10 before and after, and the mask of
+    block-LU levels stays within the tree."""
+    mesh, oc, M, case = _pair(viv, 12, viv.VIV_MIXED, pivoting=viv.VIV_PIVOT_WINDOW)
+    _mid_step_state(viv, oc, case, 41)
+    case.assemble(viv.VIV_RES | viv.VIV_JAC)
+    b = np.random.default_rng(11).standard_normal(M.n_dofs)
+    case.factor()
+    y0, _ = case.solve_rhs(b)
+    bf, ms = case.autotune()
+    assert bf > 0 and ms > 0
+    info = M.refresh_info()
+    assert 0 <= info["block_level_mask"] < (1 << info["n_levels"])
+    case.factor()
+    y1, _ = case.solve_rhs(b)
+    assert rel_l2(y1, y0) <= 1e-10, rel_l2(y1, y0)
