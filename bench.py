@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="skip viv_autotune (large-front threshold and per-level block LU choice) before "
                          "the warm-up steps")
+    ap.add_argument("--big-front", type=int, default=0,
+                    help="with --block-levels: set this schedule instead of autotuning (reproducible profiles)")
+    ap.add_argument("--block-levels", type=int, default=None,
+                    help="tree levels allowed the block LU (bit mask), with --big-front")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--sweep-cases", type=int, default=16)
     ap.add_argument("--sweep-steps", type=int, default=10)
@@ -309,6 +313,13 @@ def run_ours(args, wl, rank, world, local):
     case = viv.viv_case(M, wl["Re"], wl["Ustar"], wl["dt"], u0, precision=viv.VIV_MIXED, pivoting=piv,
                         jacobian_fp32=j32, predictor=pred)
     stream = case.stream           # every kernel of the case runs on its own stream
+    if args.block_levels is not None or args.big_front:
+        args.autotune = False
+        if args.big_front:
+            case.set_big_front(args.big_front)
+        if args.block_levels is not None:
+            case.set_block_levels(args.block_levels)
+        info = M.refresh_info()
     if args.autotune:
         tuned = case.autotune()
         info = M.refresh_info()
@@ -431,6 +442,9 @@ def run_ours(args, wl, rank, world, local):
                         "note": "second pass with a CUDA event pair around every launch (kernels_ms, roofline)"},
            "roofline": roof, "rooflines_by_kind": rooflines, "gpu_launches": launches, "clocks": clk,
            "graphs": "residual, Jacobian, factorisation and refinement sweeps replayed as CUDA graphs"}
+    out["schedule"] = {"block_lu_levels": [l for l in range(info["n_levels"]) if info["block_level_mask"] >> l & 1],
+                       "set_by": "autotune" if args.autotune else ("flags" if args.big_front or args.block_levels
+                                                                   is not None else "library defaults")}
     if args.autotune:
         out["autotune"] = {"big_front": tuned[0], "factor_ms": tuned[1],
                            "block_lu_levels": [l for l in range(info["n_levels"]) if info["block_level_mask"] >> l & 1]}

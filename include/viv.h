@@ -398,6 +398,11 @@ vivStatus viv_autotune(vivCase* c, int32_t* best_big_front, double* best_ms);
  * 128-column outer blocks); rebuilds the mesh's schedules when it changes.
  * Same scope rules as viv_autotune.  VIV_ERR_ARG if big_front <= 0. */
 vivStatus viv_set_big_front(vivCase* c, int32_t big_front);
+/* Set by hand the tree levels whose large fronts may use the block LU (bit l
+ * for level l; -1: every level), as viv_autotune chooses them: a tuned
+ * schedule can be restored without re-tuning.  Rebuilds the mesh's schedules
+ * when the set changes; same scope rules as viv_autotune. */
+vivStatus viv_set_block_levels(vivCase* c, int64_t mask);
 
 /* ---- serving: parameter sweeps with continuous admission ------------------ */
 typedef struct vivServer vivServer;

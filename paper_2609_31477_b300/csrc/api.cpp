@@ -764,6 +764,21 @@ vivStatus viv_set_big_front(vivCase* c, int32_t big_front) {
   API_END
 }
 
+vivStatus viv_set_block_levels(vivCase* c, int64_t mask) {
+  API_BEGIN
+  VIV_CHECK(c, VIV_ERR_ARG, "viv_set_block_levels: NULL case");
+  Mesh& m = c->mesh->m;
+  std::vector<int8_t> want(m.n_levels);
+  for (int l = 0; l < m.n_levels; ++l) want[l] = (l >= 64 ? mask < 0 : ((mask >> l) & 1)) ? 1 : 0;
+  if (m.level_block != want) {
+    m.level_block = want;
+    build_schedule(m, m.big_front);
+    upload_work(m, c->stream);
+    c->factored = false;
+  }
+  API_END
+}
+
 vivStatus viv_lu_solve_noalloc(vivCase* c, const double* b, double* x) {
   API_BEGIN
   VIV_CHECK(c && b && x, VIV_ERR_ARG, "NULL argument");

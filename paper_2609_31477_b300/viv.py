@@ -161,6 +161,7 @@ SIGNATURES = {
     "viv_profile_read": (C.c_int, [_P, _P, _P]),
     "viv_profile_levels": (C.c_int, [_P, _P, C.c_int32, _P]),
     "viv_set_big_front": (C.c_int, [_P, C.c_int32]),
+    "viv_set_block_levels": (C.c_int, [_P, C.c_int64]),
     "viv_last_error": (C.c_char_p, []),
     "viv_version": (C.c_char_p, []),
 }
@@ -426,6 +427,9 @@ class Case:
 
     def set_big_front(self, big_front):
         _check(_lib.viv_set_big_front(self.h, int(big_front)))
+
+    def set_block_levels(self, mask):
+        _check(_lib.viv_set_block_levels(self.h, int(mask)))
 
     def profile(self, on=True):
         _check(_lib.viv_profile(self.h, int(on)))
