@@ -36,6 +36,7 @@ WORKLOADS = {
     "viv_re200_m40": dict(m=40, Re=200.0, Ustar=10.0, dt=0.02),   # (profiling: top fronts of ~2,500)
 }
 FP32_SIMT_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12      # 148 SMs x 128 FP32 lanes x FMA x 2.032 GHz
+FP64_TFLOPS = 1.25                                       # B300 FP64, nominal
 # DRAM bytes (read + write) per 128 x 128 tile of the tensor-core Schur update (tc_pipe_kernel), from one
 # ncu capture of that kernel; None until a capture of the current kernel exists (the line's traffic is null)
 TC_DRAM_BYTES_PER_TILE = None
@@ -397,6 +398,13 @@ def run_ours(args, wl, rank, world, local):
             return {"bound": "alu", "achieved": a, "peak": FP32_SIMT_TFLOPS, "unit": "TFLOP/s",
                     "frac": a / FP32_SIMT_TFLOPS,
                     "peak_source": "FP32 SIMT: 148 SMs x 128 lanes x 2 flop x 2.032 GHz (derived)"}
+        if kind == "residual":
+            # FP64 ALU: about 4k double FMAs per element per evaluation (quadrature of the Q2-Q1-Q2
+            # element residual, counted from the kernel's loops), against the nominal FP64 rate
+            evals = n_fact + args.steps          # one per Newton iteration, one for the converged state
+            a = 8.0e3 * len(mesh["conn"]) * evals / sec / 1e12
+            return {"bound": "alu", "achieved": a, "peak": FP64_TFLOPS, "unit": "TFLOP/s", "frac": a / FP64_TFLOPS,
+                    "peak_source": "FP64 nominal 1.25 TFLOP/s (no FP64 measurement); flops approximate"}
         per = {"fwd_solve": fbytes / 2, "bwd_solve": fbytes / 2, "front_assemble": 2 * fbytes,
                "spmv": 12 * info["nnz"] + 24 * info["n_dofs"], "jacobian": 12 * info["nnz"]}.get(kind)
         if per is None:
