@@ -85,17 +85,6 @@ FT make_ft(const Mesh& m, bool blk = false) {
             m.d_solve_fused};
 }
 
-__device__ __forceinline__ int lower_bound_i(const int32_t* a, int n, int v) {
-  int lo = 0, hi = n;
-  while (lo < hi) {
-    int mid = (lo + hi) >> 1;
-    if (a[mid] < v)
-      lo = mid + 1;
-    else
-      hi = mid;
-  }
-  return lo;
-}
 
 template <class T, class S>
 __global__ void assemble_kernel(FT ft, const int32_t* work, const S* J, T* pool) {
@@ -110,15 +99,43 @@ __global__ void assemble_kernel(FT ft, const int32_t* work, const S* J, T* pool)
   const int ch = c0 / ASM_COLS;
   const int64_t base = ft.nz_off[f];
   const int32_t* cn = ft.col_nz + ft.col_nz_off[f];
-  for (int64_t q = base + cn[ch] + threadIdx.x; q < base + cn[ch + 1]; q += blockDim.x)
-    F[ft.nz_pos[q]] = (T)J[ft.nz_csr[q]];
+  {   // the original entries, four per thread in flight (index loads, then the gathers, then the stores)
+    const int64_t q1 = base + cn[ch + 1];
+    for (int64_t q0 = base + cn[ch] + threadIdx.x; q0 < q1; q0 += 4 * (int64_t)blockDim.x) {
+      int32_t pos[4], src[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t q = q0 + (int64_t)u * blockDim.x;
+        pos[u] = q < q1 ? ft.nz_pos[q] : -1;
+        src[u] = q < q1 ? ft.nz_csr[q] : 0;
+      }
+      T v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = pos[u] >= 0 ? (T)J[src[u]] : T(0);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (pos[u] >= 0) F[pos[u]] = v[u];
+    }
+  }
+  __shared__ int64_t s_col[ASM_COLS];   // parent column offsets of the child columns in this chunk
   __syncthreads();
   for (int cc = ft.child_off[f]; cc < ft.child_off[f + 1]; ++cc) {
     const int c = ft.child[cc];
     const int mc = ft.m[c], pc = ft.p[c], nc = mc - pc;
     if (nc == 0) continue;
     const int32_t* ea = ft.ea + ft.ea_off[c];
-    const int lo = lower_bound_i(ea, nc, c0), hi = lower_bound_i(ea, nc, c1);
+    // the child's columns that map into [c0, c1): ea is increasing, so the
+    // bounds are counts, taken in one parallel pass (no dependent loads)
+    int lo = 0, hi = 0;
+    for (int b0 = 0; b0 < nc; b0 += blockDim.x) {
+      const int t = b0 + threadIdx.x;
+      const int e = t < nc ? ea[t] : INT_MAX;
+      lo += __syncthreads_count(e < c0);
+      hi += __syncthreads_count(e < c1);
+    }
+    if (hi == lo) continue;   // (uniform)
+    if (threadIdx.x < hi - lo) s_col[threadIdx.x] = (int64_t)ea[lo + threadIdx.x] * m;
+    __syncthreads();
     const T* C = pool + ft.off[c] + pc + (int64_t)pc * mc;   // the child's contribution block
     // threads as (row, column group): R rows per pass, G groups of the (at
     // most ASM_COLS) child columns that map into this chunk; four columns at
@@ -136,7 +153,7 @@ __global__ void assemble_kernel(FT ft, const int32_t* work, const S* J, T* pool)
           for (int u = 0; u < 4; ++u) {
             const int k = k0 + u * G;
             if (k < hi) {
-              fo[u] = er + (int64_t)ea[k] * m;
+              fo[u] = er + s_col[k - lo];
               cv[u] = Cr[(int64_t)k * mc];
               fv[u] = F[fo[u]];
             }
