@@ -247,6 +247,27 @@ __global__ void __launch_bounds__(THREADS, 1) tc_pipe_kernel(const int32_t* __re
       };
       load_group(c0v, 0);   // before the accumulator is ready: overlaps the MMAs
       load_group(c1v, 1);
+      // this warp's rows of the next tiles' C into L2 while this tile completes
+      // (lane l: columns l, l + 32, l + 64, l + 96; a 32-row column segment
+      // spans at most two 128-byte lines)
+      for (int ahead = 1; ahead <= PREFETCH_TILES && t + ahead * tstep < t1; ++ahead) {
+        const int32_t* nx = items + (int64_t)ITEM * (t + ahead * tstep);
+        const int nf = nx[0], row0 = nx[1] + quarter * 32, ncb = nx[2], nr_end = nx[3], nc_end = nx[4];
+        if (row0 < nr_end) {
+          const int64_t nld = ld[nf];
+          const float* nbase = pool + off[nf] + (int64_t)ncb * nld + row0;
+          const int last = min(32, nr_end - row0) - 1;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int j = lane + 32 * q;
+            if (ncb + j < nc_end) {
+              const float* p0 = nbase + (int64_t)j * nld;
+              asm volatile("prefetch.global.L2 [%0];" ::"l"(p0));
+              asm volatile("prefetch.global.L2 [%0];" ::"l"(p0 + last));
+            }
+          }
+        }
+      }
       const int acc = v & 1;
       const uint32_t use = (uint32_t)(v >> 1);
       int got = 0;

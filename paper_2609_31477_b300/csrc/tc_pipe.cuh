@@ -20,7 +20,8 @@
 //           (the C read-modify-write, the dominant memory traffic) overlaps the
 //           MMAs of the next; each epilogue thread owns one tile row and keeps
 //           64 loads of C in flight (two groups of 32 columns ahead), the first
-//           of them issued before it waits for the accumulator.
+//           of them issued before it waits for the accumulator, together with
+//           L2 prefetches of its warp's rows of the next tile's C.
 //
 // Every wait is bounded.  A wait that expires sets *err and a shared abort
 // flag that ends the other roles' waits; the MMA thread then waits (bounded)
@@ -54,6 +55,7 @@ constexpr uint32_t TMEM_COLS = 256;              // two 128-column FP32 accumula
 constexpr int SPLIT_THREADS = 256;
 constexpr int ITEM = 8;                          // ints per work item
 constexpr long long WAIT_LIMIT = 1LL << 26;      // polls before a wait gives up
+constexpr int PREFETCH_TILES = 1;                // tiles ahead whose C the epilogue prefetches into L2 (2: slower)
 
 // work items
 //   split: {f, start, kind (0: rows of A, 1: columns of B), k0, klen, block, limit, check}
