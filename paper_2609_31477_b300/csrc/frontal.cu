@@ -1699,8 +1699,17 @@ __global__ void __launch_bounds__(MC_THREADS) chain_multi_kernel(FT ft, const in
       for (int r = 0; r < NR; ++r) wr[r][tid] = tid < nr ? yv[r * ldv + first + r0 + tid] : T(0);
     __syncthreads();
     const int n_apply = FWD ? b : nblk - 1 - b;
+    // the factor lines this task reads next go to L2 ahead of time: thread
+    // (column tid / 4, 32-row line tid % 4) of a 128 x 128 block
+    auto prefetch_block = [&](int col0, int ncols) {
+      const int c = tid >> 2, q2 = tid & 3;
+      if (c < ncols && 32 * q2 < nr)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(F + (int64_t)(col0 + c) * m + r0 + 32 * q2));
+    };
+    prefetch_block(r0, nr);   // the own diagonal block's inverse
     for (int k = 0; k < n_apply; ++k) {
       const int kb = FWD ? k : nblk - 1 - k, c0 = OUTER_NB * kb, nc = min(OUTER_NB, p - c0);
+      prefetch_block(c0, nc);   // (while the flag is awaited)
       if (tid == 0) {   // bounded wait for block kb
         long long it = 0;
         while (!ld_acquire_gpu(&flags[fb + kb])) {
