@@ -251,8 +251,9 @@ def test_autotune_per_level_keeps_the_solution(viv):
     """The autotuner's choices (large-front threshold, then per tree level the
     block LU or the per-panel kernels for the level's large fronts, windowed
     FP32 schedule) change the factorisation's path, not the refined solution:
-    the same right-hand side solves to 1e-10 before and after, and the mask of
-    block-LU levels stays within the tree."""
+    the same right-hand side solves to 1e-10 before and after, the mask of
+    block-LU levels stays within the tree, and forcing the block LU on every
+    level or on none (viv_set_block_levels) gives the same solution too."""
     mesh, oc, M, case = _pair(viv, 12, viv.VIV_MIXED, pivoting=viv.VIV_PIVOT_WINDOW)
     _mid_step_state(viv, oc, case, 41)
     case.assemble(viv.VIV_RES | viv.VIV_JAC)
@@ -266,3 +267,11 @@ def test_autotune_per_level_keeps_the_solution(viv):
     case.factor()
     y1, _ = case.solve_rhs(b)
     assert rel_l2(y1, y0) <= 1e-10, rel_l2(y1, y0)
+    # every level on the block LU, then none (viv_set_block_levels): same solution
+    for mask in (-1, 0):
+        case.set_block_levels(mask)
+        info = M.refresh_info()
+        assert info["block_level_mask"] == ((1 << info["n_levels"]) - 1 if mask < 0 else 0)
+        case.factor()
+        y2, _ = case.solve_rhs(b)
+        assert rel_l2(y2, y0) <= 1e-10, (mask, rel_l2(y2, y0))
