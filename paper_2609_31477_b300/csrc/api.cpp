@@ -690,7 +690,7 @@ vivStatus viv_autotune(vivCase* c, int32_t* best_big_front, double* best_ms) {
   Mesh& m = c->mesh->m;
   if (!c->step_open) begin_step(c);
   assemble(c, VIV_JAC, false);
-  const int cands[] = {96, 128, 192, 256, 384, 512, 768, 1024, 1 << 30};
+  const int cands[] = {48, 64, 80, 96, 128, 192, 256, 384, 512, 768, 1024, 1 << 30};
   cudaEvent_t e0, e1;
   VIV_CUDA(cudaEventCreate(&e0));
   VIV_CUDA(cudaEventCreate(&e1));
