@@ -28,6 +28,8 @@ X_FIX_Y = 8    # mesh position y-component prescribed
 CYL = 16       # node on the rigid cylinder boundary Gamma (multiplier lives here)
 OUTLET = 32    # informational: natural outflow boundary
 P_FIX = 64     # pressure prescribed at this (vertex) node: removes the constant
+U_FIX_Z = 128  # velocity z-component prescribed (3-D meshes)
+X_FIX_Z = 256  # mesh position z-component prescribed (3-D meshes)
                # pressure mode of all-Dirichlet problems (Q = L^2/R, Section 3.1)
 
 INLET_TAG = U_FIX_X | U_FIX_Y | X_FIX_X | X_FIX_Y   # u = u_in, x = X
@@ -315,6 +317,67 @@ def hole_square_mesh(n, R0=0.15, center=(0.5, 0.5), lo=0.0, hi=1.0):
                 Xc=np.array([cx, cy], dtype=np.float64), D=2.0 * R0, name=f"hole_square_n{n}")
 
 
+# --- 3-D: periodic extrusion of a 2-D Q2 mesh into 27-node hexahedra -------------
+# local hex node index 9 c + 3 b + a (a along xi, b along eta, c along zeta);
+# local faces 0: xi=0, 1: xi=1, 2: eta=0, 3: eta=1, 4: zeta=0, 5: zeta=1
+def extrude_periodic(mesh2d, layers, span):
+    """Extrude a 2-D Q2 mesh over z in [0, span) into `layers` layers of Q2
+    hexahedra, periodic in z: node plane 2*layers is node plane 0, and the
+    nodes of the last layer's top face carry a wrap bit (their coordinates are
+    the stored ones + span e_z).  Periodicity is on the displacement x - X
+    (the position itself jumps by span e_z across the seam).
+
+    Tags: a 2-D node whose velocity (position) is fully prescribed has its z
+    component prescribed too; cylinder nodes keep their z position (the rigid
+    body moves in x and y only); a prescribed pressure stays on plane 0 only.
+    Gamma faces become the zeta-extruded faces of the 2-D Gamma edges
+    (2-D edge 0..3 -> hex face 0..3).  Returns X (n,3), conn (E,27), tags,
+    gamma_faces (F,2), wrap (E,) node bit masks, span, Xc, D."""
+    assert layers >= 2, "a periodic extrusion needs at least two layers"
+    X2 = np.asarray(mesh2d["X"], dtype=np.float64)
+    c2 = np.asarray(mesh2d["conn"], dtype=np.int64)
+    t2 = np.asarray(mesh2d["tags"], dtype=np.int64)
+    n2, E2 = len(X2), len(c2)
+    planes = 2 * layers
+    dz = span / planes
+    X = np.zeros((planes * n2, 3))
+    for k in range(planes):
+        X[k * n2:(k + 1) * n2, :2] = X2
+        X[k * n2:(k + 1) * n2, 2] = k * dz
+    tags = np.zeros(planes * n2, dtype=np.int32)
+    t3 = t2.copy()
+    full_u = (t2 & (U_FIX_X | U_FIX_Y)) == (U_FIX_X | U_FIX_Y)
+    full_x = (t2 & (X_FIX_X | X_FIX_Y)) == (X_FIX_X | X_FIX_Y)
+    t3[full_u] |= U_FIX_Z
+    t3[full_x | ((t2 & CYL) != 0)] |= X_FIX_Z
+    for k in range(planes):
+        tk = t3 if k == 0 else (t3 & ~P_FIX)
+        tags[k * n2:(k + 1) * n2] = tk
+    conn = np.zeros((layers * E2, 27), dtype=np.int64)
+    wrap = np.zeros(layers * E2, dtype=np.int64)
+    for l in range(layers):
+        for c in range(3):
+            plane = 2 * l + c
+            wrapped = plane >= planes
+            for b in range(3):
+                for a in range(3):
+                    conn[l * E2:(l + 1) * E2, 9 * c + 3 * b + a] = (plane % planes) * n2 + c2[:, 3 * b + a]
+                    if wrapped:
+                        wrap[l * E2:(l + 1) * E2] |= 1 << (9 * c + 3 * b + a)
+    gf2 = np.asarray(mesh2d["gamma_faces"], dtype=np.int64).reshape(-1, 2)
+    gf = np.concatenate([np.stack([gf2[:, 0] + l * E2, gf2[:, 1]], 1) for l in range(layers)]) \
+        if len(gf2) else np.zeros((0, 2), dtype=np.int64)
+    return dict(X=X, conn=conn, tags=tags, gamma_faces=gf.reshape(-1, 2), wrap=wrap, span=float(span),
+                Xc=np.asarray(mesh2d.get("Xc", np.zeros(2)), dtype=np.float64), D=float(mesh2d.get("D", 0.0)),
+                name=f"{mesh2d.get('name', 'mesh')}_z{layers}")
+
+
+def viv_cylinder_mesh3d(m=7, layers=24, span=2.0 * math.pi, **kw):
+    """The cylinder O-grid of `viv_cylinder_mesh(m)` extruded over a periodic
+    span (m = 7: 555 quads per section, 24 layers: 13,320 hexahedra)."""
+    return extrude_periodic(viv_cylinder_mesh(m, **kw), layers, span)
+
+
 # --- seeded normal samples: splitmix64 + Box-Muller ----------------------------
 _M64 = (1 << 64) - 1
 
@@ -369,5 +432,8 @@ def viv_case(name):
     table = {
         "viv_re100_m12": dict(m=12, Re=100.0, Ustar=8.0, dt=0.1, steps=10),
         "viv_re200_m60": dict(m=60, Re=200.0, Ustar=10.0, dt=0.02, steps=500),
+        # 3-D: the section of viv_cylinder_mesh(m) extruded into `layers` periodic layers
+        "viv3d_re300_m7_z24": dict(m=7, layers=24, span=2.0 * math.pi, Re=300.0, Ustar=8.0, dt=0.05,
+                                   steps=100),
     }
     return dict(table[name])
