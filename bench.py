@@ -34,6 +34,9 @@ WORKLOADS = {
     "viv_re100_m12": dict(m=12, Re=100.0, Ustar=8.0, dt=0.1),
     "viv_re100_m24": dict(m=24, Re=100.0, Ustar=8.0, dt=0.05),
     "viv_re200_m40": dict(m=40, Re=200.0, Ustar=10.0, dt=0.02),   # (profiling: top fronts of ~2,500)
+    # 3-D: the m = 7 section (555 quads) extruded into 24 periodic layers over a 2 pi span
+    # (13,320 Q2-Q1 hexahedra, 662,114 unknowns), Re 300, U* 8 (L = span), dt 0.05
+    "viv3d_re300_m7_z24": dict(m=7, layers=24, span=2.0 * math.pi, Re=300.0, Ustar=8.0, dt=0.05),
 }
 FP32_SIMT_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12      # 148 SMs x 128 FP32 lanes x FMA x 2.032 GHz
 FP64_TFLOPS = 1.25                                       # B300 FP64, nominal
@@ -199,6 +202,52 @@ def oracle_sample(wl, newton_iters):
     return 1.0 / per_step, desc, time.perf_counter() - t_all
 
 
+def oracle_sample3d(wl, newton_iters):
+    """The 3-D form of `oracle_sample`: residual on the full hexahedral mesh,
+    complex-step Jacobian on 1/64 of the elements (x64), sparse LU (SuperLU)
+    of the 194-hexahedron member (the m = 3 section in 2 layers) scaled by
+    (N ratio)^2, the 3-D nested-dissection cost law."""
+    import numpy as np
+    from paper_2609_31477_b300 import inputs as I
+    from oracle.solver import sparse_lu
+    from oracle.solver3d import viv_oracle_case3d
+    t_all = time.perf_counter()
+    mesh = I.viv_cylinder_mesh3d(wl["m"], wl["layers"], wl["span"])
+    u0 = I.viv_initial_velocity(mesh, 1.0, 1e-3, 1)
+    oc = viv_oracle_case3d(mesh, wl["Re"], wl["Ustar"], wl["dt"], u0)
+    oc.u_n, oc.x_n = oc.u.copy(), oc.x.copy()
+    c0, hu, hx = oc.bdf_coefficients()
+    t0 = time.perf_counter()
+    oc.residual(c0, hu, hx, wl["dt"])
+    t_res = time.perf_counter() - t0
+    E = len(mesh["conn"])
+    sub_e = np.arange(0, E, 64)
+    conn = mesh["conn"][sub_e]
+    used, inv = np.unique(conn, return_inverse=True)
+    sub = dict(X=mesh["X"][used], conn=inv.reshape(conn.shape), tags=mesh["tags"][used] & ~I.CYL,
+               gamma_faces=np.zeros((0, 2), np.int64), wrap=mesh["wrap"][sub_e], span=mesh["span"])
+    sc = viv_oracle_case3d(sub, wl["Re"], wl["Ustar"], wl["dt"], u0[used])
+    sc.u_n, sc.x_n = sc.u.copy(), sc.x.copy()
+    c0s, hus, hxs = sc.bdf_coefficients()
+    t0 = time.perf_counter()
+    sc.jacobian(c0s, hus, hxs, wl["dt"])
+    t_jac = (time.perf_counter() - t0) * E / len(sub_e)
+    small = I.viv_cylinder_mesh3d(3, 2, wl["span"] * 2 / wl["layers"])
+    lc = viv_oracle_case3d(small, wl["Re"], wl["Ustar"], wl["dt"], I.viv_initial_velocity(small, 1.0, 1e-3, 1))
+    lc.u_n, lc.x_n = lc.u.copy(), lc.x.copy()
+    c0l, hul, hxl = lc.bdf_coefficients()
+    Js = lc.jacobian(c0l, hul, hxl, wl["dt"]).tocsc()
+    t0 = time.perf_counter()
+    sparse_lu(Js)
+    t_lus = time.perf_counter() - t0
+    t_lu = t_lus * (oc.ndof / lc.ndof) ** 2
+    per_step = newton_iters * (t_res + t_jac + t_lu) + t_res
+    desc = (f"oracle on {E}-hexahedron mesh: residual full ({t_res:.1f}s), complex-step Jacobian on 1/64 of the "
+            f"elements x64 ({t_jac:.0f}s), SuperLU of the {len(small['conn'])}-hexahedron mesh scaled by "
+            f"(N ratio)^2 ({t_lus:.1f}s -> {t_lu:.0f}s); {newton_iters:.2f} Newton iterations per step; extrapolated")
+    return 1.0 / per_step, desc, time.perf_counter() - t_all
+
+
 def host_info():
     model = "unknown"
     try:
@@ -279,7 +328,7 @@ def run_reference(args, wl, rank):
         return
     steps = []
     for i in range(args.warmup + args.steps):
-        v, desc, secs = oracle_sample(wl, 3.0)
+        v, desc, secs = (oracle_sample3d if "layers" in wl else oracle_sample)(wl, 3.0)
         if i >= args.warmup:
             steps.append(v)
     value = sum(steps) / len(steps)
@@ -304,7 +353,8 @@ def run_ours(args, wl, rank, world, local):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
     viv.load()
-    mesh = I.viv_cylinder_mesh(wl["m"])
+    three_d = "layers" in wl
+    mesh = I.viv_cylinder_mesh3d(wl["m"], wl["layers"], wl["span"]) if three_d else I.viv_cylinder_mesh(wl["m"])
     u0 = I.viv_initial_velocity(mesh, 1.0, 1e-3, 1 + rank)
     M = viv.Mesh(mesh)
     info = M.info
@@ -399,10 +449,11 @@ def run_ours(args, wl, rank, world, local):
                     "frac": a / FP32_SIMT_TFLOPS,
                     "peak_source": "FP32 SIMT: 148 SMs x 128 lanes x 2 flop x 2.032 GHz (derived)"}
         if kind == "residual":
-            # FP64 ALU: about 4k double FMAs per element per evaluation (quadrature of the Q2-Q1-Q2
-            # element residual, counted from the kernel's loops), against the nominal FP64 rate
+            # FP64 ALU: about 4k double FMAs per quad (2-D) or 75k per hexahedron (3-D) per evaluation
+            # (quadrature of the Q2-Q1-Q2 element residual, counted from the kernels' loops), against
+            # the nominal FP64 rate
             evals = n_fact + args.steps          # one per Newton iteration, one for the converged state
-            a = 8.0e3 * len(mesh["conn"]) * evals / sec / 1e12
+            a = (1.5e5 if three_d else 8.0e3) * len(mesh["conn"]) * evals / sec / 1e12
             return {"bound": "alu", "achieved": a, "peak": FP64_TFLOPS, "unit": "TFLOP/s", "frac": a / FP64_TFLOPS,
                     "peak_source": "FP64 nominal 1.25 TFLOP/s (no FP64 measurement); flops approximate"}
         per = {"fwd_solve": fbytes / 2, "bwd_solve": fbytes / 2, "front_assemble": 2 * fbytes,
@@ -434,7 +485,8 @@ def run_ours(args, wl, rank, world, local):
            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": ("f32 fronts and volume Jacobians + f64 residual/border/refinement" if j32 else
                      "f32 fronts + f64 residual/Jacobian/refinement"), "data": "synthetic",
-           "config": {"workload": args.workload, "quads": len(mesh["conn"]), "dofs": info["n_dofs"],
+           "config": {"workload": args.workload, ("hexahedra" if three_d else "quads"): len(mesh["conn"]),
+                      "dofs": info["n_dofs"],
                       "nnz": info["nnz"], "fronts": info["n_fronts"], "max_front": info["max_front"],
                       "factor_gflop": info["factor_flops"] / 1e9, **wl, "precision": "mixed",
                       "pivoting": args.pivoting, "jacobian": args.jacobian, "predictor": args.predictor,
@@ -457,6 +509,10 @@ def run_ours(args, wl, rank, world, local):
         out["autotune"] = {"big_front": tuned[0], "factor_ms": tuned[1],
                            "block_lu_levels": [l for l in range(info["n_levels"]) if info["block_level_mask"] >> l & 1]}
 
+    if three_d:
+        # the FP64 fronts of this case need ~245 GB; the threshold-pivoting path and the
+        # 2-D serving sweep are measured on the 2-D workloads
+        args.no_fp64 = args.no_threshold_path = args.no_sweep = True
     if not args.no_fp64 and rank == 0:
         c64 = viv.viv_case(M, wl["Re"], wl["Ustar"], wl["dt"], u0, precision=viv.VIV_FP64, pivoting=piv,
                            predictor=pred)
@@ -528,10 +584,10 @@ def run_ours(args, wl, rank, world, local):
     if rank == 0 and not args.no_cpu_baseline:
         # the oracle starts Newton from U^n: 3 iterations per step on this case (the GPU path's
         # count with the same starting point)
-        v, desc, secs = oracle_sample(wl, 3.0)
+        v, desc, secs = (oracle_sample3d if three_d else oracle_sample)(wl, 3.0)
         out["cpu_baseline"] = {"value": v, "unit": "time steps/s", "cores": 1, "kind": "oracle", "sample": desc,
                                "sample_seconds": round(secs, 1), "host": host_info()}
-        if args.oracle_full_steps > 0:
+        if args.oracle_full_steps > 0 and not three_d:
             out["cpu_baseline"]["full_run_small_case"] = oracle_full_run(args.oracle_full_steps)
     if rank == 0:
         print(json.dumps(out), flush=True)

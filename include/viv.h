@@ -53,7 +53,9 @@ enum {
   VIV_TAG_X_FIX_X = 4, VIV_TAG_X_FIX_Y = 8,   /* position component held (Eq. psBC) */
   VIV_TAG_CYL = 16,                            /* node on Gamma: x = X + delta, lambda lives here */
   VIV_TAG_OUTLET = 32,                         /* informational */
-  VIV_TAG_P_FIX = 64                           /* pressure held (all-Dirichlet problems) */
+  VIV_TAG_P_FIX = 64,                          /* pressure held (all-Dirichlet problems) */
+  VIV_TAG_U_FIX_Z = 128,                       /* 3-D: velocity z-component held */
+  VIV_TAG_X_FIX_Z = 256                        /* 3-D: position z-component held */
 };
 
 /* precision of the factors (and of the Jacobian; see jacobian_fp32); residual,
@@ -63,7 +65,8 @@ enum { VIV_FP64 = 0, VIV_MIXED = 1 };
 enum { VIV_RES = 1, VIV_JAC = 2 };
 /* field codes of viv_mesh_dof_labels */
 enum { VIV_F_UX = 0, VIV_F_UY = 1, VIV_F_XX = 2, VIV_F_XY = 3, VIV_F_P = 4,
-       VIV_F_LX = 5, VIV_F_LY = 6, VIV_F_DX = 7, VIV_F_DY = 8 };
+       VIV_F_LX = 5, VIV_F_LY = 6, VIV_F_DX = 7, VIV_F_DY = 8,
+       VIV_F_UZ = 9, VIV_F_XZ = 10, VIV_F_LZ = 11 };   /* z codes: 3-D meshes only */
 
 typedef struct {
   void* (*alloc)(size_t bytes, void* ctx);   /* returns device memory or NULL */
@@ -74,12 +77,23 @@ typedef struct {
 typedef struct vivMesh vivMesh;
 typedef struct vivCase vivCase;
 
-/* Mesh description (2-D).  X: n_nodes x 2 reference coordinates (row-major).
- * conn: n_elems x 9 node ids of each Q2 quad, lexicographic (node 3*b + a,
- * a along xi), positively oriented.  tags: n_nodes VIV_TAG_* bit sets.
- * gamma_faces: n_gamma_faces x 2 (element, local edge) pairs of Gamma, edges
- * 0: xi=0 (nodes 0,3,6), 1: xi=1 (2,5,8), 2: eta=0 (0,1,2), 3: eta=1 (6,7,8).
- * leaf_elems: nested-dissection leaf size in elements (0: default 4). */
+/* Mesh description.  dim 0 or 2: two dimensions; 3: three.
+ * 2-D: X: n_nodes x 2 reference coordinates (row-major).  conn: n_elems x 9
+ * node ids of each Q2 quad, lexicographic (node 3*b + a, a along xi),
+ * positively oriented.  gamma_faces: n_gamma_faces x 2 (element, local edge)
+ * pairs of Gamma, edges 0: xi=0 (nodes 0,3,6), 1: xi=1 (2,5,8), 2: eta=0
+ * (0,1,2), 3: eta=1 (6,7,8).
+ * 3-D: X: n_nodes x 3.  conn: n_elems x 27 node ids of each Q2 hexahedron
+ * (node 9*c + 3*b + a, c along zeta), positively oriented; gamma_faces:
+ * (element, local face) with faces 0/1: xi = 0/1, 2/3: eta = 0/1,
+ * 4/5: zeta = 0/1.  span > 0 makes the mesh periodic in z with that period:
+ * bit a of wrap[e] (n_elems entries, or NULL for none) says that local node a
+ * of element e sits at its stored coordinates + span e_z (the element crosses
+ * the seam); the periodicity is on the displacement x - X.  Gamma nodes move
+ * by (delta_x, delta_y, 0): their z position must be held (VIV_TAG_X_FIX_Z);
+ * the multiplier has three components there.
+ * tags: n_nodes VIV_TAG_* bit sets.  leaf_elems: nested-dissection leaf size
+ * in elements (0: default, 4 in 2-D, 2 in 3-D). */
 typedef struct {
   int64_t n_nodes, n_elems, n_gamma_faces;
   const double* X;
@@ -87,6 +101,9 @@ typedef struct {
   const int32_t* tags;
   const int64_t* gamma_faces;
   int32_t leaf_elems;
+  int32_t dim;
+  double span;
+  const int64_t* wrap;
 } vivMeshDesc;
 
 typedef struct {
@@ -114,6 +131,7 @@ typedef struct {
   double window_lu_flops;  /* LU flops of the pivot blocks (windows and block LU incl. the block inverses) */
   double window_gemm_flops;/* SIMT Schur-update flops (fronts below the large-front order) */
   int64_t block_level_mask;/* tree levels (bit l) whose large fronts may use the block LU */
+  int32_t dim;             /* 2 or 3: components of u, x and lambda per node */
 } vivMeshInfo;
 
 /* Physical and solver parameters.  rho, mu: fluid density and viscosity;
@@ -171,7 +189,8 @@ typedef struct {
    *                          U_r = pi U_inf sqrt(pi rho L / k) (Section 1), equals
    *                          Ustar; L = span_L, the length that carries the force
    *                          (1 for a 2-D section).
-   * U_inf, D and span_L default to 1 when 0.  k = 0 with Ustar = 0 is a problem
+   * U_inf and D default to 1 when 0; span_L defaults to the span of a periodic
+   * 3-D mesh, else 1.  k = 0 with Ustar = 0 is a problem
    * without a cylinder (no border unknowns). */
   double Re, Ustar, U_inf, D, span_L;
   /* Adaptive time stepping (Section 6: a target Courant number as a simple
@@ -223,7 +242,7 @@ vivStatus viv_mesh_fronts(const vivMesh* mesh, int32_t* m, int32_t* p, int32_t* 
 vivStatus viv_mesh_destroy(vivMesh* mesh);
 
 /* ---- case: state on the device ------------------------------------------ */
-/* u0: n_nodes x 2 host initial velocity (its prescribed components are the
+/* u0: n_nodes x dim host initial velocity (its prescribed components are the
  * Dirichlet values); x starts at X, p, lambda and delta at 0. */
 vivStatus viv_case_create(vivMesh* mesh, const vivParams* params, const double* u0,
                           void* stream, vivCase** out);
@@ -251,12 +270,12 @@ vivStatus viv_case_load(vivCase* c, const void* buf, size_t bytes);
 
 /* Overwrite the state.  Each pointer may be NULL (left unchanged); pointers
  * may be host or device memory (the `device` flag documents which; copies use
- * unified addressing).  u, x, lam: n_nodes x 2; p: n_nodes (vertex values);
+ * unified addressing).  u, x, lam: n_nodes x dim; p: n_nodes (vertex values);
  * delta: 2.  Inside a step (after viv_begin_step) this changes the Newton
  * iterate only; the BDF history was fixed by viv_begin_step. */
 vivStatus viv_set_state(vivCase* c, int device, const double* u, const double* p, const double* x,
                         const double* lam, const double* delta, double t);
-/* Give the previous time level (u, x at t - dt, n_nodes x 2 each); the next
+/* Give the previous time level (u, x at t - dt, n_nodes x dim each); the next
  * step then uses BDF2 instead of the BDF1 start. */
 vivStatus viv_set_history(vivCase* c, int device, const double* u_prev, const double* x_prev);
 vivStatus viv_get_state(const vivCase* c, int device, double* u, double* p, double* x, double* lam,
@@ -409,7 +428,7 @@ typedef struct vivServer vivServer;
 typedef struct {
   vivMesh* mesh;           /* device mesh (viv_mesh_create); may be shared by requests */
   vivParams params;
-  const double* u0;        /* n_nodes x 2 host initial velocity; copied at submit */
+  const double* u0;        /* n_nodes x dim host initial velocity; copied at submit */
   int32_t n_steps;         /* BDF steps to run */
   double arrival_time;     /* seconds after server creation when the request arrives */
 } vivRequest;
@@ -441,7 +460,7 @@ vivStatus viv_server_create(size_t mem_budget, int32_t max_active, vivServer** o
 vivStatus viv_server_submit(vivServer* s, const vivRequest* req, int64_t* id);
 /* finished results not yet polled (up to max); waits up to wait_ms for one */
 vivStatus viv_server_poll(vivServer* s, vivResult* out, int32_t max, int32_t* n, int32_t wait_ms);
-/* final state of a finished case: u, x, lam (n_nodes x 2), p (n_nodes), delta (2) */
+/* final state of a finished case: u, x, lam (n_nodes x dim), p (n_nodes), delta (2) */
 vivStatus viv_server_state(vivServer* s, int64_t id, double* u, double* p, double* x, double* lam,
                            double* delta);
 vivStatus viv_server_stats(vivServer* s, vivServerStats* out);

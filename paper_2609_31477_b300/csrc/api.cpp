@@ -141,7 +141,7 @@ void begin_step(vivCase* c) {
     std::swap(s.u_nm1, s.u_n);
     std::swap(s.x_nm1, s.x_n);
   }
-  const size_t n2 = 2 * m.n_nodes * sizeof(double);
+  const size_t n2 = m.dim * m.n_nodes * sizeof(double);
   VIV_CUDA(cudaMemcpyAsync(s.u_n, s.u, n2, cudaMemcpyDeviceToDevice, c->stream));
   VIV_CUDA(cudaMemcpyAsync(s.x_n, s.x, n2, cudaMemcpyDeviceToDevice, c->stream));
   const double dt = c->prm.dt;
@@ -354,7 +354,9 @@ vivStatus viv_mesh_info(const vivMesh* mesh, vivMeshInfo* info) {
   info->factor_flops = m.factor_flops;
   info->front_entries = (size_t)m.front_entries;
   size_t nodes = (size_t)m.n_nodes, nnz = (size_t)info->nnz, nd = (size_t)m.n_dofs;
-  size_t state = 8 * (17 * nodes + (size_t)m.n_elems + 3 * nd + 2 * 296 + 64) + 8 * (size_t)m.piv_entries +
+  // nodal vectors: u, x, lambda, two history levels of u and x, the BDF sums (D each), p
+  size_t state = 8 * ((9 * (size_t)m.dim + 1) * nodes + (size_t)m.n_elems + 3 * nd + 2 * 296 + 64) +
+                 8 * (size_t)m.piv_entries +
                  4 * (1 + (size_t)std::max(1, m.chain_flag_bound));   // (+ the solve chains' flags)
   if (m.n_front_dofs < m.n_dofs) state += 8 * 4 * nd;   // border: Y and the columns of B
   const size_t nv = m.n_front_dofs < m.n_dofs ? 3 : 1;   // solve workspaces: one, plus two for the border columns
@@ -375,6 +377,7 @@ vivStatus viv_mesh_info(const vivMesh* mesh, vivMeshInfo* info) {
   for (int l = 0; l < m.n_levels && l < 64; ++l)
     if (m.level_block.empty() || m.level_block[l]) info->block_level_mask |= (int64_t)1 << l;
   info->tc_image_bytes = (size_t)m.tc_img_chunks * TC_IMG_CHUNK_BYTES;
+  info->dim = m.dim;
   API_END
 }
 
@@ -430,9 +433,11 @@ vivStatus viv_case_create(vivMesh* mesh, const vivParams* prm, const double* u0,
 // Dimensionless inputs to the dimensional parameters the solver uses:
 // Re = rho U_inf D / mu, and the reduced velocity of a massless cylinder
 // U_r = pi U_inf sqrt(pi rho L / k) (Section 1) solved for k.
-static vivParams resolve_params(const vivParams& in) {
+// The force-carrying length L defaults to the span of a periodic 3-D mesh, else 1.
+static vivParams resolve_params(const vivParams& in, const Mesh& m) {
   vivParams p = in;
-  const double U = p.U_inf > 0 ? p.U_inf : 1.0, D = p.D > 0 ? p.D : 1.0, L = p.span_L > 0 ? p.span_L : 1.0;
+  const double L0 = m.dim == 3 && m.span > 0 ? m.span : 1.0;
+  const double U = p.U_inf > 0 ? p.U_inf : 1.0, D = p.D > 0 ? p.D : 1.0, L = p.span_L > 0 ? p.span_L : L0;
   if (p.mu <= 0 && p.Re > 0) p.mu = p.rho * U * D / p.Re;
   if (p.k <= 0 && p.Ustar > 0) {
     const double pi = 3.14159265358979323846;
@@ -445,7 +450,7 @@ static vivStatus case_create_impl(vivMesh* mesh, const vivParams* prm_in, const 
                                   vivCase** out, bool default_alloc) {
   API_BEGIN
   VIV_CHECK(mesh && prm_in && u0 && out, VIV_ERR_ARG, "NULL argument");
-  const vivParams resolved = resolve_params(*prm_in);
+  const vivParams resolved = resolve_params(*prm_in, mesh->m);
   const vivParams* prm = &resolved;
   VIV_CHECK(prm->dt > 0 && prm->rho > 0 && prm->mu > 0, VIV_ERR_ARG, "rho, mu (or Re) and dt must be positive");
   VIV_CHECK(prm->k >= 0, VIV_ERR_ARG, "spring stiffness k must not be negative");
@@ -457,6 +462,8 @@ static vivStatus case_create_impl(vivMesh* mesh, const vivParams* prm_in, const 
   VIV_CHECK(prm->source >= 0 && prm->source <= 3, VIV_ERR_ARG, "source must be 0 .. 3");
   VIV_CHECK(prm->cfl_target >= 0 && prm->dt_max >= 0, VIV_ERR_ARG, "cfl_target and dt_max must not be negative");
   VIV_CHECK(mesh->m.on_device, VIV_ERR_STATE, "mesh was analysed on the host only");
+  VIV_CHECK(mesh->m.dim == 2 || (prm->source == 0 && prm->cfl_target == 0), VIV_ERR_ARG,
+            "3-D meshes take no manufactured source and a constant step");
   *out = nullptr;
   vivCase* c = new vivCase();
   try {
@@ -470,20 +477,20 @@ static vivStatus case_create_impl(vivMesh* mesh, const vivParams* prm_in, const 
     c->arena.alloc = mesh->m.arena.alloc;
     c->arena.custom = mesh->m.arena.custom && !default_alloc;
     const Mesh& m = mesh->m;
-    const int64_t n = m.n_nodes, nd = m.n_dofs, nnz = m.row_ptr[m.n_dofs];
+    const int64_t n = m.n_nodes, nd = m.n_dofs, nnz = m.row_ptr[m.n_dofs], D = m.dim;
     DeviceArena& A = c->arena;
     CaseState& s = c->s;
-    s.u = A.make<double>(2 * n);
+    s.u = A.make<double>(D * n);
     s.p = A.make<double>(n);
-    s.x = A.make<double>(2 * n);
-    s.lam = A.make<double>(2 * n);
+    s.x = A.make<double>(D * n);
+    s.lam = A.make<double>(D * n);
     s.delta = A.make<double>(2);
-    s.u_n = A.make<double>(2 * n);
-    s.x_n = A.make<double>(2 * n);
-    s.u_nm1 = A.make<double>(2 * n);
-    s.x_nm1 = A.make<double>(2 * n);
-    s.hu = A.make<double>(2 * n);
-    s.hx = A.make<double>(2 * n);
+    s.u_n = A.make<double>(D * n);
+    s.x_n = A.make<double>(D * n);
+    s.u_nm1 = A.make<double>(D * n);
+    s.x_nm1 = A.make<double>(D * n);
+    s.hu = A.make<double>(D * n);
+    s.hx = A.make<double>(D * n);
     s.lame = A.make<double>(m.n_elems);
     s.R = A.make<double>(nd);
     s.dU = A.make<double>(nd);
@@ -518,13 +525,13 @@ static vivStatus case_create_impl(vivMesh* mesh, const vivParams* prm_in, const 
     s.step = A.make<double>(2);
     VIV_CUDA(cudaMallocHost(&c->h_pinned, 8 * sizeof(double)));
     cudaStream_t st = c->stream;
-    VIV_CUDA(cudaMemcpyAsync(s.u, u0, 2 * n * sizeof(double), cudaMemcpyDefault, st));
-    VIV_CUDA(cudaMemcpyAsync(s.x, m.d_X, 2 * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    VIV_CUDA(cudaMemcpyAsync(s.u, u0, D * n * sizeof(double), cudaMemcpyDefault, st));
+    VIV_CUDA(cudaMemcpyAsync(s.x, m.d_X, D * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     VIV_CUDA(cudaMemsetAsync(s.p, 0, n * sizeof(double), st));
-    VIV_CUDA(cudaMemsetAsync(s.lam, 0, 2 * n * sizeof(double), st));
+    VIV_CUDA(cudaMemsetAsync(s.lam, 0, D * n * sizeof(double), st));
     VIV_CUDA(cudaMemsetAsync(s.delta, 0, 2 * sizeof(double), st));
-    VIV_CUDA(cudaMemsetAsync(s.u_nm1, 0, 2 * n * sizeof(double), st));
-    VIV_CUDA(cudaMemsetAsync(s.x_nm1, 0, 2 * n * sizeof(double), st));
+    VIV_CUDA(cudaMemsetAsync(s.u_nm1, 0, D * n * sizeof(double), st));
+    VIV_CUDA(cudaMemsetAsync(s.x_nm1, 0, D * n * sizeof(double), st));
     VIV_CUDA(cudaMemsetAsync(s.stats, 0, 4 * sizeof(int32_t), st));
     if (mixed(c))
       prepare_kernels<float>();
@@ -558,11 +565,11 @@ vivStatus viv_set_state(vivCase* c, int, const double* u, const double* p, const
                         const double* delta, double t) {
   API_BEGIN
   VIV_CHECK(c, VIV_ERR_ARG, "NULL case");
-  const int64_t n = c->mesh->m.n_nodes;
-  copy_in(c, c->s.u, u, 2 * n);
+  const int64_t n = c->mesh->m.n_nodes, D = c->mesh->m.dim;
+  copy_in(c, c->s.u, u, D * n);
   copy_in(c, c->s.p, p, n);
-  copy_in(c, c->s.x, x, 2 * n);
-  copy_in(c, c->s.lam, lam, 2 * n);
+  copy_in(c, c->s.x, x, D * n);
+  copy_in(c, c->s.lam, lam, D * n);
   copy_in(c, c->s.delta, delta, 2);
   c->t = t;
   VIV_CUDA(cudaStreamSynchronize(c->stream));
@@ -572,10 +579,10 @@ vivStatus viv_set_state(vivCase* c, int, const double* u, const double* p, const
 vivStatus viv_set_history(vivCase* c, int, const double* u_prev, const double* x_prev) {
   API_BEGIN
   VIV_CHECK(c && u_prev && x_prev, VIV_ERR_ARG, "NULL argument");
-  const int64_t n = c->mesh->m.n_nodes;
+  const int64_t n = c->mesh->m.n_nodes, D = c->mesh->m.dim;
   // begin_step moves u_n into u_nm1 when BDF2 is on
-  copy_in(c, c->s.u_n, u_prev, 2 * n);
-  copy_in(c, c->s.x_n, x_prev, 2 * n);
+  copy_in(c, c->s.u_n, u_prev, D * n);
+  copy_in(c, c->s.x_n, x_prev, D * n);
   c->have_prev2 = true;
   VIV_CUDA(cudaStreamSynchronize(c->stream));
   API_END
@@ -586,11 +593,11 @@ vivStatus viv_get_state(const vivCase* cc, int, double* u, double* p, double* x,
   API_BEGIN
   VIV_CHECK(cc, VIV_ERR_ARG, "NULL case");
   vivCase* c = const_cast<vivCase*>(cc);
-  const int64_t n = c->mesh->m.n_nodes;
-  copy_out(c, u, c->s.u, 2 * n);
+  const int64_t n = c->mesh->m.n_nodes, D = c->mesh->m.dim;
+  copy_out(c, u, c->s.u, D * n);
   copy_out(c, p, c->s.p, n);
-  copy_out(c, x, c->s.x, 2 * n);
-  copy_out(c, lam, c->s.lam, 2 * n);
+  copy_out(c, x, c->s.x, D * n);
+  copy_out(c, lam, c->s.lam, D * n);
   copy_out(c, delta, c->s.delta, 2);
   if (t) *t = c->t;
   VIV_CUDA(cudaStreamSynchronize(c->stream));
@@ -975,7 +982,8 @@ vivStatus viv_case_params(const vivCase* c, vivParams* out) {
 namespace {
 constexpr char CKPT_MAGIC[8] = {'V', 'I', 'V', 'C', 'K', 'P', 'T', '2'};
 constexpr size_t CKPT_HEADER = 8 + 2 * 8 + 2 * 4 + 3 * 8 + 8;
-size_t ckpt_bytes(int64_t n) { return CKPT_HEADER + sizeof(double) * (size_t)(11 * n + 2); }
+// u, x, lam, u_n, x_n (D n each), p (n), delta (2)
+size_t ckpt_bytes(int64_t n, int64_t D) { return CKPT_HEADER + sizeof(double) * (size_t)(5 * D * n + n + 2); }
 }  // namespace
 
 vivStatus viv_case_save(const vivCase* cc, void* buf, size_t* bytes) {
@@ -983,8 +991,8 @@ vivStatus viv_case_save(const vivCase* cc, void* buf, size_t* bytes) {
   VIV_CHECK(cc && bytes, VIV_ERR_ARG, "NULL argument");
   VIV_CHECK(!cc->step_open, VIV_ERR_STATE, "viv_case_save inside an open time step");
   vivCase* c = const_cast<vivCase*>(cc);
-  const int64_t n = c->mesh->m.n_nodes;
-  const size_t need = ckpt_bytes(n);
+  const int64_t n = c->mesh->m.n_nodes, D = c->mesh->m.dim;
+  const size_t need = ckpt_bytes(n, D);
   if (!buf) {
     *bytes = need;
     return VIV_OK;
@@ -1008,13 +1016,13 @@ vivStatus viv_case_save(const vivCase* cc, void* buf, size_t* bytes) {
   put(&ns, 8);
   double* d = reinterpret_cast<double*>(b);   // copies go through unified addressing (any alignment)
   const CaseState& s = c->s;
-  copy_out(c, d, s.u, 2 * n);
-  copy_out(c, d + 2 * n, s.p, n);
-  copy_out(c, d + 3 * n, s.x, 2 * n);
-  copy_out(c, d + 5 * n, s.lam, 2 * n);
-  copy_out(c, d + 7 * n, s.delta, 2);
-  copy_out(c, d + 7 * n + 2, s.u_n, 2 * n);
-  copy_out(c, d + 9 * n + 2, s.x_n, 2 * n);
+  copy_out(c, d, s.u, D * n);
+  copy_out(c, d + D * n, s.p, n);
+  copy_out(c, d + D * n + n, s.x, D * n);
+  copy_out(c, d + 2 * D * n + n, s.lam, D * n);
+  copy_out(c, d + 3 * D * n + n, s.delta, 2);
+  copy_out(c, d + 3 * D * n + n + 2, s.u_n, D * n);
+  copy_out(c, d + 4 * D * n + n + 2, s.x_n, D * n);
   VIV_CUDA(cudaStreamSynchronize(c->stream));
   *bytes = need;
   API_END
@@ -1023,7 +1031,7 @@ vivStatus viv_case_save(const vivCase* cc, void* buf, size_t* bytes) {
 vivStatus viv_case_load(vivCase* c, const void* buf, size_t bytes) {
   API_BEGIN
   VIV_CHECK(c && buf, VIV_ERR_ARG, "NULL argument");
-  const int64_t n = c->mesh->m.n_nodes;
+  const int64_t n = c->mesh->m.n_nodes, D = c->mesh->m.dim;
   VIV_CHECK(bytes >= CKPT_HEADER && std::memcmp(buf, CKPT_MAGIC, 8) == 0, VIV_ERR_ARG, "not a case checkpoint");
   const unsigned char* b = static_cast<const unsigned char*>(buf) + 8;
   auto get = [&](void* v, size_t k) {
@@ -1041,20 +1049,20 @@ vivStatus viv_case_load(vivCase* c, const void* buf, size_t bytes) {
   get(&dt, 8);
   get(&dt_prev, 8);
   get(&ns, 8);
-  VIV_CHECK(n_s == n && nd_s == c->mesh->m.n_dofs && bytes >= ckpt_bytes(n), VIV_ERR_ARG,
+  VIV_CHECK(n_s == n && nd_s == c->mesh->m.n_dofs && bytes >= ckpt_bytes(n, D), VIV_ERR_ARG,
             "checkpoint was written for another mesh");
   // a constant-step case must resume with its own dt; an adaptive one resumes
   // with the saved step sizes
   VIV_CHECK(c->prm.cfl_target > 0 || dt == c->prm.dt, VIV_ERR_ARG, "checkpoint time step differs from the case's dt");
   const double* d = reinterpret_cast<const double*>(b);
   CaseState& s = c->s;
-  copy_in(c, s.u, d, 2 * n);
-  copy_in(c, s.p, d + 2 * n, n);
-  copy_in(c, s.x, d + 3 * n, 2 * n);
-  copy_in(c, s.lam, d + 5 * n, 2 * n);
-  copy_in(c, s.delta, d + 7 * n, 2);
-  copy_in(c, s.u_n, d + 7 * n + 2, 2 * n);
-  copy_in(c, s.x_n, d + 9 * n + 2, 2 * n);
+  copy_in(c, s.u, d, D * n);
+  copy_in(c, s.p, d + D * n, n);
+  copy_in(c, s.x, d + D * n + n, D * n);
+  copy_in(c, s.lam, d + 2 * D * n + n, D * n);
+  copy_in(c, s.delta, d + 3 * D * n + n, 2);
+  copy_in(c, s.u_n, d + 3 * D * n + n + 2, D * n);
+  copy_in(c, s.x_n, d + 4 * D * n + n + 2, D * n);
   VIV_CUDA(cudaStreamSynchronize(c->stream));
   c->t = t;
   c->prm.dt = dt;
@@ -1069,55 +1077,55 @@ vivStatus viv_case_load(vivCase* c, const void* buf, size_t bytes) {
 
 int64_t viv_state_size(const vivMesh* mesh) {
   if (!mesh) return -1;
-  const int64_t n = mesh->m.n_nodes;
-  return 2 * n + n + 2 * n + 2 * n + 2 + 2 * n + 2 * n + 2;
+  const int64_t n = mesh->m.n_nodes, D = mesh->m.dim;
+  return 5 * D * n + n + 2 + 2;
 }
 
-// packed host state: u(2n) p(n) x(2n) lam(2n) delta(2) u_prev(2n) x_prev(2n) [t, have_prev]
+// packed host state: u(Dn) p(n) x(Dn) lam(Dn) delta(2) u_prev(Dn) x_prev(Dn) [t, have_prev]
 vivStatus viv_step_host(vivCase* c, const double* in, double* out, vivStepInfo* info) {
   API_BEGIN
   ProfBind pb_(c);
   VIV_CHECK(c && in && out, VIV_ERR_ARG, "NULL argument");
-  const int64_t n = c->mesh->m.n_nodes;
+  const int64_t n = c->mesh->m.n_nodes, D = c->mesh->m.dim;
   const double* q = in;
-  copy_in(c, c->s.u, q, 2 * n);
-  q += 2 * n;
+  copy_in(c, c->s.u, q, D * n);
+  q += D * n;
   copy_in(c, c->s.p, q, n);
   q += n;
-  copy_in(c, c->s.x, q, 2 * n);
-  q += 2 * n;
-  copy_in(c, c->s.lam, q, 2 * n);
-  q += 2 * n;
+  copy_in(c, c->s.x, q, D * n);
+  q += D * n;
+  copy_in(c, c->s.lam, q, D * n);
+  q += D * n;
   copy_in(c, c->s.delta, q, 2);
   q += 2;
   const double* up = q;
-  q += 2 * n;
+  q += D * n;
   const double* xp = q;
-  q += 2 * n;
+  q += D * n;
   c->t = q[0];
   const bool have_prev = q[1] != 0.0;
   c->nstep = 0;
   c->have_prev2 = have_prev;
   if (have_prev) {
-    copy_in(c, c->s.u_n, up, 2 * n);
-    copy_in(c, c->s.x_n, xp, 2 * n);
+    copy_in(c, c->s.u_n, up, D * n);
+    copy_in(c, c->s.x_n, xp, D * n);
   }
   step_impl(c, info);
   double* o = out;
-  copy_out(c, o, c->s.u, 2 * n);
-  o += 2 * n;
+  copy_out(c, o, c->s.u, D * n);
+  o += D * n;
   copy_out(c, o, c->s.p, n);
   o += n;
-  copy_out(c, o, c->s.x, 2 * n);
-  o += 2 * n;
-  copy_out(c, o, c->s.lam, 2 * n);
-  o += 2 * n;
+  copy_out(c, o, c->s.x, D * n);
+  o += D * n;
+  copy_out(c, o, c->s.lam, D * n);
+  o += D * n;
   copy_out(c, o, c->s.delta, 2);
   o += 2;
-  copy_out(c, o, c->s.u_n, 2 * n);
-  o += 2 * n;
-  copy_out(c, o, c->s.x_n, 2 * n);
-  o += 2 * n;
+  copy_out(c, o, c->s.u_n, D * n);
+  o += D * n;
+  copy_out(c, o, c->s.x_n, D * n);
+  o += D * n;
   VIV_CUDA(cudaStreamSynchronize(c->stream));
   o[0] = c->t;
   o[1] = 1.0;

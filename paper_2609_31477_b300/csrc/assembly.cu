@@ -682,7 +682,9 @@ void launch_element_areas(const Mesh& m, double* lame, double scale, bool consta
     VIV_CUDA(cudaGetLastError());
     return;
   }
-  {
+  if (m.dim == 3) {
+    launch_element_volumes(m, lame, s);
+  } else {
     Launched L(K_VEC, s);
     area_kernel<<<(E + 127) / 128, 128, 0, s>>>(m.d_conn, m.d_X, E, scale, lame);
   }
@@ -757,13 +759,19 @@ static void run_assembly(const Mesh& m, const CaseState& st, const vivParams& pr
 
 void launch_residual(const Mesh& m, const CaseState& st, const vivParams& prm, cudaStream_t s) {
   VIV_CUDA(cudaMemsetAsync(st.R, 0, sizeof(double) * m.n_dofs, s));
-  run_assembly<double, false>(m, st, prm, st.R, (double*)nullptr, s);
+  if (m.dim == 3)
+    run_assembly3<double, false>(m, st, prm, st.R, (double*)nullptr, s, 3);
+  else
+    run_assembly<double, false>(m, st, prm, st.R, (double*)nullptr, s);
 }
 
 template <class T>
 void launch_jacobian(const Mesh& m, const CaseState& st, const vivParams& prm, T* vals, cudaStream_t s) {
   VIV_CUDA(cudaMemsetAsync(vals, 0, sizeof(T) * m.row_ptr[m.n_dofs], s));
-  run_assembly<T, true>(m, st, prm, nullptr, vals, s);
+  if (m.dim == 3)
+    run_assembly3<T, true>(m, st, prm, nullptr, vals, s, 3);
+  else
+    run_assembly<T, true>(m, st, prm, nullptr, vals, s);
 }
 template void launch_jacobian<double>(const Mesh&, const CaseState&, const vivParams&, double*, cudaStream_t);
 
@@ -774,9 +782,15 @@ void launch_jacobian_split(const Mesh& m, const CaseState& st, const vivParams& 
                            cudaStream_t s) {
   const int64_t nnz = m.row_ptr[m.n_dofs];
   VIV_CUDA(cudaMemsetAsync(J32, 0, sizeof(float) * nnz, s));
-  run_assembly<float, true>(m, st, prm, nullptr, J32, s, 1);
+  if (m.dim == 3)
+    run_assembly3<float, true>(m, st, prm, nullptr, J32, s, 1);
+  else
+    run_assembly<float, true>(m, st, prm, nullptr, J32, s, 1);
   launch_f32_to_f64(J64, J32, nnz, s);
-  run_assembly<double, true>(m, st, prm, nullptr, J64, s, 2);
+  if (m.dim == 3)
+    run_assembly3<double, true>(m, st, prm, nullptr, J64, s, 2);
+  else
+    run_assembly<double, true>(m, st, prm, nullptr, J64, s, 2);
   launch_f64_to_f32(J32, J64, nnz, s);
 }
 template void launch_jacobian<float>(const Mesh&, const CaseState&, const vivParams&, float*, cudaStream_t);

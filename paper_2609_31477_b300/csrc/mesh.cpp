@@ -55,6 +55,20 @@ namespace {
 
 const int VERT[4] = {0, 2, 6, 8};
 const int EDGE[4][3] = {{0, 3, 6}, {2, 5, 8}, {0, 1, 2}, {6, 7, 8}};
+const int VERT3[8] = {0, 2, 6, 8, 18, 20, 24, 26};
+
+// local node of position (s, t) on face f of a 27-node hexahedron: the face
+// holds reference coordinate f / 2 at 0 (f even) or 1 (f odd); s runs along
+// the first and t along the second of the other two directions
+int hex_face_node(int f, int s, int t) {
+  int idx[3];
+  const int axis = f / 2;
+  idx[axis] = 2 * (f % 2);
+  int q = 0;
+  for (int ax = 0; ax < 3; ++ax)
+    if (ax != axis) idx[ax] = q++ == 0 ? s : t;
+  return 9 * idx[2] + 3 * idx[1] + idx[0];
+}
 
 struct SN {
   std::vector<int> nodes;
@@ -65,36 +79,36 @@ struct SN {
 struct Dissector {
   const Mesh& m;
   int leaf;
-  std::vector<double> cx, cy;
+  std::vector<double> cen[3];   // element centroids (seam-shifted coordinates)
   std::vector<int> owner, mark;
   int stamp = 0;
   std::vector<SN> sns;
 
   Dissector(const Mesh& mm, int leaf_) : m(mm), leaf(leaf_) {
-    cx.resize(m.n_elems);
-    cy.resize(m.n_elems);
+    const int D = m.dim, P = m.npe;
+    for (int d = 0; d < D; ++d) cen[d].resize(m.n_elems);
     for (int64_t e = 0; e < m.n_elems; ++e) {
-      double sx = 0, sy = 0;
-      for (int a = 0; a < 9; ++a) {
-        int nd = m.conn[e * 9 + a];
-        sx += m.X[2 * nd];
-        sy += m.X[2 * nd + 1];
+      double sc[3] = {0, 0, 0};
+      for (int a = 0; a < P; ++a) {
+        int nd = m.conn[e * P + a];
+        for (int d = 0; d < D; ++d) sc[d] += m.X[(int64_t)D * nd + d];
+        if (D == 3 && (m.wrap[e] >> a & 1)) sc[2] += m.span;
       }
-      cx[e] = sx / 9;
-      cy[e] = sy / 9;
+      for (int d = 0; d < D; ++d) cen[d][e] = sc[d] / P;
     }
     owner.assign(m.n_nodes, -1);
     mark.assign(m.n_nodes, 0);
   }
 
   int run(std::vector<int>& el, int lo, int hi) {
+    const int P = m.npe;
     int cnt = hi - lo;
     if (cnt <= leaf) {
       int id = (int)sns.size();
       sns.emplace_back();
       for (int q = lo; q < hi; ++q)
-        for (int a = 0; a < 9; ++a) {
-          int nd = m.conn[(int64_t)el[q] * 9 + a];
+        for (int a = 0; a < P; ++a) {
+          int nd = m.conn[(int64_t)el[q] * P + a];
           if (owner[nd] < 0) {
             owner[nd] = id;
             sns[id].nodes.push_back(nd);
@@ -102,14 +116,21 @@ struct Dissector {
         }
       return id;
     }
-    double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
-    for (int q = lo; q < hi; ++q) {
-      x0 = std::min(x0, cx[el[q]]);
-      x1 = std::max(x1, cx[el[q]]);
-      y0 = std::min(y0, cy[el[q]]);
-      y1 = std::max(y1, cy[el[q]]);
+    // bisect at the median centroid along the longest extent
+    int best = 0;
+    double best_ext = -1;
+    for (int d = 0; d < m.dim; ++d) {
+      double c0 = 1e300, c1 = -1e300;
+      for (int q = lo; q < hi; ++q) {
+        c0 = std::min(c0, cen[d][el[q]]);
+        c1 = std::max(c1, cen[d][el[q]]);
+      }
+      if (c1 - c0 > best_ext) {
+        best_ext = c1 - c0;
+        best = d;
+      }
     }
-    const std::vector<double>& key = (x1 - x0 >= y1 - y0) ? cx : cy;
+    const std::vector<double>& key = cen[best];
     int mid = lo + cnt / 2;
     std::nth_element(el.begin() + lo, el.begin() + mid, el.begin() + hi, [&](int a, int b) {
       if (key[a] != key[b]) return key[a] < key[b];
@@ -117,12 +138,12 @@ struct Dissector {
     });
     ++stamp;
     for (int q = lo; q < mid; ++q)
-      for (int a = 0; a < 9; ++a) mark[m.conn[(int64_t)el[q] * 9 + a]] = stamp;
+      for (int a = 0; a < P; ++a) mark[m.conn[(int64_t)el[q] * P + a]] = stamp;
     int id = (int)sns.size();
     sns.emplace_back();
     for (int q = mid; q < hi; ++q)
-      for (int a = 0; a < 9; ++a) {
-        int nd = m.conn[(int64_t)el[q] * 9 + a];
+      for (int a = 0; a < P; ++a) {
+        int nd = m.conn[(int64_t)el[q] * P + a];
         if (mark[nd] == stamp && owner[nd] < 0) {
           owner[nd] = id;
           sns[id].nodes.push_back(nd);
@@ -171,37 +192,64 @@ void build_mesh(Mesh& m, const vivMeshDesc* d) {
   VIV_CHECK(d->n_nodes > 0 && d->n_elems > 0, VIV_ERR_ARG, "empty mesh");
   VIV_CHECK(d->n_nodes < (1LL << 30) && d->n_elems < (1LL << 28), VIV_ERR_ARG, "mesh too large");
   VIV_CHECK(d->n_gamma_faces == 0 || d->gamma_faces, VIV_ERR_ARG, "gamma_faces is NULL");
+  VIV_CHECK(d->dim == 0 || d->dim == 2 || d->dim == 3, VIV_ERR_ARG, "dim must be 2 or 3");
+  const int D = d->dim == 3 ? 3 : 2;
+  m.dim = D;
+  m.npe = D == 3 ? 27 : 9;
+  m.nvert = D == 3 ? 8 : 4;
+  m.fpe = D == 3 ? 9 : 3;
+  m.vol_pairs = D == 3 ? VOL_PAIRS3 : VOL_PAIRS;
+  m.face_pairs = D == 3 ? FACE_PAIRS3 : FACE_PAIRS;
+  const int P = m.npe;
+  const int* vert = D == 3 ? VERT3 : VERT;
   const int64_t n = d->n_nodes, E = d->n_elems, F = d->n_gamma_faces;
+  VIV_CHECK(D == 2 || E < (1LL << 31) / VOL_PAIRS3, VIV_ERR_ARG, "too many hexahedra for 32-bit element maps");
   m.n_nodes = n;
   m.n_elems = E;
   m.n_faces = F;
-  m.X.assign(d->X, d->X + 2 * n);
+  m.X.assign(d->X, d->X + D * n);
   m.tags.assign(d->tags, d->tags + n);
-  m.conn.resize(E * 9);
-  for (int64_t i = 0; i < E * 9; ++i) {
+  m.conn.resize(E * P);
+  for (int64_t i = 0; i < E * P; ++i) {
     VIV_CHECK(d->conn[i] >= 0 && d->conn[i] < n, VIV_ERR_ARG, "connectivity out of range");
     m.conn[i] = (int32_t)d->conn[i];
   }
+  m.span = D == 3 ? d->span : 0.0;
+  m.wrap.assign(D == 3 ? E : 0, 0);
+  if (D == 3 && d->wrap) {
+    for (int64_t e = 0; e < E; ++e) {
+      VIV_CHECK(d->wrap[e] >= 0 && d->wrap[e] < (1LL << 27), VIV_ERR_ARG, "wrap mask out of range");
+      VIV_CHECK(d->wrap[e] == 0 || m.span > 0, VIV_ERR_ARG, "wrapped nodes need span > 0");
+      m.wrap[e] = (int32_t)d->wrap[e];
+    }
+  }
   std::vector<char> is_vertex(n, 0), cyl(n, 0);
   for (int64_t e = 0; e < E; ++e)
-    for (int c = 0; c < 4; ++c) is_vertex[m.conn[e * 9 + VERT[c]]] = 1;
+    for (int c = 0; c < m.nvert; ++c) is_vertex[m.conn[e * P + vert[c]]] = 1;
   for (int64_t a = 0; a < n; ++a) cyl[a] = (m.tags[a] & VIV_TAG_CYL) != 0;
-  m.faces.resize(F * 3);
+  if (D == 3)
+    for (int64_t a = 0; a < n; ++a)
+      VIV_CHECK(!cyl[a] || (m.tags[a] & VIV_TAG_X_FIX_Z), VIV_ERR_ARG,
+                "3-D Gamma nodes must hold their z position (VIV_TAG_X_FIX_Z)");
+  m.faces.resize(F * m.fpe);
   m.face_elem.resize(F);
+  m.face_wrap.assign(D == 3 ? F : 0, 0);
   for (int64_t f = 0; f < F; ++f) {
     int64_t e = d->gamma_faces[2 * f], ed = d->gamma_faces[2 * f + 1];
-    VIV_CHECK(e >= 0 && e < E && ed >= 0 && ed < 4, VIV_ERR_ARG, "bad gamma face");
+    VIV_CHECK(e >= 0 && e < E && ed >= 0 && ed < 2 * D, VIV_ERR_ARG, "bad gamma face");
     m.face_elem[f] = (int32_t)e;
-    for (int b = 0; b < 3; ++b) {
-      int nd = m.conn[e * 9 + EDGE[ed][b]];
+    for (int b = 0; b < m.fpe; ++b) {
+      const int loc = D == 3 ? hex_face_node((int)ed, b % 3, b / 3) : EDGE[ed][b];
+      int nd = m.conn[e * P + loc];
       VIV_CHECK(cyl[nd], VIV_ERR_ARG, "gamma face node is not tagged CYL");
-      m.faces[f * 3 + b] = nd;
+      m.faces[f * m.fpe + b] = nd;
+      if (D == 3 && (m.wrap[e] >> loc & 1)) m.face_wrap[f] |= 1 << b;
     }
   }
   const bool has_body = F > 0;
 
   // ---- nested dissection -----------------------------------------------------
-  int leaf = d->leaf_elems > 0 ? d->leaf_elems : 4;
+  int leaf = d->leaf_elems > 0 ? d->leaf_elems : (D == 3 ? 2 : 4);
   Dissector ds(m, leaf);
   std::vector<int> el(E);
   std::iota(el.begin(), el.end(), 0);
@@ -267,15 +315,15 @@ void build_mesh(Mesh& m, const vivMeshDesc* d) {
       } else {
         int32_t t = m.tags[nd];
         int32_t* sl = &m.node_dof[(int64_t)nd * NSLOT];
-        if (!(t & VIV_TAG_U_FIX_X)) sl[S_UX] = next++;
-        if (!(t & VIV_TAG_U_FIX_Y)) sl[S_UY] = next++;
-        if (!cyl[nd] && !(t & VIV_TAG_X_FIX_X)) sl[S_XX] = next++;
-        if (!cyl[nd] && !(t & VIV_TAG_X_FIX_Y)) sl[S_XY] = next++;
+        static const int ufix[3] = {VIV_TAG_U_FIX_X, VIV_TAG_U_FIX_Y, VIV_TAG_U_FIX_Z};
+        static const int xfix[3] = {VIV_TAG_X_FIX_X, VIV_TAG_X_FIX_Y, VIV_TAG_X_FIX_Z};
+        for (int i = 0; i < D; ++i)
+          if (!(t & ufix[i])) sl[S_UX + i] = next++;
+        for (int i = 0; i < D; ++i)
+          if (!cyl[nd] && !(t & xfix[i])) sl[S_XX + i] = next++;
         if (is_vertex[nd] && !(t & VIV_TAG_P_FIX)) sl[S_P] = next++;
-        if (cyl[nd]) {
-          sl[S_LX] = next++;
-          sl[S_LY] = next++;
-        }
+        if (cyl[nd])
+          for (int i = 0; i < D; ++i) sl[S_LX + i] = next++;
       }
       node_cnt[nd] = next - node_first[nd];
     }
@@ -297,7 +345,8 @@ void build_mesh(Mesh& m, const vivMeshDesc* d) {
       int dof = m.node_dof[a * NSLOT + f];
       if (dof >= 0) {
         m.dof_node[dof] = a;
-        static const int code[NSLOT] = {VIV_F_UX, VIV_F_UY, VIV_F_XX, VIV_F_XY, VIV_F_P, VIV_F_LX, VIV_F_LY};
+        static const int code[NSLOT] = {VIV_F_UX, VIV_F_UY, VIV_F_UZ, VIV_F_XX, VIV_F_XY,
+                                        VIV_F_XZ, VIV_F_P,  VIV_F_LX, VIV_F_LY, VIV_F_LZ};
         m.dof_field[dof] = code[f];
       }
     }
@@ -309,52 +358,72 @@ void build_mesh(Mesh& m, const vivMeshDesc* d) {
   }
 
   // ---- element slot maps -------------------------------------------------------
-  auto row_slot = [&](int64_t e, int cs) -> int32_t {   // cs: 0..35 u/x, 36..39 p
-    if (cs < 36) {
-      int a = cs / 4, f = cs % 4;
-      return m.node_dof[(int64_t)m.conn[e * 9 + a] * NSLOT + f];
+  // element columns: cs = 2 D a + f (f < D: u_f of node a, else x_{f-D}), then
+  // the pressure vertices at 2 D P + c; rows: u (D P), p, x (D P)
+  const int NUX = 2 * D * P;          // u/x columns
+  const int NCOL = NUX + m.nvert;     // all columns of a momentum row
+  auto row_slot = [&](int64_t e, int cs) -> int32_t {
+    if (cs < NUX) {
+      int a = cs / (2 * D), f = cs % (2 * D);
+      return m.node_dof[(int64_t)m.conn[e * P + a] * NSLOT + (f < D ? S_UX + f : S_XX + f - D)];
     }
-    return m.node_dof[(int64_t)m.conn[e * 9 + VERT[cs - 36]] * NSLOT + S_P];
+    return m.node_dof[(int64_t)m.conn[e * P + vert[cs - NUX]] * NSLOT + S_P];
   };
   auto col_slot = [&](int64_t e, int cs) -> int32_t {
-    if (cs < 36) {
-      int a = cs / 4, f = cs % 4;
-      int nd = m.conn[e * 9 + a];
-      if (f >= 2 && cyl[nd]) return m.delta_dof[f - 2];
-      return m.node_dof[(int64_t)nd * NSLOT + f];
+    if (cs < NUX) {
+      int a = cs / (2 * D), f = cs % (2 * D);
+      int nd = m.conn[e * P + a];
+      if (f >= D && cyl[nd]) return f - D < 2 ? m.delta_dof[f - D] : -1;   // x = X + (delta, 0) on Gamma
+      return m.node_dof[(int64_t)nd * NSLOT + (f < D ? S_UX + f : S_XX + f - D)];
     }
-    return m.node_dof[(int64_t)m.conn[e * 9 + VERT[cs - 36]] * NSLOT + S_P];
+    return m.node_dof[(int64_t)m.conn[e * P + vert[cs - NUX]] * NSLOT + S_P];
   };
-  // enumerate the structural pairs of an element in canonical order
+  // enumerate the structural pairs of an element in canonical order:
+  // u rows x all columns, p rows x (u, x) columns, x rows x x columns
   auto for_pairs = [&](int64_t e, auto&& fn) {
-    for (int a = 0; a < 9; ++a)
-      for (int i = 0; i < 2; ++i)
-        for (int cs = 0; cs < 40; ++cs) fn(pairA(a, i, cs), row_slot(e, 4 * a + i), col_slot(e, cs));
-    for (int c = 0; c < 4; ++c)
-      for (int cs = 0; cs < 36; ++cs) fn(pairB(c, cs), row_slot(e, 36 + c), col_slot(e, cs));
-    for (int a = 0; a < 9; ++a)
-      for (int i = 0; i < 2; ++i)
-        for (int b = 0; b < 9; ++b)
-          for (int k = 0; k < 2; ++k)
-            fn(pairC(a, i, b, k), row_slot(e, 4 * a + 2 + i), col_slot(e, 4 * b + 2 + k));
+    int idx = 0;
+    for (int a = 0; a < P; ++a)
+      for (int i = 0; i < D; ++i)
+        for (int cs = 0; cs < NCOL; ++cs) fn(idx++, row_slot(e, 2 * D * a + i), col_slot(e, cs));
+    for (int c = 0; c < m.nvert; ++c)
+      for (int cs = 0; cs < NUX; ++cs) fn(idx++, row_slot(e, NUX + c), col_slot(e, cs));
+    for (int a = 0; a < P; ++a)
+      for (int i = 0; i < D; ++i)
+        for (int b = 0; b < P; ++b)
+          for (int k = 0; k < D; ++k)
+            fn(idx++, row_slot(e, 2 * D * a + D + i), col_slot(e, 2 * D * b + D + k));
   };
   auto for_face_pairs = [&](int64_t f, auto&& fn) {
-    const int32_t* fn_ = &m.faces[f * 3];
+    const int32_t* fn_ = &m.faces[f * m.fpe];
     auto nd_dof = [&](int b, int s) { return m.node_dof[(int64_t)fn_[b] * NSLOT + s]; };
-    for (int b = 0; b < 3; ++b)
+    if (D == 2) {
+      for (int b = 0; b < 3; ++b)
+        for (int i = 0; i < 2; ++i)
+          for (int bp = 0; bp < 3; ++bp)
+            for (int k = 0; k < 2; ++k) fn(fpairD(b, i, bp, k), nd_dof(b, S_UX + i), nd_dof(bp, S_LX + k));
+      for (int b = 0; b < 3; ++b)
+        for (int i = 0; i < 2; ++i)
+          for (int cs = 0; cs < 12; ++cs) {
+            int bp = (cs % 6) / 2, k = cs % 2;
+            int32_t c = cs < 6 ? nd_dof(bp, S_UX + k) : m.delta_dof[k];
+            fn(fpairE(b, i, cs), nd_dof(b, S_LX + i), c);
+          }
       for (int i = 0; i < 2; ++i)
         for (int bp = 0; bp < 3; ++bp)
-          for (int k = 0; k < 2; ++k) fn(fpairD(b, i, bp, k), nd_dof(b, S_UX + i), nd_dof(bp, S_LX + k));
-    for (int b = 0; b < 3; ++b)
-      for (int i = 0; i < 2; ++i)
-        for (int cs = 0; cs < 12; ++cs) {
-          int bp = (cs % 6) / 2, k = cs % 2;
-          int32_t c = cs < 6 ? nd_dof(bp, S_UX + k) : m.delta_dof[k];
-          fn(fpairE(b, i, cs), nd_dof(b, S_LX + i), c);
+          for (int k = 0; k < 2; ++k) fn(fpairF(i, bp, k), m.delta_dof[i], nd_dof(bp, S_LX + k));
+      return;
+    }
+    // 3-D: the face terms couple equal components only
+    for (int b = 0; b < 9; ++b)
+      for (int i = 0; i < 3; ++i)
+        for (int bp = 0; bp < 9; ++bp) {
+          fn(fpairD3(b, i, bp), nd_dof(b, S_UX + i), nd_dof(bp, S_LX + i));
+          fn(fpairE3(b, i, bp), nd_dof(b, S_LX + i), nd_dof(bp, S_UX + i));
         }
+    for (int b = 0; b < 9; ++b)
+      for (int i = 0; i < 2; ++i) fn(fpairG3(b, i), nd_dof(b, S_LX + i), m.delta_dof[i]);
     for (int i = 0; i < 2; ++i)
-      for (int bp = 0; bp < 3; ++bp)
-        for (int k = 0; k < 2; ++k) fn(fpairF(i, bp, k), m.delta_dof[i], nd_dof(bp, S_LX + k));
+      for (int bp = 0; bp < 9; ++bp) fn(fpairF3(i, bp), m.delta_dof[i], nd_dof(bp, S_LX + i));
   };
 
   // ---- CSR pattern -------------------------------------------------------------
@@ -387,28 +456,29 @@ void build_mesh(Mesh& m, const vivMeshDesc* d) {
     auto it = std::lower_bound(b, en, c);
     return (int32_t)(it - m.col.begin());
   };
-  m.e2nz.assign(E * VOL_PAIRS, -1);
+  const int VP = m.vol_pairs, FP = m.face_pairs;
+  m.e2nz.assign(E * VP, -1);
   for (int64_t e = 0; e < E; ++e)
-    for_pairs(e, [&](int idx, int32_t r, int32_t c) { m.e2nz[e * VOL_PAIRS + idx] = slot(r, c); });
-  m.f2nz.assign(F * FACE_PAIRS, -1);
+    for_pairs(e, [&](int idx, int32_t r, int32_t c) { m.e2nz[e * VP + idx] = slot(r, c); });
+  m.f2nz.assign(F * FP, -1);
   for (int64_t f = 0; f < F; ++f)
-    for_face_pairs(f, [&](int idx, int32_t r, int32_t c) { m.f2nz[f * FACE_PAIRS + idx] = slot(r, c); });
+    for_face_pairs(f, [&](int idx, int32_t r, int32_t c) { m.f2nz[f * FP + idx] = slot(r, c); });
   if (has_body)
     for (int i = 0; i < 2; ++i) m.dd_nz[i] = slot(m.delta_dof[i], m.delta_dof[i]);
 
   // ---- colours -------------------------------------------------------------------
-  greedy_colour(m.conn, 9, E, n, m.color_off, m.color_elems);
+  greedy_colour(m.conn, P, E, n, m.color_off, m.color_elems);
   if (F > 0)
-    greedy_colour(m.faces, 3, F, n, m.fcolor_off, m.fcolor_faces);
+    greedy_colour(m.faces, m.fpe, F, n, m.fcolor_off, m.fcolor_faces);
   else
     m.fcolor_off.assign(1, 0);
 
   // ---- symbolic factorisation on the node quotient graph ------------------------
   std::vector<std::vector<int32_t>> adj(n + 1);
   for (int64_t e = 0; e < E; ++e) {
-    for (int a = 0; a < 9; ++a) {
-      int na = m.conn[e * 9 + a];
-      for (int b = 0; b < 9; ++b) adj[na].push_back(m.conn[e * 9 + b]);
+    for (int a = 0; a < P; ++a) {
+      int na = m.conn[e * P + a];
+      for (int b = 0; b < P; ++b) adj[na].push_back(m.conn[e * P + b]);
     }
   }
   for (auto& v : adj) {
@@ -1144,6 +1214,9 @@ void upload_mesh(Mesh& m, cudaStream_t s) {
   DeviceArena& A = m.arena;
   m.d_X = A.upload(m.X, s);
   m.d_conn = A.upload(m.conn, s);
+  m.d_wrap = A.upload(m.wrap, s);
+  m.d_face_wrap = A.upload(m.face_wrap, s);
+  if (m.dim == 3) upload_hex_tables(m, s);
   m.d_tags = A.upload(m.tags, s);
   m.d_faces = A.upload(m.faces, s);
   m.d_node_dof = A.upload(m.node_dof, s);

@@ -40,7 +40,8 @@ struct Req {
 
 struct Done {
   vivResult res;
-  std::vector<double> state;   // u(2n) p(n) x(2n) lam(2n) delta(2)
+  std::vector<double> state;   // u(Dn) p(n) x(Dn) lam(Dn) delta(2)
+  int dim = 2;
 };
 
 }  // namespace
@@ -101,10 +102,12 @@ void run_case(vivServer* S, Req q, double admit_s) {
     std::strncpy(R.message, viv_last_error(), sizeof R.message - 1);
   }
   if (c) {
-    const int64_t n = q.r.mesh->m.n_nodes;
-    d.state.assign(7 * n + 2, 0.0);
+    const int64_t n = q.r.mesh->m.n_nodes, D = q.r.mesh->m.dim;
+    d.dim = (int)D;
+    d.state.assign(3 * D * n + n + 2, 0.0);
     double* b = d.state.data();
-    if (viv_get_state(c, 0, b, b + 2 * n, b + 3 * n, b + 5 * n, b + 7 * n, nullptr) != VIV_OK && R.status == VIV_OK)
+    if (viv_get_state(c, 0, b, b + D * n, b + D * n + n, b + 2 * D * n + n, b + 3 * D * n + n, nullptr) != VIV_OK &&
+        R.status == VIV_OK)
       R.status = VIV_ERR_CUDA;
     viv_case_destroy(c);
   }
@@ -221,7 +224,7 @@ vivStatus viv_server_submit(vivServer* S, const vivRequest* r, int64_t* id) {
   q.id = nid;
   q.r = *r;
   q.r.u0 = nullptr;
-  q.u0.assign(r->u0, r->u0 + 2 * r->mesh->m.n_nodes);
+  q.u0.assign(r->u0, r->u0 + r->mesh->m.dim * r->mesh->m.n_nodes);
   q.bytes = bytes;
   S->incoming.push_back(std::move(q));
   S->cv_sched.notify_all();
@@ -257,12 +260,12 @@ vivStatus viv_server_state(vivServer* S, int64_t id, double* u, double* p, doubl
     return VIV_ERR_STATE;
   }
   const std::vector<double>& st = it->second.state;
-  const size_t n = (st.size() - 2) / 7;
-  if (u) std::memcpy(u, st.data(), 2 * n * sizeof(double));
-  if (p) std::memcpy(p, st.data() + 2 * n, n * sizeof(double));
-  if (x) std::memcpy(x, st.data() + 3 * n, 2 * n * sizeof(double));
-  if (lam) std::memcpy(lam, st.data() + 5 * n, 2 * n * sizeof(double));
-  if (delta) std::memcpy(delta, st.data() + 7 * n, 2 * sizeof(double));
+  const size_t D = it->second.dim, n = (st.size() - 2) / (3 * D + 1);
+  if (u) std::memcpy(u, st.data(), D * n * sizeof(double));
+  if (p) std::memcpy(p, st.data() + D * n, n * sizeof(double));
+  if (x) std::memcpy(x, st.data() + D * n + n, D * n * sizeof(double));
+  if (lam) std::memcpy(lam, st.data() + 2 * D * n + n, D * n * sizeof(double));
+  if (delta) std::memcpy(delta, st.data() + 3 * D * n + n, 2 * sizeof(double));
   return VIV_OK;
 }
 

@@ -106,29 +106,28 @@ __global__ void __launch_bounds__(NORM_THREADS) cfl_final_kernel(const double* p
   if (threadIdx.x == 0) *out = dt * red[0];
 }
 
-// delta read back from a Gamma node's position (x = X + delta on Gamma)
-__global__ void delta_from_x_kernel(int64_t a, const double* X, const double* x, double* delta) {
-  if (threadIdx.x < 2) delta[threadIdx.x] = x[2 * a + threadIdx.x] - X[2 * a + threadIdx.x];
+// delta read back from a Gamma node's position (x = X + (delta, 0) on Gamma)
+__global__ void delta_from_x_kernel(int64_t a, int D, const double* X, const double* x, double* delta) {
+  if (threadIdx.x < 2) delta[threadIdx.x] = x[D * a + threadIdx.x] - X[D * a + threadIdx.x];
 }
 
-// U += dU for every nodal field; Gamma nodes follow x = X + delta_new
-__global__ void update_kernel(int64_t n, const int32_t* node_dof, const int32_t* tags, const double* X,
+// U += dU for every nodal field (D components of u, x, lambda); Gamma nodes
+// follow x = X + (delta_new, 0) (their z position is held)
+__global__ void update_kernel(int64_t n, int D, const int32_t* node_dof, const int32_t* tags, const double* X,
                               const int32_t* delta_dof, const double* delta, const double* dU, double* u,
                               double* p, double* x, double* lam) {
   int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (a >= n) return;
   const int32_t* d = node_dof + a * NSLOT;
-  for (int i = 0; i < 2; ++i)
-    if (d[S_UX + i] >= 0) u[2 * a + i] += dU[d[S_UX + i]];
+  for (int i = 0; i < D; ++i)
+    if (d[S_UX + i] >= 0) u[D * a + i] += dU[d[S_UX + i]];
   if (d[S_P] >= 0) p[a] += dU[d[S_P]];
   if (tags[a] & VIV_TAG_CYL) {
-    for (int i = 0; i < 2; ++i) {
-      lam[2 * a + i] += dU[d[S_LX + i]];
-      x[2 * a + i] = X[2 * a + i] + (delta[i] + dU[delta_dof[i]]);
-    }
+    for (int i = 0; i < D; ++i) lam[D * a + i] += dU[d[S_LX + i]];
+    for (int i = 0; i < 2; ++i) x[D * a + i] = X[D * a + i] + (delta[i] + dU[delta_dof[i]]);
   } else {
-    for (int i = 0; i < 2; ++i)
-      if (d[S_XX + i] >= 0) x[2 * a + i] += dU[d[S_XX + i]];
+    for (int i = 0; i < D; ++i)
+      if (d[S_XX + i] >= 0) x[D * a + i] += dU[d[S_XX + i]];
   }
 }
 
@@ -276,7 +275,7 @@ void launch_norm2(const double* v, int64_t n, double* partial, double* out, cuda
 }
 
 void launch_bdf_history(const Mesh& m, CaseState& st, double a_n, double a_nm1, bool, cudaStream_t s) {
-  int64_t n2 = 2 * m.n_nodes;
+  int64_t n2 = m.dim * m.n_nodes;
   Launched L(K_VEC, s);
   bdf_kernel<<<blocks_for(n2, 256), 256, 0, s>>>(n2, st.u_n, st.u_nm1, st.x_n, st.x_nm1, a_n, a_nm1, st.hu,
                                                    st.hx);
@@ -284,14 +283,14 @@ void launch_bdf_history(const Mesh& m, CaseState& st, double a_n, double a_nm1, 
 }
 
 void launch_extrapolate(const Mesh& m, CaseState& st, double w, cudaStream_t s) {
-  const int64_t n2 = 2 * m.n_nodes;
+  const int64_t n2 = m.dim * m.n_nodes;
   {
     Launched L(K_VEC, s);
     extrapolate_kernel<<<blocks_for(n2, 256), 256, 0, s>>>(n2, st.u_n, st.u_nm1, st.x_n, st.x_nm1, w, st.u, st.x);
   }
   if (m.n_faces > 0) {
     Launched L(K_VEC, s);
-    delta_from_x_kernel<<<1, 32, 0, s>>>(m.faces[0], m.d_X, st.x, st.delta);
+    delta_from_x_kernel<<<1, 32, 0, s>>>(m.faces[0], m.dim, m.d_X, st.x, st.delta);
   }
   VIV_CUDA(cudaGetLastError());
 }
@@ -299,7 +298,7 @@ void launch_extrapolate(const Mesh& m, CaseState& st, double w, cudaStream_t s) 
 void launch_update(const Mesh& m, CaseState& st, const double* dU, cudaStream_t s) {
   {
     Launched L(K_VEC, s);
-    update_kernel<<<blocks_for(m.n_nodes, 256), 256, 0, s>>>(m.n_nodes, m.d_node_dof, m.d_tags, m.d_X,
+    update_kernel<<<blocks_for(m.n_nodes, 256), 256, 0, s>>>(m.n_nodes, m.dim, m.d_node_dof, m.d_tags, m.d_X,
                                                               m.d_delta_dof, st.delta, dU, st.u, st.p, st.x,
                                                               st.lam);
   }

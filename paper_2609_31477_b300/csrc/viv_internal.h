@@ -49,12 +49,24 @@ struct DeviceArena {
   ~DeviceArena() { release(); }
 };
 
-// per node field slots of node_dof
-enum { S_UX = 0, S_UY = 1, S_XX = 2, S_XY = 3, S_P = 4, S_LX = 5, S_LY = 6, NSLOT = 7 };
+// per node field slots of node_dof (the z slots stay -1 on 2-D meshes)
+enum { S_UX = 0, S_UY = 1, S_UZ = 2, S_XX = 3, S_XY = 4, S_XZ = 5, S_P = 6, S_LX = 7, S_LY = 8, S_LZ = 9,
+       NSLOT = 10 };
 
 // local pairs of the element matrix scattered through e2nz (structural nonzeros)
 constexpr int VOL_PAIRS = 1188;    // u rows x (u,x,p) + p rows x (u,x) + x rows x x
 constexpr int FACE_PAIRS = 120;    // u x lambda, lambda x (u, delta), delta x lambda
+// 3-D (27-node hexahedra, 8 pressure vertices, 9-node Gamma faces): element
+// columns cs = 6 a + f (f < 3: u_f, else x_{f-3}) and 162 + c (pressure)
+constexpr int VOL_PAIRS3 = 81 * 170 + 8 * 162 + 81 * 81;   // 21,627
+constexpr int FACE_PAIRS3 = 243 + 243 + 18 + 18;            // u x lambda, lambda x u, lambda x delta, delta x lambda
+__host__ __device__ inline int pairA3(int a, int i, int cs) { return (3 * a + i) * 170 + cs; }
+__host__ __device__ inline int pairB3(int c, int cs) { return 13770 + c * 162 + cs; }
+__host__ __device__ inline int pairC3(int a, int i, int b, int k) { return 15066 + (3 * a + i) * 81 + 3 * b + k; }
+__host__ __device__ inline int fpairD3(int b, int i, int bp) { return (3 * b + i) * 9 + bp; }
+__host__ __device__ inline int fpairE3(int b, int i, int bp) { return 243 + (3 * b + i) * 9 + bp; }
+__host__ __device__ inline int fpairG3(int b, int i) { return 486 + 2 * b + i; }
+__host__ __device__ inline int fpairF3(int i, int bp) { return 504 + 9 * i + bp; }
 
 // ----- blocked factorisation schedule ---------------------------------------
 enum LaunchKind {
@@ -137,12 +149,18 @@ struct FrontTables {              // device copies
 struct Mesh {
   // host copies
   int64_t n_nodes = 0, n_elems = 0, n_faces = 0;
-  std::vector<double> X;
-  std::vector<int32_t> conn;       // E x 9
+  int dim = 2;                     // 2: Q2 quads; 3: Q2 hexahedra
+  int npe = 9, nvert = 4, fpe = 3; // nodes per element, pressure vertices, nodes per Gamma face
+  int vol_pairs = VOL_PAIRS, face_pairs = FACE_PAIRS;
+  double span = 0;                 // 3-D: period in z (0: not periodic)
+  std::vector<double> X;           // n x dim
+  std::vector<int32_t> conn;       // E x npe
+  std::vector<int32_t> wrap;       // 3-D: per element, bit a: local node a at X + span e_z
   std::vector<int32_t> tags;
-  std::vector<int32_t> faces;      // F x 3 node ids along the edge
+  std::vector<int32_t> faces;      // F x fpe node ids (along the edge / in face order)
+  std::vector<int32_t> face_wrap;  // 3-D: per face, bit b: face node b at X + span e_z
   std::vector<int32_t> face_elem;
-  std::vector<int32_t> node_dof;   // n x 7
+  std::vector<int32_t> node_dof;   // n x NSLOT
   std::vector<int32_t> delta_dof;  // 2 (or -1)
   int64_t n_dofs = 0;
   int64_t n_front_dofs = 0;        // unknowns the fronts hold: all but delta (numbered last)
@@ -211,6 +229,10 @@ struct Mesh {
   DeviceArena arena;
   double* d_X = nullptr;
   int32_t* d_conn = nullptr;
+  int32_t* d_wrap = nullptr;
+  int32_t* d_face_wrap = nullptr;
+  double* d_hex_tab = nullptr;         // 3-D: shape-function tables at the Gauss points (FP64, FP32)
+  float* d_hex_tab_f = nullptr;
   int32_t* d_tags = nullptr;
   int32_t* d_faces = nullptr;
   int32_t* d_node_dof = nullptr;
@@ -343,6 +365,12 @@ namespace viv {
 void launch_element_areas(const Mesh& m, double* lame, double scale, bool constant, double* scratch,
                           cudaStream_t s);
 void launch_quasi_init(const Mesh& m, const CaseState& st, const vivParams& prm, cudaStream_t s);
+// 3-D (hexahedral) element, face and border kernels (assembly3d.cu)
+void upload_hex_tables(Mesh& m, cudaStream_t s);
+void launch_element_volumes(const Mesh& m, double* vol, cudaStream_t s);
+template <class T, bool JAC>
+void run_assembly3(const Mesh& m, const CaseState& st, const vivParams& prm, double* R, T* vals, cudaStream_t s,
+                   int parts);
 void launch_residual(const Mesh& m, const CaseState& st, const vivParams& prm, cudaStream_t s);
 template <class T>
 void launch_jacobian(const Mesh& m, const CaseState& st, const vivParams& prm, T* vals, cudaStream_t s);

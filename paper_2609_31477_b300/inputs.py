@@ -409,19 +409,22 @@ def seeded_normals(seed, n):
 
 
 def viv_initial_velocity(mesh, U_inf=1.0, sigma=1e-3, seed=1):
-    """Nodal initial velocity: uniform inflow (U_inf, 0) plus seeded N(0, sigma^2)
-    noise on every component that no Dirichlet tag holds.  Prescribed
-    components carry their boundary value (inflow, or 0 normal to walls)."""
-    n = len(mesh["X"])
-    u = np.zeros((n, 2))
+    """Nodal initial velocity: uniform inflow (U_inf, 0[, 0]) plus seeded
+    N(0, sigma^2) noise on every component that no Dirichlet tag holds.
+    Prescribed components carry their boundary value (inflow, or 0 normal to
+    walls).  2-D or 3-D by the mesh's coordinates."""
+    n, D = np.shape(mesh["X"])
+    u = np.zeros((n, D))
     u[:, 0] = U_inf
     if sigma > 0:
-        u += sigma * seeded_normals(seed, 2 * n).reshape(n, 2)
+        u += sigma * seeded_normals(seed, D * n).reshape(n, D)
     t = mesh["tags"]
     fx = (t & U_FIX_X) != 0
     fy = (t & U_FIX_Y) != 0
     u[fx, 0] = U_inf
     u[fy, 1] = 0.0
+    if D == 3:
+        u[(t & U_FIX_Z) != 0, 2] = 0.0
     return u
 
 

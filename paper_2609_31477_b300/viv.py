@@ -23,7 +23,8 @@ STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_PIVOT", 5:
 KINDS = ("residual", "jacobian", "face_border", "front_assemble", "panel_lu", "trsm", "schur_gemm",
          "fwd_solve", "bwd_solve", "spmv", "vector", "tc_schur_gemm", "tc_split")
 KINDS_N = len(KINDS)
-FIELD = {0: "ux", 1: "uy", 2: "xx", 3: "xy", 4: "p", 5: "lx", 6: "ly", 7: "dx", 8: "dy"}
+FIELD = {0: "ux", 1: "uy", 2: "xx", 3: "xy", 4: "p", 5: "lx", 6: "ly", 7: "dx", 8: "dy",
+         9: "uz", 10: "xz", 11: "lz"}
 
 
 class VivError(RuntimeError):
@@ -35,7 +36,8 @@ class VivError(RuntimeError):
 class MeshDesc(C.Structure):
     _fields_ = [("n_nodes", C.c_int64), ("n_elems", C.c_int64), ("n_gamma_faces", C.c_int64),
                 ("X", C.c_void_p), ("conn", C.c_void_p), ("tags", C.c_void_p),
-                ("gamma_faces", C.c_void_p), ("leaf_elems", C.c_int32)]
+                ("gamma_faces", C.c_void_p), ("leaf_elems", C.c_int32), ("dim", C.c_int32),
+                ("span", C.c_double), ("wrap", C.c_void_p)]
 
 
 class MeshInfo(C.Structure):
@@ -47,7 +49,7 @@ class MeshInfo(C.Structure):
                 ("outer_flops", C.c_double), ("tc_split_chunks", C.c_int64), ("tc_tiles", C.c_int64),
                 ("tc_image_bytes", C.c_size_t), ("window_tc_flops", C.c_double),
                 ("window_lu_flops", C.c_double), ("window_gemm_flops", C.c_double),
-                ("block_level_mask", C.c_int64)]
+                ("block_level_mask", C.c_int64), ("dim", C.c_int32)]
 
 
 class Params(C.Structure):
@@ -225,9 +227,12 @@ def _desc(mesh):
     conn = np.ascontiguousarray(mesh["conn"], dtype=np.int64)
     tags = np.ascontiguousarray(mesh["tags"], dtype=np.int32)
     gf = np.ascontiguousarray(mesh["gamma_faces"], dtype=np.int64).reshape(-1, 2)
-    keep = (X, conn, tags, gf)
+    dim = int(X.shape[1])
+    wrap = np.ascontiguousarray(mesh.get("wrap", np.zeros(len(conn), np.int64)), dtype=np.int64)
+    keep = (X, conn, tags, gf, wrap)
     d = MeshDesc(len(X), len(conn), len(gf), _ptr(X).value, _ptr(conn).value, _ptr(tags).value,
-                 _ptr(gf).value if len(gf) else None, int(mesh.get("leaf_elems", 0)))
+                 _ptr(gf).value if len(gf) else None, int(mesh.get("leaf_elems", 0)), dim,
+                 float(mesh.get("span", 0.0)), _ptr(wrap).value if dim == 3 else None)
     return d, keep
 
 
@@ -258,6 +263,7 @@ class Mesh:
         self.refresh_info()
         self.n_dofs = self.info["n_dofs"]
         self.n_nodes = len(mesh["X"])
+        self.dim = int(self.info["dim"])
 
     def dof_labels(self):
         node = np.empty(self.n_dofs, np.int64)
@@ -323,6 +329,7 @@ class Case:
                                    C.c_void_p(self.stream.cuda_stream), C.byref(h)))
         self.h = h
         self.n = mesh.n_nodes
+        self.dim = mesh.dim
 
     # state ---------------------------------------------------------------------
     def resolved_params(self):
@@ -353,8 +360,8 @@ class Case:
         _check(_lib.viv_set_history(self.h, 0, _ptr(a), _ptr(b)))
 
     def get_state(self):
-        n = self.n
-        u, p, x, lam, d = (np.empty((n, 2)), np.empty(n), np.empty((n, 2)), np.empty((n, 2)), np.empty(2))
+        n, D = self.n, self.dim
+        u, p, x, lam, d = (np.empty((n, D)), np.empty(n), np.empty((n, D)), np.empty((n, D)), np.empty(2))
         t = C.c_double()
         _check(_lib.viv_get_state(self.h, 0, _ptr(u), _ptr(p), _ptr(x), _ptr(lam), _ptr(d), C.byref(t)))
         return dict(u=u, p=p, x=x, lam=lam, delta=d, t=t.value)
@@ -493,9 +500,9 @@ class Server:
         _check(_lib.viv_server_poll(self.h, buf, max_results, C.byref(n), int(wait_ms)))
         return [buf[i].as_dict() for i in range(n.value)]
 
-    def state(self, rid, n_nodes):
-        u, p, x, lam, d = (np.empty((n_nodes, 2)), np.empty(n_nodes), np.empty((n_nodes, 2)),
-                           np.empty((n_nodes, 2)), np.empty(2))
+    def state(self, rid, n_nodes, dim=2):
+        u, p, x, lam, d = (np.empty((n_nodes, dim)), np.empty(n_nodes), np.empty((n_nodes, dim)),
+                           np.empty((n_nodes, dim)), np.empty(2))
         _check(_lib.viv_server_state(self.h, rid, _ptr(u), _ptr(p), _ptr(x), _ptr(lam), _ptr(d)))
         return dict(u=u, p=p, x=x, lam=lam, delta=d)
 

@@ -7,16 +7,17 @@ from paper_2609_31477_b300 import inputs as I, viv
 
 def oracle_labels(c):
     lab = np.empty(c.ndof, dtype=object)
+    D = c.dof_u.shape[1]
     for a in range(c.n):
-        for i, f in enumerate(("ux", "uy")):
+        for i, f in enumerate(("ux", "uy", "uz")[:D]):
             if c.dof_u[a, i] >= 0:
                 lab[c.dof_u[a, i]] = (a, f)
         if c.dof_p[a] >= 0:
             lab[c.dof_p[a]] = (a, "p")
-        for i, f in enumerate(("xx", "xy")):
+        for i, f in enumerate(("xx", "xy", "xz")[:D]):
             if c.dof_x[a, i] >= 0:
                 lab[c.dof_x[a, i]] = (a, f)
-        for i, f in enumerate(("lx", "ly")):
+        for i, f in enumerate(("lx", "ly", "lz")[:D]):
             if c.dof_l[a, i] >= 0:
                 lab[c.dof_l[a, i]] = (a, f)
     if c.has_body:

@@ -40,16 +40,17 @@ def test_bad_mesh_is_rejected(lib):
 
 def _labels_oracle(c):
     lab = {}
+    D = c.dof_u.shape[1]
     for a in range(c.n):
-        for i, f in enumerate(("ux", "uy")):
+        for i, f in enumerate(("ux", "uy", "uz")[:D]):
             if c.dof_u[a, i] >= 0:
                 lab[c.dof_u[a, i]] = (a, f)
         if c.dof_p[a] >= 0:
             lab[c.dof_p[a]] = (a, "p")
-        for i, f in enumerate(("xx", "xy")):
+        for i, f in enumerate(("xx", "xy", "xz")[:D]):
             if c.dof_x[a, i] >= 0:
                 lab[c.dof_x[a, i]] = (a, f)
-        for i, f in enumerate(("lx", "ly")):
+        for i, f in enumerate(("lx", "ly", "lz")[:D]):
             if c.dof_l[a, i] >= 0:
                 lab[c.dof_l[a, i]] = (a, f)
     if c.has_body:
@@ -84,3 +85,37 @@ def test_host_analysis_matches_oracle_unknowns_and_pattern(lib):
         assert bad not in pairs
     info = M.info
     assert info["n_fronts"] > 10 and info["max_front"] >= 2 and info["factor_flops"] > 0
+
+
+def test_host_analysis_3d_matches_oracle_unknowns_and_pattern(lib):
+    """Periodic hexahedral extrusion: the library numbers the oracle's
+    unknowns (three components of u, x and lambda, the z position of Gamma
+    held) and its pattern holds every oracle Jacobian entry that is not the
+    rounding of an exact zero."""
+    from oracle.solver3d import viv_oracle_case3d
+    m = I.viv_cylinder_mesh3d(2, 2, 0.7)
+    M = viv.Mesh(m, device=False)
+    assert M.dim == 3 and M.info["dim"] == 3
+    node, field = M.dof_labels()
+    n = len(m["X"])
+    oc = viv_oracle_case3d(m, 150.0, 6.0, 0.05, np.zeros((n, 3)))
+    assert M.n_dofs == oc.ndof
+    lab = _labels_oracle(oc)
+    gpu_lab = {(int(a), viv.FIELD[int(f)]): i for i, (a, f) in enumerate(zip(node, field))}
+    assert set(gpu_lab) == set(lab.values())
+    perm = np.array([gpu_lab[lab[i]] for i in range(oc.ndof)])
+    oc.u = np.random.default_rng(1).normal(size=(n, 3))
+    oc.u_n, oc.x_n = oc.u.copy(), oc.x.copy()
+    c0, hu, hx = oc.bdf_coefficients()
+    J = oc.jacobian(c0, hu, hx, 0.05).tocoo()
+    rp, col = M.pattern()
+    rows = np.repeat(np.arange(M.n_dofs), np.diff(rp))
+    have = set(zip(rows.tolist(), col.tolist()))
+    big = np.abs(J.data) > 1e-13 * np.abs(J.data).max()
+    need = set(zip(perm[J.row[big]].tolist(), perm[J.col[big]].tolist()))
+    assert need <= have
+    kind = np.array([viv.FIELD[int(f)][0] for f in field])
+    pairs = set(zip(kind[rows].tolist(), kind[col].tolist()))
+    for bad in (("p", "p"), ("l", "l"), ("x", "u"), ("x", "p"), ("x", "l")):
+        assert bad not in pairs
+    assert M.info["front_entries"] > 0 and M.info["factor_flops"] > 0
