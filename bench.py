@@ -37,6 +37,8 @@ WORKLOADS = {
     # 3-D: the m = 7 section (555 quads) extruded into 24 periodic layers over a 2 pi span
     # (13,320 Q2-Q1 hexahedra, 662,114 unknowns), Re 300, U* 8 (L = span), dt 0.05
     "viv3d_re300_m7_z24": dict(m=7, layers=24, span=2.0 * math.pi, Re=300.0, Ustar=8.0, dt=0.05),
+    # (profiling: the m = 5 section, 251 quads, in 12 layers of the same thickness: 3,012 hexahedra)
+    "viv3d_re300_m5_z12": dict(m=5, layers=12, span=math.pi, Re=300.0, Ustar=8.0, dt=0.05),
 }
 FP32_SIMT_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12      # 148 SMs x 128 FP32 lanes x FMA x 2.032 GHz
 FP64_TFLOPS = 1.25                                       # B300 FP64, nominal
@@ -422,6 +424,10 @@ def run_ours(args, wl, rank, world, local):
     bf16_key = "bf16_tflops_sustained" if "bf16_tflops_sustained" in peaks else "bf16_tflops"
     tc_peak = peaks[bf16_key] / 2.0 / 3.0
     fbytes = 4 * info["front_entries"]
+    # factor entries p (2m - p) per front (L and U with the pivot block; a front's contribution
+    # block is not factor data): a forward or backward sweep reads about half of them
+    fr = M.fronts()
+    factor_bytes = 4 * float(np.sum(fr["p"].astype(np.float64) * (2.0 * fr["m"] - fr["p"])))
     window = args.pivoting == "window"
     tc_flops = info["window_tc_flops"] if window else info["outer_flops"]
 
@@ -456,7 +462,7 @@ def run_ours(args, wl, rank, world, local):
             a = (1.5e5 if three_d else 8.0e3) * len(mesh["conn"]) * evals / sec / 1e12
             return {"bound": "alu", "achieved": a, "peak": FP64_TFLOPS, "unit": "TFLOP/s", "frac": a / FP64_TFLOPS,
                     "peak_source": "FP64 nominal 1.25 TFLOP/s (no FP64 measurement); flops approximate"}
-        per = {"fwd_solve": fbytes / 2, "bwd_solve": fbytes / 2, "front_assemble": 2 * fbytes,
+        per = {"fwd_solve": factor_bytes / 2, "bwd_solve": factor_bytes / 2, "front_assemble": 2 * fbytes,
                "spmv": 12 * info["nnz"] + 24 * info["n_dofs"], "jacobian": 12 * info["nnz"]}.get(kind)
         if per is None:
             return None
