@@ -130,11 +130,15 @@ def viv_cylinder_mesh(m=12, D=1.0, Xc=(0.0, 0.0), half=3.0,
         t -= 2 * h
         return h, -h + t
 
+    # the square's corners (ring index m + shift) must be quad corners (even
+    # ring index) so that the O-grid cells meet the Cartesian cells edge to
+    # edge; odd m starts the ring one node later
+    shift = m % 2
     ring = np.empty((n_around, 2 * m + 1), dtype=np.int64)
     for k in range(n_around):
-        th = 2.0 * math.pi * k / n_around
+        th = 2.0 * math.pi * (k + shift) / n_around
         c = (cx + r_in * math.cos(th), cy + r_in * math.sin(th))
-        sq = square_point(perim * k / n_around)
+        sq = square_point(perim * (k + shift) / n_around)
         s_pt = (cx + sq[0], cy + sq[1])
         for r, s in enumerate(s_nodes):
             if r == 0:
@@ -315,6 +319,36 @@ def hole_square_mesh(n, R0=0.15, center=(0.5, 0.5), lo=0.0, hi=1.0):
     return dict(X=X, conn=np.array(conn, dtype=np.int64), tags=tags,
                 gamma_faces=np.array(gamma_faces, dtype=np.int64).reshape(-1, 2),
                 Xc=np.array([cx, cy], dtype=np.float64), D=2.0 * R0, name=f"hole_square_n{n}")
+
+
+# --- simplicial variant: 6-node triangles with straight edges ----------------------
+# local triangle node order: vertices 0, 1, 2, then the midpoints of edges
+# 0-1 (3), 1-2 (4), 2-0 (5); local edge e runs (v_e, midpoint, v_{e+1})
+def triangulate_q2(mesh):
+    """Split every Q2 quad of a 2-D mesh along its diagonal 0-8 into two
+    6-node triangles, (q0, q2, q8 | q1, q5, q4) and (q0, q8, q6 | q4, q7, q3),
+    and move every midside node to the midpoint of its edge's end nodes, so
+    that the edges are straight (the geometry of a P1 position field; the
+    cylinder becomes a polygon).  Tags are kept; Gamma edges map to the
+    triangle edges on the same quad edge.  Returns X, conn (2E, 6), tags,
+    gamma_faces (F, 2) [element, local edge 0..2], elem = "tri6"."""
+    X = np.array(mesh["X"], dtype=np.float64)
+    q = np.asarray(mesh["conn"], dtype=np.int64)
+    E = len(q)
+    conn = np.empty((2 * E, 6), dtype=np.int64)
+    conn[0::2] = q[:, [0, 2, 8, 1, 5, 4]]
+    conn[1::2] = q[:, [0, 8, 6, 4, 7, 3]]
+    for c in (conn[0::2], conn[1::2]):
+        for mid, (a, b) in ((3, (0, 1)), (4, (1, 2)), (5, (2, 0))):
+            X[c[:, mid]] = 0.5 * (X[c[:, a]] + X[c[:, b]])
+    # quad edge -> (triangle offset, local edge): xi=0 -> T2 edge 2, xi=1 -> T1 edge 1,
+    # eta=0 -> T1 edge 0, eta=1 -> T2 edge 1
+    emap = {0: (1, 2), 1: (0, 1), 2: (0, 0), 3: (1, 1)}
+    gf = [(2 * e + emap[ed][0], emap[ed][1]) for e, ed in np.asarray(mesh["gamma_faces"]).reshape(-1, 2)]
+    out = dict(mesh)
+    out.update(X=X, conn=conn, gamma_faces=np.array(gf, dtype=np.int64).reshape(-1, 2), elem="tri6",
+               name=mesh.get("name", "mesh") + "_tri")
+    return out
 
 
 # --- 3-D: periodic extrusion of a 2-D Q2 mesh into 27-node hexahedra -------------

@@ -1,0 +1,115 @@
+"""Pins of the oracle's P2-P1 triangle routines with a P1 position
+(oracle/fem_tri.py, oracle/solver_tri.py) against what the mathematics fixes:
+the quadrature rule's exactness, the P2 basis' nodal and partition-of-unity
+properties and its gradients, the closed-form translating box reproduced to
+rounding (every volume, Gamma and border term), and central differences of
+the residual against the assembled Jacobian."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2609_31477_b300 import inputs as I
+from oracle import fem_tri, mms
+from oracle.solver_tri import OracleCaseTri, viv_oracle_case_tri
+
+
+def test_quadrature_exact_to_degree_five():
+    s, t = fem_tri.QPTS[:, 0], fem_tri.QPTS[:, 1]
+    for i in range(7):
+        for j in range(7 - i):
+            exact = math.factorial(i) * math.factorial(j) / math.factorial(i + j + 2)
+            got = np.sum(fem_tri.QWTS * s ** i * t ** j)
+            if i + j <= 5:
+                assert abs(got - exact) <= 1e-15, (i, j)
+    # degree 6 is not integrated exactly (the rule is not over-claimed)
+    assert abs(np.sum(fem_tri.QWTS * s ** 6) - math.factorial(6) / math.factorial(8)) > 1e-8
+
+
+def test_p2_basis_nodal_partition_and_gradients():
+    nodes = np.array([[0, 0], [1, 0], [0, 1], [0.5, 0], [0.5, 0.5], [0, 0.5]], dtype=float)
+    N, _ = fem_tri.p2_basis(nodes[:, 0], nodes[:, 1])
+    assert np.allclose(N, np.eye(6), atol=1e-15)
+    rng = np.random.default_rng(0)
+    st = rng.uniform(0, 0.5, size=(20, 2))
+    N, dN = fem_tri.p2_basis(st[:, 0], st[:, 1])
+    assert np.allclose(N.sum(-1), 1.0, atol=1e-15)
+    assert np.allclose(dN.sum(-2), 0.0, atol=1e-14)
+    h = 1e-6
+    for k in range(2):
+        e = np.zeros(2)
+        e[k] = h
+        Np, _ = fem_tri.p2_basis(st[:, 0] + e[0], st[:, 1] + e[1])
+        Nm, _ = fem_tri.p2_basis(st[:, 0] - e[0], st[:, 1] - e[1])
+        assert np.allclose((Np - Nm) / (2 * h), dN[..., k], atol=1e-8)
+    # the P2 space reproduces quadratics: x^2 + 3xy at the nodes interpolates exactly
+    f = lambda p: p[..., 0] ** 2 + 3 * p[..., 0] * p[..., 1]
+    Nq, _ = fem_tri.p2_basis(st[:, 0], st[:, 1])
+    assert np.allclose(Nq @ f(nodes), f(st), atol=1e-14)
+
+
+def _box_case(sol, n, dt):
+    m = I.triangulate_q2(I.square_mesh(n, hole=(0.4, 0.6)))
+    m["tags"][0] |= I.P_FIX
+    c = OracleCaseTri(m, rho=sol.rho, mu=sol.mu, k=sol.k, dt=dt, u0=np.zeros((len(m["X"]), 2)), lame=1.0, src=sol)
+    sol.set_exact_state(c, -dt)
+    hist = (c.u.copy(), c.x.copy())
+    sol.set_exact_state(c, 0.0)
+    c.hist = hist
+    return c
+
+
+def test_translating_box_reproduced_to_rounding():
+    """The closed-form patch solution (x = X + a t: P1; u linear in space:
+    P2; p linear: P1) on triangles: BDF1 then BDF2 reproduce it to rounding,
+    with the multiplier, the border row and the force."""
+    sol = mms.translating_box()
+    c = _box_case(sol, 10, 0.1)
+    for _ in range(3):
+        norms = c.step(dirichlet=sol.set_dirichlet)
+        t = c.t
+        assert norms[-1] <= 1e-10
+        assert np.abs(c.u - sol.velocity(c.X, t)).max() < 1e-11
+        assert np.abs(c.x - sol.position(c.X, t)).max() < 1e-12
+        assert np.abs(c.p - sol.pressure(c.X, t))[c.is_vertex].max() < 1e-8
+        assert np.allclose(c.delta, sol.delta(t), atol=1e-13)
+        assert np.allclose(c.force(), sol.force(t), atol=1e-11)
+
+
+def test_jacobian_matches_central_differences():
+    m = I.triangulate_q2(I.viv_cylinder_mesh(3))
+    rng = np.random.default_rng(7)
+    n = len(m["X"])
+    c = viv_oracle_case_tri(m, Re=150.0, Ustar=6.0, dt=0.05, u0=I.viv_initial_velocity(m, 1.0, 1e-2, 3))
+    U0 = c.gather()
+    c.scatter(U0 + 0.01 * rng.normal(size=U0.shape))
+    c.u_n, c.x_n = c.u.copy(), c.x.copy()
+    c.hist = (c.u + 0.01, c.x.copy())
+    c0, hu, hx = c.bdf_coefficients()
+    J = c.jacobian(c0, hu, hx, 0.05)
+    U = c.gather()
+    h = 1e-6
+    free_x = np.nonzero(c.dof_x[:, 0] >= 0)[0]
+    cols = list(c.dof_d) + list(c.dof_l[c.cyl][:2, 0]) + list(c.dof_x[free_x[:4], 0]) + \
+        list(c.dof_u[c.is_mid & (c.dof_u[:, 1] >= 0)][:3, 1]) + list(rng.integers(0, c.ndof, 6))
+    for j in cols:
+        e = np.zeros_like(U)
+        e[j] = h
+        c.scatter(U + e)
+        Rp = c.residual(c0, hu, hx, 0.05)
+        c.scatter(U - e)
+        Rm = c.residual(c0, hu, hx, 0.05)
+        c.scatter(U)
+        fd = (Rp - Rm) / (2 * h)
+        col = J[:, j].toarray().ravel()
+        assert np.abs(col - fd).max() <= 1e-6 * max(1.0, np.abs(fd).max()), j
+
+
+def test_midside_positions_follow_the_vertices():
+    m = I.triangulate_q2(I.viv_cylinder_mesh(3))
+    c = viv_oracle_case_tri(m, Re=100.0, Ustar=8.0, dt=0.1, u0=I.viv_initial_velocity(m))
+    c.step()
+    par = c.mid_parent[c.is_mid]
+    assert np.abs(c.x[c.is_mid] - 0.5 * (c.x[par[:, 0]] + c.x[par[:, 1]])).max() <= 1e-15
+    assert np.all(c.dof_x[~c.is_vertex] < 0)
+    assert np.allclose(c.x[c.cyl] - c.X[c.cyl], c.delta, atol=1e-15)
