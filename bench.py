@@ -37,6 +37,9 @@ WORKLOADS = {
     # 3-D: the m = 7 section (555 quads) extruded into 24 periodic layers over a 2 pi span
     # (13,320 Q2-Q1 hexahedra, 662,114 unknowns), Re 300, U* 8 (L = span), dt 0.05
     "viv3d_re300_m7_z24": dict(m=7, layers=24, span=2.0 * math.pi, Re=300.0, Ustar=8.0, dt=0.05),
+    # the paper's own spaces (P2-P1 triangles, P1 position) on the headline mesh split into
+    # 77,600 triangles with straight edges
+    "viv_tri_re200_m60": dict(m=60, tri=True, Re=200.0, Ustar=10.0, dt=0.02),
     # (profiling: the m = 5 section, 251 quads, in 12 layers of the same thickness: 3,012 hexahedra)
     "viv3d_re300_m5_z12": dict(m=5, layers=12, span=math.pi, Re=300.0, Ustar=8.0, dt=0.05),
 }
@@ -165,10 +168,14 @@ def oracle_sample(wl, newton_iters):
     import numpy as np
     from paper_2609_31477_b300 import inputs as I
     from oracle.solver import sparse_lu, viv_oracle_case
+    from oracle.solver_tri import viv_oracle_case_tri
+    tri = bool(wl.get("tri"))
+    make_mesh = (lambda m: I.triangulate_q2(I.viv_cylinder_mesh(m))) if tri else I.viv_cylinder_mesh
+    make_case = viv_oracle_case_tri if tri else viv_oracle_case
     t_all = time.perf_counter()
-    mesh = I.viv_cylinder_mesh(wl["m"])
+    mesh = make_mesh(wl["m"])
     u0 = I.viv_initial_velocity(mesh, 1.0, 1e-3, 1)
-    oc = viv_oracle_case(mesh, wl["Re"], wl["Ustar"], wl["dt"], u0)
+    oc = make_case(mesh, wl["Re"], wl["Ustar"], wl["dt"], u0)
     oc.u_n, oc.x_n = oc.u.copy(), oc.x.copy()
     c0, hu, hx = oc.bdf_coefficients()
     t0 = time.perf_counter()
@@ -181,15 +188,15 @@ def oracle_sample(wl, newton_iters):
     used, inv = np.unique(conn, return_inverse=True)
     sub = dict(X=mesh["X"][used], conn=inv.reshape(conn.shape), tags=mesh["tags"][used] & ~I.CYL,
                gamma_faces=np.zeros((0, 2), np.int64))
-    sc = viv_oracle_case(sub, wl["Re"], wl["Ustar"], wl["dt"], u0[used])
+    sc = make_case(sub, wl["Re"], wl["Ustar"], wl["dt"], u0[used])
     sc.u_n, sc.x_n = sc.u.copy(), sc.x.copy()
     c0s, hus, hxs = sc.bdf_coefficients()
     t0 = time.perf_counter()
     sc.jacobian(c0s, hus, hxs, wl["dt"])
     t_jac = (time.perf_counter() - t0) * E / len(sub_e)
     # LU on the 6,208-quad member of the family
-    m24 = I.viv_cylinder_mesh(24)
-    lc = viv_oracle_case(m24, wl["Re"], wl["Ustar"], wl["dt"], I.viv_initial_velocity(m24, 1.0, 1e-3, 1))
+    m24 = make_mesh(24)
+    lc = make_case(m24, wl["Re"], wl["Ustar"], wl["dt"], I.viv_initial_velocity(m24, 1.0, 1e-3, 1))
     lc.u_n, lc.x_n = lc.u.copy(), lc.x.copy()
     c0l, hul, hxl = lc.bdf_coefficients()
     J24 = lc.jacobian(c0l, hul, hxl, wl["dt"]).tocsc()
@@ -198,8 +205,9 @@ def oracle_sample(wl, newton_iters):
     t_lu24 = time.perf_counter() - t0
     t_lu = t_lu24 * (oc.ndof / lc.ndof) ** 1.5
     per_step = newton_iters * (t_res + t_jac + t_lu) + t_res
-    desc = (f"oracle on {E}-quad mesh: residual full ({t_res:.2f}s), complex-step Jacobian on 1/32 of the "
-            f"elements x32 ({t_jac:.1f}s), SuperLU of the {len(m24['conn'])}-quad mesh scaled by (N ratio)^1.5 "
+    kind = "triangle" if tri else "quad"
+    desc = (f"oracle on {E}-{kind} mesh: residual full ({t_res:.2f}s), complex-step Jacobian on 1/32 of the "
+            f"elements x32 ({t_jac:.1f}s), SuperLU of the {len(m24['conn'])}-{kind} mesh scaled by (N ratio)^1.5 "
             f"({t_lu24:.1f}s -> {t_lu:.0f}s); {newton_iters:.2f} Newton iterations per step; extrapolated")
     return 1.0 / per_step, desc, time.perf_counter() - t_all
 
@@ -355,8 +363,13 @@ def run_ours(args, wl, rank, world, local):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
     viv.load()
-    three_d = "layers" in wl
-    mesh = I.viv_cylinder_mesh3d(wl["m"], wl["layers"], wl["span"]) if three_d else I.viv_cylinder_mesh(wl["m"])
+    three_d, tri = "layers" in wl, bool(wl.get("tri"))
+    if three_d:
+        mesh = I.viv_cylinder_mesh3d(wl["m"], wl["layers"], wl["span"])
+    elif tri:
+        mesh = I.triangulate_q2(I.viv_cylinder_mesh(wl["m"]))
+    else:
+        mesh = I.viv_cylinder_mesh(wl["m"])
     u0 = I.viv_initial_velocity(mesh, 1.0, 1e-3, 1 + rank)
     M = viv.Mesh(mesh)
     info = M.info
@@ -455,11 +468,11 @@ def run_ours(args, wl, rank, world, local):
                     "frac": a / FP32_SIMT_TFLOPS,
                     "peak_source": "FP32 SIMT: 148 SMs x 128 lanes x 2 flop x 2.032 GHz (derived)"}
         if kind == "residual":
-            # FP64 ALU: about 4k double FMAs per quad (2-D) or 75k per hexahedron (3-D) per evaluation
+            # FP64 ALU: about 4k double FMAs per quad (2-D), 1.5k per triangle or 75k per hexahedron (3-D)
             # (quadrature of the Q2-Q1-Q2 element residual, counted from the kernels' loops), against
             # the nominal FP64 rate
             evals = n_fact + args.steps          # one per Newton iteration, one for the converged state
-            a = (1.5e5 if three_d else 8.0e3) * len(mesh["conn"]) * evals / sec / 1e12
+            a = (1.5e5 if three_d else (3.0e3 if tri else 8.0e3)) * len(mesh["conn"]) * evals / sec / 1e12
             return {"bound": "alu", "achieved": a, "peak": FP64_TFLOPS, "unit": "TFLOP/s", "frac": a / FP64_TFLOPS,
                     "peak_source": "FP64 nominal 1.25 TFLOP/s (no FP64 measurement); flops approximate"}
         per = {"fwd_solve": factor_bytes / 2, "bwd_solve": factor_bytes / 2, "front_assemble": 2 * fbytes,
@@ -491,7 +504,8 @@ def run_ours(args, wl, rank, world, local):
            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": ("f32 fronts and volume Jacobians + f64 residual/border/refinement" if j32 else
                      "f32 fronts + f64 residual/Jacobian/refinement"), "data": "synthetic",
-           "config": {"workload": args.workload, ("hexahedra" if three_d else "quads"): len(mesh["conn"]),
+           "config": {"workload": args.workload,
+                      ("hexahedra" if three_d else ("triangles" if tri else "quads")): len(mesh["conn"]),
                       "dofs": info["n_dofs"],
                       "nnz": info["nnz"], "fronts": info["n_fronts"], "max_front": info["max_front"],
                       "factor_gflop": info["factor_flops"] / 1e9, **wl, "precision": "mixed",
@@ -519,6 +533,8 @@ def run_ours(args, wl, rank, world, local):
         # the FP64 fronts of this case need ~245 GB; the threshold-pivoting path and the
         # 2-D serving sweep are measured on the 2-D workloads
         args.no_fp64 = args.no_threshold_path = args.no_sweep = True
+    if tri:
+        args.no_threshold_path = args.no_sweep = True   # (measured on the Q2 workloads)
     if not args.no_fp64 and rank == 0:
         c64 = viv.viv_case(M, wl["Re"], wl["Ustar"], wl["dt"], u0, precision=viv.VIV_FP64, pivoting=piv,
                            predictor=pred)
@@ -593,7 +609,7 @@ def run_ours(args, wl, rank, world, local):
         v, desc, secs = (oracle_sample3d if three_d else oracle_sample)(wl, 3.0)
         out["cpu_baseline"] = {"value": v, "unit": "time steps/s", "cores": 1, "kind": "oracle", "sample": desc,
                                "sample_seconds": round(secs, 1), "host": host_info()}
-        if args.oracle_full_steps > 0 and not three_d:
+        if args.oracle_full_steps > 0 and not three_d and not tri:
             out["cpu_baseline"]["full_run_small_case"] = oracle_full_run(args.oracle_full_steps)
     if rank == 0:
         print(json.dumps(out), flush=True)

@@ -92,8 +92,17 @@ typedef struct vivCase vivCase;
  * the seam); the periodicity is on the displacement x - X.  Gamma nodes move
  * by (delta_x, delta_y, 0): their z position must be held (VIV_TAG_X_FIX_Z);
  * the multiplier has three components there.
+ * elem_type VIV_ELEM_TRI_P2P1 (2-D only): the paper's own spaces (Section 3.3),
+ * P2 velocity on 6-node triangles, P1 pressure and P1 mesh position on the
+ * vertices, P2 multiplier traces: conn n_elems x 6 (vertices 0, 1, 2
+ * counter-clockwise, then the midpoints of edges 0-1, 1-2, 2-0), gamma_faces
+ * (element, local edge e = (v_e, midpoint, v_{e+1})); every midside node must
+ * sit at the midpoint of its edge (straight edges; VIV_ERR_ARG otherwise).  A
+ * midside node carries no position unknown: its position is the mean of the
+ * edge's end vertices, which the library keeps in the nodal x array.
  * tags: n_nodes VIV_TAG_* bit sets.  leaf_elems: nested-dissection leaf size
- * in elements (0: default, 4 in 2-D, 2 in 3-D). */
+ * in elements (0: default, 4 in 2-D, 2 in 3-D, 8 for triangles). */
+enum { VIV_ELEM_Q2 = 0, VIV_ELEM_TRI_P2P1 = 1 };
 typedef struct {
   int64_t n_nodes, n_elems, n_gamma_faces;
   const double* X;
@@ -104,6 +113,7 @@ typedef struct {
   int32_t dim;
   double span;
   const int64_t* wrap;
+  int32_t elem_type;
 } vivMeshDesc;
 
 typedef struct {
@@ -132,6 +142,7 @@ typedef struct {
   double window_gemm_flops;/* SIMT Schur-update flops (fronts below the large-front order) */
   int64_t block_level_mask;/* tree levels (bit l) whose large fronts may use the block LU */
   int32_t dim;             /* 2 or 3: components of u, x and lambda per node */
+  int32_t elem_type;       /* VIV_ELEM_Q2 or VIV_ELEM_TRI_P2P1 */
 } vivMeshInfo;
 
 /* Physical and solver parameters.  rho, mu: fluid density and viscosity;

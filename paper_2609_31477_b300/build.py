@@ -6,7 +6,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libviv.so")
-SOURCES = ["api.cpp", "mesh.cpp", "prof.cpp", "server.cpp", "assembly.cu", "assembly3d.cu", "frontal.cu", "vecops.cu", "noalloc.cu", "tc_pipe.cu", "analysis.cpp"]
+SOURCES = ["api.cpp", "mesh.cpp", "prof.cpp", "server.cpp", "assembly.cu", "assembly3d.cu", "assembly_tri.cu", "frontal.cu", "vecops.cu", "noalloc.cu", "tc_pipe.cu", "analysis.cpp"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-O3", "--expt-relaxed-constexpr"]

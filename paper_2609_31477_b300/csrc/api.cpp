@@ -378,6 +378,7 @@ vivStatus viv_mesh_info(const vivMesh* mesh, vivMeshInfo* info) {
     if (m.level_block.empty() || m.level_block[l]) info->block_level_mask |= (int64_t)1 << l;
   info->tc_image_bytes = (size_t)m.tc_img_chunks * TC_IMG_CHUNK_BYTES;
   info->dim = m.dim;
+  info->elem_type = m.tri ? VIV_ELEM_TRI_P2P1 : VIV_ELEM_Q2;
   API_END
 }
 
@@ -462,8 +463,8 @@ static vivStatus case_create_impl(vivMesh* mesh, const vivParams* prm_in, const 
   VIV_CHECK(prm->source >= 0 && prm->source <= 3, VIV_ERR_ARG, "source must be 0 .. 3");
   VIV_CHECK(prm->cfl_target >= 0 && prm->dt_max >= 0, VIV_ERR_ARG, "cfl_target and dt_max must not be negative");
   VIV_CHECK(mesh->m.on_device, VIV_ERR_STATE, "mesh was analysed on the host only");
-  VIV_CHECK(mesh->m.dim == 2 || (prm->source == 0 && prm->cfl_target == 0), VIV_ERR_ARG,
-            "3-D meshes take no manufactured source and a constant step");
+  VIV_CHECK((mesh->m.dim == 2 && !mesh->m.tri) || (prm->source == 0 && prm->cfl_target == 0), VIV_ERR_ARG,
+            "3-D and triangle meshes take no manufactured source and a constant step");
   *out = nullptr;
   vivCase* c = new vivCase();
   try {

@@ -684,6 +684,8 @@ void launch_element_areas(const Mesh& m, double* lame, double scale, bool consta
   }
   if (m.dim == 3) {
     launch_element_volumes(m, lame, s);
+  } else if (m.tri) {
+    launch_triangle_areas(m, lame, s);
   } else {
     Launched L(K_VEC, s);
     area_kernel<<<(E + 127) / 128, 128, 0, s>>>(m.d_conn, m.d_X, E, scale, lame);
@@ -720,7 +722,8 @@ static void run_assembly(const Mesh& m, const CaseState& st, const vivParams& pr
   A.source = prm.source;
   A.source_amp = prm.source_amp;
   A.step = st.step;
-  int ncol = (parts & 1) ? (int)m.color_off.size() - 1 : 0;
+  if ((parts & 1) && m.tri) run_assembly_tri<T, JAC>(m, st, prm, R, vals, s);
+  int ncol = (parts & 1) && !m.tri ? (int)m.color_off.size() - 1 : 0;
   for (int c = 0; c < ncol; ++c) {
     A.elems = m.d_color_elems + m.color_off[c];
     A.n = m.color_off[c + 1] - m.color_off[c];

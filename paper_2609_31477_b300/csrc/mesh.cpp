@@ -56,6 +56,8 @@ namespace {
 const int VERT[4] = {0, 2, 6, 8};
 const int EDGE[4][3] = {{0, 3, 6}, {2, 5, 8}, {0, 1, 2}, {6, 7, 8}};
 const int VERT3[8] = {0, 2, 6, 8, 18, 20, 24, 26};
+const int VERT_TRI[3] = {0, 1, 2};
+const int EDGE_TRI[3][3] = {{0, 3, 1}, {1, 4, 2}, {2, 5, 0}};   // (v_e, midpoint, v_{e+1})
 
 // local node of position (s, t) on face f of a 27-node hexahedron: the face
 // holds reference coordinate f / 2 at 0 (f even) or 1 (f odd); s runs along
@@ -194,14 +196,18 @@ void build_mesh(Mesh& m, const vivMeshDesc* d) {
   VIV_CHECK(d->n_gamma_faces == 0 || d->gamma_faces, VIV_ERR_ARG, "gamma_faces is NULL");
   VIV_CHECK(d->dim == 0 || d->dim == 2 || d->dim == 3, VIV_ERR_ARG, "dim must be 2 or 3");
   const int D = d->dim == 3 ? 3 : 2;
+  VIV_CHECK(d->elem_type == VIV_ELEM_Q2 || (d->elem_type == VIV_ELEM_TRI_P2P1 && D == 2), VIV_ERR_ARG,
+            "elem_type must be VIV_ELEM_Q2, or VIV_ELEM_TRI_P2P1 in two dimensions");
+  const bool tri = d->elem_type == VIV_ELEM_TRI_P2P1;
   m.dim = D;
-  m.npe = D == 3 ? 27 : 9;
-  m.nvert = D == 3 ? 8 : 4;
+  m.tri = tri;
+  m.npe = tri ? 6 : (D == 3 ? 27 : 9);
+  m.nvert = tri ? 3 : (D == 3 ? 8 : 4);
   m.fpe = D == 3 ? 9 : 3;
-  m.vol_pairs = D == 3 ? VOL_PAIRS3 : VOL_PAIRS;
+  m.vol_pairs = tri ? TRI_PAIRS : (D == 3 ? VOL_PAIRS3 : VOL_PAIRS);
   m.face_pairs = D == 3 ? FACE_PAIRS3 : FACE_PAIRS;
   const int P = m.npe;
-  const int* vert = D == 3 ? VERT3 : VERT;
+  const int* vert = tri ? VERT_TRI : (D == 3 ? VERT3 : VERT);
   const int64_t n = d->n_nodes, E = d->n_elems, F = d->n_gamma_faces;
   VIV_CHECK(D == 2 || E < (1LL << 31) / VOL_PAIRS3, VIV_ERR_ARG, "too many hexahedra for 32-bit element maps");
   m.n_nodes = n;
@@ -227,6 +233,21 @@ void build_mesh(Mesh& m, const vivMeshDesc* d) {
   for (int64_t e = 0; e < E; ++e)
     for (int c = 0; c < m.nvert; ++c) is_vertex[m.conn[e * P + vert[c]]] = 1;
   for (int64_t a = 0; a < n; ++a) cyl[a] = (m.tags[a] & VIV_TAG_CYL) != 0;
+  m.mid_parent.assign(tri ? 2 * n : 0, -1);
+  if (tri) {   // midside nodes: their edge's end vertices, and straight edges
+    double ext = 0;
+    for (int64_t a = 0; a < 2 * n; ++a) ext = std::max(ext, std::fabs(m.X[a]));
+    for (int64_t e = 0; e < E; ++e)
+      for (int k = 0; k < 3; ++k) {
+        const int mid = m.conn[e * 6 + 3 + k], va = m.conn[e * 6 + k], vb = m.conn[e * 6 + (k + 1) % 3];
+        for (int i = 0; i < 2; ++i)
+          VIV_CHECK(std::fabs(m.X[2 * mid + i] - 0.5 * (m.X[2 * va + i] + m.X[2 * vb + i])) <= 1e-12 * (1 + ext),
+                    VIV_ERR_ARG, "a midside node is not at the midpoint of its edge");
+        VIV_CHECK(!is_vertex[mid], VIV_ERR_ARG, "a node is a vertex of one triangle and a midside node of another");
+        m.mid_parent[2 * mid] = va;
+        m.mid_parent[2 * mid + 1] = vb;
+      }
+  }
   if (D == 3)
     for (int64_t a = 0; a < n; ++a)
       VIV_CHECK(!cyl[a] || (m.tags[a] & VIV_TAG_X_FIX_Z), VIV_ERR_ARG,
@@ -236,10 +257,10 @@ void build_mesh(Mesh& m, const vivMeshDesc* d) {
   m.face_wrap.assign(D == 3 ? F : 0, 0);
   for (int64_t f = 0; f < F; ++f) {
     int64_t e = d->gamma_faces[2 * f], ed = d->gamma_faces[2 * f + 1];
-    VIV_CHECK(e >= 0 && e < E && ed >= 0 && ed < 2 * D, VIV_ERR_ARG, "bad gamma face");
+    VIV_CHECK(e >= 0 && e < E && ed >= 0 && ed < (tri ? 3 : 2 * D), VIV_ERR_ARG, "bad gamma face");
     m.face_elem[f] = (int32_t)e;
     for (int b = 0; b < m.fpe; ++b) {
-      const int loc = D == 3 ? hex_face_node((int)ed, b % 3, b / 3) : EDGE[ed][b];
+      const int loc = D == 3 ? hex_face_node((int)ed, b % 3, b / 3) : (tri ? EDGE_TRI[ed][b] : EDGE[ed][b]);
       int nd = m.conn[e * P + loc];
       VIV_CHECK(cyl[nd], VIV_ERR_ARG, "gamma face node is not tagged CYL");
       m.faces[f * m.fpe + b] = nd;
@@ -249,7 +270,7 @@ void build_mesh(Mesh& m, const vivMeshDesc* d) {
   const bool has_body = F > 0;
 
   // ---- nested dissection -----------------------------------------------------
-  int leaf = d->leaf_elems > 0 ? d->leaf_elems : (D == 3 ? 2 : 4);
+  int leaf = d->leaf_elems > 0 ? d->leaf_elems : (tri ? 8 : (D == 3 ? 2 : 4));
   Dissector ds(m, leaf);
   std::vector<int> el(E);
   std::iota(el.begin(), el.end(), 0);
@@ -319,8 +340,9 @@ void build_mesh(Mesh& m, const vivMeshDesc* d) {
         static const int xfix[3] = {VIV_TAG_X_FIX_X, VIV_TAG_X_FIX_Y, VIV_TAG_X_FIX_Z};
         for (int i = 0; i < D; ++i)
           if (!(t & ufix[i])) sl[S_UX + i] = next++;
+        const bool has_x = !cyl[nd] && (!tri || is_vertex[nd]);   // triangles: P1 position
         for (int i = 0; i < D; ++i)
-          if (!cyl[nd] && !(t & xfix[i])) sl[S_XX + i] = next++;
+          if (has_x && !(t & xfix[i])) sl[S_XX + i] = next++;
         if (is_vertex[nd] && !(t & VIV_TAG_P_FIX)) sl[S_P] = next++;
         if (cyl[nd])
           for (int i = 0; i < D; ++i) sl[S_LX + i] = next++;
@@ -380,7 +402,30 @@ void build_mesh(Mesh& m, const vivMeshDesc* d) {
   };
   // enumerate the structural pairs of an element in canonical order:
   // u rows x all columns, p rows x (u, x) columns, x rows x x columns
+  // triangles: u columns 2 a + i, vertex position columns 12 + 2 v + k, pressure 18 + c
+  auto tri_col = [&](int64_t e, int cs) -> int32_t {
+    if (cs < 12) return m.node_dof[(int64_t)m.conn[e * 6 + cs / 2] * NSLOT + S_UX + cs % 2];
+    if (cs < 18) {
+      const int nd = m.conn[e * 6 + (cs - 12) / 2], k = (cs - 12) % 2;
+      return cyl[nd] ? m.delta_dof[k] : m.node_dof[(int64_t)nd * NSLOT + S_XX + k];
+    }
+    return m.node_dof[(int64_t)m.conn[e * 6 + cs - 18] * NSLOT + S_P];
+  };
   auto for_pairs = [&](int64_t e, auto&& fn) {
+    if (tri) {
+      auto nd = [&](int a) { return (int64_t)m.conn[e * 6 + a] * NSLOT; };
+      for (int a = 0; a < 6; ++a)
+        for (int i = 0; i < 2; ++i)
+          for (int cs = 0; cs < 21; ++cs) fn(tpairA(a, i, cs), m.node_dof[nd(a) + S_UX + i], tri_col(e, cs));
+      for (int c = 0; c < 3; ++c)
+        for (int cs = 0; cs < 18; ++cs) fn(tpairB(c, cs), m.node_dof[nd(c) + S_P], tri_col(e, cs));
+      for (int v = 0; v < 3; ++v)
+        for (int i = 0; i < 2; ++i)
+          for (int w = 0; w < 3; ++w)
+            for (int k = 0; k < 2; ++k)
+              fn(tpairC(v, i, w, k), m.node_dof[nd(v) + S_XX + i], tri_col(e, 12 + 2 * w + k));
+      return;
+    }
     int idx = 0;
     for (int a = 0; a < P; ++a)
       for (int i = 0; i < D; ++i)
@@ -1215,6 +1260,7 @@ void upload_mesh(Mesh& m, cudaStream_t s) {
   m.d_X = A.upload(m.X, s);
   m.d_conn = A.upload(m.conn, s);
   m.d_wrap = A.upload(m.wrap, s);
+  m.d_mid_parent = A.upload(m.mid_parent, s);
   m.d_face_wrap = A.upload(m.face_wrap, s);
   if (m.dim == 3) upload_hex_tables(m, s);
   m.d_tags = A.upload(m.tags, s);

@@ -302,6 +302,7 @@ void launch_update(const Mesh& m, CaseState& st, const double* dU, cudaStream_t 
                                                               m.d_delta_dof, st.delta, dU, st.u, st.p, st.x,
                                                               st.lam);
   }
+  if (m.tri) launch_midside_positions(m, st.x, s);   // P1 position: midpoints follow the vertices
   {
     Launched L(K_VEC, s);
     delta_update_kernel<<<1, 32, 0, s>>>(m.d_delta_dof, dU, st.delta);

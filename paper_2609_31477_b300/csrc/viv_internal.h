@@ -63,6 +63,12 @@ constexpr int FACE_PAIRS3 = 243 + 243 + 18 + 18;            // u x lambda, lambd
 __host__ __device__ inline int pairA3(int a, int i, int cs) { return (3 * a + i) * 170 + cs; }
 __host__ __device__ inline int pairB3(int c, int cs) { return 13770 + c * 162 + cs; }
 __host__ __device__ inline int pairC3(int a, int i, int b, int k) { return 15066 + (3 * a + i) * 81 + 3 * b + k; }
+// P2-P1 triangles with a P1 position: columns u (2 a + i, a < 6), x of the
+// vertices (12 + 2 v + k), pressure (18 + c); rows u (12), p (3), x (6)
+constexpr int TRI_PAIRS = 12 * 21 + 3 * 18 + 6 * 6;   // 342
+__host__ __device__ inline int tpairA(int a, int i, int cs) { return (2 * a + i) * 21 + cs; }
+__host__ __device__ inline int tpairB(int c, int cs) { return 252 + c * 18 + cs; }
+__host__ __device__ inline int tpairC(int v, int i, int w, int k) { return 306 + (2 * v + i) * 6 + 2 * w + k; }
 __host__ __device__ inline int fpairD3(int b, int i, int bp) { return (3 * b + i) * 9 + bp; }
 __host__ __device__ inline int fpairE3(int b, int i, int bp) { return 243 + (3 * b + i) * 9 + bp; }
 __host__ __device__ inline int fpairG3(int b, int i) { return 486 + 2 * b + i; }
@@ -150,6 +156,8 @@ struct Mesh {
   // host copies
   int64_t n_nodes = 0, n_elems = 0, n_faces = 0;
   int dim = 2;                     // 2: Q2 quads; 3: Q2 hexahedra
+  bool tri = false;                // P2-P1 triangles with a P1 position (2-D)
+  std::vector<int32_t> mid_parent; // triangles: per node the end vertices of its edge (-1: a vertex)
   int npe = 9, nvert = 4, fpe = 3; // nodes per element, pressure vertices, nodes per Gamma face
   int vol_pairs = VOL_PAIRS, face_pairs = FACE_PAIRS;
   double span = 0;                 // 3-D: period in z (0: not periodic)
@@ -230,6 +238,7 @@ struct Mesh {
   double* d_X = nullptr;
   int32_t* d_conn = nullptr;
   int32_t* d_wrap = nullptr;
+  int32_t* d_mid_parent = nullptr;
   int32_t* d_face_wrap = nullptr;
   double* d_hex_tab = nullptr;         // 3-D: shape-function tables at the Gauss points (FP64, FP32)
   float* d_hex_tab_f = nullptr;
@@ -365,6 +374,11 @@ namespace viv {
 void launch_element_areas(const Mesh& m, double* lame, double scale, bool constant, double* scratch,
                           cudaStream_t s);
 void launch_quasi_init(const Mesh& m, const CaseState& st, const vivParams& prm, cudaStream_t s);
+// P2-P1 triangle element kernels and the midside positions (assembly_tri.cu)
+template <class T, bool JAC>
+void run_assembly_tri(const Mesh& m, const CaseState& st, const vivParams& prm, double* R, T* vals, cudaStream_t s);
+void launch_triangle_areas(const Mesh& m, double* area, cudaStream_t s);
+void launch_midside_positions(const Mesh& m, double* x, cudaStream_t s);
 // 3-D (hexahedral) element, face and border kernels (assembly3d.cu)
 void upload_hex_tables(Mesh& m, cudaStream_t s);
 void launch_element_volumes(const Mesh& m, double* vol, cudaStream_t s);

@@ -37,7 +37,7 @@ class MeshDesc(C.Structure):
     _fields_ = [("n_nodes", C.c_int64), ("n_elems", C.c_int64), ("n_gamma_faces", C.c_int64),
                 ("X", C.c_void_p), ("conn", C.c_void_p), ("tags", C.c_void_p),
                 ("gamma_faces", C.c_void_p), ("leaf_elems", C.c_int32), ("dim", C.c_int32),
-                ("span", C.c_double), ("wrap", C.c_void_p)]
+                ("span", C.c_double), ("wrap", C.c_void_p), ("elem_type", C.c_int32)]
 
 
 class MeshInfo(C.Structure):
@@ -49,7 +49,8 @@ class MeshInfo(C.Structure):
                 ("outer_flops", C.c_double), ("tc_split_chunks", C.c_int64), ("tc_tiles", C.c_int64),
                 ("tc_image_bytes", C.c_size_t), ("window_tc_flops", C.c_double),
                 ("window_lu_flops", C.c_double), ("window_gemm_flops", C.c_double),
-                ("block_level_mask", C.c_int64), ("dim", C.c_int32)]
+                ("block_level_mask", C.c_int64), ("dim", C.c_int32),
+                ("elem_type", C.c_int32)]
 
 
 class Params(C.Structure):
@@ -232,7 +233,8 @@ def _desc(mesh):
     keep = (X, conn, tags, gf, wrap)
     d = MeshDesc(len(X), len(conn), len(gf), _ptr(X).value, _ptr(conn).value, _ptr(tags).value,
                  _ptr(gf).value if len(gf) else None, int(mesh.get("leaf_elems", 0)), dim,
-                 float(mesh.get("span", 0.0)), _ptr(wrap).value if dim == 3 else None)
+                 float(mesh.get("span", 0.0)), _ptr(wrap).value if dim == 3 else None,
+                 1 if mesh.get("elem") == "tri6" else 0)
     return d, keep
 
 

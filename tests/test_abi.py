@@ -119,3 +119,34 @@ def test_host_analysis_3d_matches_oracle_unknowns_and_pattern(lib):
     for bad in (("p", "p"), ("l", "l"), ("x", "u"), ("x", "p"), ("x", "l")):
         assert bad not in pairs
     assert M.info["front_entries"] > 0 and M.info["factor_flops"] > 0
+
+
+def test_host_analysis_triangles_match_oracle_unknowns_and_pattern(lib):
+    """P2-P1 triangles with a P1 position: the library numbers the oracle's
+    unknowns (no position unknowns at midside nodes) and its pattern holds
+    every oracle Jacobian entry."""
+    from oracle.solver_tri import viv_oracle_case_tri
+    m = I.triangulate_q2(I.viv_cylinder_mesh(4))
+    M = viv.Mesh(m, device=False)
+    assert M.info["elem_type"] == 1 and M.dim == 2
+    node, field = M.dof_labels()
+    oc = viv_oracle_case_tri(m, 100.0, 8.0, 0.1, I.viv_initial_velocity(m))
+    assert M.n_dofs == oc.ndof
+    lab = _labels_oracle(oc)
+    gpu_lab = {(int(a), viv.FIELD[int(f)]): i for i, (a, f) in enumerate(zip(node, field))}
+    assert set(gpu_lab) == set(lab.values())
+    perm = np.array([gpu_lab[lab[i]] for i in range(oc.ndof)])
+    oc.u_n, oc.x_n = oc.u.copy(), oc.x.copy()
+    c0, hu, hx = oc.bdf_coefficients()
+    J = oc.jacobian(c0, hu, hx, 0.1).tocoo()
+    rp, col = M.pattern()
+    rows = np.repeat(np.arange(M.n_dofs), np.diff(rp))
+    have = set(zip(rows.tolist(), col.tolist()))
+    need = set(zip(perm[J.row].tolist(), perm[J.col].tolist()))
+    assert need <= have
+    # a midside node off its edge's midpoint is rejected
+    bad = dict(m)
+    bad["X"] = np.array(m["X"])
+    bad["X"][m["conn"][0, 3], 0] += 1e-3
+    with pytest.raises(viv.VivError):
+        viv.Mesh(bad, device=False)
