@@ -538,6 +538,7 @@ static vivStatus case_create_impl(vivMesh* mesh, const vivParams* prm_in, const 
       prepare_kernels<float>();
     else
       prepare_kernels<double>();
+    if (m.dim == 3) prepare_hex_kernels();
     noalloc_prepare();   // the allocation-free solve's fixed array is committed here, not on its first call
     launch_element_areas(m, s.lame, c->prm.lame_scale, c->prm.lame_constant != 0, s.scal + 1, st);
     if (c->prm.source == 3) launch_quasi_init(m, s, c->prm, st);   // the exact state at t = 0

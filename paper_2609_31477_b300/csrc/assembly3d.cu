@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <mutex>
 #include <type_traits>
 #include <vector>
 
@@ -563,14 +564,26 @@ std::vector<double> hex_tables_host() {
 
 template <class T, bool JAC>
 void set_hex_smem() {
-  static bool done = false;   // per instantiation; the attribute is per device function
-  if (done) return;
   VIV_CUDA(cudaFuncSetAttribute(hex_kernel<T, JAC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)hex_smem_bytes<T>()));
-  done = true;
 }
 
 }  // namespace
+
+// the element kernels' shared-memory limit, once per device before any launch
+// (case creation; the serving loop's worker threads may get here concurrently)
+void prepare_hex_kernels() {
+  constexpr int MAX_DEV = 64;
+  static std::once_flag once[MAX_DEV];
+  int dev = 0;
+  VIV_CUDA(cudaGetDevice(&dev));
+  VIV_CHECK(dev >= 0 && dev < MAX_DEV, VIV_ERR_ARG, "device index out of range");
+  std::call_once(once[dev], [] {
+    set_hex_smem<double, false>();
+    set_hex_smem<double, true>();
+    set_hex_smem<float, true>();
+  });
+}
 
 void upload_hex_tables(Mesh& m, cudaStream_t s) {
   std::vector<double> t = hex_tables_host();
@@ -591,7 +604,7 @@ template <class T, bool JAC>
 void run_assembly3(const Mesh& m, const CaseState& st, const vivParams& prm, double* R, T* vals, cudaStream_t s,
                    int parts) {
   if (parts & 1) {
-    set_hex_smem<T, JAC>();
+    prepare_hex_kernels();
     Asm3Args A;
     A.conn = m.d_conn;
     A.wrap = m.d_wrap;

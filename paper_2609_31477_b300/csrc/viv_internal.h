@@ -381,6 +381,7 @@ void launch_triangle_areas(const Mesh& m, double* area, cudaStream_t s);
 void launch_midside_positions(const Mesh& m, double* x, cudaStream_t s);
 // 3-D (hexahedral) element, face and border kernels (assembly3d.cu)
 void upload_hex_tables(Mesh& m, cudaStream_t s);
+void prepare_hex_kernels();
 void launch_element_volumes(const Mesh& m, double* vol, cudaStream_t s);
 template <class T, bool JAC>
 void run_assembly3(const Mesh& m, const CaseState& st, const vivParams& prm, double* R, T* vals, cudaStream_t s,
