@@ -216,6 +216,13 @@ typedef struct {
   double cfl_target, dt_max;
   int32_t lame_constant;   /* 1: lambda_s = mu_s = lame_scale on every element (the
                               manufactured solutions); 0 (default): lame_scale min|K_0|/|K_0| */
+  int32_t factor_reuse;    /* mixed path: 0 (default, as in Section 6) factors the Jacobian at
+                              every Newton iteration; 1 factors it at a step's first iteration
+                              only: later iterations assemble their Jacobian and solve with it by
+                              FP64 iterative refinement preconditioned with the factors at hand,
+                              refactoring when refinement stalls (contraction worse than 1/2, or
+                              not converged within the sweep limit).  The Newton correction is the
+                              same to the refinement tolerance; fewer factorisations, more sweeps. */
 } vivParams;
 enum { VIV_PIVOT_THRESHOLD = 0, VIV_PIVOT_WINDOW = 1 };
 
@@ -230,6 +237,7 @@ typedef struct {
   double force[2];         /* F_fluid = -int_Gamma lambda */
   double dt;               /* size of this step */
   double cfl;              /* Courant number of the new state (0 unless cfl_target > 0) */
+  int32_t reused_factor_solves; /* Newton iterations solved with reused factors (factor_reuse) */
 } vivStepInfo;
 
 /* ---- mesh: numbering, sparsity, nested dissection, symbolic factorisation

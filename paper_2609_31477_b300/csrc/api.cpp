@@ -819,7 +819,10 @@ vivStatus viv_update(vivCase* c) {
 // final = true: the closing correction of a converged mixed-path step: at
 // least two sweeps, then until the linear residual is below 1e-6 of its
 // right-hand side or stops falling (see step_impl)
-static int refined_solve_graphs(vivCase* c, bool final = false) {
+// stale: the factors belong to an earlier Newton iterate (factor_reuse); the
+// loop then also stops when a sweep contracts the residual by less than 1/2,
+// and *converged says whether the tolerance was reached
+static int refined_solve_graphs(vivCase* c, bool final = false, bool stale = false, bool* converged = nullptr) {
   const Mesh& m = c->mesh->m;
   CaseState& s = c->s;
   const int64_t n = m.n_dofs;
@@ -848,11 +851,18 @@ static int refined_solve_graphs(vivCase* c, bool final = false) {
     });
     ++sweeps;
     const double nr = read_scalar(c, s.scal + 3);
+    if (stale && !std::isfinite(nr)) {   // a stale preconditioner diverged: refactor
+      if (converged) *converged = false;
+      return sweeps;
+    }
     VIV_CHECK(std::isfinite(nr), VIV_ERR_NONFINITE, "refinement residual is not finite");
+    const bool done = nb == 0 || nr <= std::max(tol * nb, abs_tol);
+    if (converged) *converged = done || final;
     if (sweeps >= max_sweeps || nb == 0) break;
     if (final && sweeps < 2) continue;   // (see step_impl)
-    if (nr <= std::max(tol * nb, abs_tol)) break;
+    if (done) break;
     if (final && nr > 0.5 * prev) break;   // at the FP64 floor: further sweeps only add rounding
+    if (stale && nr > 0.5 * prev) break;   // the stale factors no longer precondition well
     prev = nr;
   }
   return sweeps;
@@ -862,7 +872,7 @@ static void step_impl(vivCase* c, vivStepInfo* info) {
   const Mesh& m = c->mesh->m;
   begin_step(c);
   const double tol = c->prm.newton_tol;
-  int iters = 0, sweeps = 0;
+  int iters = 0, sweeps = 0, reused = 0;
   double n0 = 0, nr = 0;
   int32_t st_acc[2] = {0, 0};
   bool polished = false;
@@ -908,9 +918,19 @@ static void step_impl(vivCase* c, vivStepInfo* info) {
               "Newton did not converge in " + std::to_string(c->prm.max_newton) + " iterations (|R| = " +
                   fmt_e(nr) + ", tolerance " + fmt_e(tol) + ")");
     run_graph(c, c->g_jac, [&] { jacobian(c); });
-    run_graph(c, c->g_fac, [&] { factor(c); });
-    c->factored = true;
-    sweeps += refined_solve_graphs(c);
+    bool solved = false;
+    if (c->prm.factor_reuse && mixed(c) && it > 0 && c->factored) {
+      // the factors of this step's first iterate precondition the refined solve
+      // with the current Jacobian; refactor if refinement stalls
+      sweeps += refined_solve_graphs(c, false, true, &solved);
+      reused += solved ? 1 : 0;
+    }
+    if (!solved) {
+      run_graph(c, c->g_fac, [&] { factor(c); });
+      c->factored = true;
+      sweeps += refined_solve_graphs(c);
+      ++iters;
+    }
     int32_t stv[4];
     VIV_CUDA(cudaMemcpyAsync(stv, c->s.stats, sizeof(stv), cudaMemcpyDeviceToHost, c->stream));
     VIV_CUDA(cudaStreamSynchronize(c->stream));
@@ -918,7 +938,6 @@ static void step_impl(vivCase* c, vivStepInfo* info) {
     VIV_CHECK(stv[3] == 0, VIV_ERR_PIVOT, "the border Schur block of the cylinder position is singular");
     st_acc[0] += stv[0];
     st_acc[1] += stv[1];
-    ++iters;
   }
   // the loop ends on a converged residual of the updated state
   const double dt_used = c->prm.dt;
@@ -941,6 +960,7 @@ static void step_impl(vivCase* c, vivStepInfo* info) {
     info->dt = dt_used;
     info->cfl = cfl;
     info->newton_iters = iters;
+    info->reused_factor_solves = reused;
     info->refine_sweeps = sweeps;
     info->perturbed_pivots = st_acc[0];
     info->threshold_misses = st_acc[1];

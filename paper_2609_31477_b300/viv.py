@@ -61,20 +61,22 @@ class Params(C.Structure):
                 ("pivoting", C.c_int32), ("jacobian_fp32", C.c_int32), ("predictor", C.c_int32),
                 ("Re", C.c_double), ("Ustar", C.c_double), ("U_inf", C.c_double), ("D", C.c_double),
                 ("span_L", C.c_double), ("cfl_target", C.c_double), ("dt_max", C.c_double),
-                ("lame_constant", C.c_int32)]
+                ("lame_constant", C.c_int32), ("factor_reuse", C.c_int32)]
 
 
 class StepInfo(C.Structure):
     _fields_ = [("newton_iters", C.c_int32), ("refine_sweeps", C.c_int32),
                 ("perturbed_pivots", C.c_int32), ("threshold_misses", C.c_int32),
                 ("res_norm0", C.c_double), ("res_norm", C.c_double), ("t", C.c_double),
-                ("delta", C.c_double * 2), ("force", C.c_double * 2), ("dt", C.c_double), ("cfl", C.c_double)]
+                ("delta", C.c_double * 2), ("force", C.c_double * 2), ("dt", C.c_double), ("cfl", C.c_double),
+                ("reused_factor_solves", C.c_int32)]
 
     def as_dict(self):
         return dict(newton_iters=self.newton_iters, refine_sweeps=self.refine_sweeps,
                     perturbed_pivots=self.perturbed_pivots, threshold_misses=self.threshold_misses,
                     res_norm0=self.res_norm0, res_norm=self.res_norm, t=self.t,
-                    delta=list(self.delta), force=list(self.force), dt=self.dt, cfl=self.cfl)
+                    delta=list(self.delta), force=list(self.force), dt=self.dt, cfl=self.cfl,
+                    reused_factor_solves=self.reused_factor_solves)
 
 
 class ForceStats(C.Structure):
@@ -315,12 +317,14 @@ class Case:
     def __init__(self, mesh: Mesh, u0, rho, mu, k, dt, precision=VIV_FP64, lame_scale=1.0,
                  newton_tol=1e-10, max_newton=25, refine_tol=0.0, refine_max=0, pivot_threshold=0.01,
                  stream=None, source=0, source_amp=0.0, pivoting=0, jacobian_fp32=0, predictor=0,
-                 Re=0.0, Ustar=0.0, U_inf=0.0, D=0.0, span_L=0.0, cfl_target=0.0, dt_max=0.0, lame_constant=0):
+                 Re=0.0, Ustar=0.0, U_inf=0.0, D=0.0, span_L=0.0, cfl_target=0.0, dt_max=0.0, lame_constant=0,
+                 factor_reuse=0):
         lib = load()
         self.mesh = mesh
         self.params = Params(rho, mu, k, dt, lame_scale, newton_tol, max_newton, precision, refine_tol,
                              refine_max, pivot_threshold, source, source_amp, pivoting, jacobian_fp32,
-                             predictor, Re, Ustar, U_inf, D, span_L, cfl_target, dt_max, lame_constant)
+                             predictor, Re, Ustar, U_inf, D, span_L, cfl_target, dt_max, lame_constant,
+                             factor_reuse)
         u0 = np.ascontiguousarray(u0, dtype=np.float64)
         import torch
         # each case owns a non-default stream (graphs cannot capture the legacy stream)

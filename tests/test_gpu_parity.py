@@ -195,24 +195,30 @@ def cylinder_reference():
     return mesh, oc, states
 
 
-@pytest.mark.parametrize("precision,pivoting,jac32,pred", [("fp64", "threshold", 0, 0), ("mixed", "threshold", 0, 0),
-                                                           ("fp64", "window", 0, 0), ("mixed", "window", 0, 0),
-                                                           ("mixed", "window", 1, 0), ("mixed", "window", 1, 1)])
-def test_cylinder_ten_steps_match_oracle(viv, cylinder_reference, precision, pivoting, jac32, pred):
+@pytest.mark.parametrize("precision,pivoting,jac32,pred,reuse", [
+    ("fp64", "threshold", 0, 0, 0), ("mixed", "threshold", 0, 0, 0), ("fp64", "window", 0, 0, 0),
+    ("mixed", "window", 0, 0, 0), ("mixed", "window", 1, 0, 0), ("mixed", "window", 1, 1, 0),
+    ("mixed", "window", 1, 1, 1)])
+def test_cylinder_ten_steps_match_oracle(viv, cylinder_reference, precision, pivoting, jac32, pred, reuse):
     mesh, oc, states = cylinder_reference
     prec = viv.VIV_FP64 if precision == "fp64" else viv.VIV_MIXED
     piv = viv.VIV_PIVOT_THRESHOLD if pivoting == "threshold" else viv.VIV_PIVOT_WINDOW
     u0 = I.viv_initial_velocity(mesh, 1.0, 1e-3, 1)
     M = viv.Mesh(mesh)
-    case = viv.viv_case(M, RE, USTAR, DT, u0, precision=prec, pivoting=piv, jacobian_fp32=jac32, predictor=pred)
+    case = viv.viv_case(M, RE, USTAR, DT, u0, precision=prec, pivoting=piv, jacobian_fp32=jac32, predictor=pred,
+                        factor_reuse=reuse)
+    reused = 0
     for s in range(10):
         info = case.step()
+        reused += info["reused_factor_solves"]
         assert info["res_norm"] <= 1e-10
         st = case.get_state()
         ref = states[s]
         for k, v in ref.items():
             setattr(oc, k, v)
         _compare_fields(oc, st)
+    if reuse:   # the reuse did happen (later Newton iterations solved with the first iterate's factors)
+        assert reused >= 5
 
 
 def test_large_front_threshold_and_level_profile(viv):
