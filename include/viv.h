@@ -99,7 +99,8 @@ typedef struct vivCase vivCase;
  * (element, local edge e = (v_e, midpoint, v_{e+1})); every midside node must
  * sit at the midpoint of its edge (straight edges; VIV_ERR_ARG otherwise).  A
  * midside node carries no position unknown: its position is the mean of the
- * edge's end vertices, which the library keeps in the nodal x array.
+ * edge's end vertices, which the library keeps in the nodal x array (and
+ * restores from the vertices in positions the caller passes in, off Gamma).
  * tags: n_nodes VIV_TAG_* bit sets.  leaf_elems: nested-dissection leaf size
  * in elements (0: default, 4 in 2-D, 2 in 3-D, 8 for triangles). */
 enum { VIV_ELEM_Q2 = 0, VIV_ELEM_TRI_P2P1 = 1 };

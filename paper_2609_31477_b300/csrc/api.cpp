@@ -571,6 +571,7 @@ vivStatus viv_set_state(vivCase* c, int, const double* u, const double* p, const
   copy_in(c, c->s.u, u, D * n);
   copy_in(c, c->s.p, p, n);
   copy_in(c, c->s.x, x, D * n);
+  if (x && c->mesh->m.tri) launch_midside_positions(c->mesh->m, c->s.x, c->stream);   // (P1 position)
   copy_in(c, c->s.lam, lam, D * n);
   copy_in(c, c->s.delta, delta, 2);
   c->t = t;
@@ -585,6 +586,7 @@ vivStatus viv_set_history(vivCase* c, int, const double* u_prev, const double* x
   // begin_step moves u_n into u_nm1 when BDF2 is on
   copy_in(c, c->s.u_n, u_prev, D * n);
   copy_in(c, c->s.x_n, x_prev, D * n);
+  if (c->mesh->m.tri) launch_midside_positions(c->mesh->m, c->s.x_n, c->stream);
   c->have_prev2 = true;
   VIV_CUDA(cudaStreamSynchronize(c->stream));
   API_END
@@ -1115,6 +1117,7 @@ vivStatus viv_step_host(vivCase* c, const double* in, double* out, vivStepInfo* 
   copy_in(c, c->s.p, q, n);
   q += n;
   copy_in(c, c->s.x, q, D * n);
+  if (c->mesh->m.tri) launch_midside_positions(c->mesh->m, c->s.x, c->stream);
   q += D * n;
   copy_in(c, c->s.lam, q, D * n);
   q += D * n;
@@ -1131,6 +1134,7 @@ vivStatus viv_step_host(vivCase* c, const double* in, double* out, vivStepInfo* 
   if (have_prev) {
     copy_in(c, c->s.u_n, up, D * n);
     copy_in(c, c->s.x_n, xp, D * n);
+    if (c->mesh->m.tri) launch_midside_positions(c->mesh->m, c->s.x_n, c->stream);
   }
   step_impl(c, info);
   double* o = out;
