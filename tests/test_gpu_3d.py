@@ -130,10 +130,12 @@ def _compare(oc, st, tol_field=1e-9, tol_delta=1e-8):
     return errs
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_threshold", "mixed_reuse"])
 def test_steps_match_oracle_3d(viv, precision):
     prec = viv.VIV_FP64 if precision == "fp64" else viv.VIV_MIXED
-    extra = {} if precision == "fp64" else dict(pivoting=viv.VIV_PIVOT_WINDOW, jacobian_fp32=1)
+    extra = {"fp64": {}, "mixed": dict(pivoting=viv.VIV_PIVOT_WINDOW, jacobian_fp32=1),
+             "mixed_threshold": dict(pivoting=viv.VIV_PIVOT_THRESHOLD),
+             "mixed_reuse": dict(pivoting=viv.VIV_PIVOT_WINDOW, jacobian_fp32=1, predictor=1, factor_reuse=1)}[precision]
     mesh, oc, M, case = _pair(viv, prec, **extra)
     for _ in range(2):
         oc.step()
