@@ -16,7 +16,8 @@ Local numbering: vertices 0, 1, 2, midpoints of edges 0-1, 1-2, 2-0 (3, 4,
 
 Parity: pinned by the rule's exactness on monomials, the basis' nodal and
 partition-of-unity properties, the closed-form translating box reproduced to
-rounding and central differences of the residual (tests/test_oracle_tri.py).
+rounding, central differences of the residual, and the convergence orders
+Section 5.1 reports for these spaces (tests/test_oracle_tri.py).
 """
 from __future__ import annotations
 
@@ -78,7 +79,8 @@ def volume_residual(Xv, xv, ue, pv, hu, hxv, c0, rho, mu, lam_s, mu_s, src=None,
     """Element contributions of Eq. weak_system on P2-P1 triangles with a P1
     position.  Xv, xv, hxv: (E, 3, 2) vertex arrays; ue, hu: (E, 6, 2); pv:
     (E, 3).  Returns Ru (E, 6, 2), Rp (E, 3), Rx (E, 3, 2) (pseudo-solid rows
-    at the vertices).  `src` as in `fem.volume_residual`."""
+    at the vertices).  `src` (manufactured solutions) supplies f_u, g_p at the
+    current physical quadrature points and f_x at the reference ones."""
     E = Xv.shape[0]
     dt_ = np.result_type(xv, ue, pv, hu, hxv)
     Ru = np.zeros((E, 6, 2), dtype=dt_)
@@ -112,8 +114,9 @@ def volume_residual(Xv, xv, ue, pv, hu, hxv, c0, rho, mu, lam_s, mu_s, src=None,
         Rx += wq * det0[:, None, None] * (lam_s[:, None, None] * g1_0 * tr[:, None, None]
                                           + 2.0 * mu_s[:, None, None] * np.matmul(g1_0, np.swapaxes(eps, 1, 2)))
         if src is not None:
+            # Eulerian sources at the discrete physical point (see mms.volume_at)
             Xq = np.matmul(M, Xv)
-            fu, gp, fx = src.volume(Xq, t)
+            fu, gp, fx = src.volume_at(np.matmul(M, xv), Xq, t)
             Ru -= wq * det[:, None, None] * N[None, :, None] * fu[:, None, :]
             Rp += wq * det[:, None] * M[None, :] * gp[:, None]
             Rx -= wq * det0[:, None, None] * M[None, :, None] * fx[:, None, :]

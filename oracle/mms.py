@@ -37,8 +37,9 @@ def _vec_fun(exprs, args):
 
     def call(*a):
         shape = np.broadcast(*a).shape
+        dt_ = np.result_type(*a, np.float64)   # complex arguments (complex step) stay complex
         out = f(*a)
-        return np.stack([np.broadcast_to(np.asarray(o, dtype=np.float64), shape) for o in out], axis=-1)
+        return np.stack([np.broadcast_to(np.asarray(o, dtype=dt_), shape) for o in out], axis=-1)
     return call
 
 
@@ -68,6 +69,9 @@ class _Manufactured:
         sub = {x_: cx, y_: cy}
         self._fu = _vec_fun([fu[0].subs(sub), fu[1].subs(sub)], (X_, Y_, t_))
         self._gp = sy.lambdify((X_, Y_, t_), gp.subs(sub), "numpy")
+        # the same fluid sources as fields of the physical coordinates
+        self._fu_x = _vec_fun([fu[0], fu[1]], (x_, y_, t_))
+        self._gp_x = sy.lambdify((x_, y_, t_), gp, "numpy")
         self._fx = _vec_fun([fx[0], fx[1]], (X_, Y_, t_))
         wx, wy = sy.diff(cx, t_), sy.diff(cy, t_)
         self._gl = _vec_fun([ux.subs(sub) - wx, uy.subs(sub) - wy], (X_, Y_, t_))
@@ -103,6 +107,17 @@ class _Manufactured:
         X, Y = Xq[..., 0], Xq[..., 1]
         gp = np.broadcast_to(np.asarray(self._gp(X, Y, t), dtype=np.float64), X.shape)
         return self._fu(X, Y, t), gp, self._fx(X, Y, t)
+
+    def volume_at(self, xq, Xq, t):
+        """Fluid sources at the physical points xq (the discrete current
+        position of the quadrature points), pseudo-solid source at the
+        reference points Xq.  For a P1 position field x_h differs from chi by
+        O(h^2), and evaluating the Eulerian sources at chi(Xq) would leave an
+        O(h^2) defect in the continuity equations' compatibility, which a
+        single pinned pressure vertex amplifies."""
+        x, y = xq[..., 0], xq[..., 1]
+        gp = np.broadcast_to(np.asarray(self._gp_x(x, y, t)), x.shape)
+        return self._fu_x(x, y, t), gp, self._fx(Xq[..., 0], Xq[..., 1], t)
 
     def gamma(self, Xq, t):
         return self._gl(Xq[..., 0], Xq[..., 1], t)
@@ -318,6 +333,17 @@ class QuasiMMS:
         return (self._fu_x(xq[..., 0], xq[..., 1], t), self._gp_x(xq[..., 0], xq[..., 1], t),
                 self._fx(Xq[..., 0], Xq[..., 1], t))
 
+    def volume_at(self, xq, Xq, t):
+        """Fluid sources at the physical points xq (the discrete current
+        position of the quadrature points), pseudo-solid source at the
+        reference points Xq.  For a P1 position field x_h differs from chi by
+        O(h^2), and evaluating the Eulerian sources at chi(Xq) would leave an
+        O(h^2) defect in the continuity equations' compatibility, which a
+        single pinned pressure vertex amplifies."""
+        x, y = xq[..., 0], xq[..., 1]
+        gp = np.broadcast_to(np.asarray(self._gp_x(x, y, t)), x.shape)
+        return self._fu_x(x, y, t), gp, self._fx(Xq[..., 0], Xq[..., 1], t)
+
     def gamma(self, Xq, t):
         return np.zeros(Xq.shape[:-1] + (2,))
 
@@ -372,6 +398,41 @@ def error_norms(case, sol, t):
         eu1 += np.sum(w * det * np.sum((Lh - Lx) ** 2, axis=(1, 2)))
         ep2 += np.sum(w * det * (ph - px) ** 2)
         Fh = np.einsum('eai,eaj->eij', xe, g0)
+        Fx = sol._grad_chi(Xq[:, 0], Xq[:, 1], t).reshape(-1, 2, 2)
+        xx = sol._chi(Xq[:, 0], Xq[:, 1], t)
+        ex2 += np.sum(w * det0 * np.sum((xq - xx) ** 2, axis=1))
+        ex1 += np.sum(w * det0 * np.sum((Fh - Fx) ** 2, axis=(1, 2)))
+    return dict(u_l2=np.sqrt(eu2), u_h1=np.sqrt(eu1), p_l2=np.sqrt(ep2),
+                x_l2=np.sqrt(ex2), x_h1=np.sqrt(ex1))
+
+
+def error_norms_tri(case, sol, t):
+    """The norms of `error_norms` for a P2-P1 triangle case with a P1
+    position (oracle/solver_tri.py), measured with the 7-point rule: u and p
+    on the current (affine) triangles, x on the reference ones."""
+    from . import fem_tri
+    c = case.conn
+    cv = c[:, :3]
+    Xv, xv, ue, pv = case.X[cv], case.x[cv], case.u[c], case.p[cv]
+    _, Jinv, det = fem_tri.affine(xv)
+    _, Jinv0, det0 = fem_tri.affine(Xv)
+    h0 = np.matmul(fem_tri.DM[None], Jinv0)             # reference P1 gradients (E, 3, 2)
+    Fh = np.einsum('evi,evj->eij', xv, h0)              # grad_X x_h, constant per triangle
+    eu2 = eu1 = ep2 = ex2 = ex1 = 0.0
+    for q in range(len(fem_tri.QWTS)):
+        N, M, w = fem_tri.N_Q[q], fem_tri.M_Q[q], fem_tri.QWTS[q]
+        g = np.matmul(fem_tri.DN_Q[q][None], Jinv)
+        Xq = np.einsum('v,evi->ei', M, Xv)
+        xq = np.einsum('v,evi->ei', M, xv)
+        uh = np.einsum('a,eai->ei', N, ue)
+        Lh = np.einsum('eai,eaj->eij', ue, g)
+        ph = np.einsum('v,ev->e', M, pv)
+        ux = sol._u_phys(xq[:, 0], xq[:, 1], t)
+        Lx = sol._grad_u_phys(xq[:, 0], xq[:, 1], t).reshape(-1, 2, 2)
+        px = np.broadcast_to(sol._p_phys(xq[:, 0], xq[:, 1], t), ph.shape)
+        eu2 += np.sum(w * det * np.sum((uh - ux) ** 2, axis=1))
+        eu1 += np.sum(w * det * np.sum((Lh - Lx) ** 2, axis=(1, 2)))
+        ep2 += np.sum(w * det * (ph - px) ** 2)
         Fx = sol._grad_chi(Xq[:, 0], Xq[:, 1], t).reshape(-1, 2, 2)
         xx = sol._chi(Xq[:, 0], Xq[:, 1], t)
         ex2 += np.sum(w * det0 * np.sum((xq - xx) ** 2, axis=1))

@@ -325,26 +325,46 @@ def hole_square_mesh(n, R0=0.15, center=(0.5, 0.5), lo=0.0, hi=1.0):
 # local triangle node order: vertices 0, 1, 2, then the midpoints of edges
 # 0-1 (3), 1-2 (4), 2-0 (5); local edge e runs (v_e, midpoint, v_{e+1})
 def triangulate_q2(mesh):
-    """Split every Q2 quad of a 2-D mesh along its diagonal 0-8 into two
-    6-node triangles, (q0, q2, q8 | q1, q5, q4) and (q0, q8, q6 | q4, q7, q3),
-    and move every midside node to the midpoint of its edge's end nodes, so
-    that the edges are straight (the geometry of a P1 position field; the
-    cylinder becomes a polygon).  Tags are kept; Gamma edges map to the
-    triangle edges on the same quad edge.  Returns X, conn (2E, 6), tags,
-    gamma_faces (F, 2) [element, local edge 0..2], elem = "tri6"."""
+    """Split every Q2 quad of a 2-D mesh along a diagonal into two 6-node
+    triangles - along 0-8, (q0, q2, q8 | q1, q5, q4) and (q0, q8, q6 | q4, q7,
+    q3), or, where that would leave a triangle with all three vertices on the
+    mesh boundary (a mesh corner), along 2-6, (q0, q2, q6 | q1, q4, q3) and
+    (q2, q8, q6 | q5, q7, q4): Taylor-Hood P2-P1 leaves the pressure of such
+    a triangle uncontrolled.  Every midside node moves to the midpoint of its
+    edge's end nodes, so that the edges are straight (the geometry of a P1
+    position field; the cylinder becomes a polygon).  Tags are kept; Gamma
+    edges map to the triangle edges on the same quad edge.  Returns X, conn
+    (2E, 6), tags, gamma_faces (F, 2) [element, local edge 0..2], elem =
+    "tri6"."""
     X = np.array(mesh["X"], dtype=np.float64)
     q = np.asarray(mesh["conn"], dtype=np.int64)
     E = len(q)
+    # boundary vertices: the end nodes of quad edges that belong to one quad only
+    edges = {}
+    for a, b in ((0, 2), (2, 8), (8, 6), (6, 0)):
+        for e in range(E):
+            key = (min(q[e, a], q[e, b]), max(q[e, a], q[e, b]))
+            edges[key] = edges.get(key, 0) + 1
+    on_bnd = np.zeros(len(X), bool)
+    for (a, b), cnt in edges.items():
+        if cnt == 1:
+            on_bnd[a] = on_bnd[b] = True
+    bad08 = (on_bnd[q[:, 0]] & on_bnd[q[:, 2]] & on_bnd[q[:, 8]]) | (on_bnd[q[:, 0]] & on_bnd[q[:, 8]] & on_bnd[q[:, 6]])
+    bad26 = (on_bnd[q[:, 0]] & on_bnd[q[:, 2]] & on_bnd[q[:, 6]]) | (on_bnd[q[:, 2]] & on_bnd[q[:, 8]] & on_bnd[q[:, 6]])
+    flip = bad08 & ~bad26
     conn = np.empty((2 * E, 6), dtype=np.int64)
-    conn[0::2] = q[:, [0, 2, 8, 1, 5, 4]]
-    conn[1::2] = q[:, [0, 8, 6, 4, 7, 3]]
+    conn[0::2] = np.where(flip[:, None], q[:, [0, 2, 6, 1, 4, 3]], q[:, [0, 2, 8, 1, 5, 4]])
+    conn[1::2] = np.where(flip[:, None], q[:, [2, 8, 6, 5, 7, 4]], q[:, [0, 8, 6, 4, 7, 3]])
     for c in (conn[0::2], conn[1::2]):
         for mid, (a, b) in ((3, (0, 1)), (4, (1, 2)), (5, (2, 0))):
             X[c[:, mid]] = 0.5 * (X[c[:, a]] + X[c[:, b]])
-    # quad edge -> (triangle offset, local edge): xi=0 -> T2 edge 2, xi=1 -> T1 edge 1,
-    # eta=0 -> T1 edge 0, eta=1 -> T2 edge 1
+    # quad edge -> (triangle offset, local edge); diagonal 0-8: xi=0 -> T2 edge 2,
+    # xi=1 -> T1 edge 1, eta=0 -> T1 edge 0, eta=1 -> T2 edge 1; diagonal 2-6:
+    # xi=0 -> T1 edge 2, xi=1 -> T2 edge 0, eta=0 -> T1 edge 0, eta=1 -> T2 edge 1
     emap = {0: (1, 2), 1: (0, 1), 2: (0, 0), 3: (1, 1)}
-    gf = [(2 * e + emap[ed][0], emap[ed][1]) for e, ed in np.asarray(mesh["gamma_faces"]).reshape(-1, 2)]
+    emap_flip = {0: (0, 2), 1: (1, 0), 2: (0, 0), 3: (1, 1)}
+    gf = [(2 * e + (emap_flip if flip[e] else emap)[ed][0], (emap_flip if flip[e] else emap)[ed][1])
+          for e, ed in np.asarray(mesh["gamma_faces"]).reshape(-1, 2)]
     out = dict(mesh)
     out.update(X=X, conn=conn, gamma_faces=np.array(gf, dtype=np.int64).reshape(-1, 2), elem="tri6",
                name=mesh.get("name", "mesh") + "_tri")

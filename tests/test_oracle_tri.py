@@ -2,8 +2,9 @@
 (oracle/fem_tri.py, oracle/solver_tri.py) against what the mathematics fixes:
 the quadrature rule's exactness, the P2 basis' nodal and partition-of-unity
 properties and its gradients, the closed-form translating box reproduced to
-rounding (every volume, Gamma and border term), and central differences of
-the residual against the assembled Jacobian."""
+rounding (every volume, Gamma and border term), central differences of the
+residual against the assembled Jacobian, and the orders of convergence the
+paper reports for these spaces (Section 5.1)."""
 import math
 
 import numpy as np
@@ -113,3 +114,26 @@ def test_midside_positions_follow_the_vertices():
     assert np.abs(c.x[c.is_mid] - 0.5 * (c.x[par[:, 0]] + c.x[par[:, 1]])).max() <= 1e-15
     assert np.all(c.dof_x[~c.is_vertex] < 0)
     assert np.allclose(c.x[c.cyl] - c.X[c.cyl], c.delta, atol=1e-15)
+
+
+def test_steady_mms_rates_match_the_paper():
+    """Section 5.1 reports, for these spaces (P2-P1, P1 position), order 2 for
+    the velocity H1-seminorm and the pressure L2-norm and order 1 for the
+    position H1-seminorm; the steady manufactured solution on the deformed
+    unit square, split into triangles at n = 4, 8, 16, reproduces them (and
+    order 3 / 2 for the velocity / position L2 errors)."""
+    sol = mms.steady_mms()
+    errs = []
+    for n in (4, 8, 16):
+        m = I.triangulate_q2(I.square_mesh(n))
+        m["tags"][0] |= I.P_FIX
+        c = OracleCaseTri(m, rho=sol.rho, mu=sol.mu, k=0.0, dt=1e8, u0=np.zeros((len(m["X"]), 2)), lame=1.0,
+                          src=sol)
+        sol.set_dirichlet(c, 0.0)
+        c.step(dirichlet=sol.set_dirichlet)
+        errs.append(mms.error_norms_tri(c, sol, c.t))
+    r = {k: np.log2(errs[1][k] / errs[2][k]) for k in errs[0]}
+    assert abs(r["u_h1"] - 2) < 0.15, r
+    assert r["p_l2"] > 1.8, r
+    assert abs(r["x_h1"] - 1) < 0.1, r
+    assert abs(r["u_l2"] - 3) < 0.2 and abs(r["x_l2"] - 2) < 0.15, r
