@@ -389,9 +389,15 @@ vivStatus viv_update(vivCase* c);
  * offset), so both paths land on the same discrete solution.  info nullable. */
 vivStatus viv_step(vivCase* c, vivStepInfo* info);
 /* Same step with host buffers: uploads the state and history, steps, and
- * downloads the new state (the end-to-end form of one step). */
+ * downloads the new state (the end-to-end form of one step).  Packed state
+ * (doubles, D = the mesh's dim, n = n_nodes): u (n x D), p (n), x (n x D),
+ * lambda (n x D), delta (2), u and x of the previous level (n x D each),
+ * then the time and a flag (nonzero: the previous level is valid, so the
+ * step is BDF2).  state_out receives the new state with the stepped-from
+ * level as the previous one, the new time and flag 1.  Host buffers of
+ * viv_state_size doubles; VIV_ERR_ARG on NULL. */
 vivStatus viv_step_host(vivCase* c, const double* state_in, double* state_out, vivStepInfo* info);
-/* size in doubles of the packed host state used by viv_step_host */
+/* size in doubles of the packed host state used by viv_step_host: 5 D n + n + 4 */
 int64_t viv_state_size(const vivMesh* mesh);
 
 /* ---- force history analysis (host only, no device work) ------------------ */
