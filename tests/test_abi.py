@@ -150,3 +150,23 @@ def test_host_analysis_triangles_match_oracle_unknowns_and_pattern(lib):
     bad["X"][m["conn"][0, 3], 0] += 1e-3
     with pytest.raises(viv.VivError):
         viv.Mesh(bad, device=False)
+
+
+def test_bad_3d_and_triangle_meshes_are_rejected(lib):
+    """Host-side validation of the 3-D and triangle descriptions: wrapped nodes
+    without a span, a Gamma node whose z position is free, a face index out of
+    range, and triangles on a 3-D mesh."""
+    m = I.viv_cylinder_mesh3d(2, 2, 0.7)
+    viv.Mesh(m, device=False)          # the valid mesh analyses
+    bad = dict(m, span=0.0)
+    with pytest.raises(viv.VivError):
+        viv.Mesh(bad, device=False)
+    bad = dict(m, tags=np.array(m["tags"]) & ~I.X_FIX_Z)
+    with pytest.raises(viv.VivError):
+        viv.Mesh(bad, device=False)
+    gf = np.array(m["gamma_faces"])
+    gf[0, 1] = 6
+    with pytest.raises(viv.VivError):
+        viv.Mesh(dict(m, gamma_faces=gf), device=False)
+    with pytest.raises(viv.VivError):
+        viv.Mesh(dict(m, elem="tri6"), device=False)
