@@ -40,6 +40,8 @@ WORKLOADS = {
     # the paper's own spaces (P2-P1 triangles, P1 position) on the headline mesh split into
     # 77,600 triangles with straight edges
     "viv_tri_re200_m60": dict(m=60, tri=True, Re=200.0, Ustar=10.0, dt=0.02),
+    # (profiling: the m = 4 section, 188 quads, in 8 layers of the same thickness: 1,504 hexahedra, 5.5 GB)
+    "viv3d_re300_m4_z8": dict(m=4, layers=8, span=2.0 * math.pi / 3.0, Re=300.0, Ustar=8.0, dt=0.05),
     # (profiling: the m = 5 section, 251 quads, in 12 layers of the same thickness: 3,012 hexahedra)
     "viv3d_re300_m5_z12": dict(m=5, layers=12, span=math.pi, Re=300.0, Ustar=8.0, dt=0.05),
 }
