@@ -15,9 +15,9 @@ Gauss point 9 k + 3 j + i, pressure vertex 4 f + 2 d + c0 (local node
 along the second in-face reference direction (xi before eta before zeta).
 
 Parity: pinned by the reduction of a z-independent state on an extruded mesh
-to the pinned 2-D routines, by covariance under rotations of space, and by
-the closed-form translating box reproduced to rounding
-(tests/test_oracle_3d.py).
+to the pinned 2-D routines, by covariance under rotations of space, by the
+closed-form translating box reproduced to rounding, and by the optimal
+convergence orders of a manufactured solution (tests/test_oracle_3d.py).
 """
 from __future__ import annotations
 
@@ -116,14 +116,17 @@ def element_volumes(Xe):
     return vol
 
 
-def volume_residual(Xe, xe, ue, pe, hu, hx, c0, rho, mu, lam_s, mu_s):
+def volume_residual(Xe, xe, ue, pe, hu, hx, c0, rho, mu, lam_s, mu_s, src=None):
     """Element volume terms of Eq. weak_system on hexahedra: with
     u_dot = c0 u + hu, w = c0 x + hx (nodal rates),
       Ru[a,i] = int_Ot N_a rho (u_dot + ((u - w).grad) u)_i + (grad N_a)_j sigma_ij,
       Rp[c]   = -int_Ot M_c div u,
       Rx[a,i] = int_O0 lam_s (grad_X N_a)_i tr eps + 2 mu_s (grad_X N_a)_j eps_ij,
     sigma = -p I + mu (grad u + grad u^T), eps = sym grad_X (x - X).
-    Xe, xe, ue, hu, hx: (E, 27, 3); pe: (E, 8); lam_s, mu_s: (E,)."""
+    Xe, xe, ue, hu, hx: (E, 27, 3); pe: (E, 8); lam_s, mu_s: (E,).
+    `src` (manufactured solutions only) supplies f_u, g_p at the current
+    physical quadrature points and f_x at the reference ones:
+    Ru -= int N f_u, Rp += int M g_p, Rx -= int_O0 N f_x."""
     E = Xe.shape[0]
     dt_ = np.result_type(xe, ue, pe, hu, hx)
     Ru = np.zeros((E, 27, 3), dtype=dt_)
@@ -153,6 +156,11 @@ def volume_residual(Xe, xe, ue, pe, hu, hx, c0, rho, mu, lam_s, mu_s):
         tr = eps[:, 0, 0] + eps[:, 1, 1] + eps[:, 2, 2]
         Rx += wq * det0[:, None, None] * (lam_s[:, None, None] * g0 * tr[:, None, None]
                                           + 2.0 * mu_s[:, None, None] * np.matmul(g0, np.swapaxes(eps, 1, 2)))
+        if src is not None:
+            fu, gp, fx = src.volume_at(np.matmul(N, xe), np.matmul(N, Xe), 0.0)
+            Ru -= wq * det[:, None, None] * N[None, :, None] * fu[:, None, :]
+            Rp += wq * det[:, None] * M[None, :] * gp[:, None]
+            Rx -= wq * det0[:, None, None] * N[None, :, None] * fx[:, None, :]
     return Ru, Rp, Rx
 
 

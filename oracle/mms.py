@@ -439,3 +439,98 @@ def error_norms_tri(case, sol, t):
         ex1 += np.sum(w * det0 * np.sum((Fh - Fx) ** 2, axis=(1, 2)))
     return dict(u_l2=np.sqrt(eu2), u_h1=np.sqrt(eu1), p_l2=np.sqrt(ep2),
                 x_l2=np.sqrt(ex2), x_h1=np.sqrt(ex1))
+
+
+# --- 3-D: a steady manufactured solution on a box periodic in z -------------------
+Z_, z_ = sy.symbols("Z z", real=True)
+
+
+class SteadyMMS3D:
+    """Section 5.1's three-dimensional check, as a steady problem on the box
+    [0,1]^2 x [0,1) periodic in z (the spanwise direction of the 3-D
+    workload): smooth velocity and pressure with 2 pi z dependence, a mesh
+    deformed by x = X + A sin(pi X) sin(pi Y) (1, 1, cos 2 pi Z) (identity on
+    the x and y faces, periodic in z), lambda_s = mu_s = 1, and the matching
+    sources: f_u = rho (u.grad) u - div sigma, g_p = div u,
+    f_x = -div_X sigma_s(chi).  The fluid sources are fields of the physical
+    coordinates, evaluated at the discrete current quadrature points."""
+
+    def __init__(self, rho=9.876, mu=1.234, amp=0.05):
+        self.rho, self.mu = rho, mu
+        pi = sy.pi
+        c2 = sy.cos(2 * pi * z_)
+        u = sy.Matrix([sy.sin(pi * x_) * sy.cos(pi * y_) * c2,
+                       sy.cos(pi * x_) * sy.sin(pi * y_) * c2,
+                       sy.sin(pi * x_) * sy.sin(pi * y_) * sy.sin(2 * pi * z_)])
+        p = sy.cos(pi * x_) * sy.cos(pi * y_) * sy.cos(2 * pi * z_)
+        xs = (x_, y_, z_)
+        grad = sy.Matrix(3, 3, lambda i, j: sy.diff(u[i], xs[j]))
+        sigma = -p * sy.eye(3) + mu * (grad + grad.T)
+        divs = sy.Matrix([sum(sy.diff(sigma[i, j], xs[j]) for j in range(3)) for i in range(3)])
+        fu = rho * grad * u - divs
+        gp = grad[0, 0] + grad[1, 1] + grad[2, 2]
+        bump = amp * sy.sin(pi * X_) * sy.sin(pi * Y_)
+        chi = sy.Matrix([X_ + bump, Y_ + bump, Z_ + bump * sy.cos(2 * pi * Z_)])
+        Xs = (X_, Y_, Z_)
+        F = sy.Matrix(3, 3, lambda i, j: sy.diff(chi[i], Xs[j]))
+        eps = (F + F.T) / 2 - sy.eye(3)
+        sig_s = (eps[0, 0] + eps[1, 1] + eps[2, 2]) * sy.eye(3) + 2 * eps
+        fx = -sy.Matrix([sum(sy.diff(sig_s[i, j], Xs[j]) for j in range(3)) for i in range(3)])
+        self._fu = _vec_fun(list(fu), xs)
+        self._gp = sy.lambdify(xs, gp, "numpy")
+        self._fx = _vec_fun(list(fx), Xs)
+        self._u = _vec_fun(list(u), xs)
+        self._grad_u = _vec_fun(list(grad), xs)
+        self._p = sy.lambdify(xs, p, "numpy")
+        self._chi = _vec_fun(list(chi), Xs)
+
+    def volume_at(self, xq, Xq, t):
+        x, y, z = xq[..., 0], xq[..., 1], xq[..., 2]
+        gp = np.broadcast_to(np.asarray(self._gp(x, y, z)), x.shape)
+        return self._fu(x, y, z), gp, self._fx(Xq[..., 0], Xq[..., 1], Xq[..., 2])
+
+    def set_dirichlet(self, case, t):
+        """Prescribed components at their exact values (positions through chi,
+        velocity and pressure at the prescribed positions)."""
+        from .solver3d import U_FIX_X, U_FIX_Y, U_FIX_Z, X_FIX_X, X_FIX_Y, X_FIX_Z, P_FIX
+        tg = case.tags
+        xe = self._chi(case.X[:, 0], case.X[:, 1], case.X[:, 2])
+        for i, bit in enumerate((X_FIX_X, X_FIX_Y, X_FIX_Z)):
+            m = (tg & bit) != 0
+            case.x[m, i] = xe[m, i]
+        ue = self._u(xe[:, 0], xe[:, 1], xe[:, 2])
+        for i, bit in enumerate((U_FIX_X, U_FIX_Y, U_FIX_Z)):
+            m = (tg & bit) != 0
+            case.u[m, i] = ue[m, i]
+        m = (tg & P_FIX) != 0
+        case.p[m] = np.broadcast_to(self._p(xe[:, 0], xe[:, 1], xe[:, 2]), m.shape)[m]
+
+
+def error_norms3d(case, sol):
+    """u in L2 and H1-seminorm and p in L2 over the current hexahedra,
+    x in L2 over the reference ones (3x3x3 Gauss points)."""
+    from . import fem3d
+    c = case.conn
+    Xe = case.X[c] + case.shift
+    xe = case.x[c] + case.shift
+    ue = case.u[c]
+    pe = case.p[c[:, fem3d.VERTEX_LOCAL]]
+    eu2 = eu1 = ep2 = ex2 = 0.0
+    for q in range(27):
+        N, M, w = fem3d.N_Q[q], fem3d.M_Q[q], fem3d.W_Q[q]
+        g, det = fem3d.physical_gradients(xe, q)
+        _, det0 = fem3d.physical_gradients(Xe, q)
+        xq = np.einsum('a,eai->ei', N, xe)
+        Xq = np.einsum('a,eai->ei', N, Xe)
+        uh = np.einsum('a,eai->ei', N, ue)
+        Lh = np.einsum('eai,eaj->eij', ue, g)
+        ph = np.einsum('c,ec->e', M, pe)
+        ux = sol._u(xq[:, 0], xq[:, 1], xq[:, 2])
+        Lx = sol._grad_u(xq[:, 0], xq[:, 1], xq[:, 2]).reshape(-1, 3, 3)
+        px = np.broadcast_to(sol._p(xq[:, 0], xq[:, 1], xq[:, 2]), ph.shape)
+        xx = sol._chi(Xq[:, 0], Xq[:, 1], Xq[:, 2])
+        eu2 += np.sum(w * det * np.sum((uh - ux) ** 2, axis=1))
+        eu1 += np.sum(w * det * np.sum((Lh - Lx) ** 2, axis=(1, 2)))
+        ep2 += np.sum(w * det * (ph - px) ** 2)
+        ex2 += np.sum(w * det0 * np.sum((xq - xx) ** 2, axis=1))
+    return dict(u_l2=np.sqrt(eu2), u_h1=np.sqrt(eu1), p_l2=np.sqrt(ep2), x_l2=np.sqrt(ex2))

@@ -34,7 +34,7 @@ class OracleCase3D(OracleCase):
     """State arrays: u (n,3), p (n,) [vertices], x (n,3), lam (n,3) [Gamma],
     delta (2,)."""
 
-    def __init__(self, mesh, rho, mu, k, dt, u0, lame="inverse_volume"):
+    def __init__(self, mesh, rho, mu, k, dt, u0, lame="inverse_volume", src=None):
         self.mesh = mesh
         self.X = np.asarray(mesh["X"], dtype=np.float64)
         self.conn = np.asarray(mesh["conn"], dtype=np.int64)
@@ -51,7 +51,7 @@ class OracleCase3D(OracleCase):
             else np.zeros((0, 9, 3))
         self.rho, self.mu, self.k, self.dt = rho, mu, k, dt
         self.dt_prev = dt
-        self.src = None
+        self.src = src   # (steady manufactured solutions only: no Gamma source)
         n = len(self.X)
         self.n = n
         vol = fem3d.element_volumes(self.X[self.conn] + self.shift)
@@ -144,7 +144,7 @@ class OracleCase3D(OracleCase):
         Xe, xe, ue, pe, hue, _ = self._element_inputs(u, p, x, hu, hx)
         hxe = self._element_hx(hx, c0)
         Ru_e, Rp_e, Rx_e = fem3d.volume_residual(Xe, xe, ue, pe, hue, hxe, c0, self.rho, self.mu,
-                                                 self.lam_s, self.mu_s)
+                                                 self.lam_s, self.mu_s, self.src)
         dt_ = Ru_e.dtype
         Ru = np.zeros((n, 3), dt_)
         Rp = np.zeros(n, dt_)
@@ -200,7 +200,7 @@ class OracleCase3D(OracleCase):
                     pe_c[sl, a] += 1j * H_CS
             parts = fem3d.volume_residual(np.tile(Xe, (P, 1, 1)), xe_c, ue_c, pe_c, np.tile(hue, (P, 1, 1)),
                                           np.tile(hxe, (P, 1, 1)), c0, self.rho, self.mu,
-                                          np.tile(self.lam_s, P), np.tile(self.mu_s, P))
+                                          np.tile(self.lam_s, P), np.tile(self.mu_s, P), self.src)
             for k_, (kind, a, i) in enumerate(part):
                 sl = slice(k_ * E, (k_ + 1) * E)
                 col = col_u[:, a, i] if kind == "u" else (col_x[:, a, i] if kind == "x" else col_p[:, a])
