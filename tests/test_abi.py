@@ -170,3 +170,24 @@ def test_bad_3d_and_triangle_meshes_are_rejected(lib):
         viv.Mesh(dict(m, gamma_faces=gf), device=False)
     with pytest.raises(viv.VivError):
         viv.Mesh(dict(m, elem="tri6"), device=False)
+
+
+@pytest.mark.parametrize("family", ["quad", "tri", "hex"])
+def test_symbolic_factorisation_covers_every_unknown_once(lib, family):
+    """The nested dissection and symbolic factorisation of each element
+    family: every unknown but the two border ones is a pivot of exactly one
+    front, a front's order is at least its pivot count, parents sit on higher
+    tree levels and the predicted storage is the sum of the fronts' squares."""
+    mesh = {"quad": lambda: I.viv_cylinder_mesh(4),
+            "tri": lambda: I.triangulate_q2(I.viv_cylinder_mesh(4)),
+            "hex": lambda: I.viv_cylinder_mesh3d(2, 2, 0.7)}[family]()
+    M = viv.Mesh(mesh, device=False)
+    fr = M.fronts()
+    m, p, lev, par = (fr[k].astype(np.int64) for k in ("m", "p", "level", "parent"))
+    assert p.sum() == M.n_dofs - 2
+    assert np.all(m >= p) and np.all(p >= 0)
+    child = par >= 0
+    assert np.all(lev[par[child]] > lev[child])
+    assert (~child).sum() >= 1 and np.all(par < len(m))
+    assert M.info["front_entries"] == int((m * m).sum())
+    assert M.info["max_front"] == int(m.max())
