@@ -243,7 +243,15 @@ def _desc(mesh):
 class Mesh:
     """Mesh analysed by the library: numbering, CSR pattern, e2nz, nested
     dissection, symbolic factorisation.  device=False analyses on the host
-    only (no GPU needed)."""
+    only (no GPU needed).
+
+    `mesh` is a dict: X (n, 2) or (n, 3) reference coordinates (the dimension
+    follows), conn (E, 9) Q2 quads, (E, 27) Q2 hexahedra or (E, 6) P2-P1
+    triangles with elem="tri6", tags (n,) VIV_TAG bit sets, gamma_faces (F, 2)
+    (element, local edge or face); 3-D meshes periodic in z add span and wrap
+    (per element, the bit mask of local nodes at X + span e_z), and
+    leaf_elems optionally sets the dissection's leaf size.  The generators of
+    paper_2609_31477_b300.inputs return such dicts."""
 
     def __init__(self, mesh, device=True, torch_alloc=True, stream=None):
         lib = load()
