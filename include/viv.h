@@ -259,6 +259,19 @@ vivStatus viv_mesh_pattern(const vivMesh* mesh, int64_t* row_ptr, int32_t* col);
 /* per front (supernode, in elimination order): order m, pivots p, tree level
  * (0 = leaves) and parent (-1 for the root); host buffers of n_fronts */
 vivStatus viv_mesh_fronts(const vivMesh* mesh, int32_t* m, int32_t* p, int32_t* level, int32_t* parent);
+/* The element-to-nonzero maps the element kernels scatter through, for callers
+ * that add element contributions of their own to the Jacobian's CSR values:
+ * per element, the CSR value index (or -1: the row or column is not an
+ * unknown) of every structural pair of its local matrix, in the family's
+ * fixed pair order (momentum rows against every column, continuity rows
+ * against the velocity and position columns, pseudo-solid rows against the
+ * position columns; Gamma position columns are the delta columns); per Gamma
+ * edge or face, the same for its multiplier and border couplings.  *n_elem and
+ * *n_face receive the entries per element and per face; the arrays (host,
+ * n_elems x *n_elem and n_gamma_faces x *n_face int32) are filled when not
+ * NULL. */
+vivStatus viv_mesh_element_slots(const vivMesh* mesh, int32_t* elem_slots, int32_t* face_slots, int32_t* n_elem,
+                                 int32_t* n_face);
 vivStatus viv_mesh_destroy(vivMesh* mesh);
 
 /* ---- case: state on the device ------------------------------------------ */

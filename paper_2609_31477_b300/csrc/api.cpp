@@ -412,6 +412,18 @@ vivStatus viv_mesh_fronts(const vivMesh* mesh, int32_t* m_, int32_t* p_, int32_t
   API_END
 }
 
+vivStatus viv_mesh_element_slots(const vivMesh* mesh, int32_t* elem_slots, int32_t* face_slots, int32_t* n_elem,
+                                 int32_t* n_face) {
+  API_BEGIN
+  VIV_CHECK(mesh, VIV_ERR_ARG, "NULL mesh");
+  const Mesh& m = mesh->m;
+  if (n_elem) *n_elem = m.vol_pairs;
+  if (n_face) *n_face = m.face_pairs;
+  if (elem_slots) std::memcpy(elem_slots, m.e2nz.data(), m.e2nz.size() * sizeof(int32_t));
+  if (face_slots) std::memcpy(face_slots, m.f2nz.data(), m.f2nz.size() * sizeof(int32_t));
+  API_END
+}
+
 vivStatus viv_mesh_destroy(vivMesh* mesh) {
   API_BEGIN
   delete mesh;

@@ -16,6 +16,7 @@
 #include <cmath>
 #include <cstring>
 #include <numeric>
+#include <thread>
 
 #include "viv_internal.h"
 
@@ -159,6 +160,23 @@ struct Dissector {
     return id;
   }
 };
+
+// fn(begin, end) over [0, n) split among host threads; each index is handled
+// by one thread, and the loops using it write disjoint outputs or sort
+// afterwards, so the tables do not depend on the thread count
+template <class Fn>
+void parallel_for(int64_t n, Fn&& fn) {
+  const int64_t hw = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  const int64_t T = std::max<int64_t>(1, std::min<int64_t>(hw, n / 1024 + 1));
+  if (T == 1) {
+    fn((int64_t)0, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  th.reserve(T);
+  for (int64_t t = 0; t < T; ++t) th.emplace_back([&fn, n, t, T] { fn(n * t / T, n * (t + 1) / T); });
+  for (auto& x : th) x.join();
+}
 
 int greedy_colour(const std::vector<int32_t>& items, int per, int64_t count, int64_t n_nodes,
                   std::vector<int32_t>& off, std::vector<int32_t>& order) {
@@ -472,28 +490,55 @@ void build_mesh(Mesh& m, const vivMeshDesc* d) {
   };
 
   // ---- CSR pattern -------------------------------------------------------------
+  // every structural pair (element pairs, face pairs, the border diagonal) once
+  // per occurrence, bucketed by row in two passes (count, fill), then each row
+  // sorted and made unique
   {
-    std::vector<std::vector<int32_t>> rows(m.n_dofs);
-    for (int64_t e = 0; e < E; ++e)
-      for_pairs(e, [&](int, int32_t r, int32_t c) {
-        if (r >= 0 && c >= 0) rows[r].push_back(c);
-      });
+    const int64_t N = m.n_dofs;
+    std::vector<int64_t> off(N + 1, 0);
+    parallel_for(E, [&](int64_t e0, int64_t e1) {
+      for (int64_t e = e0; e < e1; ++e)
+        for_pairs(e, [&](int, int32_t r, int32_t c) {
+          if (r >= 0 && c >= 0) __atomic_fetch_add(&off[r + 1], (int64_t)1, __ATOMIC_RELAXED);
+        });
+    });
     for (int64_t f = 0; f < F; ++f)
       for_face_pairs(f, [&](int, int32_t r, int32_t c) {
-        if (r >= 0 && c >= 0) rows[r].push_back(c);
+        if (r >= 0 && c >= 0) ++off[r + 1];
       });
     if (has_body)
-      for (int i = 0; i < 2; ++i) rows[m.delta_dof[i]].push_back(m.delta_dof[i]);
-    m.row_ptr.assign(m.n_dofs + 1, 0);
-    for (int64_t r = 0; r < m.n_dofs; ++r) {
-      auto& v = rows[r];
-      std::sort(v.begin(), v.end());
-      v.erase(std::unique(v.begin(), v.end()), v.end());
-      m.row_ptr[r + 1] = m.row_ptr[r] + (int64_t)v.size();
-    }
-    VIV_CHECK(m.row_ptr[m.n_dofs] < (1LL << 31), VIV_ERR_ARG, "too many nonzeros for int32 CSR slots");
-    m.col.resize(m.row_ptr[m.n_dofs]);
-    for (int64_t r = 0; r < m.n_dofs; ++r) std::copy(rows[r].begin(), rows[r].end(), m.col.begin() + m.row_ptr[r]);
+      for (int i = 0; i < 2; ++i) ++off[m.delta_dof[i] + 1];
+    for (int64_t r = 0; r < N; ++r) off[r + 1] += off[r];
+    std::vector<int32_t> buf(off[N]);
+    std::vector<int64_t> pos(off.begin(), off.end() - 1);
+    parallel_for(E, [&](int64_t e0, int64_t e1) {
+      for (int64_t e = e0; e < e1; ++e)
+        for_pairs(e, [&](int, int32_t r, int32_t c) {
+          if (r >= 0 && c >= 0) buf[__atomic_fetch_add(&pos[r], (int64_t)1, __ATOMIC_RELAXED)] = c;
+        });
+    });
+    for (int64_t f = 0; f < F; ++f)
+      for_face_pairs(f, [&](int, int32_t r, int32_t c) {
+        if (r >= 0 && c >= 0) buf[pos[r]++] = c;
+      });
+    if (has_body)
+      for (int i = 0; i < 2; ++i) buf[pos[m.delta_dof[i]]++] = m.delta_dof[i];
+    std::vector<int64_t> len(N);
+    parallel_for(N, [&](int64_t r0, int64_t r1) {
+      for (int64_t r = r0; r < r1; ++r) {
+        auto b = buf.begin() + off[r], en = buf.begin() + off[r + 1];
+        std::sort(b, en);
+        len[r] = std::unique(b, en) - b;
+      }
+    });
+    m.row_ptr.assign(N + 1, 0);
+    for (int64_t r = 0; r < N; ++r) m.row_ptr[r + 1] = m.row_ptr[r] + len[r];
+    VIV_CHECK(m.row_ptr[N] < (1LL << 31), VIV_ERR_ARG, "too many nonzeros for int32 CSR slots");
+    m.col.resize(m.row_ptr[N]);
+    parallel_for(N, [&](int64_t r0, int64_t r1) {
+      for (int64_t r = r0; r < r1; ++r)
+        std::copy(buf.begin() + off[r], buf.begin() + off[r] + len[r], m.col.begin() + m.row_ptr[r]);
+    });
   }
   auto slot = [&](int32_t r, int32_t c) -> int32_t {
     if (r < 0 || c < 0) return -1;
@@ -503,8 +548,10 @@ void build_mesh(Mesh& m, const vivMeshDesc* d) {
   };
   const int VP = m.vol_pairs, FP = m.face_pairs;
   m.e2nz.assign(E * VP, -1);
-  for (int64_t e = 0; e < E; ++e)
-    for_pairs(e, [&](int idx, int32_t r, int32_t c) { m.e2nz[e * VP + idx] = slot(r, c); });
+  parallel_for(E, [&](int64_t e0, int64_t e1) {
+    for (int64_t e = e0; e < e1; ++e)
+      for_pairs(e, [&](int idx, int32_t r, int32_t c) { m.e2nz[e * VP + idx] = slot(r, c); });
+  });
   m.f2nz.assign(F * FP, -1);
   for (int64_t f = 0; f < F; ++f)
     for_face_pairs(f, [&](int idx, int32_t r, int32_t c) { m.f2nz[f * FP + idx] = slot(r, c); });

@@ -128,6 +128,7 @@ SIGNATURES = {
     "viv_mesh_dof_labels": (C.c_int, [_P, _P, _P]),
     "viv_mesh_pattern": (C.c_int, [_P, _P, _P]),
     "viv_mesh_fronts": (C.c_int, [_P, _P, _P, _P, _P]),
+    "viv_mesh_element_slots": (C.c_int, [_P, _P, _P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "viv_mesh_destroy": (C.c_int, [_P]),
     "viv_case_create": (C.c_int, [_P, C.POINTER(Params), _P, _P, C.POINTER(_P)]),
     "viv_case_destroy": (C.c_int, [_P]),
@@ -303,6 +304,17 @@ class Mesh:
         a = [np.empty(n, np.int32) for _ in range(4)]
         _check(_lib.viv_mesh_fronts(self.h, *[_ptr(x) for x in a]))
         return dict(m=a[0], p=a[1], level=a[2], parent=a[3])
+
+    def element_slots(self):
+        """CSR value index of every structural pair of every element (E, pairs)
+        and Gamma edge/face (F, pairs) - viv_mesh_element_slots."""
+        ne, nf = C.c_int32(), C.c_int32()
+        _check(_lib.viv_mesh_element_slots(self.h, None, None, C.byref(ne), C.byref(nf)))
+        E, F = len(self.mesh["conn"]), len(np.asarray(self.mesh["gamma_faces"]).reshape(-1, 2))
+        es = np.empty((E, ne.value), np.int32)
+        fs = np.empty((F, nf.value), np.int32)
+        _check(_lib.viv_mesh_element_slots(self.h, _ptr(es), _ptr(fs), C.byref(ne), C.byref(nf)))
+        return es, fs
 
     def state_size(self):
         return int(_lib.viv_state_size(self.h))

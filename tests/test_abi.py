@@ -191,3 +191,32 @@ def test_symbolic_factorisation_covers_every_unknown_once(lib, family):
     assert (~child).sum() >= 1 and np.all(par < len(m))
     assert M.info["front_entries"] == int((m * m).sum())
     assert M.info["max_front"] == int(m.max())
+
+
+@pytest.mark.parametrize("family", ["quad", "tri", "hex"])
+def test_element_slots_cover_the_pattern(lib, family):
+    """viv_mesh_element_slots: every CSR value is reached by some element or
+    face pair (or is a border diagonal), and every element pair's slot lies in
+    a row and a column of that element's unknowns (delta for Gamma
+    positions)."""
+    mesh = {"quad": lambda: I.viv_cylinder_mesh(4),
+            "tri": lambda: I.triangulate_q2(I.viv_cylinder_mesh(4)),
+            "hex": lambda: I.viv_cylinder_mesh3d(2, 2, 0.7)}[family]()
+    M = viv.Mesh(mesh, device=False)
+    rp, col = M.pattern()
+    es, fs = M.element_slots()
+    nnz = len(col)
+    hit = np.zeros(nnz, bool)
+    hit[es[es >= 0]] = True
+    hit[fs[fs >= 0]] = True
+    node, _ = M.dof_labels()
+    n_nodes = len(mesh["X"])
+    dd = [s for s in range(nnz) if node[np.searchsorted(rp, s, side="right") - 1] == n_nodes and node[col[s]] == n_nodes]
+    hit[dd] = True
+    assert hit.all()
+    rows = np.searchsorted(rp, np.arange(nnz), side="right") - 1
+    conn = np.asarray(mesh["conn"])
+    for e in range(0, len(conn), max(1, len(conn) // 25)):
+        s = es[e][es[e] >= 0]
+        nodes = set(conn[e].tolist()) | {n_nodes}
+        assert set(node[rows[s]].tolist()) <= nodes and set(node[col[s]].tolist()) <= nodes
