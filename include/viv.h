@@ -101,6 +101,8 @@ typedef struct vivCase vivCase;
  * midside node carries no position unknown: its position is the mean of the
  * edge's end vertices, which the library keeps in the nodal x array (and
  * restores from the vertices in positions the caller passes in, off Gamma).
+ * Every element must be positively oriented (its corner edge vectors at local
+ * node 0 span a positive area or volume; VIV_ERR_ARG otherwise).
  * tags: n_nodes VIV_TAG_* bit sets.  leaf_elems: nested-dissection leaf size
  * in elements (0: default, 4 in 2-D, 2 in 3-D, 8 for triangles). */
 enum { VIV_ELEM_Q2 = 0, VIV_ELEM_TRI_P2P1 = 1 };

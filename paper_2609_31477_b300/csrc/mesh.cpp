@@ -247,6 +247,30 @@ void build_mesh(Mesh& m, const vivMeshDesc* d) {
       m.wrap[e] = (int32_t)d->wrap[e];
     }
   }
+  // every element positively oriented: the corner edge vectors at local node
+  // 0 (quads and hexahedra: along xi, eta, zeta; triangles: to vertices 1, 2)
+  // span a positive area / volume, wrapped nodes at their shifted position
+  for (int64_t e = 0; e < E; ++e) {
+    auto pt = [&](int a, double* v) {
+      const int nd = m.conn[e * P + a];
+      for (int i = 0; i < D; ++i) v[i] = m.X[(int64_t)D * nd + i];
+      if (D == 3 && (m.wrap[e] >> a & 1)) v[2] += m.span;
+    };
+    double o[3], a[3], b[3], c[3] = {0, 0, 0};
+    pt(0, o);
+    pt(tri ? 1 : 2, a);
+    pt(tri ? 2 : 6, b);
+    if (D == 3) pt(18, c);
+    for (int i = 0; i < D; ++i) {
+      a[i] -= o[i];
+      b[i] -= o[i];
+      c[i] -= o[i];
+    }
+    const double vol = D == 2 ? a[0] * b[1] - a[1] * b[0]
+                              : a[0] * (b[1] * c[2] - b[2] * c[1]) - a[1] * (b[0] * c[2] - b[2] * c[0]) +
+                                    a[2] * (b[0] * c[1] - b[1] * c[0]);
+    VIV_CHECK(vol > 0, VIV_ERR_ARG, "element " + std::to_string(e) + " is not positively oriented");
+  }
   std::vector<char> is_vertex(n, 0), cyl(n, 0);
   for (int64_t e = 0; e < E; ++e)
     for (int c = 0; c < m.nvert; ++c) is_vertex[m.conn[e * P + vert[c]]] = 1;

@@ -220,3 +220,17 @@ def test_element_slots_cover_the_pattern(lib, family):
         s = es[e][es[e] >= 0]
         nodes = set(conn[e].tolist()) | {n_nodes}
         assert set(node[rows[s]].tolist()) <= nodes and set(node[col[s]].tolist()) <= nodes
+
+
+@pytest.mark.parametrize("family", ["quad", "tri", "hex"])
+def test_negatively_oriented_elements_are_rejected(lib, family):
+    """Mirroring the mesh in y turns every element inside out: the analysis
+    rejects it instead of producing negative Jacobian determinants."""
+    mesh = {"quad": lambda: I.viv_cylinder_mesh(3),
+            "tri": lambda: I.triangulate_q2(I.viv_cylinder_mesh(3)),
+            "hex": lambda: I.viv_cylinder_mesh3d(2, 2, 0.7)}[family]()
+    viv.Mesh(mesh, device=False)
+    X = np.array(mesh["X"])
+    X[:, 1] *= -1.0
+    with pytest.raises(viv.VivError):
+        viv.Mesh(dict(mesh, X=X), device=False)
